@@ -1,0 +1,267 @@
+"""ctypes front end of the plain FP64 CPU oracle (``sbm_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: imported by ``tests/``, by ``__graft_entry__.smoke()``
+and by the CPU-baseline leg of ``bench.py``.  The product path never imports it.
+
+Every function takes and returns numpy float64 arrays in the packed layout of the
+C ABI: node (i, j, k) at ``i + nx*(j + ny*k)``, component ``p`` at offset
+``p*nnodes``; cell (i, j, k) at ``i + (nx-1)*(j + (ny-1)*k)``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "sbm_oracle.c")
+_HDR = os.path.join(_HERE, "sbm_oracle.h")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "libsbm_oracle.so")
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (plain -O2, no FMA contraction)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Problem(C.Structure):
+    _fields_ = [("dim", C.c_int), ("n", C.c_int * 3), ("h", C.c_double),
+                ("c11", C.c_double), ("c12", C.c_double), ("c44", C.c_double),
+                ("dirichlet", C.c_uint * 3)]
+
+
+class _Opts(C.Structure):
+    _fields_ = [("nu1", C.c_int), ("nu2", C.c_int), ("omega", C.c_double),
+                ("smoother", C.c_int), ("tol", C.c_double), ("max_cycles", C.c_int)]
+
+
+_lib = None
+_dp = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
+
+
+def _L():
+    global _lib
+    if _lib is None:
+        lib = C.CDLL(build())
+        P = C.POINTER(_Problem)
+        sig = {
+            "orc_nnodes": (C.c_long, [P]),
+            "orc_ncells": (C.c_long, [P]),
+            "orc_is_dirichlet": (C.c_int, [P, C.c_int, C.c_int, C.c_int, C.c_int]),
+            "orc_element_matrix": (None, [P, _dp]),
+            "orc_apply": (None, [P, _dp, _dp, _dp]),
+            "orc_residual": (None, [P, _dp, _dp, _dp, _dp]),
+            "orc_diagonal": (None, [P, _dp, _dp]),
+            "orc_norm_free": (C.c_double, [P, _dp]),
+            "orc_jacobi_sweep": (None, [P, _dp, _dp, _dp, C.c_double]),
+            "orc_gs_sweep": (None, [P, _dp, _dp, _dp, C.c_int]),
+            "orc_can_coarsen": (C.c_int, [P]),
+            "orc_coarse_problem": (None, [P, P]),
+            "orc_coarsen_psi": (None, [P, _dp, _dp]),
+            "orc_restrict": (None, [P, _dp, _dp]),
+            "orc_prolong_add": (None, [P, _dp, _dp]),
+            "orc_num_levels": (C.c_int, [P]),
+            "orc_assemble_dense": (None, [P, _dp, _dp]),
+            "orc_direct_solve": (C.c_int, [P, _dp, _dp, _dp]),
+            "orc_mg_solve": (C.c_int, [P, _dp, _dp, _dp, C.POINTER(_Opts), _dp, C.POINTER(C.c_int)]),
+            "orc_dJdpsi": (None, [P, _dp, _dp, _dp]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+FACES = {"-x": 0, "+x": 1, "-y": 2, "+y": 3, "-z": 4, "+z": 5}
+
+
+@dataclass
+class Problem:
+    """Grid, moduli and Dirichlet faces of one level (mirrors ``orc_problem``)."""
+    dim: int
+    n: tuple
+    h: float
+    c11: float
+    c12: float
+    c44: float
+    dirichlet: tuple = (0, 0, 0)   # per component: bitmask over faces
+
+    def __post_init__(self):
+        n = tuple(int(v) for v in self.n)
+        if self.dim == 2 and len(n) == 2:
+            n = n + (1,)
+        self.n = n
+        self.dirichlet = tuple(int(v) for v in (tuple(self.dirichlet) + (0, 0, 0))[:3])
+
+    @property
+    def nnodes(self) -> int:
+        return self.n[0] * self.n[1] * self.n[2]
+
+    @property
+    def ncells(self) -> int:
+        nz = (self.n[2] - 1) if self.dim == 3 else 1
+        return (self.n[0] - 1) * (self.n[1] - 1) * nz
+
+    @property
+    def ndofs(self) -> int:
+        return self.dim * self.nnodes
+
+    def c(self) -> _Problem:
+        p = _Problem()
+        p.dim = self.dim
+        p.n[:] = list(self.n)
+        p.h = self.h
+        p.c11, p.c12, p.c44 = self.c11, self.c12, self.c44
+        p.dirichlet[:] = list(self.dirichlet)
+        return p
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def element_matrix(P: Problem) -> np.ndarray:
+    nd = (1 << P.dim) * P.dim
+    Ke = np.zeros(nd * nd)
+    _L().orc_element_matrix(C.byref(P.c()), Ke)
+    return Ke.reshape(nd, nd)
+
+
+def apply(P: Problem, psi, u) -> np.ndarray:
+    out = np.zeros(P.ndofs)
+    _L().orc_apply(C.byref(P.c()), _f64(psi), _f64(u), out)
+    return out
+
+
+def residual(P: Problem, psi, f, u) -> np.ndarray:
+    out = np.zeros(P.ndofs)
+    _L().orc_residual(C.byref(P.c()), _f64(psi), _f64(f), _f64(u), out)
+    return out
+
+
+def diagonal(P: Problem, psi) -> np.ndarray:
+    out = np.zeros(P.ndofs)
+    _L().orc_diagonal(C.byref(P.c()), _f64(psi), out)
+    return out
+
+
+def norm_free(P: Problem, r) -> float:
+    return _L().orc_norm_free(C.byref(P.c()), _f64(r))
+
+
+def dirichlet_mask(P: Problem) -> np.ndarray:
+    """Boolean mask over dofs, True where the dof is Dirichlet."""
+    m = np.zeros((P.dim, P.n[2], P.n[1], P.n[0]), dtype=bool)
+    lib, pc = _L(), P.c()
+    for p in range(P.dim):
+        for k in range(P.n[2]):
+            for j in range(P.n[1]):
+                for i in range(P.n[0]):
+                    m[p, k, j, i] = bool(lib.orc_is_dirichlet(C.byref(pc), i, j, k, p))
+    return m.reshape(-1)
+
+
+def jacobi_sweep(P: Problem, psi, f, u, omega: float) -> np.ndarray:
+    u = _f64(u).copy()
+    _L().orc_jacobi_sweep(C.byref(P.c()), _f64(psi), _f64(f), u, omega)
+    return u
+
+
+def gs_sweep(P: Problem, psi, f, u, descending: bool = False) -> np.ndarray:
+    u = _f64(u).copy()
+    _L().orc_gs_sweep(C.byref(P.c()), _f64(psi), _f64(f), u, int(descending))
+    return u
+
+
+def can_coarsen(P: Problem) -> bool:
+    return bool(_L().orc_can_coarsen(C.byref(P.c())))
+
+
+def coarse_problem(P: Problem) -> Problem:
+    out = _Problem()
+    _L().orc_coarse_problem(C.byref(P.c()), C.byref(out))
+    return Problem(out.dim, tuple(out.n), out.h, out.c11, out.c12, out.c44, tuple(out.dirichlet))
+
+
+def num_levels(P: Problem) -> int:
+    return _L().orc_num_levels(C.byref(P.c()))
+
+
+def coarsen_psi(P: Problem, psi) -> np.ndarray:
+    out = np.zeros(coarse_problem(P).ncells)
+    _L().orc_coarsen_psi(C.byref(P.c()), _f64(psi), out)
+    return out
+
+
+def restrict(P: Problem, r) -> np.ndarray:
+    out = np.zeros(coarse_problem(P).ndofs)
+    _L().orc_restrict(C.byref(P.c()), _f64(r), out)
+    return out
+
+
+def prolong_add(P: Problem, e_c, u) -> np.ndarray:
+    u = _f64(u).copy()
+    _L().orc_prolong_add(C.byref(P.c()), _f64(e_c), u)
+    return u
+
+
+def assemble_dense(P: Problem, psi) -> np.ndarray:
+    K = np.zeros(P.ndofs * P.ndofs)
+    _L().orc_assemble_dense(C.byref(P.c()), _f64(psi), K)
+    return K.reshape(P.ndofs, P.ndofs)
+
+
+def direct_solve(P: Problem, psi, f, u0) -> np.ndarray:
+    u = _f64(u0).copy()
+    st = _L().orc_direct_solve(C.byref(P.c()), _f64(psi), _f64(f), u)
+    if st != 0:
+        raise RuntimeError(f"orc_direct_solve status {st}")
+    return u
+
+
+@dataclass
+class MGResult:
+    u: np.ndarray
+    status: int
+    cycles: int
+    history: np.ndarray = field(repr=False)
+
+
+def mg_solve(P: Problem, psi, f, u0, *, nu1=2, nu2=2, omega=2.0 / 3.0, smoother="jacobi",
+             tol=1e-10, max_cycles=500) -> MGResult:
+    u = _f64(u0).copy()
+    o = _Opts(nu1, nu2, omega, 1 if smoother in ("gs", "mcgs", "rbgs") else 0, tol, max_cycles)
+    hist = np.full(max_cycles + 1, np.nan)
+    cyc = C.c_int(0)
+    st = _L().orc_mg_solve(C.byref(P.c()), _f64(psi), _f64(f), u, C.byref(o), hist, C.byref(cyc))
+    return MGResult(u, st, cyc.value, hist[: cyc.value + 1])
+
+
+def dJdpsi(P: Problem, u, lam) -> np.ndarray:
+    out = np.zeros(P.ncells)
+    _L().orc_dJdpsi(C.byref(P.c()), _f64(u), _f64(lam), out)
+    return out
+
+
+def floor_psi(psi, psi_min: float) -> np.ndarray:
+    """psi <- max(psi, psi_min): the floor that keeps the operator definite."""
+    return np.maximum(_f64(psi), psi_min)
+
+
+def simp(rho, psi_min: float, q: float = 3.0):
+    """SIMP stiffness map psi = psi_min + (1 - psi_min) rho^q and its derivative."""
+    rho = _f64(rho)
+    return psi_min + (1.0 - psi_min) * rho ** q, (1.0 - psi_min) * q * rho ** (q - 1.0)

@@ -1,0 +1,623 @@
+/*
+ * sbm_oracle.c — plain FP64 CPU oracle.  TEST INFRASTRUCTURE ONLY (see the
+ * header for who may use it and for the layout).  Every loop follows the
+ * definition it names, in the order the definition states it; nothing is
+ * blocked, fused or reordered for speed.
+ */
+#include "sbm_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------ grid */
+
+long orc_nnodes(const orc_problem *P) { return (long)P->n[0] * P->n[1] * P->n[2]; }
+
+static int ncell_axis(const orc_problem *P, int a)
+{
+    if (a == 2 && P->dim == 2) return 1;
+    return P->n[a] - 1;
+}
+
+long orc_ncells(const orc_problem *P)
+{
+    return (long)ncell_axis(P, 0) * ncell_axis(P, 1) * ncell_axis(P, 2);
+}
+
+static long nid(const orc_problem *P, int i, int j, int k)
+{
+    return i + (long)P->n[0] * (j + (long)P->n[1] * k);
+}
+
+static long cid(const orc_problem *P, int i, int j, int k)
+{
+    return i + (long)(P->n[0] - 1) * (j + (long)(P->n[1] - 1) * k);
+}
+
+/* Dirichlet dofs sit only on the faces of the box (Sec. 2.1: essential
+ * conditions are not imposed on the diffuse boundary).  A dof on an edge or
+ * corner is Dirichlet if any face it lies on is Dirichlet for that component. */
+int orc_is_dirichlet(const orc_problem *P, int i, int j, int k, int p)
+{
+    unsigned m = P->dirichlet[p];
+    if ((m & 1u) && i == 0) return 1;
+    if ((m & 2u) && i == P->n[0] - 1) return 1;
+    if ((m & 4u) && j == 0) return 1;
+    if ((m & 8u) && j == P->n[1] - 1) return 1;
+    if (P->dim == 3) {
+        if ((m & 16u) && k == 0) return 1;
+        if ((m & 32u) && k == P->n[2] - 1) return 1;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------- element matrix */
+
+/* Fourth-order stiffness of an axis-aligned cubic crystal:
+ *   C_iiii = c11, C_iijj = c12 (i != j), C_ijij = C_ijji = c44 (i != j). */
+static double cubic_C(const orc_problem *P, int i, int j, int k, int l)
+{
+    if (i == j && k == l) return (i == k) ? P->c11 : P->c12;
+    if (i != j && ((i == k && j == l) || (i == l && j == k))) return P->c44;
+    return 0.0;
+}
+
+/* Q1 shape function of a corner along one axis and its derivative (unit cell). */
+static double shape1(int bit, double xi) { return bit ? xi : 1.0 - xi; }
+static double dshape1(int bit) { return bit ? 1.0 : -1.0; }
+
+void orc_element_matrix(const orc_problem *P, double *Ke)
+{
+    const int d = P->dim, nc = 1 << d, nd = nc * d;
+    const double h = P->h;
+    const double gp[2] = {0.5 - 0.5 / sqrt(3.0), 0.5 + 0.5 / sqrt(3.0)};
+    const double w = pow(h, d) / nc;           /* Gauss weight, 2 points per axis */
+    double eps[8][3][3][3];                    /* eps[corner][comp][i][j] at one Gauss point */
+    double sig[8][3][3][3];
+    memset(Ke, 0, sizeof(double) * nd * nd);
+    for (int g = 0; g < nc; ++g) {
+        double xi[3];
+        for (int a = 0; a < d; ++a) xi[a] = gp[(g >> a) & 1];
+        for (int c = 0; c < nc; ++c) {
+            double dN[3];                     /* physical gradient of N_c */
+            for (int a = 0; a < d; ++a) {
+                double v = dshape1((c >> a) & 1) / h;
+                for (int b = 0; b < d; ++b)
+                    if (b != a) v *= shape1((c >> b) & 1, xi[b]);
+                dN[a] = v;
+            }
+            for (int p = 0; p < d; ++p) {
+                /* strain of the displacement field N_c e_p:  eps_ij = (d_ip dN_j + d_jp dN_i)/2 */
+                for (int i = 0; i < d; ++i)
+                    for (int j = 0; j < d; ++j)
+                        eps[c][p][i][j] = 0.5 * ((i == p ? dN[j] : 0.0) + (j == p ? dN[i] : 0.0));
+                for (int i = 0; i < d; ++i)
+                    for (int j = 0; j < d; ++j) {
+                        double s = 0.0;
+                        for (int k = 0; k < d; ++k)
+                            for (int l = 0; l < d; ++l) s += cubic_C(P, i, j, k, l) * eps[c][p][k][l];
+                        sig[c][p][i][j] = s;
+                    }
+            }
+        }
+        for (int a = 0; a < nc; ++a)
+            for (int p = 0; p < d; ++p)
+                for (int b = 0; b < nc; ++b)
+                    for (int q = 0; q < d; ++q) {
+                        double s = 0.0;
+                        for (int i = 0; i < d; ++i)
+                            for (int j = 0; j < d; ++j) s += eps[a][p][i][j] * sig[b][q][i][j];
+                        Ke[(a * d + p) * nd + (b * d + q)] += w * s;
+                    }
+    }
+    const double scale = pow(h, -d);            /* FD scaling: (Ku)_n ~ -div(psi C grad u)(x_n) */
+    for (int e = 0; e < nd * nd; ++e) Ke[e] *= scale;
+}
+
+/* ------------------------------------------------------------- operator */
+
+static void cell_corner(const orc_problem *P, int ci, int cj, int ck, int a, int *i, int *j, int *k)
+{
+    *i = ci + (a & 1);
+    *j = cj + ((a >> 1) & 1);
+    *k = (P->dim == 3) ? ck + ((a >> 2) & 1) : 0;
+}
+
+void orc_apply(const orc_problem *P, const double *psi, const double *u, double *Ku)
+{
+    const int d = P->dim, nc = 1 << d, nd = nc * d;
+    const long N = orc_nnodes(P);
+    double Ke[24 * 24], ue[24], fe[24];
+    orc_element_matrix(P, Ke);
+    memset(Ku, 0, sizeof(double) * d * N);
+    for (int ck = 0; ck < ncell_axis(P, 2); ++ck)
+        for (int cj = 0; cj < ncell_axis(P, 1); ++cj)
+            for (int ci = 0; ci < ncell_axis(P, 0); ++ci) {
+                const double pc = psi[cid(P, ci, cj, ck)];
+                long node[8];
+                for (int a = 0; a < nc; ++a) {
+                    int i, j, k;
+                    cell_corner(P, ci, cj, ck, a, &i, &j, &k);
+                    node[a] = nid(P, i, j, k);
+                    for (int q = 0; q < d; ++q) ue[a * d + q] = u[q * N + node[a]];
+                }
+                for (int r = 0; r < nd; ++r) {
+                    double s = 0.0;
+                    for (int c = 0; c < nd; ++c) s += Ke[r * nd + c] * ue[c];
+                    fe[r] = s;
+                }
+                for (int a = 0; a < nc; ++a)
+                    for (int p = 0; p < d; ++p) Ku[p * N + node[a]] += pc * fe[a * d + p];
+            }
+}
+
+void orc_residual(const orc_problem *P, const double *psi, const double *f,
+                  const double *u, double *r)
+{
+    const int d = P->dim;
+    const long N = orc_nnodes(P);
+    orc_apply(P, psi, u, r);
+    for (int k = 0; k < P->n[2]; ++k)
+        for (int j = 0; j < P->n[1]; ++j)
+            for (int i = 0; i < P->n[0]; ++i)
+                for (int p = 0; p < d; ++p) {
+                    long e = p * N + nid(P, i, j, k);
+                    r[e] = orc_is_dirichlet(P, i, j, k, p) ? 0.0 : f[e] - r[e];
+                }
+}
+
+void orc_diagonal(const orc_problem *P, const double *psi, double *D)
+{
+    const int d = P->dim, nc = 1 << d, nd = nc * d;
+    const long N = orc_nnodes(P);
+    double Ke[24 * 24];
+    orc_element_matrix(P, Ke);
+    memset(D, 0, sizeof(double) * d * N);
+    for (int ck = 0; ck < ncell_axis(P, 2); ++ck)
+        for (int cj = 0; cj < ncell_axis(P, 1); ++cj)
+            for (int ci = 0; ci < ncell_axis(P, 0); ++ci) {
+                const double pc = psi[cid(P, ci, cj, ck)];
+                for (int a = 0; a < nc; ++a) {
+                    int i, j, k;
+                    cell_corner(P, ci, cj, ck, a, &i, &j, &k);
+                    for (int p = 0; p < d; ++p)
+                        D[p * N + nid(P, i, j, k)] += pc * Ke[(a * d + p) * nd + (a * d + p)];
+                }
+            }
+}
+
+double orc_norm_free(const orc_problem *P, const double *r)
+{
+    const long N = orc_nnodes(P);
+    double s = 0.0;
+    for (int p = 0; p < P->dim; ++p)
+        for (int k = 0; k < P->n[2]; ++k)
+            for (int j = 0; j < P->n[1]; ++j)
+                for (int i = 0; i < P->n[0]; ++i)
+                    if (!orc_is_dirichlet(P, i, j, k, p)) {
+                        double v = r[p * N + nid(P, i, j, k)];
+                        s += v * v;
+                    }
+    return sqrt(s);
+}
+
+/* -------------------------------------------------------------- smoothers */
+
+/* Jacobi (Sec. 2.3): u^{n+1} = D^-1 (b - (A - D) u^n), damped:
+ * u <- u + omega D^-1 (f - K u) on free dofs. */
+void orc_jacobi_sweep(const orc_problem *P, const double *psi, const double *f,
+                      double *u, double omega)
+{
+    const int d = P->dim;
+    const long N = orc_nnodes(P);
+    double *r = malloc(sizeof(double) * d * N);
+    double *D = malloc(sizeof(double) * d * N);
+    orc_residual(P, psi, f, u, r);
+    orc_diagonal(P, psi, D);
+    for (int p = 0; p < d; ++p)
+        for (int k = 0; k < P->n[2]; ++k)
+            for (int j = 0; j < P->n[1]; ++j)
+                for (int i = 0; i < P->n[0]; ++i)
+                    if (!orc_is_dirichlet(P, i, j, k, p)) {
+                        long e = p * N + nid(P, i, j, k);
+                        u[e] += omega * r[e] / D[e];
+                    }
+    free(r);
+    free(D);
+}
+
+/* Row (n,p) of K u, gathered from the cells around node n. */
+static double apply_row(const orc_problem *P, const double *Ke, const double *psi,
+                        const double *u, int i, int j, int k, int p)
+{
+    const int d = P->dim, nc = 1 << d, nd = nc * d;
+    const long N = orc_nnodes(P);
+    double s = 0.0;
+    for (int a = 0; a < nc; ++a) {          /* n is corner a of cell (i,j,k) - offset(a) */
+        int ci = i - (a & 1), cj = j - ((a >> 1) & 1), ck = (d == 3) ? k - ((a >> 2) & 1) : 0;
+        if (ci < 0 || cj < 0 || ck < 0) continue;
+        if (ci >= ncell_axis(P, 0) || cj >= ncell_axis(P, 1) || ck >= ncell_axis(P, 2)) continue;
+        const double pc = psi[cid(P, ci, cj, ck)];
+        for (int b = 0; b < nc; ++b) {
+            int bi, bj, bk;
+            cell_corner(P, ci, cj, ck, b, &bi, &bj, &bk);
+            for (int q = 0; q < d; ++q)
+                s += pc * Ke[(a * d + p) * nd + (b * d + q)] * u[q * N + nid(P, bi, bj, bk)];
+        }
+    }
+    return s;
+}
+
+/* 2^d-colour Gauss-Seidel: colour = (i&1) + 2(j&1) [+ 4(k&1)].  Nodes of one
+ * colour do not couple through the 3^d stencil; within a node the components
+ * are relaxed in order x, y[, z] using the latest values. */
+void orc_gs_sweep(const orc_problem *P, const double *psi, const double *f,
+                  double *u, int descending)
+{
+    const int d = P->dim, ncol = 1 << d, nc = 1 << d, nd = nc * d;
+    const long N = orc_nnodes(P);
+    double Ke[24 * 24];
+    orc_element_matrix(P, Ke);
+    double *D = malloc(sizeof(double) * d * N);
+    orc_diagonal(P, psi, D);
+    for (int s = 0; s < ncol; ++s) {
+        const int col = descending ? ncol - 1 - s : s;
+        for (int k = 0; k < P->n[2]; ++k)
+            for (int j = 0; j < P->n[1]; ++j)
+                for (int i = 0; i < P->n[0]; ++i) {
+                    int c = (i & 1) + 2 * (j & 1) + (d == 3 ? 4 * (k & 1) : 0);
+                    if (c != col) continue;
+                    for (int p = 0; p < d; ++p) {
+                        if (orc_is_dirichlet(P, i, j, k, p)) continue;
+                        long e = p * N + nid(P, i, j, k);
+                        double r = f[e] - apply_row(P, Ke, psi, u, i, j, k, p);
+                        u[e] += r / D[e];
+                    }
+                }
+    }
+    free(D);
+}
+
+/* ------------------------------------------------------ level transfers */
+
+/* Coarsen while every active N-1 is even and every coarse N-1 stays >= 4. */
+int orc_can_coarsen(const orc_problem *P)
+{
+    for (int a = 0; a < P->dim; ++a) {
+        int m = P->n[a] - 1;
+        if (m % 2 != 0 || m / 2 < 4) return 0;
+    }
+    return 1;
+}
+
+void orc_coarse_problem(const orc_problem *fine, orc_problem *coarse)
+{
+    *coarse = *fine;
+    for (int a = 0; a < fine->dim; ++a) coarse->n[a] = (fine->n[a] - 1) / 2 + 1;
+    coarse->h = 2.0 * fine->h;
+}
+
+int orc_num_levels(const orc_problem *P)
+{
+    orc_problem a = *P, b;
+    int L = 1;
+    while (orc_can_coarsen(&a)) {
+        orc_coarse_problem(&a, &b);
+        a = b;
+        ++L;
+    }
+    return L;
+}
+
+/* Coarse material = average of the 2^d fine cells it covers (Sec. 2.4: the
+ * material model is a vector space, so averaging is well defined). */
+void orc_coarsen_psi(const orc_problem *fine, const double *psi_f, double *psi_c)
+{
+    orc_problem C;
+    orc_coarse_problem(fine, &C);
+    const int d = fine->dim, nc = 1 << d;
+    for (int K = 0; K < ncell_axis(&C, 2); ++K)
+        for (int J = 0; J < ncell_axis(&C, 1); ++J)
+            for (int I = 0; I < ncell_axis(&C, 0); ++I) {
+                double s = 0.0;
+                for (int a = 0; a < nc; ++a) {
+                    int i = 2 * I + (a & 1), j = 2 * J + ((a >> 1) & 1), k = (d == 3) ? 2 * K + ((a >> 2) & 1) : 0;
+                    s += psi_f[cid(fine, i, j, k)];
+                }
+                psi_c[cid(&C, I, J, K)] = s / nc;
+            }
+}
+
+/* Linear interpolation weight between fine offset m and coarse node 2I. */
+static double pw(int off)
+{
+    if (off == 0) return 1.0;
+    if (off == 1 || off == -1) return 0.5;
+    return 0.0;
+}
+
+/* r_c = P^T r_f / 2^d, zero at coarse Dirichlet dofs. */
+void orc_restrict(const orc_problem *fine, const double *r_f, double *r_c)
+{
+    orc_problem C;
+    orc_coarse_problem(fine, &C);
+    const int d = fine->dim;
+    const long Nf = orc_nnodes(fine), Nc = orc_nnodes(&C);
+    const double scale = 1.0 / (1 << d);
+    for (int p = 0; p < d; ++p)
+        for (int K = 0; K < C.n[2]; ++K)
+            for (int J = 0; J < C.n[1]; ++J)
+                for (int I = 0; I < C.n[0]; ++I) {
+                    double s = 0.0;
+                    if (!orc_is_dirichlet(&C, I, J, K, p)) {
+                        int k0 = (d == 3) ? -1 : 0, k1 = (d == 3) ? 1 : 0;
+                        for (int dk = k0; dk <= k1; ++dk)
+                            for (int dj = -1; dj <= 1; ++dj)
+                                for (int di = -1; di <= 1; ++di) {
+                                    int i = 2 * I + di, j = 2 * J + dj, k = (d == 3) ? 2 * K + dk : 0;
+                                    if (i < 0 || j < 0 || k < 0) continue;
+                                    if (i >= fine->n[0] || j >= fine->n[1] || k >= fine->n[2]) continue;
+                                    s += pw(di) * pw(dj) * (d == 3 ? pw(dk) : 1.0) * r_f[p * Nf + nid(fine, i, j, k)];
+                                }
+                        s *= scale;
+                    }
+                    r_c[p * Nc + nid(&C, I, J, K)] = s;
+                }
+}
+
+/* u_f += P e_c on free fine dofs. */
+void orc_prolong_add(const orc_problem *fine, const double *e_c, double *u_f)
+{
+    orc_problem C;
+    orc_coarse_problem(fine, &C);
+    const int d = fine->dim;
+    const long Nf = orc_nnodes(fine), Nc = orc_nnodes(&C);
+    for (int p = 0; p < d; ++p)
+        for (int k = 0; k < fine->n[2]; ++k)
+            for (int j = 0; j < fine->n[1]; ++j)
+                for (int i = 0; i < fine->n[0]; ++i) {
+                    if (orc_is_dirichlet(fine, i, j, k, p)) continue;
+                    double s = 0.0;
+                    for (int K = k / 2; K <= (k + 1) / 2 && K < C.n[2]; ++K)
+                        for (int J = j / 2; J <= (j + 1) / 2 && J < C.n[1]; ++J)
+                            for (int I = i / 2; I <= (i + 1) / 2 && I < C.n[0]; ++I)
+                                s += pw(i - 2 * I) * pw(j - 2 * J) * (d == 3 ? pw(k - 2 * K) : 1.0) *
+                                     e_c[p * Nc + nid(&C, I, J, K)];
+                    u_f[p * Nf + nid(fine, i, j, k)] += s;
+                }
+}
+
+/* ------------------------------------------------------------ dense solve */
+
+void orc_assemble_dense(const orc_problem *P, const double *psi, double *K)
+{
+    const int d = P->dim;
+    const long N = orc_nnodes(P), n = d * N;
+    double *e = calloc(n, sizeof(double));
+    double *col = malloc(sizeof(double) * n);
+    for (long c = 0; c < n; ++c) {           /* column c = K e_c */
+        e[c] = 1.0;
+        orc_apply(P, psi, e, col);
+        for (long r = 0; r < n; ++r) K[r * n + c] = col[r];
+        e[c] = 0.0;
+    }
+    free(e);
+    free(col);
+}
+
+/* In-place Cholesky A = L L^T (lower triangle), m x m row-major. */
+static int cholesky(double *A, long m)
+{
+    for (long j = 0; j < m; ++j) {
+        double s = A[j * m + j];
+        for (long k = 0; k < j; ++k) s -= A[j * m + k] * A[j * m + k];
+        if (!(s > 0.0)) return 3;
+        double ljj = sqrt(s);
+        A[j * m + j] = ljj;
+        for (long i = j + 1; i < m; ++i) {
+            double t = A[i * m + j];
+            for (long k = 0; k < j; ++k) t -= A[i * m + k] * A[j * m + k];
+            A[i * m + j] = t / ljj;
+        }
+    }
+    return 0;
+}
+
+static void cholesky_solve(const double *L, long m, double *b)
+{
+    for (long i = 0; i < m; ++i) {
+        double s = b[i];
+        for (long k = 0; k < i; ++k) s -= L[i * m + k] * b[k];
+        b[i] = s / L[i * m + i];
+    }
+    for (long i = m - 1; i >= 0; --i) {
+        double s = b[i];
+        for (long k = i + 1; k < m; ++k) s -= L[k * m + i] * b[k];
+        b[i] = s / L[i * m + i];
+    }
+}
+
+/* free-dof index list (dof = p*N + node) */
+static long free_dofs(const orc_problem *P, long *list)
+{
+    const long N = orc_nnodes(P);
+    long m = 0;
+    for (int p = 0; p < P->dim; ++p)
+        for (int k = 0; k < P->n[2]; ++k)
+            for (int j = 0; j < P->n[1]; ++j)
+                for (int i = 0; i < P->n[0]; ++i)
+                    if (!orc_is_dirichlet(P, i, j, k, p)) list[m++] = p * N + nid(P, i, j, k);
+    return m;
+}
+
+typedef struct {
+    long m;
+    long *dofs;
+    double *L;
+} orc_chol;
+
+static int chol_factor(const orc_problem *P, const double *psi, orc_chol *c)
+{
+    const long n = P->dim * orc_nnodes(P);
+    double *K = malloc(sizeof(double) * n * n);
+    orc_assemble_dense(P, psi, K);
+    c->dofs = malloc(sizeof(long) * n);
+    c->m = free_dofs(P, c->dofs);
+    c->L = malloc(sizeof(double) * c->m * c->m);
+    for (long a = 0; a < c->m; ++a)
+        for (long b = 0; b < c->m; ++b) c->L[a * c->m + b] = K[c->dofs[a] * n + c->dofs[b]];
+    free(K);
+    return cholesky(c->L, c->m);
+}
+
+static void chol_free(orc_chol *c)
+{
+    free(c->dofs);
+    free(c->L);
+}
+
+/* u_F += K_FF^-1 (f - K u)_F : exact solve in correction form. */
+static void chol_correct(const orc_problem *P, const double *psi, const orc_chol *c,
+                         const double *f, double *u)
+{
+    const long n = P->dim * orc_nnodes(P);
+    double *r = malloc(sizeof(double) * n);
+    double *b = malloc(sizeof(double) * c->m);
+    orc_residual(P, psi, f, u, r);
+    for (long a = 0; a < c->m; ++a) b[a] = r[c->dofs[a]];
+    cholesky_solve(c->L, c->m, b);
+    for (long a = 0; a < c->m; ++a) u[c->dofs[a]] += b[a];
+    free(r);
+    free(b);
+}
+
+int orc_direct_solve(const orc_problem *P, const double *psi, const double *f, double *u)
+{
+    orc_chol c;
+    int st = chol_factor(P, psi, &c);
+    if (st == 0) chol_correct(P, psi, &c, f, u);
+    chol_free(&c);
+    return st;
+}
+
+/* -------------------------------------------------------------- V-cycle */
+
+typedef struct {
+    orc_problem P;
+    double *psi, *u, *f, *r;
+} orc_level;
+
+static void smooth(orc_level *L, const orc_mg_opts *o, int nsweeps, int descending)
+{
+    for (int s = 0; s < nsweeps; ++s) {
+        if (o->smoother == 1) orc_gs_sweep(&L->P, L->psi, L->f, L->u, descending);
+        else orc_jacobi_sweep(&L->P, L->psi, L->f, L->u, o->omega);
+    }
+}
+
+/* V(nu1, nu2): smooth, restrict the residual, recurse from a zero guess,
+ * prolongate the correction, smooth (Sec. 2.2: refined levels extend the
+ * multigrid coarse/fine sequence; here every level covers the whole box). */
+static void vcycle(orc_level *lev, int l, const orc_mg_opts *o, const orc_chol *bottom)
+{
+    orc_level *L = &lev[l];
+    if (l == 0) {
+        chol_correct(&L->P, L->psi, bottom, L->f, L->u);
+        return;
+    }
+    orc_level *C = &lev[l - 1];
+    smooth(L, o, o->nu1, 0);
+    orc_residual(&L->P, L->psi, L->f, L->u, L->r);
+    orc_restrict(&L->P, L->r, C->f);
+    memset(C->u, 0, sizeof(double) * C->P.dim * orc_nnodes(&C->P));
+    vcycle(lev, l - 1, o, bottom);
+    orc_prolong_add(&L->P, C->u, L->u);
+    smooth(L, o, o->nu2, 1);
+}
+
+int orc_mg_solve(const orc_problem *P, const double *psi, const double *f, double *u,
+                 const orc_mg_opts *o, double *hist, int *cycles)
+{
+    const int nl = orc_num_levels(P);
+    orc_level *lev = calloc(nl, sizeof(orc_level));
+    /* finest level = index nl-1 */
+    lev[nl - 1].P = *P;
+    for (int l = nl - 2; l >= 0; --l) orc_coarse_problem(&lev[l + 1].P, &lev[l].P);
+    for (int l = 0; l < nl; ++l) {
+        const long N = orc_nnodes(&lev[l].P), NC = orc_ncells(&lev[l].P);
+        const int d = P->dim;
+        lev[l].psi = malloc(sizeof(double) * NC);
+        lev[l].r = malloc(sizeof(double) * d * N);
+        if (l < nl - 1) {
+            lev[l].u = calloc(d * N, sizeof(double));
+            lev[l].f = calloc(d * N, sizeof(double));
+        }
+    }
+    memcpy(lev[nl - 1].psi, psi, sizeof(double) * orc_ncells(P));
+    lev[nl - 1].u = u;
+    lev[nl - 1].f = (double *)f;
+    for (int l = nl - 1; l > 0; --l) orc_coarsen_psi(&lev[l].P, lev[l].psi, lev[l - 1].psi);
+
+    orc_chol bottom;
+    int status = chol_factor(&lev[0].P, lev[0].psi, &bottom);
+    int ncyc = 0;
+    if (status == 0) {
+        double *r = lev[nl - 1].r;
+        orc_residual(P, psi, f, u, r);
+        const double r0 = orc_norm_free(P, r);
+        double rel = 1.0;
+        if (hist) hist[0] = 1.0;
+        status = 1;
+        if (r0 == 0.0) status = 0;
+        while (status == 1 && ncyc < o->max_cycles) {
+            vcycle(lev, nl - 1, o, &bottom);
+            ++ncyc;
+            orc_residual(P, psi, f, u, r);
+            rel = orc_norm_free(P, r) / r0;
+            if (hist) hist[ncyc] = rel;
+            if (!isfinite(rel) || rel > 1e10) status = 2;
+            else if (rel <= o->tol) status = 0;
+        }
+    }
+    chol_free(&bottom);
+    for (int l = 0; l < nl; ++l) {
+        free(lev[l].psi);
+        free(lev[l].r);
+        if (l < nl - 1) {
+            free(lev[l].u);
+            free(lev[l].f);
+        }
+    }
+    free(lev);
+    if (cycles) *cycles = ncyc;
+    return status;
+}
+
+/* ------------------------------------------------------------- gradient */
+
+/* For J with adjoint lambda (K lambda = dJ/du, lambda = 0 on Dirichlet dofs):
+ * dJ/dpsi_c = -lambda_c^T S_c u_c, S_c the unit-psi element matrix. */
+void orc_dJdpsi(const orc_problem *P, const double *u, const double *lam, double *g)
+{
+    const int d = P->dim, nc = 1 << d, nd = nc * d;
+    const long N = orc_nnodes(P);
+    double Ke[24 * 24], ue[24], le[24];
+    orc_element_matrix(P, Ke);
+    for (int ck = 0; ck < ncell_axis(P, 2); ++ck)
+        for (int cj = 0; cj < ncell_axis(P, 1); ++cj)
+            for (int ci = 0; ci < ncell_axis(P, 0); ++ci) {
+                for (int a = 0; a < nc; ++a) {
+                    int i, j, k;
+                    cell_corner(P, ci, cj, ck, a, &i, &j, &k);
+                    for (int q = 0; q < d; ++q) {
+                        ue[a * d + q] = u[q * N + nid(P, i, j, k)];
+                        le[a * d + q] = lam[q * N + nid(P, i, j, k)];
+                    }
+                }
+                double s = 0.0;
+                for (int r = 0; r < nd; ++r)
+                    for (int c = 0; c < nd; ++c) s += le[r] * Ke[r * nd + c] * ue[c];
+                g[cid(P, ci, cj, ck)] = -s;
+            }
+}

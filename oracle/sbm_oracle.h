@@ -1,0 +1,102 @@
+/*
+ * sbm_oracle.h — plain, slow, FP64 CPU oracle for the smooth-boundary-method
+ * (SBM) elasticity multigrid solve of Agrawal & Runnels (arXiv 2212.02362).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path links, loads or calls
+ * this code.  It is used by tests/, by __graft_entry__.smoke() (to check one
+ * small GPU solve) and by bench.py's CPU-baseline leg.  It shares no source with
+ * the CUDA library: every formula here is written from the paper's equations
+ * and from textbook finite-element definitions.
+ *
+ * What is computed (paper section and equation in brackets):
+ *   - The strong form div(psi C grad u) = source  [Sec. 2.1, eq. SBMLinearElasticity]
+ *     with u at nodes and psi in cells [Sec. 2.3], discretised as the cell-flux
+ *     (Q1, 2^d-point Gauss) operator
+ *        (K u)_n = h^-d sum_{cells c containing n} psi_c  int_c B_n^T C B u_c .
+ *     In 1D this is exactly minus C times the cell-placed-psi stencil of Sec. 2.3.
+ *   - Damped Jacobi  u <- u + omega D^-1 (f - K u)            [Sec. 2.3, Jacobi eq.]
+ *   - 2^d-colour Gauss-Seidel (colour = index parity)          [Sec. 2.3: "Gauss-Seidel"]
+ *   - Coarse psi = mean of the 2^d fine cells                  [Sec. 2.4: model averaging]
+ *   - Full-weighting restriction R = P^T / 2^d, (bi/tri)linear prolongation P,
+ *     V(nu1,nu2) cycle, dense Cholesky bottom solve            [Sec. 2.2 level sequence]
+ *   - Dense direct solve, adjoint solve and dJ/dpsi_c = -lambda_c^T S_c u_c.
+ *
+ * Layout (the same packed layout as the C ABI of the CUDA library):
+ *   node (i,j,k)  -> i + nx*(j + ny*k);     component p at offset p*nnodes
+ *   cell (i,j,k)  -> i + (nx-1)*(j + (ny-1)*k)   (cell with lower corner node (i,j,k))
+ *   2D problems have nz = 1 and cells (nx-1)*(ny-1).
+ * Faces: 0:-x 1:+x 2:-y 3:+y 4:-z 5:+z.
+ */
+#ifndef SBM_ORACLE_H
+#define SBM_ORACLE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+    int dim;               /* 2 (plane strain) or 3 */
+    int n[3];              /* nodes per axis; n[2] == 1 when dim == 2 */
+    double h;              /* node spacing, equal on all axes */
+    double c11, c12, c44;  /* axis-aligned cubic moduli (isotropic: lambda+2mu, lambda, mu) */
+    unsigned dirichlet[3]; /* per component p: bit f set => face f is Dirichlet for p */
+} orc_problem;
+
+typedef struct {
+    int nu1, nu2;          /* pre / post smoothing sweeps */
+    double omega;          /* Jacobi damping */
+    int smoother;          /* 0 = damped Jacobi, 1 = 2^d-colour Gauss-Seidel */
+    double tol;            /* stop when ||f - K u|| / ||f - K u0|| <= tol */
+    int max_cycles;
+} orc_mg_opts;
+
+long orc_nnodes(const orc_problem *P);
+long orc_ncells(const orc_problem *P);
+int  orc_is_dirichlet(const orc_problem *P, int i, int j, int k, int p);
+
+/* Element matrix of one cell with unit psi, FD scaled (h^-d), (2^d d) x (2^d d),
+ * row index = corner*d + component.  Corner bit a gives the offset on axis a. */
+void orc_element_matrix(const orc_problem *P, double *Ke);
+
+/* Ku over all dofs (no Dirichlet masking). */
+void orc_apply(const orc_problem *P, const double *psi, const double *u, double *Ku);
+/* r = f - K u on free dofs, 0 on Dirichlet dofs. */
+void orc_residual(const orc_problem *P, const double *psi, const double *f,
+                  const double *u, double *r);
+/* D_{n,p} = K_{(n,p),(n,p)} */
+void orc_diagonal(const orc_problem *P, const double *psi, double *D);
+/* Euclidean norm over free dofs, summed in index order. */
+double orc_norm_free(const orc_problem *P, const double *r);
+
+void orc_jacobi_sweep(const orc_problem *P, const double *psi, const double *f,
+                      double *u, double omega);
+/* one sweep over all 2^d colours, ascending (descending != 0: descending) */
+void orc_gs_sweep(const orc_problem *P, const double *psi, const double *f,
+                  double *u, int descending);
+
+int  orc_can_coarsen(const orc_problem *P);
+void orc_coarse_problem(const orc_problem *fine, orc_problem *coarse);
+void orc_coarsen_psi(const orc_problem *fine, const double *psi_f, double *psi_c);
+void orc_restrict(const orc_problem *fine, const double *r_f, double *r_c);
+void orc_prolong_add(const orc_problem *fine, const double *e_c, double *u_f);
+int  orc_num_levels(const orc_problem *P);
+
+/* Dense (ndof x ndof) row-major assembly of K over all dofs. */
+void orc_assemble_dense(const orc_problem *P, const double *psi, double *K);
+/* Solve K_FF u_F = f_F - K_FD u_D by dense Cholesky; u holds Dirichlet values
+ * on entry.  Returns 0, or 3 if the free-dof matrix is not positive definite. */
+int  orc_direct_solve(const orc_problem *P, const double *psi, const double *f, double *u);
+
+/* Multigrid solve.  u holds the initial guess and Dirichlet values on entry.
+ * hist (max_cycles+1 entries, may be NULL) receives relres after each cycle.
+ * Returns 0 converged, 1 not converged in max_cycles, 2 diverged, 3 bottom failed. */
+int  orc_mg_solve(const orc_problem *P, const double *psi, const double *f, double *u,
+                  const orc_mg_opts *o, double *hist, int *cycles);
+
+/* g_c = -lambda_c^T S_c u_c for every cell (S_c = unit-psi element matrix). */
+void orc_dJdpsi(const orc_problem *P, const double *u, const double *lam, double *g);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
