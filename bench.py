@@ -1,0 +1,364 @@
+#!/usr/bin/env python3
+"""Benchmark: time to relative residual 1e-10 of the SBM elasticity multigrid
+solve, in MDOF/s (dofs of the finest grid / time-to-tolerance).
+
+Workload (default): the 3D damaged cubic crystal on 129^3 nodes (6.44 M dofs),
+C11 = 1.0, C12 = 0.6, C44 = 0.5, psi = 1 - damage of 3 seeded random ellipsoids
+(tanh width 2h), psi_min = 1e-4, z = 0 clamped, top face pulled by 0.01.  The
+timed solve is the FP32 V-cycle inside FP64 defect correction ("mixed"); the
+plain FP64 solve of the same problem is timed beside it.
+
+One step = one complete solve from the initial guess to relres <= 1e-10 with the
+inputs resident in HBM.  L2 is flushed (256 MB write) between timed steps.  Under
+torchrun every rank solves its own replica (the solve is not sharded: replicas
+only) and the JSON value is the total over ranks.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "SBM elasticity MG time-to-relres 1e-10 (MDOF/s), FP32+refine vs FP64; HBM GB/s"
+UNIT = "MDOF/s"
+GOLDEN = os.path.join(ROOT, "tests", "golden", "damage_3d_129_oracle.json")
+FP64_PEAK_GFLOPS = 1250.0       # GB300 FP64 rate (vector and tensor), from the hardware table
+FP32_PEAK_GFLOPS = 152 * 128 * 2 * 2.070   # 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz
+
+
+def workload(name: str):
+    if name == "damage_3d_129":
+        return W.damage3d(129)
+    if name == "damage_3d_65":
+        return W.damage3d(65)
+    if name == "topopt_3d":
+        return W.topopt3d()
+    if name == "plate_hole_2d":
+        return W.plate_hole(65)
+    raise SystemExit(f"unknown workload {name}")
+
+
+def workload_config(wk, precision):
+    return {"workload": f"{wk.name} {'x'.join(str(v) for v in wk.n[:wk.dim])} nodes",
+            "dofs": wk.ndofs, "moduli_c11_c12_c44": list(wk.moduli), "psi_min": wk.psi_min,
+            "precision": precision, "tol": 1e-10, "cycle": "V(2,2) damped Jacobi",
+            "omega": wk.omega, "l2": "flushed (256 MB write) between timed steps"}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.samples = []
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100",
+                 "-i", str(gpu_index)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append((time.time(), [x.strip() for x in line.split(",")]))
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self, t0, t1):
+        rows = [s for t, s in self.samples if t0 <= t <= t1] or [s for _, s in self.samples[-5:]]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for name, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(num(r[2]) or 0 for r in rows),
+                "power_w_max": max(num(r[3]) or 0 for r in rows),
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def oracle_cycle_sample(wk, ncycles=1):
+    """Time ``ncycles`` V-cycles of the CPU oracle on the full workload (single thread)."""
+    import oracle
+    oracle.build()
+    P = oracle.Problem(wk.dim, wk.n, wk.h, *wk.moduli, dirichlet=wk.dirichlet_bits())
+    psi = oracle.floor_psi(wk.psi, wk.psi_min)
+    t = time.perf_counter()
+    oracle.mg_solve(P, psi, wk.f, wk.u0, omega=wk.omega, tol=0.0, max_cycles=ncycles)
+    return (time.perf_counter() - t) / ncycles
+
+
+def oracle_cycles_to_tol(name):
+    if name == "damage_3d_129" and os.path.exists(GOLDEN):
+        return int(json.load(open(GOLDEN))["cycles_to_1e-10"]), "oracle golden record"
+    return None, None
+
+
+def run_reference(args, rank, world):
+    """The CPU oracle as it stands (single thread) on a bounded sample: each step is
+    one full-size oracle V-cycle; time-to-tolerance = per-cycle time x the oracle's
+    cycles to 1e-10 (from its golden record, else the GPU FP64 count is unavailable
+    here and the sample is reported per cycle)."""
+    if rank != 0:
+        return
+    wk = workload(args.workload)
+    cyc, src = oracle_cycles_to_tol(args.workload)
+    times = []
+    for i in range(args.warmup + args.steps):
+        t = oracle_cycle_sample(wk, 1)
+        if i >= args.warmup:
+            times.append(t)
+    per_cycle = statistics.mean(times)
+    ncyc = cyc if cyc else 1
+    value = wk.ndofs / (per_cycle * ncyc) / 1e6
+    sample = (f"{args.steps} full-size oracle V-cycles ({per_cycle:.2f} s each), time-to-1e-10 = per-cycle "
+              f"time x {ncyc} cycles ({src or 'cycle count unavailable: one cycle'})")
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": per_cycle * ncyc * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference", "config": workload_config(wk, "fp64"),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    torch.cuda.set_device(local_rank)
+    import paper_2212_02362_gb300 as sbm
+    from paper_2212_02362_gb300 import _capi
+    import ctypes as C
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+
+    wk = workload(args.workload)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.Stream(device=dev)
+    t64 = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).to(dev)
+
+    def make_grid(precision):
+        g = sbm.Grid(wk.dim, wk.n, wk.h, precision=precision, device=local_rank, stream=stream.cuda_stream)
+        g.set_moduli(sbm.SBM_CUBIC, wk.moduli)
+        for face, comp, value in wk.bcs:
+            g.set_bc(face, comp, sbm.SBM_DIRICHLET, float(value))
+        return g
+
+    psi_d, f_d, u0_d = t64(wk.psi), t64(wk.f), t64(wk.u0)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    opts = {"omega": wk.omega, "tol": 1e-10}
+
+    def timed_solves(g, nsteps, nwarm):
+        with torch.cuda.stream(stream):
+            g.set_psi(psi_d, wk.psi_min)
+            g.set_source(f_d)
+            u = torch.empty_like(u0_d)
+            infos, ms = [], []
+            for i in range(nwarm + nsteps):
+                flush.zero_()
+                u.copy_(u0_d)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                info = g.solve(u, **opts)
+                e1.record(stream)
+                e1.synchronize()
+                if i >= nwarm:
+                    infos.append(info)
+                    ms.append(e0.elapsed_time(e1))
+        return infos, ms, u
+
+    # ---- mixed precision (the headline) ----
+    gmix = make_grid(args.precision)
+    # warm-up untimed
+    timed_solves(gmix, 0, args.warmup)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    gpu_index = int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local_rank)).split(",")[local_rank]) \
+        if os.environ.get("CUDA_VISIBLE_DEVICES") else local_rank
+    sampler = ClockSampler(gpu_index) if rank == 0 else None
+    time.sleep(0.3 if sampler else 0)
+    t_wall0 = time.time()
+    infos, ms, u = timed_solves(gmix, args.steps, 0)
+    torch.cuda.synchronize()
+    t_wall1 = time.time()
+    if dist:
+        dist.barrier()
+    total_ms = sum(ms)
+    tmax = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+    if dist:
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    total_ms = float(tmax.item())
+    ms_per_step = total_ms / args.steps
+    value = world * wk.ndofs * args.steps / (total_ms / 1e3) / 1e6
+    cycles = infos[-1].cycles
+    launches = sum(i_.launches for i_ in infos)
+
+    # ---- kernel roofline (dominant kernel, timed live on the grid stream) ----
+    ms_k, bytes_k, flops_k = C.c_double(), C.c_double(), C.c_double()
+    kid = {"residual64": _capi.SBM_K_RESIDUAL64, "jacobi": _capi.SBM_K_JACOBI}[args.roofline_kernel]
+    with torch.cuda.stream(stream):
+        _capi.check(sbm.lib().sbm_time_kernel(gmix._h, kid, 20, C.byref(ms_k), C.byref(bytes_k), C.byref(flops_k)),
+                    gmix._h)
+    hbm_peak, peak_kind = peaks()
+    if args.roofline_kernel == "residual64":
+        achieved = flops_k.value / (ms_k.value * 1e-3) / 1e9
+        roof = {"bound": "alu", "kernel": "k_sweep3<double,float,residual> (FP64 defect residual)",
+                "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+                "frac": achieved / FP64_PEAK_GFLOPS, "peak_kind": "nominal FP64 rate of the hardware table",
+                "algorithmic_flops": flops_k.value, "algorithmic_bytes": bytes_k.value,
+                "ms_per_launch": ms_k.value, "traffic": None}
+    else:
+        achieved = bytes_k.value / (ms_k.value * 1e-3) / 1e9
+        roof = {"bound": "hbm", "kernel": "k_sweep3<float,float,jacobi> (FP32 Jacobi sweep, finest level)",
+                "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+                "peak_kind": f"{peak_kind} (copy bandwidth)", "algorithmic_bytes": bytes_k.value,
+                "algorithmic_flops": flops_k.value, "ms_per_launch": ms_k.value, "traffic": None,
+                "alu_frac_fp32": flops_k.value / (ms_k.value * 1e-3) / 1e9 / FP32_PEAK_GFLOPS}
+    if args.traffic is not None:
+        roof["traffic"] = args.traffic
+
+    # ---- plain FP64 solve of the same problem ----
+    fp64 = None
+    if args.precision == "mixed" and not args.skip_fp64:
+        g64 = make_grid("fp64")
+        timed_solves(g64, 0, 1)
+        i64, ms64, u64 = timed_solves(g64, max(1, min(args.steps, 2)), 0)
+        fp64 = {"ms_per_step": statistics.mean(ms64), "value": wk.ndofs / (statistics.mean(ms64) / 1e3) / 1e6,
+                "cycles": i64[-1].cycles,
+                "max_rel_diff_vs_mixed": float((u64 - u).abs().max() / u64.abs().max())}
+        del g64
+
+    # ---- end to end through the public API: host inputs in, host result out ----
+    psi_h = torch.from_numpy(np.ascontiguousarray(wk.psi)).pin_memory()
+    f_h = torch.from_numpy(np.ascontiguousarray(wk.f)).pin_memory()
+    u0_h = torch.from_numpy(np.ascontiguousarray(wk.u0)).pin_memory()
+    out_h = torch.empty_like(u0_h).pin_memory()
+    e2e_ms = []
+    with torch.cuda.stream(stream):
+        psi_e, f_e, u_e = torch.empty_like(psi_d), torch.empty_like(f_d), torch.empty_like(u0_d)
+        for i in range(1 + min(args.steps, 3)):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            psi_e.copy_(psi_h, non_blocking=True)
+            f_e.copy_(f_h, non_blocking=True)
+            u_e.copy_(u0_h, non_blocking=True)
+            gmix.set_psi(psi_e, wk.psi_min)
+            gmix.set_source(f_e)
+            gmix.solve(u_e, **opts)
+            out_h.copy_(u_e, non_blocking=True)
+            e1.record(stream)
+            e1.synchronize()
+            if i > 0:
+                e2e_ms.append(e0.elapsed_time(e1))
+    e2e_val = world * wk.ndofs / (statistics.mean(e2e_ms) / 1e3) / 1e6
+    h2d = (psi_h.numel() + f_h.numel() + u0_h.numel()) * 8
+    d2h = out_h.numel() * 8
+
+    clocks = None
+    if sampler:
+        sampler.stop()
+        clocks = sampler.summary(t_wall0, t_wall1)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.skip_cpu:
+        per_cycle = oracle_cycle_sample(wk, 1)
+        ncyc, src = oracle_cycles_to_tol(args.workload)
+        if ncyc is None:
+            ncyc, src = (fp64 or {}).get("cycles", cycles), "GPU FP64 cycle count"
+        cpu = {"value": wk.ndofs / (per_cycle * ncyc) / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"1 full-size oracle V-cycle ({per_cycle:.2f} s, single thread) x {ncyc} cycles to "
+                         f"1e-10 ({src})"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64",
+                "data": "synthetic (seeded damage field)", "config": workload_config(wk, args.precision),
+                "cycles_to_tol": cycles, "vcycles_per_s": cycles / (ms_per_step / 1e3),
+                "fp64_solve": fp64, "roofline": roof, "cpu_baseline": cpu,
+                "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                        "note": "host->device inputs, psi set-up (coarsening, bottom inverse), solve, result->host"},
+                "gpu_launches": launches, "clocks": clocks,
+                "wall_s_timed": t_wall1 - t_wall0}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="damage_3d_129")
+    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--roofline-kernel", choices=["residual64", "jacobi"], default="jacobi")
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="DRAM bytes per launch of the roofline kernel from an ncu capture")
+    ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    from paper_2212_02362_gb300 import build
+    if rank == 0:
+        build.build()
+    run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

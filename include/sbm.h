@@ -1,0 +1,199 @@
+/*
+ * sbm.h — C ABI of the GB300 (sm_103a) multigrid solver for smooth-boundary-
+ * method (SBM) linear elasticity (Agrawal & Runnels, arXiv 2212.02362).
+ *
+ * The solved problem is the diffuse-boundary equilibrium equation of Sec. 2.1
+ * (eq. SBMLinearElasticity):   div(psi sigma) = source,  sigma = C grad u,
+ * with the displacement u stored at grid nodes and the indicator psi stored in
+ * cells (Sec. 2.3), psi floored at psi_min so that the operator stays definite.
+ * It is discretised as the cell-flux operator
+ *     (K u)_n = h^-d  sum_{cells c containing n}  psi_c  int_c B_n^T C B u_c,
+ * which reduces in 1D to minus C times the cell-placed-psi stencil of Sec. 2.3,
+ * and solved with a geometric multigrid V-cycle (Sec. 2.2) whose smoother is
+ * damped Jacobi or 2^d-colour Gauss-Seidel (Sec. 2.3); coarse psi is the mean of
+ * the fine cells (Sec. 2.4).  The equation solved is K u = f on free dofs, with
+ * f = -(psi b + t |grad psi|) in the paper's notation.
+ *
+ * Conventions shared by every entry point
+ *  - Arrays are packed, component-major ("SoA"):
+ *        node (i,j,k), component p  ->  p*nnodes + i + nx*(j + ny*k)
+ *        cell (i,j,k)               ->  i + (nx-1)*(j + (ny-1)*k)
+ *    (cell (i,j,k) has lower corner node (i,j,k); 2D grids have nz = 1 and
+ *    (nx-1)*(ny-1) cells).  Faces: 0:-x 1:+x 2:-y 3:+y 4:-z 5:+z.
+ *  - Pointers documented as "device" must be CUDA device (or managed) memory of
+ *    the grid's device; the library checks this with cudaPointerGetAttributes and
+ *    returns SBM_ERR_ARG otherwise.  Pointers documented as "host" are plain host
+ *    memory.  The caller owns every buffer it passes; sbm_set_* copy what they
+ *    need into library-owned device storage, so inputs may be freed afterwards.
+ *  - All work is ordered on the stream given in sbm_grid_desc.  Entry points
+ *    that return results to the host (sbm_solve, sbm_adjoint, norms) synchronise
+ *    that stream before returning.
+ *  - No entry point aborts or throws.  Each returns a status; on failure
+ *    sbm_last_error() gives a one-line description.  A handle is not thread-safe.
+ */
+#ifndef SBM_H
+#define SBM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sbm_grid_s *sbm_grid;          /* opaque; created and freed by the library */
+
+typedef enum {
+    SBM_OK = 0,
+    SBM_ERR_ARG = 1,       /* bad argument: null/host pointer, size, index, value */
+    SBM_ERR_STATE = 2,     /* call out of order (e.g. solve before sbm_set_psi) */
+    SBM_ERR_CUDA = 3,      /* a CUDA runtime call failed */
+    SBM_ERR_OOM = 4,       /* device allocation failed */
+    SBM_ERR_NOCONV = 5,    /* max_cycles reached before the tolerance */
+    SBM_ERR_DIVERGED = 6   /* relative residual not finite or above 1e10 */
+} sbm_status;
+
+enum { SBM_FP64 = 0, SBM_MIXED = 1 };                  /* precision of the V-cycle */
+enum { SBM_JACOBI = 0, SBM_MCGS = 1 };                  /* smoother */
+enum { SBM_CUBIC = 0, SBM_ISO_LAME = 1, SBM_ISO_ENU = 2 };  /* moduli kinds */
+enum { SBM_FREE = 0, SBM_DIRICHLET = 1, SBM_DIRICHLET_FROM_U = 2 };  /* face conditions */
+
+typedef struct {
+    int dim;               /* 2 (plane strain) or 3 */
+    int n[3];              /* nodes per axis; n[2] = 1 when dim == 2; every n >= 2 */
+    double h;              /* node spacing (equal on every axis), > 0 */
+    int precision;         /* SBM_FP64: every level in FP64.  SBM_MIXED: FP32 V-cycle
+                              inside an FP64 defect correction (FP64 fine residual,
+                              update and norms) */
+    void *stream;          /* cudaStream_t to order all work on; NULL: the library creates
+                              its own blocking stream (ordered after legacy-stream work) */
+    int device;            /* CUDA device ordinal the grid lives on */
+} sbm_grid_desc;
+
+typedef struct {
+    double tol;            /* stop when ||f - K u||_2 / ||f - K u_0||_2 <= tol (free dofs) */
+    int max_cycles;        /* outer iterations (V-cycles in FP64 mode) */
+    int nu1, nu2;          /* pre / post smoothing sweeps */
+    double omega;          /* Jacobi damping (ignored by SBM_MCGS) */
+    int smoother;          /* SBM_JACOBI or SBM_MCGS */
+    int inner_cycles;      /* SBM_MIXED: FP32 V-cycles per FP64 defect (>= 1) */
+    int use_graph;         /* 1: replay the cycle as a CUDA graph; 0: launch eagerly */
+} sbm_opts;
+
+typedef struct {
+    int status;            /* the sbm_status the call returned */
+    int cycles;            /* outer iterations performed */
+    int vcycles;           /* V-cycles performed (cycles * inner_cycles in mixed mode) */
+    int levels;            /* multigrid levels */
+    double r0;             /* ||f - K u_0||_2 */
+    double relres;         /* final relative residual */
+    double *history;       /* host, optional: relres after each outer iteration, [0] = 1 */
+    int history_capacity;  /* entries available in history */
+    double setup_ms;       /* device time of psi/bottom set-up triggered by this call */
+    double solve_ms;       /* device time of the solve (CUDA events on the grid stream) */
+    long long launches;    /* library kernels launched by the call (graph nodes included) */
+} sbm_info;
+
+/* Fill opts with the defaults tol 1e-10, max_cycles 500, V(2,2), omega 2/3,
+ * Jacobi, inner_cycles 1, use_graph 1. */
+void sbm_default_opts(sbm_opts *opts);
+
+const char *sbm_status_string(int status);
+/* Last error message of a handle (or of the library when grid is NULL). */
+const char *sbm_last_error(sbm_grid grid);
+
+/* Create a grid and its multigrid hierarchy: levels are coarsened by 2 while
+ * every (n-1) is even and stays >= 4 after halving (Sec. 2.2 level sequence).
+ * Allocates all level storage on desc->device.  Returns SBM_ERR_ARG for a bad
+ * descriptor, SBM_ERR_OOM / SBM_ERR_CUDA on allocation failure. */
+sbm_status sbm_grid_create(const sbm_grid_desc *desc, sbm_grid *out);
+sbm_status sbm_grid_destroy(sbm_grid grid);
+/* Number of multigrid levels and the node counts of level l (0 = coarsest). */
+sbm_status sbm_grid_levels(sbm_grid grid, int *nlevels);
+sbm_status sbm_grid_level_shape(sbm_grid grid, int level, int n[3], double *h);
+
+/* psi in cells (Sec. 2.3), device, FP64, packed cell layout of the finest
+ * level.  psi <- max(psi, psi_min), psi_min > 0; coarse levels get the mean of
+ * their 2^d fine cells (Sec. 2.4).  NaN or Inf in psi gives SBM_ERR_ARG.
+ * `level` must be the finest level index (nlevels-1). */
+sbm_status sbm_set_psi(sbm_grid grid, int level, const double *psi_cells, double psi_min);
+/* SIMP stiffness map for topology optimisation (Sec. 3.3 uses a power of the
+ * order parameter as the stiffness factor): psi = psi_min + (1 - psi_min) rho^q,
+ * rho in cells (device, FP64).  The density is kept so that sbm_adjoint can
+ * also return dJ/drho. */
+sbm_status sbm_set_density(sbm_grid grid, int level, const double *rho_cells,
+                           double psi_min, double q);
+/* Uniform moduli (Sec. 2.4 vector-space parameters): SBM_CUBIC p = (C11, C12, C44)
+ * axis-aligned; SBM_ISO_LAME p = (lambda, mu, -); SBM_ISO_ENU p = (E, nu, -). */
+sbm_status sbm_set_moduli(sbm_grid grid, int kind, const double p[3]);
+/* Face condition for one component.  SBM_DIRICHLET writes `value` into u on that
+ * face before each solve (faces written in order 0..5, so a later face wins on
+ * shared edges); SBM_DIRICHLET_FROM_U keeps the values the caller put in u;
+ * SBM_FREE is the traction-free (natural) condition of the cell-flux form. */
+sbm_status sbm_set_bc(sbm_grid grid, int face, int comp, int type, double value);
+/* Right-hand side f (device, FP64, packed node layout, finest level), K u = f. */
+sbm_status sbm_set_source(sbm_grid grid, int level, const double *f_nodes);
+
+/* Solve K u = f.  u (device, FP64, packed) holds the initial guess on entry and
+ * the solution on return; Dirichlet dofs are set from the face conditions and
+ * never changed by the iteration.  opts may be NULL (defaults); info may be NULL.
+ * Synchronises the grid stream.  Returns SBM_OK, SBM_ERR_NOCONV or
+ * SBM_ERR_DIVERGED (info is filled in all three cases). */
+sbm_status sbm_solve(sbm_grid grid, double *u, const sbm_opts *opts, sbm_info *info);
+
+/* Adjoint of a solve: lambda solves K lambda = dJdu with homogeneous Dirichlet
+ * conditions (the same multigrid), then for every cell
+ *     dJdpsi_c = -lambda_c^T S_c u_c      (S_c: unit-psi cell matrix),
+ * the sensitivity of J(u(psi)) to psi_c.  u: the solution (device, packed);
+ * dJdu, lambda: device, packed nodes; dJdpsi: device, packed cells; dJdrho
+ * (optional, may be NULL) receives dJdpsi * dpsi/drho when the stiffness was set
+ * by sbm_set_density, and is zeroed where the psi_min floor is active otherwise.
+ * Status as for sbm_solve. */
+sbm_status sbm_adjoint(sbm_grid grid, const double *u, const double *dJdu, double *lambda,
+                       double *dJdpsi, double *dJdrho, const sbm_opts *opts, sbm_info *info);
+
+/* ---- single steps of the hot path, for parity tests and custom drivers ---- */
+/* All step calls take packed device arrays of the given level and run the same
+ * kernels as the solve.  `fp32` selects the FP32 kernels (inputs and outputs
+ * are still FP64 arrays; values are rounded to FP32 on entry). */
+
+/* Ku over all dofs, no Dirichlet masking (Sec. 2.1 operator). */
+sbm_status sbm_apply(sbm_grid grid, int level, int fp32, const double *u, double *Ku);
+/* r = f - K u on free dofs, 0 on Dirichlet dofs; *norm (host, may be NULL)
+ * receives ||r||_2 over free dofs (deterministic two-pass reduction). */
+sbm_status sbm_residual(sbm_grid grid, int level, int fp32, const double *f, const double *u,
+                        double *r, double *norm);
+/* One smoothing sweep in place on u (damped Jacobi with omega, or one 2^d-colour
+ * Gauss-Seidel sweep, colours ascending or descending), Sec. 2.3. */
+sbm_status sbm_smooth(sbm_grid grid, int level, int fp32, int smoother, double omega,
+                      int descending, const double *f, double *u);
+/* r_c = P^T r_f / 2^d (full weighting), zero on coarse Dirichlet dofs; level is the
+ * fine level (>= 1), r_c has the layout of level-1. */
+sbm_status sbm_restrict(sbm_grid grid, int level, int fp32, const double *r_f, double *r_c);
+/* u_f += P e_c (bi/trilinear) on free fine dofs; level is the fine level (>= 1). */
+sbm_status sbm_prolong_add(sbm_grid grid, int level, int fp32, const double *e_c, double *u_f);
+/* Copy of the psi the library holds for a level (after flooring / coarsening). */
+sbm_status sbm_get_psi(sbm_grid grid, int level, double *psi_cells);
+/* Bottom solve on the coarsest level: u_F += K_FF^-1 (f - K u)_F (device arrays). */
+sbm_status sbm_bottom_correct(sbm_grid grid, int fp32, const double *f, double *u);
+/* dJdpsi_c = -lambda_c^T S_c u_c for every cell of the finest level. */
+sbm_status sbm_dJdpsi(sbm_grid grid, const double *u, const double *lambda, double *dJdpsi);
+
+/* ---- measurement ---- */
+enum { SBM_K_RESIDUAL64 = 0, SBM_K_JACOBI = 1, SBM_K_RESIDUAL = 2 };
+/* Launch one hot-path kernel of the finest level `reps` times back to back on
+ * the grid stream between two CUDA events (after one untimed launch) and report
+ * the mean duration per launch (host, ms), together with the algorithmic DRAM
+ * bytes and floating-point operations of one launch (host, may be NULL):
+ *   SBM_K_RESIDUAL64  the FP64 defect residual (FP32 output on SBM_MIXED grids)
+ *   SBM_K_JACOBI      one damped-Jacobi sweep in the V-cycle precision
+ *   SBM_K_RESIDUAL    the V-cycle residual in the V-cycle precision
+ * Bytes count one read of u, f and psi and one write of the output per node;
+ * flops count the sum-factorised cell arithmetic per cell plus the per-node
+ * gather and update.  Uses the level's work buffers (overwrites them). */
+sbm_status sbm_time_kernel(sbm_grid grid, int which, int reps, double *ms_per_launch,
+                           double *bytes_per_launch, double *flops_per_launch);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,242 @@
+"""GB300-native multigrid solver for smooth-boundary-method (SBM) elasticity.
+
+Agrawal & Runnels, "Robust, strong form mechanics on an adaptive structured
+grid" (arXiv 2212.02362): the diffuse-boundary equilibrium equation
+div(psi C grad u) = source (Sec. 2.1), u at nodes and psi in cells (Sec. 2.3),
+solved by geometric multigrid (Sec. 2.2) with Jacobi or colour Gauss-Seidel
+smoothing.  Every step runs in the CUDA kernels of ``libsbm.so``; this module
+only marshals torch tensors (device memory and streams) to the C ABI declared
+in ``include/sbm.h``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+
+import torch
+
+from . import _capi
+from ._capi import (SBM_CUBIC, SBM_DIRICHLET, SBM_DIRICHLET_FROM_U, SBM_ERR_DIVERGED, SBM_ERR_NOCONV,
+                    SBM_FP64, SBM_FREE, SBM_ISO_ENU, SBM_ISO_LAME, SBM_JACOBI, SBM_MCGS, SBM_MIXED, SBM_OK,
+                    SBMError)
+
+__all__ = ["Grid", "SolveInfo", "SBMSolve", "SBMError", "SBM_FP64", "SBM_MIXED", "SBM_JACOBI", "SBM_MCGS",
+           "SBM_CUBIC", "SBM_ISO_LAME", "SBM_ISO_ENU", "SBM_FREE", "SBM_DIRICHLET", "SBM_DIRICHLET_FROM_U",
+           "FACES", "lib"]
+
+FACES = {"-x": 0, "+x": 1, "-y": 2, "+y": 3, "-z": 4, "+z": 5}
+
+
+def lib():
+    return _capi.load()
+
+
+def _ptr(t: torch.Tensor, dtype=torch.float64) -> int:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != dtype or not t.is_contiguous():
+        raise TypeError("expected a contiguous CUDA float64 tensor")
+    return t.data_ptr()
+
+
+@dataclass
+class SolveInfo:
+    status: int
+    cycles: int
+    vcycles: int
+    levels: int
+    r0: float
+    relres: float
+    history: list
+    solve_ms: float
+    launches: int = 0
+
+    @property
+    def converged(self) -> bool:
+        return self.status == SBM_OK
+
+
+def make_opts(tol=1e-10, max_cycles=500, nu1=2, nu2=2, omega=2.0 / 3.0, smoother="jacobi",
+              inner_cycles=1, use_graph=True) -> _capi.sbm_opts:
+    o = _capi.sbm_opts()
+    lib().sbm_default_opts(C.byref(o))
+    o.tol, o.max_cycles, o.nu1, o.nu2, o.omega = tol, max_cycles, nu1, nu2, omega
+    o.smoother = SBM_MCGS if smoother in ("gs", "mcgs", "rbgs") else SBM_JACOBI
+    o.inner_cycles, o.use_graph = inner_cycles, int(bool(use_graph))
+    return o
+
+
+class Grid:
+    """One node-centred grid (2D plane strain or 3D) and its multigrid hierarchy."""
+
+    def __init__(self, dim: int, n, h: float, precision: str = "fp64", device: int = 0, stream=None):
+        n = tuple(int(v) for v in n)
+        if dim == 2 and len(n) == 2:
+            n = n + (1,)
+        d = _capi.sbm_grid_desc()
+        d.dim = dim
+        d.n[:] = list(n)
+        d.h = h
+        d.precision = SBM_MIXED if precision == "mixed" else SBM_FP64
+        d.stream = stream
+        d.device = device
+        self._h = C.c_void_p()
+        _capi.check(lib().sbm_grid_create(C.byref(d), C.byref(self._h)), None)
+        self.dim, self.n, self.h, self.precision, self.device = dim, n, h, precision, device
+        nl = C.c_int()
+        self._check(lib().sbm_grid_levels(self._h, C.byref(nl)))
+        self.nlevels = nl.value
+        self.psi_min = None
+
+    # -- bookkeeping
+    def _check(self, st, allow=(SBM_OK,)):
+        return _capi.check(st, self._h, allow)
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().sbm_grid_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def finest(self) -> int:
+        return self.nlevels - 1
+
+    def level_shape(self, level: int):
+        n = (C.c_int * 3)()
+        h = C.c_double()
+        self._check(lib().sbm_grid_level_shape(self._h, level, n, C.byref(h)))
+        return tuple(n), h.value
+
+    def nnodes(self, level=None):
+        n, _ = self.level_shape(self.finest if level is None else level)
+        return n[0] * n[1] * n[2]
+
+    def ncells(self, level=None):
+        n, _ = self.level_shape(self.finest if level is None else level)
+        return (n[0] - 1) * (n[1] - 1) * ((n[2] - 1) if self.dim == 3 else 1)
+
+    # -- set-up
+    def set_psi(self, psi: torch.Tensor, psi_min: float):
+        self._check(lib().sbm_set_psi(self._h, self.finest, _ptr(psi), psi_min))
+        self.psi_min = psi_min
+
+    def set_density(self, rho: torch.Tensor, psi_min: float, q: float = 3.0):
+        self._check(lib().sbm_set_density(self._h, self.finest, _ptr(rho), psi_min, q))
+        self.psi_min = psi_min
+
+    def set_moduli(self, kind: int, params):
+        arr = (C.c_double * 3)(*[float(v) for v in (list(params) + [0.0, 0.0, 0.0])[:3]])
+        self._check(lib().sbm_set_moduli(self._h, kind, arr))
+
+    def set_bc(self, face, comp: int, kind: int = SBM_DIRICHLET, value: float = 0.0):
+        face = FACES[face] if isinstance(face, str) else int(face)
+        self._check(lib().sbm_set_bc(self._h, face, comp, kind, value))
+
+    def set_source(self, f: torch.Tensor):
+        self._check(lib().sbm_set_source(self._h, self.finest, _ptr(f)))
+
+    # -- solves
+    def solve(self, u: torch.Tensor, raise_on_fail: bool = True, **opts) -> SolveInfo:
+        o = make_opts(**opts)
+        info, hist = self._info(o.max_cycles)
+        st = lib().sbm_solve(self._h, _ptr(u), C.byref(o), C.byref(info))
+        self._check(st, allow=(SBM_OK,) if raise_on_fail else (SBM_OK, SBM_ERR_NOCONV, SBM_ERR_DIVERGED))
+        return self._to_info(info, hist)
+
+    def adjoint(self, u: torch.Tensor, dJdu: torch.Tensor, want_rho: bool = False, **opts):
+        o = make_opts(**opts)
+        info, hist = self._info(o.max_cycles)
+        lam = torch.empty_like(dJdu)
+        g = torch.empty(self.ncells(), dtype=torch.float64, device=u.device)
+        grho = torch.empty_like(g) if want_rho else None
+        st = lib().sbm_adjoint(self._h, _ptr(u), _ptr(dJdu), _ptr(lam), _ptr(g),
+                               _ptr(grho) if grho is not None else None, C.byref(o), C.byref(info))
+        self._check(st)
+        return lam, g, grho, self._to_info(info, hist)
+
+    def _info(self, cap):
+        info = _capi.sbm_info()
+        hist = (C.c_double * (cap + 1))()
+        info.history = C.cast(hist, C.POINTER(C.c_double))
+        info.history_capacity = cap + 1
+        return info, hist
+
+    @staticmethod
+    def _to_info(info, hist) -> SolveInfo:
+        n = min(info.cycles + 1, info.history_capacity)
+        return SolveInfo(info.status, info.cycles, info.vcycles, info.levels, info.r0, info.relres,
+                         [hist[i] for i in range(n)], info.solve_ms, info.launches)
+
+    # -- single steps of the hot path
+    def apply(self, level: int, u: torch.Tensor, fp32: bool = False) -> torch.Tensor:
+        out = torch.empty_like(u)
+        self._check(lib().sbm_apply(self._h, level, int(fp32), _ptr(u), _ptr(out)))
+        return out
+
+    def residual(self, level: int, f: torch.Tensor, u: torch.Tensor, fp32: bool = False):
+        out = torch.empty_like(u)
+        nrm = C.c_double()
+        self._check(lib().sbm_residual(self._h, level, int(fp32), _ptr(f), _ptr(u), _ptr(out), C.byref(nrm)))
+        return out, nrm.value
+
+    def smooth(self, level: int, f: torch.Tensor, u: torch.Tensor, smoother="jacobi", omega=2.0 / 3.0,
+               descending=False, fp32=False) -> torch.Tensor:
+        out = u.clone()
+        sm = SBM_MCGS if smoother in ("gs", "mcgs") else SBM_JACOBI
+        self._check(lib().sbm_smooth(self._h, level, int(fp32), sm, omega, int(descending), _ptr(f), _ptr(out)))
+        return out
+
+    def restrict(self, level: int, r: torch.Tensor, fp32=False) -> torch.Tensor:
+        nc = self.nnodes(level - 1) * self.dim
+        out = torch.empty(nc, dtype=torch.float64, device=r.device)
+        self._check(lib().sbm_restrict(self._h, level, int(fp32), _ptr(r), _ptr(out)))
+        return out
+
+    def prolong_add(self, level: int, e_c: torch.Tensor, u: torch.Tensor, fp32=False) -> torch.Tensor:
+        out = u.clone()
+        self._check(lib().sbm_prolong_add(self._h, level, int(fp32), _ptr(e_c), _ptr(out)))
+        return out
+
+    def get_psi(self, level: int) -> torch.Tensor:
+        out = torch.empty(self.ncells(level), dtype=torch.float64, device=torch.device("cuda", self.device))
+        self._check(lib().sbm_get_psi(self._h, level, _ptr(out)))
+        return out
+
+    def bottom_correct(self, f: torch.Tensor, u: torch.Tensor, fp32=False) -> torch.Tensor:
+        out = u.clone()
+        self._check(lib().sbm_bottom_correct(self._h, int(fp32), _ptr(f), _ptr(out)))
+        return out
+
+    def dJdpsi(self, u: torch.Tensor, lam: torch.Tensor) -> torch.Tensor:
+        out = torch.empty(self.ncells(), dtype=torch.float64, device=u.device)
+        self._check(lib().sbm_dJdpsi(self._h, _ptr(u), _ptr(lam), _ptr(out)))
+        return out
+
+
+class SBMSolve(torch.autograd.Function):
+    """u = solve(K(psi(rho)) u = f) with the gradient of a loss of u w.r.t. rho.
+
+    forward(rho, grid, u0, opts): sets the SIMP stiffness psi = psi_min + (1 - psi_min)
+    rho^q on the grid (grid.psi_min, grid.q), solves from u0 and returns u.
+    backward: the incoming dL/du is the right-hand side of the adjoint multigrid
+    solve; the fused kernel returns dL/drho = -p'(rho) lambda_c^T S_c u_c.
+    """
+
+    @staticmethod
+    def forward(ctx, rho, grid, u0, opts):
+        grid.set_density(rho.detach().contiguous(), grid.psi_min, getattr(grid, "q", 3.0))
+        u = u0.detach().clone().contiguous()
+        grid.solve(u, **(opts or {}))
+        ctx.grid, ctx.opts = grid, opts
+        ctx.save_for_backward(u)
+        return u
+
+    @staticmethod
+    def backward(ctx, grad_u):
+        (u,) = ctx.saved_tensors
+        _, _, grho, _ = ctx.grid.adjoint(u, grad_u.contiguous(), want_rho=True, **(ctx.opts or {}))
+        return grho, None, None, None

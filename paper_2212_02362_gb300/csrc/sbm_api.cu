@@ -1,0 +1,1003 @@
+// sbm_api.cu — the C ABI (include/sbm.h): grid and level hierarchy, set-up of
+// psi / moduli / boundary conditions, the multigrid driver (FP64 V-cycles, or
+// FP32 V-cycles inside an FP64 defect correction), CUDA-graph replay of one
+// outer iteration, the adjoint solve and the single-step entry points.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/sbm.h"
+#include "sbm_common.cuh"
+
+using namespace sbm;
+
+namespace {
+
+thread_local std::string g_lib_error;
+
+struct Level {
+    Geom g{};
+    double h = 0;
+    double *psi64 = nullptr;
+    float *psi32 = nullptr;
+    double *du[2] = {nullptr, nullptr}, *df = nullptr, *dr = nullptr;
+    float *su[2] = {nullptr, nullptr}, *sf = nullptr, *sr = nullptr;
+    Coef<double> c64{};
+    Coef<float> c32{};
+    double *Ke64 = nullptr;   // unit-psi cell matrix (GS smoother)
+    float *Ke32 = nullptr;
+};
+
+struct GraphSlot {
+    bool valid = false;
+    cudaGraphExec_t exec = nullptr;
+    int mixed = 0, smoother = 0, nu1 = 0, nu2 = 0, inner = 0;
+    double omega = 0;
+    const double *rhs = nullptr;
+    unsigned version = 0;
+    long long body_launches = 0;
+};
+
+}  // namespace
+
+struct sbm_grid_s {
+    sbm_grid_desc desc{};
+    cudaStream_t st = nullptr;
+    bool own_stream = false;
+    int dev = 0;
+    int nl = 0;
+    Level L[kMaxLevels];
+    double mod[3] = {0, 0, 0};
+    bool has_moduli = false, has_psi = false;
+    int bct[6][3] = {};
+    double bcv[6][3] = {};
+    double *fsrc = nullptr, *fadj = nullptr;     // finest-level right-hand sides (level layout)
+    double *psi_raw = nullptr, *rho = nullptr;    // packed finest cells
+    int density = 0;
+    double psi_min = 0, q = 3;
+    double *part = nullptr;
+    long long npart = 0;
+    double *scal = nullptr;     // device scalars, see k_norm_final
+    double *hscal = nullptr;    // pinned host copy
+    int *dbad = nullptr;
+    int nb = 0;                 // bottom dofs
+    double *A64 = nullptr, *gjtmp = nullptr;
+    float *A32 = nullptr;
+    int *gather = nullptr;
+    bool bottom_ready = false;
+    unsigned version = 1;
+    GraphSlot slots[2];
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    std::string err;
+};
+
+namespace {
+
+sbm_status fail(sbm_grid G, sbm_status st, const std::string &msg)
+{
+    if (G) G->err = msg;
+    else g_lib_error = msg;
+    return st;
+}
+
+#define CK(...)                                                                               \
+    do {                                                                                      \
+        cudaError_t e_ = (__VA_ARGS__);                                                       \
+        if (e_ != cudaSuccess)                                                                \
+            return fail(G, e_ == cudaErrorMemoryAllocation ? SBM_ERR_OOM : SBM_ERR_CUDA,      \
+                        std::string(#__VA_ARGS__) + ": " + cudaGetErrorString(e_));           \
+    } while (0)
+
+#define CKE(...)                                  \
+    do {                                          \
+        cudaError_t e_ = (__VA_ARGS__);           \
+        if (e_ != cudaSuccess) return e_;         \
+    } while (0)
+
+bool is_dev_ptr(const void *p, int dev)
+{
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) && a.device == dev;
+}
+
+long long nnodes(const Geom &g) { return (long long)g.nx * g.ny * g.nz; }
+long long ncells_h(const Geom &g) { return (long long)(g.nx - 1) * (g.ny - 1) * (g.dim == 3 ? g.nz - 1 : 1); }
+
+template <typename T> struct P;
+template <> struct P<double> {
+    static double *u(Level &L, int i) { return L.du[i]; }
+    static double *f(Level &L) { return L.df; }
+    static double *r(Level &L) { return L.dr; }
+    static const double *psi(Level &L) { return L.psi64; }
+    static const Coef<double> &c(Level &L) { return L.c64; }
+    static const double *Ke(Level &L) { return L.Ke64; }
+    static const double *A(sbm_grid G) { return G->A64; }
+};
+template <> struct P<float> {
+    static float *u(Level &L, int i) { return L.su[i]; }
+    static float *f(Level &L) { return L.sf; }
+    static float *r(Level &L) { return L.sr; }
+    static const float *psi(Level &L) { return L.psi32; }
+    static const Coef<float> &c(Level &L) { return L.c32; }
+    static const float *Ke(Level &L) { return L.Ke32; }
+    static const float *A(sbm_grid G) { return G->A32; }
+};
+
+struct Opts {
+    sbm_opts o;
+};
+
+template <typename T>
+cudaError_t sweep(sbm_grid G, int l, int mode, const T *u, const T *f, T *out, double *part, double omega)
+{
+    Level &L = G->L[l];
+    SweepArgs<T, T> a;
+    a.g = L.g;
+    a.u = u;
+    a.f = f;
+    a.psi = P<T>::psi(L);
+    a.out = out;
+    a.part = part;
+    a.c = P<T>::c(L);
+    for (int p = 0; p < 3; ++p) a.wk[p] = (L.c64.kdiag[p] != 0.0) ? T(omega / L.c64.kdiag[p]) : T(0);
+    a.kchunk = 0;
+    return launch_sweep<T, T>(mode, a, G->st);
+}
+
+template <typename T>
+cudaError_t smooth(sbm_grid G, int l, int &cur, const sbm_opts &o, int nsweeps, bool descending, const T *f)
+{
+    Level &L = G->L[l];
+    const int ncol = 1 << L.g.dim;
+    for (int s = 0; s < nsweeps; ++s) {
+        if (o.smoother == SBM_MCGS) {
+            for (int c = 0; c < ncol; ++c)
+                CKE(launch_gs<T>(L.g, P<T>::psi(L), P<T>::Ke(L), f, P<T>::u(L, cur), descending ? ncol - 1 - c : c, G->st));
+        } else {
+            CKE(sweep<T>(G, l, kJacobi, P<T>::u(L, cur), f, P<T>::u(L, 1 - cur), nullptr, o.omega));
+            cur ^= 1;
+        }
+    }
+    return cudaSuccess;
+}
+
+size_t level_bytes(const Level &L, size_t elem) { return (size_t)L.g.dim * L.g.cs * elem; }
+
+// V(nu1, nu2) on level l: u = P<T>::u(L, cur), right-hand side f.  Coarse levels
+// start from a zero correction; the coarsest is solved with the dense inverse.
+template <typename T>
+cudaError_t vcycle(sbm_grid G, int l, int &cur, const sbm_opts &o, const T *f)
+{
+    Level &L = G->L[l];
+    if (l == 0) {
+        if (G->nl == 1) {
+            CKE(sweep<T>(G, 0, kResidual, P<T>::u(L, cur), f, P<T>::r(L), nullptr, 0.0));
+            CKE(launch_bottom_apply<T>(G->nb, P<T>::A(G), G->gather, P<T>::r(L), P<T>::u(L, cur), 1, G->st));
+        } else {
+            CKE(launch_bottom_apply<T>(G->nb, P<T>::A(G), G->gather, f, P<T>::u(L, cur), 0, G->st));
+        }
+        return cudaSuccess;
+    }
+    Level &C = G->L[l - 1];
+    CKE(smooth<T>(G, l, cur, o, o.nu1, false, f));
+    CKE(sweep<T>(G, l, kResidual, P<T>::u(L, cur), f, P<T>::r(L), nullptr, 0.0));
+    CKE(launch_restrict<T>(L.g, C.g, P<T>::r(L), P<T>::f(C), G->st));
+    int cc = 0;
+    if (l - 1 > 0) CKE(cudaMemsetAsync(P<T>::u(C, 0), 0, level_bytes(C, sizeof(T)), G->st));
+    CKE(vcycle<T>(G, l - 1, cc, o, P<T>::f(C)));
+    CKE(launch_prolong_add<T>(L.g, C.g, P<T>::u(C, cc), P<T>::u(L, cur), G->st));
+    CKE(smooth<T>(G, l, cur, o, o.nu2, true, f));
+    return cudaSuccess;
+}
+
+// FP64 residual of the finest level with block partial sums -> scal[which..].
+// In mixed mode the residual is written rounded to FP32 as the inner right-hand side.
+cudaError_t residual64(sbm_grid G, const double *rhs, int mixed, int which)
+{
+    Level &L = G->L[G->nl - 1];
+    cudaError_t e;
+    if (mixed) {
+        SweepArgs<double, float> a;
+        a.g = L.g;
+        a.u = L.du[0];
+        a.f = rhs;
+        a.psi = L.psi64;
+        a.out = L.sf;
+        a.part = G->part;
+        a.c = L.c64;
+        a.wk[0] = a.wk[1] = a.wk[2] = 0.0;
+        a.kchunk = 0;
+        e = launch_sweep<double, float>(kResidual, a, G->st);
+    } else {
+        e = sweep<double>(G, G->nl - 1, kResidual, L.du[0], rhs, L.dr, G->part, 0.0);
+    }
+    if (e != cudaSuccess) return e;
+    return launch_norm_final(G->part, (int)sweep_blocks(L.g), G->scal, which, G->st);
+}
+
+// One outer iteration: V-cycle(s) and the FP64 residual + norm of the result.
+cudaError_t enqueue_body(sbm_grid G, const sbm_opts &o, const double *rhs)
+{
+    const int fine = G->nl - 1;
+    Level &L = G->L[fine];
+    if (G->desc.precision == SBM_MIXED) {
+        CKE(cudaMemsetAsync(L.su[0], 0, level_bytes(L, sizeof(float)), G->st));
+        int cur = 0;
+        for (int it = 0; it < o.inner_cycles; ++it) CKE(vcycle<float>(G, fine, cur, o, L.sf));
+        CKE(launch_add<float>((long long)L.g.dim * L.g.cs, L.su[cur], L.du[0], G->st));
+        return residual64(G, rhs, 1, 2);
+    }
+    int cur = 0;
+    CKE(vcycle<double>(G, fine, cur, o, rhs));
+    if (cur != 0) CKE(cudaMemcpyAsync(L.du[0], L.du[1], level_bytes(L, sizeof(double)), cudaMemcpyDeviceToDevice, G->st));
+    return residual64(G, rhs, 0, 2);
+}
+
+sbm_status setup_bottom(sbm_grid G)
+{
+    if (G->bottom_ready) return SBM_OK;
+    Level &B = G->L[0];
+    const long long n = G->nb;
+    CK(cudaMemsetAsync(G->A64, 0, sizeof(double) * n * n, G->st));
+    CK(launch_bottom_assemble(B.g, B.psi64, B.c64, G->A64, G->st));
+    CK(launch_bottom_dirichlet(B.g, G->A64, G->st));
+    CK(launch_gauss_jordan((int)n, G->A64, G->gjtmp, G->st));
+    CK(launch_round(n * n, G->A64, G->A32, G->st));
+    G->bottom_ready = true;
+    return SBM_OK;
+}
+
+void make_level_coefs(sbm_grid G)
+{
+    for (int l = 0; l < G->nl; ++l) {
+        Level &L = G->L[l];
+        L.c64 = make_coef<double>(L.g.dim, L.h, G->mod[0], G->mod[1], G->mod[2]);
+        L.c32 = make_coef<float>(L.g.dim, L.h, G->mod[0], G->mod[1], G->mod[2]);
+    }
+}
+
+sbm_status upload_Ke(sbm_grid G)
+{
+    for (int l = 0; l < G->nl; ++l) {
+        Level &L = G->L[l];
+        const int d = L.g.dim, nc = 1 << d, nd = nc * d;
+        std::vector<double> Ke(nd * nd);
+        std::vector<float> Kf(nd * nd);
+        for (int b = 0; b < nc; ++b)
+            for (int q = 0; q < d; ++q) {
+                if (d == 3) {
+                    double U[3][8] = {};
+                    U[q][b] = 1.0;
+                    cell_forces3<double>(U, 1.0, L.c64);
+                    for (int a = 0; a < 8; ++a)
+                        for (int p = 0; p < 3; ++p) Ke[(a * 3 + p) * nd + b * 3 + q] = U[p][a];
+                } else {
+                    double U[2][4] = {};
+                    U[q][b] = 1.0;
+                    cell_forces2<double>(U, 1.0, L.c64);
+                    for (int a = 0; a < 4; ++a)
+                        for (int p = 0; p < 2; ++p) Ke[(a * 2 + p) * nd + b * 2 + q] = U[p][a];
+                }
+            }
+        for (int e = 0; e < nd * nd; ++e) Kf[e] = float(Ke[e]);
+        CK(cudaMemcpy(L.Ke64, Ke.data(), sizeof(double) * nd * nd, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(L.Ke32, Kf.data(), sizeof(float) * nd * nd, cudaMemcpyHostToDevice));
+    }
+    return SBM_OK;
+}
+
+sbm_status check_ready(sbm_grid G)
+{
+    if (!G) return fail(nullptr, SBM_ERR_ARG, "null grid");
+    if (!G->has_moduli) return fail(G, SBM_ERR_STATE, "moduli not set (sbm_set_moduli)");
+    if (!G->has_psi) return fail(G, SBM_ERR_STATE, "psi not set (sbm_set_psi / sbm_set_density)");
+    return SBM_OK;
+}
+
+sbm_status validate_opts(sbm_grid G, const sbm_opts &o)
+{
+    if (!(o.tol >= 0.0) || o.max_cycles < 1 || o.nu1 < 0 || o.nu2 < 0 || o.nu1 + o.nu2 < 1 ||
+        (o.smoother != SBM_JACOBI && o.smoother != SBM_MCGS) || !(o.omega > 0.0 && o.omega < 2.0) ||
+        o.inner_cycles < 1)
+        return fail(G, SBM_ERR_ARG, "invalid sbm_opts");
+    return SBM_OK;
+}
+
+void set_dirichlet_bits(sbm_grid G)
+{
+    for (int l = 0; l < G->nl; ++l)
+        for (int p = 0; p < 3; ++p) {
+            unsigned m = 0;
+            for (int f = 0; f < 6; ++f)
+                if (G->bct[f][p] != SBM_FREE) m |= 1u << f;
+            G->L[l].g.dm[p] = (p < G->desc.dim) ? m : 0u;
+        }
+}
+
+// Run outer iterations until relres <= tol.  u lives in the finest du[0].
+sbm_status run_solve(sbm_grid G, const sbm_opts &o, const double *rhs, sbm_info *info, int slot)
+{
+    sbm_status st = setup_bottom(G);
+    if (st != SBM_OK) return st;
+    const int mixed = G->desc.precision == SBM_MIXED;
+    const long long launches0 = g_launches;
+    long long replayed = 0;
+    CK(cudaEventRecord(G->ev0, G->st));
+    CK(residual64(G, rhs, mixed, 0));
+    CK(cudaMemcpyAsync(G->hscal, G->scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, G->st));
+    CK(cudaStreamSynchronize(G->st));
+    const double r0 = G->hscal[1];
+    if (info) {
+        info->r0 = r0;
+        info->levels = G->nl;
+        if (info->history && info->history_capacity > 0) info->history[0] = 1.0;
+    }
+    GraphSlot &gs = G->slots[slot];
+    if (o.use_graph) {
+        const bool match = gs.valid && gs.mixed == mixed && gs.smoother == o.smoother && gs.nu1 == o.nu1 &&
+                           gs.nu2 == o.nu2 && gs.inner == o.inner_cycles && gs.omega == o.omega && gs.rhs == rhs &&
+                           gs.version == G->version;
+        if (!match) {
+            if (gs.valid) cudaGraphExecDestroy(gs.exec);
+            gs.valid = false;
+            cudaGraph_t graph;
+            CK(cudaStreamBeginCapture(G->st, cudaStreamCaptureModeThreadLocal));
+            const long long c0 = g_launches;
+            cudaError_t e = enqueue_body(G, o, rhs);
+            const long long nbody = g_launches - c0;
+            g_launches = c0;
+            cudaError_t e2 = cudaStreamEndCapture(G->st, &graph);
+            if (e != cudaSuccess || e2 != cudaSuccess) {
+                if (e2 == cudaSuccess) cudaGraphDestroy(graph);
+                return fail(G, SBM_ERR_CUDA, std::string("graph capture: ") +
+                                                 cudaGetErrorString(e != cudaSuccess ? e : e2));
+            }
+            e = cudaGraphInstantiate(&gs.exec, graph, 0ULL);
+            cudaGraphDestroy(graph);
+            if (e != cudaSuccess) return fail(G, SBM_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+            gs.valid = true;
+            gs.mixed = mixed;
+            gs.smoother = o.smoother;
+            gs.nu1 = o.nu1;
+            gs.nu2 = o.nu2;
+            gs.inner = o.inner_cycles;
+            gs.omega = o.omega;
+            gs.rhs = rhs;
+            gs.version = G->version;
+            gs.body_launches = nbody;
+        }
+    }
+    int cyc = 0;
+    double rel = 1.0;
+    sbm_status status = SBM_ERR_NOCONV;
+    if (r0 == 0.0) {
+        status = SBM_OK;
+        rel = 0.0;
+    }
+    while (status == SBM_ERR_NOCONV && cyc < o.max_cycles) {
+        if (o.use_graph) {
+            CK(cudaGraphLaunch(gs.exec, G->st));
+            replayed += gs.body_launches;
+        } else {
+            CK(enqueue_body(G, o, rhs));
+        }
+        CK(cudaMemcpyAsync(G->hscal + 4, G->scal + 4, sizeof(double), cudaMemcpyDeviceToHost, G->st));
+        CK(cudaStreamSynchronize(G->st));
+        ++cyc;
+        rel = G->hscal[4];
+        if (info && info->history && cyc < info->history_capacity) info->history[cyc] = rel;
+        if (!std::isfinite(rel) || rel > 1e10) status = SBM_ERR_DIVERGED;
+        else if (rel <= o.tol) status = SBM_OK;
+    }
+    CK(cudaEventRecord(G->ev1, G->st));
+    CK(cudaEventSynchronize(G->ev1));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, G->ev0, G->ev1);
+    if (info) {
+        info->status = status;
+        info->cycles = cyc;
+        info->vcycles = cyc * (mixed ? o.inner_cycles : 1);
+        info->relres = rel;
+        info->solve_ms = ms;
+        info->launches = g_launches - launches0 + replayed;
+    }
+    if (status == SBM_ERR_NOCONV) G->err = "max_cycles reached before the tolerance";
+    if (status == SBM_ERR_DIVERGED) G->err = "relative residual not finite or above 1e10";
+    return status;
+}
+
+sbm_status check_level(sbm_grid G, int level)
+{
+    if (!G) return fail(nullptr, SBM_ERR_ARG, "null grid");
+    if (level < 0 || level >= G->nl) return fail(G, SBM_ERR_ARG, "level out of range");
+    return SBM_OK;
+}
+
+}  // namespace
+
+// ========================================================================= ABI
+
+extern "C" {
+
+void sbm_default_opts(sbm_opts *o)
+{
+    if (!o) return;
+    o->tol = 1e-10;
+    o->max_cycles = 500;
+    o->nu1 = 2;
+    o->nu2 = 2;
+    o->omega = 2.0 / 3.0;
+    o->smoother = SBM_JACOBI;
+    o->inner_cycles = 1;
+    o->use_graph = 1;
+}
+
+const char *sbm_status_string(int s)
+{
+    switch (s) {
+    case SBM_OK: return "SBM_OK";
+    case SBM_ERR_ARG: return "SBM_ERR_ARG";
+    case SBM_ERR_STATE: return "SBM_ERR_STATE";
+    case SBM_ERR_CUDA: return "SBM_ERR_CUDA";
+    case SBM_ERR_OOM: return "SBM_ERR_OOM";
+    case SBM_ERR_NOCONV: return "SBM_ERR_NOCONV";
+    case SBM_ERR_DIVERGED: return "SBM_ERR_DIVERGED";
+    default: return "unknown status";
+    }
+}
+
+const char *sbm_last_error(sbm_grid G) { return G ? G->err.c_str() : g_lib_error.c_str(); }
+
+sbm_status sbm_grid_destroy(sbm_grid G)
+{
+    if (!G) return SBM_OK;
+    cudaSetDevice(G->dev);
+    if (G->st) cudaStreamSynchronize(G->st);
+    for (auto &s : G->slots)
+        if (s.valid) cudaGraphExecDestroy(s.exec);
+    for (int l = 0; l < G->nl; ++l) {
+        Level &L = G->L[l];
+        void *ptrs[] = {L.psi64, L.psi32, L.du[0], L.du[1], L.df, L.dr, L.su[0], L.su[1], L.sf, L.sr, L.Ke64, L.Ke32};
+        for (void *p : ptrs)
+            if (p) cudaFree(p);
+    }
+    void *ptrs[] = {G->fsrc, G->fadj, G->psi_raw, G->rho, G->part, G->scal, G->dbad, G->A64, G->A32, G->gjtmp, G->gather};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    if (G->hscal) cudaFreeHost(G->hscal);
+    if (G->ev0) cudaEventDestroy(G->ev0);
+    if (G->ev1) cudaEventDestroy(G->ev1);
+    if (G->own_stream && G->st) cudaStreamDestroy(G->st);
+    delete G;
+    return SBM_OK;
+}
+
+sbm_status sbm_grid_create(const sbm_grid_desc *d, sbm_grid *out)
+{
+    sbm_grid G = nullptr;
+    if (!d || !out) return fail(nullptr, SBM_ERR_ARG, "null descriptor or output");
+    *out = nullptr;
+    if (d->dim != 2 && d->dim != 3) return fail(nullptr, SBM_ERR_ARG, "dim must be 2 or 3");
+    if (d->n[0] < 2 || d->n[1] < 2 || (d->dim == 3 && d->n[2] < 2) || (d->dim == 2 && d->n[2] != 1))
+        return fail(nullptr, SBM_ERR_ARG, "node counts must be >= 2 (n[2] == 1 in 2D)");
+    if (!(d->h > 0.0) || !std::isfinite(d->h)) return fail(nullptr, SBM_ERR_ARG, "h must be positive");
+    if (d->precision != SBM_FP64 && d->precision != SBM_MIXED) return fail(nullptr, SBM_ERR_ARG, "bad precision");
+    const double nodes = (double)d->n[0] * d->n[1] * d->n[2];
+    if (nodes > 2.0e9) return fail(nullptr, SBM_ERR_ARG, "grid too large");
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || d->device < 0 || d->device >= ndev) {
+        cudaGetLastError();
+        return fail(nullptr, SBM_ERR_CUDA, "no CUDA device with the requested ordinal");
+    }
+    G = new sbm_grid_s();
+    G->desc = *d;
+    G->dev = d->device;
+    CK(cudaSetDevice(G->dev));
+    if (d->stream) {
+        G->st = (cudaStream_t)d->stream;
+    } else {
+        CK(cudaStreamCreate(&G->st));   // blocking: ordered after legacy-stream work
+        G->own_stream = true;
+    }
+    // hierarchy: halve while every (n-1) is even and stays >= 4 after halving
+    int n[3] = {d->n[0], d->n[1], d->n[2]};
+    double h = d->h;
+    std::vector<std::pair<std::vector<int>, double>> shapes;
+    shapes.push_back({{n[0], n[1], n[2]}, h});
+    while ((int)shapes.size() < kMaxLevels) {
+        bool ok = true;
+        for (int a = 0; a < d->dim; ++a) {
+            const int m = n[a] - 1;
+            if (m % 2 != 0 || m / 2 < 4) ok = false;
+        }
+        if (!ok) break;
+        for (int a = 0; a < d->dim; ++a) n[a] = (n[a] - 1) / 2 + 1;
+        h *= 2.0;
+        shapes.push_back({{n[0], n[1], n[2]}, h});
+    }
+    G->nl = (int)shapes.size();
+    for (int l = 0; l < G->nl; ++l) {
+        const auto &sh = shapes[G->nl - 1 - l];   // level 0 = coarsest
+        Level &L = G->L[l];
+        L.h = sh.second;
+        Geom &g = L.g;
+        g.dim = d->dim;
+        g.nx = sh.first[0];
+        g.ny = sh.first[1];
+        g.nz = sh.first[2];
+        g.sx = (g.nx + 7) / 8 * 8;
+        g.sy = (long long)g.sx * g.ny;
+        g.cs = (g.sy * g.nz + 63) / 64 * 64;
+        const size_t nd = (size_t)g.dim * g.cs;
+        CK(cudaMalloc(&L.psi64, sizeof(double) * g.cs));
+        CK(cudaMalloc(&L.psi32, sizeof(float) * g.cs));
+        CK(cudaMemset(L.psi64, 0, sizeof(double) * g.cs));
+        CK(cudaMemset(L.psi32, 0, sizeof(float) * g.cs));
+        double **dptrs[] = {&L.du[0], &L.du[1], &L.df, &L.dr};
+        for (double **p : dptrs) {
+            CK(cudaMalloc(p, sizeof(double) * nd));
+            CK(cudaMemset(*p, 0, sizeof(double) * nd));
+        }
+        float **sptrs[] = {&L.su[0], &L.su[1], &L.sf, &L.sr};
+        for (float **p : sptrs) {
+            CK(cudaMalloc(p, sizeof(float) * nd));
+            CK(cudaMemset(*p, 0, sizeof(float) * nd));
+        }
+        const int nk = (1 << g.dim) * g.dim;
+        CK(cudaMalloc(&L.Ke64, sizeof(double) * nk * nk));
+        CK(cudaMalloc(&L.Ke32, sizeof(float) * nk * nk));
+    }
+    Level &F = G->L[G->nl - 1];
+    const size_t nfd = (size_t)F.g.dim * F.g.cs;
+    CK(cudaMalloc(&G->fsrc, sizeof(double) * nfd));
+    CK(cudaMemset(G->fsrc, 0, sizeof(double) * nfd));
+    CK(cudaMalloc(&G->fadj, sizeof(double) * nfd));
+    CK(cudaMemset(G->fadj, 0, sizeof(double) * nfd));
+    const long long nc = ncells_h(F.g);
+    CK(cudaMalloc(&G->psi_raw, sizeof(double) * nc));
+    CK(cudaMalloc(&G->rho, sizeof(double) * nc));
+    G->npart = sweep_blocks(F.g);
+    CK(cudaMalloc(&G->part, sizeof(double) * G->npart));
+    CK(cudaMalloc(&G->scal, sizeof(double) * 16));
+    CK(cudaMemset(G->scal, 0, sizeof(double) * 16));
+    CK(cudaMallocHost(&G->hscal, sizeof(double) * 16));
+    CK(cudaMalloc(&G->dbad, sizeof(int)));
+    // bottom
+    Level &B = G->L[0];
+    G->nb = (int)(nnodes(B.g) * B.g.dim);
+    if ((long long)G->nb * G->nb > (1LL << 28)) {
+        sbm_grid_destroy(G);
+        return fail(nullptr, SBM_ERR_ARG, "coarsest level too large for the dense bottom solve");
+    }
+    CK(cudaMalloc(&G->A64, sizeof(double) * G->nb * G->nb));
+    CK(cudaMalloc(&G->A32, sizeof(float) * G->nb * G->nb));
+    CK(cudaMalloc(&G->gjtmp, sizeof(double) * 2 * G->nb));
+    CK(cudaMalloc(&G->gather, sizeof(int) * G->nb));
+    {
+        std::vector<int> gi(G->nb);
+        const long long N = nnodes(B.g);
+        for (int p = 0; p < B.g.dim; ++p)
+            for (int k = 0; k < B.g.nz; ++k)
+                for (int j = 0; j < B.g.ny; ++j)
+                    for (int i = 0; i < B.g.nx; ++i)
+                        gi[p * N + i + (long long)B.g.nx * (j + (long long)B.g.ny * k)] = (int)(p * B.g.cs + gidx(B.g, i, j, k));
+        CK(cudaMemcpy(G->gather, gi.data(), sizeof(int) * G->nb, cudaMemcpyHostToDevice));
+    }
+    CK(cudaEventCreate(&G->ev0));
+    CK(cudaEventCreate(&G->ev1));
+    for (int f = 0; f < 6; ++f)
+        for (int p = 0; p < 3; ++p) G->bct[f][p] = SBM_FREE;
+    set_dirichlet_bits(G);
+    *out = G;
+    return SBM_OK;
+}
+
+sbm_status sbm_grid_levels(sbm_grid G, int *nl)
+{
+    if (!G || !nl) return fail(G, SBM_ERR_ARG, "null argument");
+    *nl = G->nl;
+    return SBM_OK;
+}
+
+sbm_status sbm_grid_level_shape(sbm_grid G, int level, int n[3], double *h)
+{
+    sbm_status s = check_level(G, level);
+    if (s != SBM_OK) return s;
+    if (n) {
+        n[0] = G->L[level].g.nx;
+        n[1] = G->L[level].g.ny;
+        n[2] = G->L[level].g.nz;
+    }
+    if (h) *h = G->L[level].h;
+    return SBM_OK;
+}
+
+static sbm_status finish_psi(sbm_grid G)
+{
+    for (int l = G->nl - 1; l > 0; --l)
+        CK(launch_coarsen_psi(G->L[l].g, G->L[l - 1].g, G->L[l].psi64, G->L[l - 1].psi64, G->st));
+    for (int l = 0; l < G->nl; ++l) CK(launch_round_cells(G->L[l].g, G->L[l].psi64, G->L[l].psi32, G->st));
+    int bad = 0;
+    CK(cudaMemcpyAsync(&bad, G->dbad, sizeof(int), cudaMemcpyDeviceToHost, G->st));
+    CK(cudaStreamSynchronize(G->st));
+    if (bad) {
+        G->has_psi = false;
+        return fail(G, SBM_ERR_ARG, "psi/rho contains non-finite or negative values");
+    }
+    G->has_psi = true;
+    G->bottom_ready = false;
+    return SBM_OK;
+}
+
+sbm_status sbm_set_psi(sbm_grid G, int level, const double *psi, double psi_min)
+{
+    if (!G) return fail(nullptr, SBM_ERR_ARG, "null grid");
+    if (level != G->nl - 1) return fail(G, SBM_ERR_ARG, "psi must be given on the finest level");
+    if (!is_dev_ptr(psi, G->dev)) return fail(G, SBM_ERR_ARG, "psi is not a device pointer of the grid's device");
+    if (!(psi_min > 0.0) || !std::isfinite(psi_min)) return fail(G, SBM_ERR_ARG, "psi_min must be positive");
+    CK(cudaSetDevice(G->dev));
+    Level &F = G->L[G->nl - 1];
+    CK(cudaMemsetAsync(G->dbad, 0, sizeof(int), G->st));
+    CK(cudaMemcpyAsync(G->psi_raw, psi, sizeof(double) * ncells_h(F.g), cudaMemcpyDeviceToDevice, G->st));
+    CK(launch_set_psi(F.g, psi, psi_min, F.psi64, G->dbad, G->st));
+    G->density = 0;
+    G->psi_min = psi_min;
+    return finish_psi(G);
+}
+
+sbm_status sbm_set_density(sbm_grid G, int level, const double *rho, double psi_min, double q)
+{
+    if (!G) return fail(nullptr, SBM_ERR_ARG, "null grid");
+    if (level != G->nl - 1) return fail(G, SBM_ERR_ARG, "rho must be given on the finest level");
+    if (!is_dev_ptr(rho, G->dev)) return fail(G, SBM_ERR_ARG, "rho is not a device pointer of the grid's device");
+    if (!(psi_min > 0.0 && psi_min < 1.0) || !(q >= 1.0)) return fail(G, SBM_ERR_ARG, "need 0 < psi_min < 1, q >= 1");
+    CK(cudaSetDevice(G->dev));
+    Level &F = G->L[G->nl - 1];
+    CK(cudaMemsetAsync(G->dbad, 0, sizeof(int), G->st));
+    CK(cudaMemcpyAsync(G->rho, rho, sizeof(double) * ncells_h(F.g), cudaMemcpyDeviceToDevice, G->st));
+    CK(launch_set_density(F.g, rho, psi_min, q, F.psi64, G->dbad, G->st));
+    G->density = 1;
+    G->psi_min = psi_min;
+    G->q = q;
+    return finish_psi(G);
+}
+
+sbm_status sbm_set_moduli(sbm_grid G, int kind, const double p[3])
+{
+    if (!G || !p) return fail(G, SBM_ERR_ARG, "null argument");
+    double c11, c12, c44;
+    if (kind == SBM_CUBIC) {
+        c11 = p[0];
+        c12 = p[1];
+        c44 = p[2];
+    } else if (kind == SBM_ISO_LAME) {
+        c11 = p[0] + 2.0 * p[1];
+        c12 = p[0];
+        c44 = p[1];
+    } else if (kind == SBM_ISO_ENU) {
+        const double E = p[0], nu = p[1];
+        if (!(nu > -1.0 && nu < 0.5)) return fail(G, SBM_ERR_ARG, "Poisson ratio must be in (-1, 0.5)");
+        const double lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu)), mu = E / (2.0 * (1.0 + nu));
+        c11 = lam + 2.0 * mu;
+        c12 = lam;
+        c44 = mu;
+    } else {
+        return fail(G, SBM_ERR_ARG, "unknown moduli kind");
+    }
+    if (!std::isfinite(c11) || !std::isfinite(c12) || !std::isfinite(c44) || !(c44 > 0.0) || !(c11 > std::fabs(c12)))
+        return fail(G, SBM_ERR_ARG, "moduli are not positive definite");
+    if (G->desc.dim == 3 && !(c11 + 2.0 * c12 > 0.0)) return fail(G, SBM_ERR_ARG, "moduli are not positive definite");
+    CK(cudaSetDevice(G->dev));
+    G->mod[0] = c11;
+    G->mod[1] = c12;
+    G->mod[2] = c44;
+    make_level_coefs(G);
+    sbm_status s = upload_Ke(G);
+    if (s != SBM_OK) return s;
+    G->has_moduli = true;
+    G->bottom_ready = false;
+    ++G->version;
+    return SBM_OK;
+}
+
+sbm_status sbm_set_bc(sbm_grid G, int face, int comp, int type, double value)
+{
+    if (!G) return fail(nullptr, SBM_ERR_ARG, "null grid");
+    if (face < 0 || face >= 2 * G->desc.dim) return fail(G, SBM_ERR_ARG, "face out of range");
+    if (comp < 0 || comp >= G->desc.dim) return fail(G, SBM_ERR_ARG, "component out of range");
+    if (type != SBM_FREE && type != SBM_DIRICHLET && type != SBM_DIRICHLET_FROM_U)
+        return fail(G, SBM_ERR_ARG, "unknown face condition");
+    if (!std::isfinite(value)) return fail(G, SBM_ERR_ARG, "non-finite boundary value");
+    G->bct[face][comp] = type;
+    G->bcv[face][comp] = value;
+    set_dirichlet_bits(G);
+    G->bottom_ready = false;
+    ++G->version;
+    return SBM_OK;
+}
+
+sbm_status sbm_set_source(sbm_grid G, int level, const double *f)
+{
+    if (!G) return fail(nullptr, SBM_ERR_ARG, "null grid");
+    if (level != G->nl - 1) return fail(G, SBM_ERR_ARG, "the source must be given on the finest level");
+    if (!is_dev_ptr(f, G->dev)) return fail(G, SBM_ERR_ARG, "f is not a device pointer of the grid's device");
+    CK(cudaSetDevice(G->dev));
+    Level &F = G->L[G->nl - 1];
+    CK(launch_pack<double, double>(F.g, F.g.dim, f, G->fsrc, G->st));
+    CK(cudaStreamSynchronize(G->st));
+    return SBM_OK;
+}
+
+sbm_status sbm_solve(sbm_grid G, double *u, const sbm_opts *opts, sbm_info *info)
+{
+    sbm_status s = check_ready(G);
+    if (s != SBM_OK) return s;
+    if (!is_dev_ptr(u, G->dev)) return fail(G, SBM_ERR_ARG, "u is not a device pointer of the grid's device");
+    sbm_opts o;
+    sbm_default_opts(&o);
+    if (opts) o = *opts;
+    if ((s = validate_opts(G, o)) != SBM_OK) return s;
+    CK(cudaSetDevice(G->dev));
+    Level &F = G->L[G->nl - 1];
+    CK(launch_pack<double, double>(F.g, F.g.dim, u, F.du[0], G->st));
+    for (int f = 0; f < 2 * F.g.dim; ++f)
+        for (int p = 0; p < F.g.dim; ++p)
+            if (G->bct[f][p] == SBM_DIRICHLET) CK(launch_set_face(F.g, f, p, G->bcv[f][p], F.du[0], G->st));
+    s = run_solve(G, o, G->fsrc, info, 0);
+    if (s != SBM_OK && s != SBM_ERR_NOCONV && s != SBM_ERR_DIVERGED) return s;
+    CK(launch_unpack<double, double>(F.g, F.g.dim, F.du[0], u, G->st));
+    CK(cudaStreamSynchronize(G->st));
+    return s;
+}
+
+sbm_status sbm_adjoint(sbm_grid G, const double *u, const double *dJdu, double *lambda, double *dJdpsi,
+                       double *dJdrho, const sbm_opts *opts, sbm_info *info)
+{
+    sbm_status s = check_ready(G);
+    if (s != SBM_OK) return s;
+    if (!is_dev_ptr(u, G->dev) || !is_dev_ptr(dJdu, G->dev) || !is_dev_ptr(lambda, G->dev) ||
+        !is_dev_ptr(dJdpsi, G->dev) || (dJdrho && !is_dev_ptr(dJdrho, G->dev)))
+        return fail(G, SBM_ERR_ARG, "u, dJdu, lambda, dJdpsi (and dJdrho) must be device pointers of the grid's device");
+    sbm_opts o;
+    sbm_default_opts(&o);
+    if (opts) o = *opts;
+    if ((s = validate_opts(G, o)) != SBM_OK) return s;
+    CK(cudaSetDevice(G->dev));
+    Level &F = G->L[G->nl - 1];
+    CK(launch_pack<double, double>(F.g, F.g.dim, dJdu, G->fadj, G->st));
+    CK(cudaMemsetAsync(F.du[0], 0, level_bytes(F, sizeof(double)), G->st));   // lambda_0 = 0, homogeneous Dirichlet
+    s = run_solve(G, o, G->fadj, info, 1);
+    if (s != SBM_OK && s != SBM_ERR_NOCONV && s != SBM_ERR_DIVERGED) return s;
+    CK(launch_unpack<double, double>(F.g, F.g.dim, F.du[0], lambda, G->st));
+    CK(launch_dJdpsi(F.g, F.c64, u, lambda, dJdpsi, dJdrho, G->rho, G->psi_raw, G->psi_min, G->q, G->density, G->st));
+    CK(cudaStreamSynchronize(G->st));
+    return s;
+}
+
+// ------------------------------------------------------------------ steps
+
+sbm_status sbm_apply(sbm_grid G, int level, int fp32, const double *u, double *Ku)
+{
+    sbm_status s = check_level(G, level);
+    if (s != SBM_OK) return s;
+    if (!G->has_moduli || !G->has_psi) return check_ready(G);
+    if (!is_dev_ptr(u, G->dev) || !is_dev_ptr(Ku, G->dev)) return fail(G, SBM_ERR_ARG, "u and Ku must be device pointers");
+    CK(cudaSetDevice(G->dev));
+    Level &L = G->L[level];
+    if (fp32) {
+        CK(launch_pack<double, float>(L.g, L.g.dim, u, L.su[1], G->st));
+        CK(sweep<float>(G, level, kApply, L.su[1], nullptr, L.sr, nullptr, 0.0));
+        CK(launch_unpack<float, double>(L.g, L.g.dim, L.sr, Ku, G->st));
+    } else {
+        CK(launch_pack<double, double>(L.g, L.g.dim, u, L.du[1], G->st));
+        CK(sweep<double>(G, level, kApply, L.du[1], nullptr, L.dr, nullptr, 0.0));
+        CK(launch_unpack<double, double>(L.g, L.g.dim, L.dr, Ku, G->st));
+    }
+    CK(cudaStreamSynchronize(G->st));
+    return SBM_OK;
+}
+
+sbm_status sbm_residual(sbm_grid G, int level, int fp32, const double *f, const double *u, double *r, double *norm)
+{
+    sbm_status s = check_level(G, level);
+    if (s != SBM_OK) return s;
+    if (!G->has_moduli || !G->has_psi) return check_ready(G);
+    if (!is_dev_ptr(u, G->dev) || !is_dev_ptr(f, G->dev) || !is_dev_ptr(r, G->dev))
+        return fail(G, SBM_ERR_ARG, "f, u and r must be device pointers");
+    CK(cudaSetDevice(G->dev));
+    Level &L = G->L[level];
+    const int nb = (int)sweep_blocks(L.g);
+    if (fp32) {
+        CK(launch_pack<double, float>(L.g, L.g.dim, u, L.su[1], G->st));
+        CK(launch_pack<double, float>(L.g, L.g.dim, f, L.sf, G->st));
+        CK(sweep<float>(G, level, kResidual, L.su[1], L.sf, L.sr, G->part, 0.0));
+        CK(launch_unpack<float, double>(L.g, L.g.dim, L.sr, r, G->st));
+    } else {
+        CK(launch_pack<double, double>(L.g, L.g.dim, u, L.du[1], G->st));
+        CK(launch_pack<double, double>(L.g, L.g.dim, f, L.df, G->st));
+        CK(sweep<double>(G, level, kResidual, L.du[1], L.df, L.dr, G->part, 0.0));
+        CK(launch_unpack<double, double>(L.g, L.g.dim, L.dr, r, G->st));
+    }
+    CK(launch_norm_final(G->part, nb, G->scal, 5, G->st));
+    CK(cudaMemcpyAsync(G->hscal + 5, G->scal + 5, 2 * sizeof(double), cudaMemcpyDeviceToHost, G->st));
+    CK(cudaStreamSynchronize(G->st));
+    if (norm) *norm = G->hscal[6];
+    return SBM_OK;
+}
+
+sbm_status sbm_smooth(sbm_grid G, int level, int fp32, int smoother, double omega, int descending, const double *f,
+                      double *u)
+{
+    sbm_status s = check_level(G, level);
+    if (s != SBM_OK) return s;
+    if (!G->has_moduli || !G->has_psi) return check_ready(G);
+    if (!is_dev_ptr(u, G->dev) || !is_dev_ptr(f, G->dev)) return fail(G, SBM_ERR_ARG, "f and u must be device pointers");
+    if (smoother != SBM_JACOBI && smoother != SBM_MCGS) return fail(G, SBM_ERR_ARG, "unknown smoother");
+    CK(cudaSetDevice(G->dev));
+    sbm_opts o;
+    sbm_default_opts(&o);
+    o.smoother = smoother;
+    o.omega = omega;
+    Level &L = G->L[level];
+    int cur = 0;
+    if (fp32) {
+        CK(launch_pack<double, float>(L.g, L.g.dim, u, L.su[0], G->st));
+        CK(launch_pack<double, float>(L.g, L.g.dim, f, L.sf, G->st));
+        CK(smooth<float>(G, level, cur, o, 1, descending != 0, L.sf));
+        CK(launch_unpack<float, double>(L.g, L.g.dim, L.su[cur], u, G->st));
+    } else {
+        CK(launch_pack<double, double>(L.g, L.g.dim, u, L.du[0], G->st));
+        CK(launch_pack<double, double>(L.g, L.g.dim, f, L.df, G->st));
+        CK(smooth<double>(G, level, cur, o, 1, descending != 0, L.df));
+        CK(launch_unpack<double, double>(L.g, L.g.dim, L.du[cur], u, G->st));
+    }
+    CK(cudaStreamSynchronize(G->st));
+    return SBM_OK;
+}
+
+sbm_status sbm_restrict(sbm_grid G, int level, int fp32, const double *rf, double *rc)
+{
+    sbm_status s = check_level(G, level);
+    if (s != SBM_OK) return s;
+    if (level < 1) return fail(G, SBM_ERR_ARG, "restriction needs a fine level >= 1");
+    if (!is_dev_ptr(rf, G->dev) || !is_dev_ptr(rc, G->dev)) return fail(G, SBM_ERR_ARG, "device pointers required");
+    CK(cudaSetDevice(G->dev));
+    Level &L = G->L[level], &C = G->L[level - 1];
+    if (fp32) {
+        CK(launch_pack<double, float>(L.g, L.g.dim, rf, L.sr, G->st));
+        CK(launch_restrict<float>(L.g, C.g, L.sr, C.sf, G->st));
+        CK(launch_unpack<float, double>(C.g, C.g.dim, C.sf, rc, G->st));
+    } else {
+        CK(launch_pack<double, double>(L.g, L.g.dim, rf, L.dr, G->st));
+        CK(launch_restrict<double>(L.g, C.g, L.dr, C.df, G->st));
+        CK(launch_unpack<double, double>(C.g, C.g.dim, C.df, rc, G->st));
+    }
+    CK(cudaStreamSynchronize(G->st));
+    return SBM_OK;
+}
+
+sbm_status sbm_prolong_add(sbm_grid G, int level, int fp32, const double *ec, double *uf)
+{
+    sbm_status s = check_level(G, level);
+    if (s != SBM_OK) return s;
+    if (level < 1) return fail(G, SBM_ERR_ARG, "prolongation needs a fine level >= 1");
+    if (!is_dev_ptr(ec, G->dev) || !is_dev_ptr(uf, G->dev)) return fail(G, SBM_ERR_ARG, "device pointers required");
+    CK(cudaSetDevice(G->dev));
+    Level &L = G->L[level], &C = G->L[level - 1];
+    if (fp32) {
+        CK(launch_pack<double, float>(C.g, C.g.dim, ec, C.su[1], G->st));
+        CK(launch_pack<double, float>(L.g, L.g.dim, uf, L.su[1], G->st));
+        CK(launch_prolong_add<float>(L.g, C.g, C.su[1], L.su[1], G->st));
+        CK(launch_unpack<float, double>(L.g, L.g.dim, L.su[1], uf, G->st));
+    } else {
+        CK(launch_pack<double, double>(C.g, C.g.dim, ec, C.du[1], G->st));
+        CK(launch_pack<double, double>(L.g, L.g.dim, uf, L.du[1], G->st));
+        CK(launch_prolong_add<double>(L.g, C.g, C.du[1], L.du[1], G->st));
+        CK(launch_unpack<double, double>(L.g, L.g.dim, L.du[1], uf, G->st));
+    }
+    CK(cudaStreamSynchronize(G->st));
+    return SBM_OK;
+}
+
+sbm_status sbm_get_psi(sbm_grid G, int level, double *psi)
+{
+    sbm_status s = check_level(G, level);
+    if (s != SBM_OK) return s;
+    if (!G->has_psi) return fail(G, SBM_ERR_STATE, "psi not set");
+    if (!is_dev_ptr(psi, G->dev)) return fail(G, SBM_ERR_ARG, "psi must be a device pointer");
+    CK(cudaSetDevice(G->dev));
+    CK(launch_get_cells(G->L[level].g, G->L[level].psi64, psi, G->st));
+    CK(cudaStreamSynchronize(G->st));
+    return SBM_OK;
+}
+
+sbm_status sbm_bottom_correct(sbm_grid G, int fp32, const double *f, double *u)
+{
+    sbm_status s = check_ready(G);
+    if (s != SBM_OK) return s;
+    if (!is_dev_ptr(u, G->dev) || !is_dev_ptr(f, G->dev)) return fail(G, SBM_ERR_ARG, "f and u must be device pointers");
+    CK(cudaSetDevice(G->dev));
+    if ((s = setup_bottom(G)) != SBM_OK) return s;
+    Level &B = G->L[0];
+    if (fp32) {
+        CK(launch_pack<double, float>(B.g, B.g.dim, u, B.su[1], G->st));
+        CK(launch_pack<double, float>(B.g, B.g.dim, f, B.sf, G->st));
+        CK(sweep<float>(G, 0, kResidual, B.su[1], B.sf, B.sr, nullptr, 0.0));
+        CK(launch_bottom_apply<float>(G->nb, G->A32, G->gather, B.sr, B.su[1], 1, G->st));
+        CK(launch_unpack<float, double>(B.g, B.g.dim, B.su[1], u, G->st));
+    } else {
+        CK(launch_pack<double, double>(B.g, B.g.dim, u, B.du[1], G->st));
+        CK(launch_pack<double, double>(B.g, B.g.dim, f, B.df, G->st));
+        CK(sweep<double>(G, 0, kResidual, B.du[1], B.df, B.dr, nullptr, 0.0));
+        CK(launch_bottom_apply<double>(G->nb, G->A64, G->gather, B.dr, B.du[1], 1, G->st));
+        CK(launch_unpack<double, double>(B.g, B.g.dim, B.du[1], u, G->st));
+    }
+    CK(cudaStreamSynchronize(G->st));
+    return SBM_OK;
+}
+
+sbm_status sbm_dJdpsi(sbm_grid G, const double *u, const double *lam, double *g)
+{
+    sbm_status s = check_ready(G);
+    if (s != SBM_OK) return s;
+    if (!is_dev_ptr(u, G->dev) || !is_dev_ptr(lam, G->dev) || !is_dev_ptr(g, G->dev))
+        return fail(G, SBM_ERR_ARG, "u, lambda and dJdpsi must be device pointers");
+    CK(cudaSetDevice(G->dev));
+    Level &F = G->L[G->nl - 1];
+    CK(launch_dJdpsi(F.g, F.c64, u, lam, g, nullptr, nullptr, nullptr, 0.0, 3.0, 0, G->st));
+    CK(cudaStreamSynchronize(G->st));
+    return SBM_OK;
+}
+
+sbm_status sbm_time_kernel(sbm_grid G, int which, int reps, double *ms, double *bytes, double *flops)
+{
+    sbm_status s = check_ready(G);
+    if (s != SBM_OK) return s;
+    if (which < SBM_K_RESIDUAL64 || which > SBM_K_RESIDUAL || reps < 1) return fail(G, SBM_ERR_ARG, "bad kernel id or reps");
+    CK(cudaSetDevice(G->dev));
+    const int fine = G->nl - 1;
+    Level &L = G->L[fine];
+    const int mixed = G->desc.precision == SBM_MIXED;
+    const int d = L.g.dim;
+    const double nn = (double)nnodes(L.g), nc = (double)ncells_h(L.g);
+    const double cellf = d == 3 ? 195.0 : 38.0, nodef = d == 3 ? 41.0 : 26.0;
+    auto launch = [&]() -> cudaError_t {
+        if (which == SBM_K_RESIDUAL64) return residual64(G, G->fsrc, mixed, 5);
+        int cur = 0;
+        sbm_opts o;
+        sbm_default_opts(&o);
+        o.nu1 = 1;
+        if (which == SBM_K_JACOBI) {
+            if (mixed) return smooth<float>(G, fine, cur, o, 1, false, L.sf);
+            return smooth<double>(G, fine, cur, o, 1, false, L.df);
+        }
+        if (mixed) return sweep<float>(G, fine, kResidual, L.su[0], L.sf, L.sr, nullptr, 0.0);
+        return sweep<double>(G, fine, kResidual, L.du[0], L.df, L.dr, nullptr, 0.0);
+    };
+    CK(launch());
+    CK(cudaEventRecord(G->ev0, G->st));
+    for (int r = 0; r < reps; ++r) CK(launch());
+    CK(cudaEventRecord(G->ev1, G->st));
+    CK(cudaEventSynchronize(G->ev1));
+    float t = 0.f;
+    CK(cudaEventElapsedTime(&t, G->ev0, G->ev1));
+    if (ms) *ms = t / reps;
+    // per node: read u and f (d values each), psi (one cell per node), write d outputs
+    double per_node;
+    if (which == SBM_K_RESIDUAL64) per_node = mixed ? (8.0 * d + 8.0 * d + 8.0 + 4.0 * d) : (8.0 * (3 * d + 1));
+    else per_node = (mixed ? 4.0 : 8.0) * (3 * d + 1);
+    if (bytes) *bytes = per_node * nn;
+    if (flops) *flops = cellf * nc + (which == SBM_K_JACOBI ? nodef : nodef - 11.0) * nn;
+    return SBM_OK;
+}
+
+}  // extern "C"

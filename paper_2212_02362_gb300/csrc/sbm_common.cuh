@@ -1,0 +1,116 @@
+// sbm_common.cuh — level geometry, kernel argument structs and launcher
+// declarations shared by the translation units of libsbm.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sbm_cell.cuh"
+
+namespace sbm {
+
+constexpr int kMaxLevels = 16;
+
+// Internal layout of one level: node (i,j,k), component p at
+//   p*cs + i + sx*(j + ny*k)
+// with the x pitch sx a multiple of 8 elements (rows start 32-byte aligned for
+// FP32, 64-byte for FP64).  Cells use the same indexing (cell (i,j,k) has lower
+// corner node (i,j,k)); the last row/column/plane of the cell array is unused.
+struct Geom {
+    int dim;
+    int nx, ny, nz;
+    int sx;
+    long long sy;          // sx * ny
+    long long cs;          // component stride (>= sy * nz, multiple of 64)
+    unsigned dm[3];        // Dirichlet face bits per component (faces 0..5)
+};
+
+__host__ __device__ __forceinline__ long long gidx(const Geom &g, int i, int j, int k)
+{
+    return (long long)i + (long long)g.sx * ((long long)j + (long long)g.ny * k);
+}
+
+__host__ __device__ __forceinline__ bool is_dir(const Geom &g, int p, int i, int j, int k)
+{
+    const unsigned m = g.dm[p];
+    return ((m & 1u) && i == 0) || ((m & 2u) && i == g.nx - 1) || ((m & 4u) && j == 0) ||
+           ((m & 8u) && j == g.ny - 1) || ((m & 16u) && k == 0) || ((m & 32u) && k == g.nz - 1);
+}
+
+enum SweepMode { kApply = 0, kResidual = 1, kJacobi = 2 };
+
+template <typename T, typename TO>
+struct SweepArgs {
+    Geom g;
+    const T *u;            // input displacement (level layout)
+    const T *f;            // right-hand side (residual / Jacobi)
+    const T *psi;          // cells
+    TO *out;               // Ku, r, or the smoothed u (must not alias u for Jacobi)
+    double *part;          // per-block partial sums of r^2 (residual), may be null
+    Coef<T> c;
+    T wk[3];               // Jacobi: omega / kdiag[p]
+    int kchunk;            // node planes per block along z (3D)
+};
+
+// ---- launchers (defined in k_stencil.cu / k_misc.cu) ----------------------
+
+// Number of kernels the launchers have enqueued (graph capture included).
+extern long long g_launches;
+
+// Tile shape of the stencil kernels (cells per block along x and y).
+void sweep_grid(const Geom &g, int *grid, int *kchunk);   // grid[3]; returns blocks
+long long sweep_blocks(const Geom &g);
+
+template <typename T, typename TO>
+cudaError_t launch_sweep(int mode, const SweepArgs<T, TO> &a, cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_gs(const Geom &g, const T *psi, const T *Ke, const T *f, T *u, int colour,
+                      cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_restrict(const Geom &gf, const Geom &gc, const T *rf, T *fc, cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_prolong_add(const Geom &gf, const Geom &gc, const T *ec, T *uf, cudaStream_t s);
+
+cudaError_t launch_coarsen_psi(const Geom &gf, const Geom &gc, const double *pf, double *pc,
+                               cudaStream_t s);
+
+// packed (user) <-> level layout copies, with conversion
+template <typename TS, typename TD>
+cudaError_t launch_pack(const Geom &g, int ncomp, const TS *packed, TD *lev, cudaStream_t s);
+template <typename TS, typename TD>
+cudaError_t launch_unpack(const Geom &g, int ncomp, const TS *lev, TD *packed, cudaStream_t s);
+// cells: packed (nx-1)(ny-1)(nz-1) <-> level layout; floor with psi_min, count non-finite
+cudaError_t launch_set_psi(const Geom &g, const double *packed, double psi_min, double *lev,
+                           int *bad, cudaStream_t s);
+cudaError_t launch_set_density(const Geom &g, const double *rho, double psi_min, double q,
+                               double *lev, int *bad, cudaStream_t s);
+cudaError_t launch_get_cells(const Geom &g, const double *lev, double *packed, cudaStream_t s);
+cudaError_t launch_round_cells(const Geom &g, const double *src, float *dst, cudaStream_t s);
+// write a face value into Dirichlet dofs of one component
+cudaError_t launch_set_face(const Geom &g, int face, int comp, double value, double *u,
+                            cudaStream_t s);
+// u64 += e (FP32 or FP64) over n elements
+template <typename TE>
+cudaError_t launch_add(long long n, const TE *e, double *u, cudaStream_t s);
+// deterministic final reduction of block partials: out[0] = sum, optional relres
+cudaError_t launch_norm_final(const double *part, int nparts, double *scal, int which,
+                              cudaStream_t s);
+// bottom: dense assembly, Dirichlet rows/cols, Gauss-Jordan inverse, matvec
+cudaError_t launch_bottom_assemble(const Geom &g, const double *psi, const Coef<double> &c,
+                                   double *A, cudaStream_t s);
+cudaError_t launch_bottom_dirichlet(const Geom &g, double *A, cudaStream_t s);
+cudaError_t launch_gauss_jordan(int n, double *A, double *tmp, cudaStream_t s);
+cudaError_t launch_round(long long n, const double *src, float *dst, cudaStream_t s);
+template <typename T>
+cudaError_t launch_bottom_apply(int n, const T *Ainv, const int *gather, const T *b, T *u,
+                                int accumulate, cudaStream_t s);
+// dJ/dpsi_c = -lambda_c^T S_c u_c (packed u, lambda; packed cell output) and the
+// optional chain rule through the SIMP map or the psi_min floor.
+cudaError_t launch_dJdpsi(const Geom &g, const Coef<double> &c, const double *u, const double *lam,
+                          double *g_out, double *grho_out, const double *rho, const double *psi_raw,
+                          double psi_min, double q, int density, cudaStream_t s);
+
+}  // namespace sbm
