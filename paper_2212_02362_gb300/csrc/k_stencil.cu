@@ -315,7 +315,7 @@ void sweep_grid(const Geom &g, int *grid, int *kchunk)
         const int target = 4 * 152;                       // blocks wanted to fill the SMs
         int nchunks = (target + xy - 1) / xy;
         int ch = (g.nz - 1 + nchunks - 1) / nchunks;
-        if (ch < 4) ch = 4;
+        if (ch < 2) ch = 2;
         if (ch > g.nz - 1) ch = g.nz - 1;
         grid[2] = (g.nz - 1 + ch - 1) / ch;
         *kchunk = ch;

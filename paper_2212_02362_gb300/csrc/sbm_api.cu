@@ -2,11 +2,14 @@
 // psi / moduli / boundary conditions, the multigrid driver (FP64 V-cycles, or
 // FP32 V-cycles inside an FP64 defect correction), CUDA-graph replay of one
 // outer iteration, the adjoint solve and the single-step entry points.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -30,6 +33,8 @@ struct Level {
     Coef<float> c32{};
     double *Ke64 = nullptr;   // unit-psi cell matrix (GS smoother)
     float *Ke32 = nullptr;
+    CUtensorMap tm32[2];      // TMA descriptors of su[0], su[1] (3D levels)
+    bool has_tm = false;
 };
 
 struct GraphSlot {
@@ -61,6 +66,7 @@ struct sbm_grid_s {
     double psi_min = 0, q = 3;
     double *part = nullptr;
     long long npart = 0;
+    int *derr = nullptr;        // device error flag of the TMA kernels
     double *scal = nullptr;     // device scalars, see k_norm_final
     double *hscal = nullptr;    // pinned host copy
     int *dbad = nullptr;
@@ -151,6 +157,64 @@ cudaError_t sweep(sbm_grid G, int l, int mode, const T *u, const T *f, T *out, d
     for (int p = 0; p < 3; ++p) a.wk[p] = (L.c64.kdiag[p] != 0.0) ? T(omega / L.c64.kdiag[p]) : T(0);
     a.kchunk = 0;
     return launch_sweep<T, T>(mode, a, G->st);
+}
+
+// FP32 3D sweeps whose input is one of the level's TMA-described buffers use the
+// TMA + packed-FP32x2 kernel; everything else the generic kernel.
+template <>
+cudaError_t sweep<float>(sbm_grid G, int l, int mode, const float *u, const float *f, float *out, double *part,
+                         double omega)
+{
+    Level &L = G->L[l];
+    SweepArgs<float, float> a;
+    a.g = L.g;
+    a.u = u;
+    a.f = f;
+    a.psi = L.psi32;
+    a.out = out;
+    a.part = part;
+    a.c = L.c32;
+    for (int p = 0; p < 3; ++p) a.wk[p] = (L.c64.kdiag[p] != 0.0) ? float(omega / L.c64.kdiag[p]) : 0.f;
+    a.kchunk = 0;
+    if (L.has_tm && (u == L.su[0] || u == L.su[1]))
+        return launch_sweep_f2(mode, a, &L.tm32[u == L.su[0] ? 0 : 1], G->derr, G->st);
+    return launch_sweep<float, float>(mode, a, G->st);
+}
+
+long long sweep_nblocks(sbm_grid G, int l, bool fp32, const void *u)
+{
+    Level &L = G->L[l];
+    if (fp32 && L.has_tm && (u == L.su[0] || u == L.su[1])) return sweep_blocks_f2(L.g);
+    return sweep_blocks(L.g);
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+// 4D (x, y, z, component) map of one FP32 level buffer; box = 40 x 10 x 1 x 3 nodes
+// (the staged plane of the TMA sweep), zero fill outside the grid.
+bool encode_plane_map(CUtensorMap *m, float *buf, const Geom &g)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return false;
+    cuuint64_t dims[4] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz, 3};
+    cuuint64_t strides[3] = {(cuuint64_t)g.sx * 4, (cuuint64_t)g.sy * 4, (cuuint64_t)g.cs * 4};
+    cuuint32_t box[4] = {40, 10, 1, 3};
+    cuuint32_t estr[4] = {1, 1, 1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, buf, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 template <typename T>
@@ -402,6 +466,14 @@ sbm_status run_solve(sbm_grid G, const sbm_opts &o, const double *rhs, sbm_info 
     CK(cudaEventSynchronize(G->ev1));
     float ms = 0.f;
     cudaEventElapsedTime(&ms, G->ev0, G->ev1);
+    {
+        int herr = 0;
+        CK(cudaMemcpy(&herr, G->derr, sizeof(int), cudaMemcpyDeviceToHost));
+        if (herr) {
+            cudaMemset(G->derr, 0, sizeof(int));
+            return fail(G, SBM_ERR_CUDA, "a TMA pipeline wait timed out in the FP32 sweep kernel");
+        }
+    }
     if (info) {
         info->status = status;
         info->cycles = cyc;
@@ -423,6 +495,8 @@ sbm_status check_level(sbm_grid G, int level)
 }
 
 }  // namespace
+
+void sbm::set_library_error(const char *msg) { g_lib_error = msg; }
 
 // ========================================================================= ABI
 
@@ -470,7 +544,8 @@ sbm_status sbm_grid_destroy(sbm_grid G)
         for (void *p : ptrs)
             if (p) cudaFree(p);
     }
-    void *ptrs[] = {G->fsrc, G->fadj, G->psi_raw, G->rho, G->part, G->scal, G->dbad, G->A64, G->A32, G->gjtmp, G->gather};
+    void *ptrs[] = {G->fsrc, G->fadj, G->psi_raw, G->rho, G->part, G->scal, G->dbad, G->A64, G->A32, G->gjtmp, G->gather,
+                    G->derr};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (G->hscal) cudaFreeHost(G->hscal);
@@ -552,6 +627,8 @@ sbm_status sbm_grid_create(const sbm_grid_desc *d, sbm_grid *out)
             CK(cudaMalloc(p, sizeof(float) * nd));
             CK(cudaMemset(*p, 0, sizeof(float) * nd));
         }
+        if (g.dim == 3)
+            L.has_tm = encode_plane_map(&L.tm32[0], L.su[0], g) && encode_plane_map(&L.tm32[1], L.su[1], g);
         const int nk = (1 << g.dim) * g.dim;
         CK(cudaMalloc(&L.Ke64, sizeof(double) * nk * nk));
         CK(cudaMalloc(&L.Ke32, sizeof(float) * nk * nk));
@@ -565,8 +642,12 @@ sbm_status sbm_grid_create(const sbm_grid_desc *d, sbm_grid *out)
     const long long nc = ncells_h(F.g);
     CK(cudaMalloc(&G->psi_raw, sizeof(double) * nc));
     CK(cudaMalloc(&G->rho, sizeof(double) * nc));
-    G->npart = sweep_blocks(F.g);
+    G->npart = 1;
+    for (int l = 0; l < G->nl; ++l)
+        G->npart = std::max(G->npart, std::max(sweep_blocks(G->L[l].g), sweep_blocks_f2(G->L[l].g)));
     CK(cudaMalloc(&G->part, sizeof(double) * G->npart));
+    CK(cudaMalloc(&G->derr, sizeof(int)));
+    CK(cudaMemset(G->derr, 0, sizeof(int)));
     CK(cudaMalloc(&G->scal, sizeof(double) * 16));
     CK(cudaMemset(G->scal, 0, sizeof(double) * 16));
     CK(cudaMallocHost(&G->hscal, sizeof(double) * 16));
@@ -815,7 +896,7 @@ sbm_status sbm_residual(sbm_grid G, int level, int fp32, const double *f, const 
         return fail(G, SBM_ERR_ARG, "f, u and r must be device pointers");
     CK(cudaSetDevice(G->dev));
     Level &L = G->L[level];
-    const int nb = (int)sweep_blocks(L.g);
+    const int nb = (int)sweep_nblocks(G, level, fp32 != 0, fp32 ? (const void *)L.su[1] : (const void *)L.du[1]);
     if (fp32) {
         CK(launch_pack<double, float>(L.g, L.g.dim, u, L.su[1], G->st));
         CK(launch_pack<double, float>(L.g, L.g.dim, f, L.sf, G->st));

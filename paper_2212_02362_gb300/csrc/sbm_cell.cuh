@@ -29,6 +29,26 @@
 
 namespace sbm {
 
+// a * b + c; float and double contract to one FMA (nvcc --fmad default).
+__host__ __device__ __forceinline__ float madd(float a, float b, float c) { return a * b + c; }
+__host__ __device__ __forceinline__ double madd(double a, double b, double c) { return a * b + c; }
+
+#ifdef __CUDACC__
+// Two FP32 lanes in one 64-bit register pair, computed with the packed FP32x2
+// instructions of sm_100+ (one FADD2 / FMUL2 / FFMA2 per pair).  The 3D FP32
+// stencil evaluates two z layers of cells at once in this type.
+struct F2 {
+    float2 v;
+    __device__ __forceinline__ F2() {}
+    __device__ __forceinline__ explicit F2(float x) : v(make_float2(x, x)) {}
+    __device__ __forceinline__ F2(float lo, float hi) : v(make_float2(lo, hi)) {}
+};
+__device__ __forceinline__ F2 operator+(F2 a, F2 b) { F2 r; r.v = __fadd2_rn(a.v, b.v); return r; }
+__device__ __forceinline__ F2 operator-(F2 a, F2 b) { F2 r; r.v = __ffma2_rn(b.v, make_float2(-1.f, -1.f), a.v); return r; }
+__device__ __forceinline__ F2 operator*(F2 a, F2 b) { F2 r; r.v = __fmul2_rn(a.v, b.v); return r; }
+__device__ __forceinline__ F2 madd(F2 a, F2 b, F2 c) { F2 r; r.v = __ffma2_rn(a.v, b.v, c.v); return r; }
+#endif
+
 template <typename T>
 struct Coef {
     T a11, a12, a44, ad;   // class 0: W0 (C11, C12, C44, C11 - C12) / h^2
@@ -94,18 +114,18 @@ __host__ __device__ __forceinline__ void cell_forces3(T (&U)[3][8], T psi, const
     const T b1 = psi * c.b1, b12 = psi * c.b12, b44 = psi * c.b44, c2 = psi * c.c2;
     // class 0: the mean gradient (all nine entries)
     const T ltr = a12 * (U[0][1] + U[1][2] + U[2][4]);
-    const T sxx = ad * U[0][1] + ltr, syy = ad * U[1][2] + ltr, szz = ad * U[2][4] + ltr;
+    const T sxx = madd(ad, U[0][1], ltr), syy = madd(ad, U[1][2], ltr), szz = madd(ad, U[2][4], ltr);
     const T sxy = a44 * (U[1][1] + U[0][2]);
     const T sxz = a44 * (U[2][1] + U[0][4]);
     const T syz = a44 * (U[2][2] + U[1][4]);
     // class 1: gradients linear along one axis
     const T S = U[2][3] + U[1][5] + U[0][6];
-    const T d03 = b1 * U[0][3] + b12 * U[2][6];
-    const T d26 = b1 * U[2][6] + b12 * U[0][3];
-    const T d13 = b1 * U[1][3] + b12 * U[2][5];
-    const T d25 = b1 * U[2][5] + b12 * U[1][3];
-    const T d05 = b1 * U[0][5] + b12 * U[1][6];
-    const T d16 = b1 * U[1][6] + b12 * U[0][5];
+    const T d03 = madd(b1, U[0][3], b12 * U[2][6]);
+    const T d26 = madd(b1, U[2][6], b12 * U[0][3]);
+    const T d13 = madd(b1, U[1][3], b12 * U[2][5]);
+    const T d25 = madd(b1, U[2][5], b12 * U[1][3]);
+    const T d05 = madd(b1, U[0][5], b12 * U[1][6]);
+    const T d16 = madd(b1, U[1][6], b12 * U[0][5]);
     const T d23 = b44 * (S + U[2][3]);
     const T d15 = b44 * (S + U[1][5]);
     const T d06 = b44 * (S + U[0][6]);

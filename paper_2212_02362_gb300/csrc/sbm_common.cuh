@@ -57,12 +57,22 @@ struct SweepArgs {
 // Number of kernels the launchers have enqueued (graph capture included).
 extern long long g_launches;
 
+// Message returned by sbm_last_error(NULL) (defined in sbm_api.cu).
+void set_library_error(const char *msg);
+
 // Tile shape of the stencil kernels (cells per block along x and y).
 void sweep_grid(const Geom &g, int *grid, int *kchunk);   // grid[3]; returns blocks
 long long sweep_blocks(const Geom &g);
 
 template <typename T, typename TO>
 cudaError_t launch_sweep(int mode, const SweepArgs<T, TO> &a, cudaStream_t s);
+
+// FP32 3D sweep with TMA plane staging and packed FP32x2 arithmetic
+// (k_stencil_tma.cu).  tmap: CUtensorMap of a.u as 4D (x, y, z, component) with
+// a 40 x 10 x 1 x 3 box; err: device flag set when an mbarrier wait times out.
+cudaError_t launch_sweep_f2(int mode, const SweepArgs<float, float> &a, const void *tmap, int *err,
+                            cudaStream_t s);
+long long sweep_blocks_f2(const Geom &g);
 
 template <typename T>
 cudaError_t launch_gs(const Geom &g, const T *psi, const T *Ke, const T *f, T *u, int colour,
