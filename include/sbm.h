@@ -193,6 +193,40 @@ enum { SBM_K_RESIDUAL64 = 0, SBM_K_JACOBI = 1, SBM_K_RESIDUAL = 2 };
 sbm_status sbm_time_kernel(sbm_grid grid, int which, int reps, double *ms_per_launch,
                            double *bytes_per_launch, double *flops_per_launch);
 
+/* ---- allocation-free entry point ---- */
+
+/* Stencil blocks whose partial sums fit the fixed scratch array of
+ * sbm_residual_noalloc: 16384 doubles (128 KiB) plus 8 result slots. */
+#define SBM_NOALLOC_MAX_BLOCKS 16384
+
+/* r = f - K u on free dofs (0 on Dirichlet dofs) and ||r||_2 over free dofs, in
+ * FP64, on buffers the caller owns: no grid handle and no device allocation.
+ * The paper has no counterpart to this call.  It is for callers that cannot call
+ * cudaMalloc: an application whose device memory belongs to its own pool allocator,
+ * code that must not trigger the implicit device synchronisation of cudaMalloc and
+ * cudaFree, or a process too close to its memory limit to build the level
+ * hierarchy that sbm_grid_create allocates.
+ * Scratch: the per-block partial sums and the result live in one fixed device array
+ * of SBM_NOALLOC_MAX_BLOCKS + 8 doubles inside the library, which every GPU that
+ * loads the library holds until the process exits.  The first call on a device
+ * looks up that array's device address (cudaGetSymbolAddress, with the device
+ * current); make this first call before any stream capture.  All calls share the
+ * array and it keeps the last call's contents, so calls that overlap on the GPU
+ * (other streams or host threads) race: the caller must serialise them.
+ * dim: 2 or 3.  n: nodes per axis (n[2] = 1 in 2D).  h: spacing.  moduli: (C11, C12,
+ * C44) of an axis-aligned cubic material (isotropic: lambda + 2 mu, lambda, mu).
+ * dirichlet_faces[p]: bit f set => face f (0:-x 1:+x 2:-y 3:+y 4:-z 5:+z) is
+ * Dirichlet for component p.  psi (device, FP64): the floored cell values in
+ * node-indexed layout, cell (i,j,k) at i + nx*(j + ny*k), the last x, y (and z)
+ * slot unused.  f, u (device, FP64, packed nodes) in; r (device, packed nodes) out;
+ * norm (host) out.  stream: cudaStream_t, NULL = legacy default; the call
+ * synchronises it.  A grid that needs more than SBM_NOALLOC_MAX_BLOCKS stencil
+ * blocks is rejected with SBM_ERR_ARG before any device work; sbm_last_error(NULL)
+ * describes every failure. */
+sbm_status sbm_residual_noalloc(int dim, const int n[3], double h, const double moduli[3],
+                                const unsigned dirichlet_faces[3], const double *psi, const double *f,
+                                const double *u, double *r, double *norm, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

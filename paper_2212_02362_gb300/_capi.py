@@ -17,6 +17,7 @@ SBM_JACOBI, SBM_MCGS = 0, 1
 SBM_CUBIC, SBM_ISO_LAME, SBM_ISO_ENU = 0, 1, 2
 SBM_FREE, SBM_DIRICHLET, SBM_DIRICHLET_FROM_U = 0, 1, 2
 SBM_K_RESIDUAL64, SBM_K_JACOBI, SBM_K_RESIDUAL = 0, 1, 2
+SBM_NOALLOC_MAX_BLOCKS = 16384
 
 
 class sbm_grid_desc(C.Structure):
@@ -66,6 +67,9 @@ _SIGS = {
     "sbm_dJdpsi": (C.c_int, [_grid, _dptr, _dptr, _dptr]),
     "sbm_time_kernel": (C.c_int, [_grid, C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                   C.POINTER(C.c_double)]),
+    "sbm_residual_noalloc": (C.c_int, [C.c_int, C.POINTER(C.c_int), C.c_double, C.POINTER(C.c_double),
+                                       C.POINTER(C.c_uint), _dptr, _dptr, _dptr, _dptr, C.POINTER(C.c_double),
+                                       C.c_void_p]),
 }
 
 EXPORTED = tuple(_SIGS)
