@@ -265,3 +265,100 @@ def simp(rho, psi_min: float, q: float = 3.0):
     """SIMP stiffness map psi = psi_min + (1 - psi_min) rho^q and its derivative."""
     rho = _f64(rho)
     return psi_min + (1.0 - psi_min) * rho ** q, (1.0 - psi_min) * q * rho ** (q - 1.0)
+
+
+# ------------------------------------------------------------------ BSAMR
+
+class _Amr(C.Structure):
+    _fields_ = [("base", _Problem), ("nlev", C.c_int), ("lo", (C.c_int * 3) * 8), ("hi", (C.c_int * 3) * 8)]
+
+
+_AMR_SIGS = {
+    "orc_amr_level_problem": (None, [C.POINTER(_Amr), C.c_int, C.POINTER(_Problem)]),
+    "orc_amr_owned": (C.c_int, [C.POINTER(_Amr), C.c_int, C.c_int, C.c_int, C.c_int]),
+    "orc_amr_coarsen_psi": (None, [C.POINTER(_Amr), C.POINTER(C.POINTER(C.c_double))]),
+    "orc_amr_fill": (None, [C.POINTER(_Amr), C.POINTER(C.POINTER(C.c_double))]),
+    "orc_amr_residual": (None, [C.POINTER(_Amr)] + [C.POINTER(C.POINTER(C.c_double))] * 4),
+}
+
+
+def _La():
+    lib = _L()
+    if not getattr(lib, "_amr_ready", False):
+        for name, (res, args) in _AMR_SIGS.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        lib._amr_ready = True
+    return lib
+
+
+@dataclass
+class Amr:
+    """Level 0 = ``base`` (whole box); level a >= 1 refines level a-1 by 2 on the node
+    box ``boxes[a-1] = (lo, hi)`` given in level-a node indices.  Level a >= 1 arrays
+    live on the box grown by one padding node per side (see sbm_oracle.h)."""
+    base: Problem
+    boxes: list
+
+    @property
+    def nlev(self):
+        return 1 + len(self.boxes)
+
+    def c(self) -> _Amr:
+        s = _Amr()
+        s.base = self.base.c()
+        s.nlev = self.nlev
+        for a, (lo, hi) in enumerate(self.boxes, start=1):
+            lo3 = list(lo) + [0] * (3 - len(lo))
+            hi3 = list(hi) + [0] * (3 - len(hi))
+            for ax in range(3):
+                s.lo[a][ax] = lo3[ax]
+                s.hi[a][ax] = hi3[ax]
+        return s
+
+    def level_problem(self, a) -> Problem:
+        out = _Problem()
+        _La().orc_amr_level_problem(C.byref(self.c()), a, C.byref(out))
+        return Problem(out.dim, tuple(out.n), out.h, out.c11, out.c12, out.c44, tuple(out.dirichlet))
+
+    def origin(self, a):
+        """global level-a index of local node 0 of level a's storage"""
+        if a == 0:
+            return (0, 0, 0)
+        lo = list(self.boxes[a - 1][0]) + [0] * 3
+        return tuple(lo[ax] - 1 if ax < self.base.dim else 0 for ax in range(3))
+
+    def global_n(self, a):
+        return tuple((self.base.n[ax] - 1) * 2 ** a + 1 if ax < self.base.dim else 1 for ax in range(3))
+
+    def owned(self, a, i, j, k=0) -> bool:
+        return bool(_La().orc_amr_owned(C.byref(self.c()), a, i, j, k))
+
+
+def _ptrs(arrs):
+    arr = (C.POINTER(C.c_double) * len(arrs))()
+    for i, a in enumerate(arrs):
+        assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+        arr[i] = a.ctypes.data_as(C.POINTER(C.c_double))
+    return arr
+
+
+def amr_coarsen_psi(A: Amr, psis):
+    """In place: coarse cells under each patch <- mean of the fine cells."""
+    _La().orc_amr_coarsen_psi(C.byref(A.c()), _ptrs(psis))
+    return psis
+
+
+def amr_fill(A: Amr, us):
+    """In place: injection of owned fine values to covered coarse nodes, then
+    ghost fill of every patch from its parent level."""
+    _La().orc_amr_fill(C.byref(A.c()), _ptrs(us))
+    return us
+
+
+def amr_residual(A: Amr, psis, fs, us):
+    """Composite residual per level (u is filled in place)."""
+    rs = [np.zeros_like(u) for u in us]
+    _La().orc_amr_residual(C.byref(A.c()), _ptrs(psis), _ptrs(fs), _ptrs(us), _ptrs(rs))
+    return rs

@@ -621,3 +621,186 @@ void orc_dJdpsi(const orc_problem *P, const double *u, const double *lam, double
                 g[cid(P, ci, cj, ck)] = -s;
             }
 }
+
+/* ------------------------------------------------------------------- BSAMR */
+
+static int amr_N(const orc_amr *A, int a, int axis)
+{
+    if (axis >= A->base.dim) return 1;
+    return (A->base.n[axis] - 1) * (1 << a) + 1;
+}
+
+void orc_amr_level_problem(const orc_amr *A, int a, orc_problem *P)
+{
+    *P = A->base;
+    if (a == 0) return;
+    for (int ax = 0; ax < 3; ++ax)
+        P->n[ax] = (ax < A->base.dim) ? A->hi[a][ax] - A->lo[a][ax] + 3 : 1;
+    P->h = A->base.h / (double)(1 << a);
+    P->dirichlet[0] = P->dirichlet[1] = P->dirichlet[2] = 0u;
+}
+
+/* global level-a node -> local index in the level's storage, or -1 if outside it */
+static long amr_local(const orc_amr *A, int a, int g[3])
+{
+    orc_problem P;
+    orc_amr_level_problem(A, a, &P);
+    int l[3];
+    for (int ax = 0; ax < 3; ++ax) {
+        l[ax] = (a == 0 || ax >= A->base.dim) ? g[ax] : g[ax] - A->lo[a][ax] + 1;
+        if (l[ax] < 0 || l[ax] >= P.n[ax]) return -1;
+    }
+    return l[0] + (long)P.n[0] * (l[1] + (long)P.n[1] * l[2]);
+}
+
+static int amr_in_box_owned_axes(const orc_amr *A, int a, int i, int j, int k)
+{
+    const int g[3] = {i, j, k};
+    for (int ax = 0; ax < A->base.dim; ++ax) {
+        const int lo = A->lo[a][ax], hi = A->hi[a][ax], N = amr_N(A, a, ax);
+        const int inside = (g[ax] > lo && g[ax] < hi) || (g[ax] == lo && lo == 0) || (g[ax] == hi && hi == N - 1);
+        if (!inside) return 0;
+    }
+    return 1;
+}
+
+int orc_amr_owned(const orc_amr *A, int a, int i, int j, int k)
+{
+    if (a > 0 && !amr_in_box_owned_axes(A, a, i, j, k)) return 0;
+    if (a == 0) {
+        if (i < 0 || j < 0 || k < 0 || i >= amr_N(A, 0, 0) || j >= amr_N(A, 0, 1) || k >= amr_N(A, 0, 2)) return 0;
+    }
+    if (a + 1 < A->nlev) {
+        const int d3 = A->base.dim == 3;
+        if (orc_amr_owned(A, a + 1, 2 * i, 2 * j, d3 ? 2 * k : 0)) return 0;     /* covered */
+    }
+    return 1;
+}
+
+static int amr_dirichlet(const orc_amr *A, int a, int g[3], int p)
+{
+    const unsigned m = A->base.dirichlet[p];
+    for (int ax = 0; ax < A->base.dim; ++ax) {
+        if ((m & (1u << (2 * ax))) && g[ax] == 0) return 1;
+        if ((m & (1u << (2 * ax + 1))) && g[ax] == amr_N(A, a, ax) - 1) return 1;
+    }
+    return 0;
+}
+
+/* loop over the storage nodes of level a, giving global coordinates and local index */
+#define AMR_FOR_NODES(A, a, P, g, loc)                                                  \
+    for (int l2_ = 0; l2_ < (P).n[2]; ++l2_)                                            \
+        for (int l1_ = 0; l1_ < (P).n[1]; ++l1_)                                        \
+            for (int l0_ = 0; l0_ < (P).n[0]; ++l0_)                                    \
+                for (int once_ = 1; once_; once_ = 0)                                   \
+                    for (long loc = l0_ + (long)(P).n[0] * (l1_ + (long)(P).n[1] * l2_); once_; once_ = 0) \
+                        for (int g[3] = {(a) ? l0_ + (A)->lo[a][0] - 1 : l0_,           \
+                                         (a) ? l1_ + (A)->lo[a][1] - 1 : l1_,           \
+                                         ((a) && (A)->base.dim == 3) ? l2_ + (A)->lo[a][2] - 1 : l2_}; \
+                             once_; once_ = 0)
+
+void orc_amr_coarsen_psi(const orc_amr *A, double *const *psi)
+{
+    const int d = A->base.dim, nc = 1 << d;
+    for (int a = A->nlev - 1; a >= 1; --a) {
+        orc_problem Pf, Pc;
+        orc_amr_level_problem(A, a, &Pf);
+        orc_amr_level_problem(A, a - 1, &Pc);
+        /* coarse cell C (level a-1) covers fine cells 2C .. 2C+1; it is inside box a
+         * when 2C >= lo and 2C + 2 <= hi on every axis */
+        const int ncx = Pc.n[0] - 1, ncy = Pc.n[1] - 1, ncz = (d == 3) ? Pc.n[2] - 1 : 1;
+        for (int lk = 0; lk < ncz; ++lk)
+            for (int lj = 0; lj < ncy; ++lj)
+                for (int li = 0; li < ncx; ++li) {
+                    int C[3] = {li, lj, lk};
+                    if (a - 1 > 0)
+                        for (int ax = 0; ax < d; ++ax) C[ax] += A->lo[a - 1][ax] - 1;
+                    int in = 1;
+                    for (int ax = 0; ax < d; ++ax)
+                        if (2 * C[ax] < A->lo[a][ax] || 2 * C[ax] + 2 > A->hi[a][ax]) in = 0;
+                    if (!in) continue;
+                    double s = 0.0;
+                    for (int c = 0; c < nc; ++c) {
+                        int fl[3] = {0, 0, 0};
+                        for (int ax = 0; ax < d; ++ax) fl[ax] = 2 * C[ax] + ((c >> ax) & 1) - A->lo[a][ax] + 1;
+                        s += psi[a][fl[0] + (long)(Pf.n[0] - 1) * (fl[1] + (long)(Pf.n[1] - 1) * fl[2])];
+                    }
+                    psi[a - 1][li + (long)ncx * (lj + (long)ncy * lk)] = s / nc;
+                }
+    }
+}
+
+void orc_amr_fill(const orc_amr *A, double *const *u)
+{
+    const int d = A->base.dim;
+    /* injection, finest first */
+    for (int a = A->nlev - 1; a >= 1; --a) {
+        orc_problem Pf, Pc;
+        orc_amr_level_problem(A, a, &Pf);
+        orc_amr_level_problem(A, a - 1, &Pc);
+        const long Nf = orc_nnodes(&Pf), Nc = orc_nnodes(&Pc);
+        AMR_FOR_NODES(A, a, Pf, g, loc) {
+            int even = 1;
+            for (int ax = 0; ax < d; ++ax) even &= (g[ax] % 2 == 0);
+            if (!even || !orc_amr_owned(A, a, g[0], g[1], g[2])) continue;
+            int gc[3] = {g[0] / 2, g[1] / 2, d == 3 ? g[2] / 2 : 0};
+            const long lc = amr_local(A, a - 1, gc);
+            for (int p = 0; p < d; ++p) u[a - 1][p * Nc + lc] = u[a][p * Nf + loc];
+        }
+    }
+    /* ghosts, coarsest first: (bi/tri)linear interpolation of level a-1 */
+    for (int a = 1; a < A->nlev; ++a) {
+        orc_problem Pf, Pc;
+        orc_amr_level_problem(A, a, &Pf);
+        orc_amr_level_problem(A, a - 1, &Pc);
+        const long Nf = orc_nnodes(&Pf), Nc = orc_nnodes(&Pc);
+        AMR_FOR_NODES(A, a, Pf, g, loc) {
+            if (orc_amr_owned(A, a, g[0], g[1], g[2])) continue;
+            int outside = 0;
+            for (int ax = 0; ax < d; ++ax)
+                if (g[ax] < 0 || g[ax] > amr_N(A, a, ax) - 1) outside = 1;
+            for (int p = 0; p < d; ++p) {
+                double s = 0.0;
+                if (!outside) {
+                    /* average over the 2^(odd axes) coarse nodes around g/2 */
+                    int nodd = 0;
+                    for (int ax = 0; ax < d; ++ax) nodd += g[ax] & 1;
+                    for (int c = 0; c < (1 << d); ++c) {
+                        int gc[3] = {0, 0, 0}, skip = 0;
+                        for (int ax = 0; ax < d; ++ax) {
+                            const int bit = (c >> ax) & 1;
+                            if (!(g[ax] & 1) && bit) skip = 1;
+                            gc[ax] = (g[ax] >> 1) + ((g[ax] & 1) ? bit : 0);
+                        }
+                        if (skip) continue;
+                        s += u[a - 1][p * Nc + amr_local(A, a - 1, gc)];
+                    }
+                    s /= (double)(1 << nodd);
+                }
+                u[a][p * Nf + loc] = s;
+            }
+        }
+    }
+}
+
+void orc_amr_residual(const orc_amr *A, double *const *psi, double *const *f, double *const *u,
+                      double *const *r)
+{
+    const int d = A->base.dim;
+    orc_amr_fill(A, u);
+    for (int a = 0; a < A->nlev; ++a) {
+        orc_problem P;
+        orc_amr_level_problem(A, a, &P);
+        const long N = orc_nnodes(&P);
+        double *Ku = malloc(sizeof(double) * d * N);
+        orc_apply(&P, psi[a], u[a], Ku);
+        AMR_FOR_NODES(A, a, P, g, loc) {
+            const int own = orc_amr_owned(A, a, g[0], g[1], g[2]);
+            for (int p = 0; p < d; ++p) {
+                const long e = p * N + loc;
+                r[a][e] = (own && !amr_dirichlet(A, a, g, p)) ? f[a][e] - Ku[e] : 0.0;
+            }
+        }
+        free(Ku);
+    }
+}

@@ -96,6 +96,46 @@ int  orc_mg_solve(const orc_problem *P, const double *psi, const double *f, doub
 /* g_c = -lambda_c^T S_c u_c for every cell (S_c = unit-psi element matrix). */
 void orc_dJdpsi(const orc_problem *P, const double *u, const double *lam, double *g);
 
+/* ------------------------------------------------------------ BSAMR composite
+ * Block-structured refinement (Sec. 2.2): level 0 is the whole box; patch level
+ * a >= 1 refines level a-1 by 2 on one node box [lo, hi] given in level-a node
+ * indices (even corners, properly nested).  Level a is stored on the box grown by
+ * one padding node on every side: nodes [lo-1, hi+1], cells [lo-1, hi]; arrays are
+ * packed over that padded box (x fastest, component-major).  Level 0 arrays are
+ * the ordinary full-grid arrays.
+ *
+ * Composite problem (reflux-free reading of Sec. 2.2):
+ *  - a patch node is OWNED by its level when on every axis it is inside the box or
+ *    on a box face that lies on the domain boundary; owned nodes obey the fine
+ *    equation (K_a u_a)_n = f_a(n);
+ *  - the other box nodes (interface) and the padding nodes are GHOSTS, filled from
+ *    level a-1 by (bi/tri)linear interpolation (coincident nodes copy);
+ *  - a level a-1 node coinciding with an owned level-a node is COVERED: its value
+ *    is the injected fine value and it carries no equation; the other level a-1
+ *    nodes obey the coarse equation with covered neighbours injected;
+ *  - coarse cells inside the box hold the mean of their 2^d fine cells.
+ * The padding layer gives every interface node a complete fine stencil, which
+ * the multigrid restriction uses so that it is the same full weighting everywhere.
+ */
+typedef struct {
+    orc_problem base;
+    int nlev;                   /* 1 + number of patch levels (<= 8) */
+    int lo[8][3], hi[8][3];     /* [a] for a >= 1 */
+} orc_amr;
+
+/* Problem (grid, h, moduli, Dirichlet faces) of the padded patch grid of level a. */
+void orc_amr_level_problem(const orc_amr *A, int a, orc_problem *P);
+/* 1 if level-a node (global level-a indices) is owned by level a. */
+int  orc_amr_owned(const orc_amr *A, int a, int i, int j, int k);
+/* Coarse cells under each patch <- mean of the fine cells (finest first). */
+void orc_amr_coarsen_psi(const orc_amr *A, double *const *psi);
+/* Injection (covered coarse <- fine, finest first) then ghost fill (coarsest first). */
+void orc_amr_fill(const orc_amr *A, double *const *u);
+/* Composite residual: r_a = f_a - K_a u_a on owned free dofs of every level, 0 on
+ * ghost, covered and Dirichlet dofs.  u is filled (injection + ghosts) in place. */
+void orc_amr_residual(const orc_amr *A, double *const *psi, double *const *f, double *const *u,
+                      double *const *r);
+
 #ifdef __cplusplus
 }
 #endif
