@@ -653,28 +653,38 @@ static long amr_local(const orc_amr *A, int a, int g[3])
     return l[0] + (long)P.n[0] * (l[1] + (long)P.n[1] * l[2]);
 }
 
-static int amr_in_box_owned_axes(const orc_amr *A, int a, int i, int j, int k)
+/* Level-a node g is inside level a's solve region: inside the domain for the base
+ * level; for a patch, inside its box on every axis or on a box face that lies on
+ * the domain boundary. */
+static int amr_box_owned(const orc_amr *A, int a, const int g[3])
 {
-    const int g[3] = {i, j, k};
     for (int ax = 0; ax < A->base.dim; ++ax) {
-        const int lo = A->lo[a][ax], hi = A->hi[a][ax], N = amr_N(A, a, ax);
-        const int inside = (g[ax] > lo && g[ax] < hi) || (g[ax] == lo && lo == 0) || (g[ax] == hi && hi == N - 1);
-        if (!inside) return 0;
+        const int N = amr_N(A, a, ax);
+        if (a == 0) {
+            if (g[ax] < 0 || g[ax] > N - 1) return 0;
+        } else {
+            const int lo = A->lo[a][ax], hi = A->hi[a][ax];
+            const int inside = (g[ax] > lo && g[ax] < hi) || (g[ax] == lo && lo == 0) || (g[ax] == hi && hi == N - 1);
+            if (!inside) return 0;
+        }
     }
     return 1;
 }
 
+/* Covered: the node coincides with a node of the next finer level's solve region.
+ * That node is either owned by the finer level or itself covered, so by induction
+ * the finest level whose region contains the point owns it. */
+static int amr_covered(const orc_amr *A, int a, const int g[3])
+{
+    if (a + 1 >= A->nlev) return 0;
+    const int g2[3] = {2 * g[0], 2 * g[1], A->base.dim == 3 ? 2 * g[2] : 0};
+    return amr_box_owned(A, a + 1, g2);
+}
+
 int orc_amr_owned(const orc_amr *A, int a, int i, int j, int k)
 {
-    if (a > 0 && !amr_in_box_owned_axes(A, a, i, j, k)) return 0;
-    if (a == 0) {
-        if (i < 0 || j < 0 || k < 0 || i >= amr_N(A, 0, 0) || j >= amr_N(A, 0, 1) || k >= amr_N(A, 0, 2)) return 0;
-    }
-    if (a + 1 < A->nlev) {
-        const int d3 = A->base.dim == 3;
-        if (orc_amr_owned(A, a + 1, 2 * i, 2 * j, d3 ? 2 * k : 0)) return 0;     /* covered */
-    }
-    return 1;
+    const int g[3] = {i, j, k};
+    return amr_box_owned(A, a, g) && !amr_covered(A, a, g);
 }
 
 static int amr_dirichlet(const orc_amr *A, int a, int g[3], int p)
@@ -742,7 +752,7 @@ void orc_amr_fill(const orc_amr *A, double *const *u)
         AMR_FOR_NODES(A, a, Pf, g, loc) {
             int even = 1;
             for (int ax = 0; ax < d; ++ax) even &= (g[ax] % 2 == 0);
-            if (!even || !orc_amr_owned(A, a, g[0], g[1], g[2])) continue;
+            if (!even || !amr_box_owned(A, a, g)) continue;
             int gc[3] = {g[0] / 2, g[1] / 2, d == 3 ? g[2] / 2 : 0};
             const long lc = amr_local(A, a - 1, gc);
             for (int p = 0; p < d; ++p) u[a - 1][p * Nc + lc] = u[a][p * Nf + loc];
@@ -755,7 +765,7 @@ void orc_amr_fill(const orc_amr *A, double *const *u)
         orc_amr_level_problem(A, a - 1, &Pc);
         const long Nf = orc_nnodes(&Pf), Nc = orc_nnodes(&Pc);
         AMR_FOR_NODES(A, a, Pf, g, loc) {
-            if (orc_amr_owned(A, a, g[0], g[1], g[2])) continue;
+            if (amr_box_owned(A, a, g)) continue;      /* owned, or covered (injected) */
             int outside = 0;
             for (int ax = 0; ax < d; ++ax)
                 if (g[ax] < 0 || g[ax] > amr_N(A, a, ax) - 1) outside = 1;
@@ -793,7 +803,21 @@ void orc_amr_residual(const orc_amr *A, double *const *psi, double *const *f, do
         orc_amr_level_problem(A, a, &P);
         const long N = orc_nnodes(&P);
         double *Ku = malloc(sizeof(double) * d * N);
-        orc_apply(&P, psi[a], u[a], Ku);
+        /* padding cells beyond a domain face are not part of the body */
+        const long nc = orc_ncells(&P);
+        double *pa = malloc(sizeof(double) * nc);
+        const int ncx = P.n[0] - 1, ncy = P.n[1] - 1;
+        for (long c = 0; c < nc; ++c) {
+            int C[3] = {(int)(c % ncx), (int)((c / ncx) % ncy), (int)(c / ((long)ncx * ncy))};
+            int in = 1;
+            for (int ax = 0; ax < d; ++ax) {
+                const int gc = a ? C[ax] + A->lo[a][ax] - 1 : C[ax];
+                if (gc < 0 || gc > amr_N(A, a, ax) - 2) in = 0;
+            }
+            pa[c] = in ? psi[a][c] : 0.0;
+        }
+        orc_apply(&P, pa, u[a], Ku);
+        free(pa);
         AMR_FOR_NODES(A, a, P, g, loc) {
             const int own = orc_amr_owned(A, a, g[0], g[1], g[2]);
             for (int p = 0; p < d; ++p) {

@@ -110,10 +110,13 @@ void orc_dJdpsi(const orc_problem *P, const double *u, const double *lam, double
  *    equation (K_a u_a)_n = f_a(n);
  *  - the other box nodes (interface) and the padding nodes are GHOSTS, filled from
  *    level a-1 by (bi/tri)linear interpolation (coincident nodes copy);
- *  - a level a-1 node coinciding with an owned level-a node is COVERED: its value
- *    is the injected fine value and it carries no equation; the other level a-1
+ *  - a level a-1 node coinciding with a level-a node of the box region (owned or
+ *    itself covered by level a+1) is COVERED: its value is the injected value of
+ *    the finest level whose region contains the point, and it carries no
+ *    equation; so every point is owned by exactly one level.  The other level a-1
  *    nodes obey the coarse equation with covered neighbours injected;
- *  - coarse cells inside the box hold the mean of their 2^d fine cells.
+ *  - coarse cells inside the box hold the mean of their 2^d fine cells; padding
+ *    cells beyond a domain face are not part of the body (their psi is ignored).
  * The padding layer gives every interface node a complete fine stencil, which
  * the multigrid restriction uses so that it is the same full weighting everywhere.
  */
@@ -125,7 +128,8 @@ typedef struct {
 
 /* Problem (grid, h, moduli, Dirichlet faces) of the padded patch grid of level a. */
 void orc_amr_level_problem(const orc_amr *A, int a, orc_problem *P);
-/* 1 if level-a node (global level-a indices) is owned by level a. */
+/* 1 if level-a node (global level-a indices) is owned by level a (in its box
+ * region and not covered by a finer level). */
 int  orc_amr_owned(const orc_amr *A, int a, int i, int j, int k);
 /* Coarse cells under each patch <- mean of the fine cells (finest first). */
 void orc_amr_coarsen_psi(const orc_amr *A, double *const *psi);

@@ -1,8 +1,10 @@
 """Pins of the oracle's block-structured refinement (composite problem of the
 reflux-free reading of Sec. 2.2): exact ghost interpolation of linear fields,
-coarse psi = fine means, a patch that covers the whole domain reproduces the
-uniformly refined solution (P10), and the composite problem reproduces affine
-displacement fields exactly (patch test through the coarse/fine interface)."""
+coarse psi = fine means, every point owned by exactly one level, a patch (or a
+nested pair of patches) that covers the whole domain reproduces the uniformly
+refined solution with the coarser levels holding its injection (P10), psi of
+padding cells beyond the domain is ignored, and the composite problem reproduces
+affine displacement fields exactly (patch test through the coarse/fine interface)."""
 import numpy as np
 import pytest
 
@@ -76,30 +78,92 @@ def test_coarse_psi_under_patch_is_fine_mean(oracle_lib):
                 assert c[J, I] == before.reshape(8, 8)[J, I]
 
 
-@pytest.mark.parametrize("dim,n0", [(2, 9), (3, 5)])
-def test_P10_patch_over_whole_domain_equals_uniform_fine_solution(oracle_lib, dim, n0):
-    nf = 2 * (n0 - 1) + 1
-    bits = (4, 4 | 8, 4) if dim == 2 else (16, 16, 16 | 32)
-    A = _amr(dim, n0, [((0,) * dim, (nf - 1,) * dim)], bits=bits)
-    rng_psi = lambda X, Y, Z: 0.05 + 0.95 * (0.5 + 0.5 * np.sin(7 * X + 3 * Y + 5 * Z))
-    psis = oracle.amr_coarsen_psi(A, _psi(A, rng_psi))
-    us, fs = _zeros(A), _zeros(A)
-    # Dirichlet data on the fine level (top face pulled), load on the fine level
-    P1 = A.level_problem(1)
-    X, Y, Z = level_coords(A, 1)
-    top = (Y == nf - 1) if dim == 2 else (Z == nf - 1)
-    us[1][(dim - 1) * P1.nnodes:dim * P1.nnodes][top] = 0.01
-    fs[1][:P1.nnodes] = W.uniform(5, P1.nnodes, -1, 1)
-    sol = dense_solve(A, psis, fs, us)
-    # uniform fine problem on the same nodes (strip the padding)
+@pytest.mark.parametrize("dim,n0,boxes", [
+    (2, 9, [((4, 4), (12, 12)), ((10, 10), (22, 22)), ((22, 22), (42, 42))]),
+    (2, 9, [((0, 4), (12, 16)), ((0, 10), (14, 30))]),
+    (3, 5, [((2, 2, 2), (6, 6, 6)), ((6, 6, 4), (10, 10, 10))]),
+])
+def test_every_point_is_owned_by_exactly_one_level(oracle_lib, dim, n0, boxes):
+    """Brute force over all levels: a point of the domain that lies in level a's
+    box region is owned by exactly one level (the finest whose region contains it)."""
+    A = _amr(dim, n0, boxes)
+    top = A.nlev - 1
+    owners = {}
+    region = []
+    for a in range(A.nlev):
+        X, Y, Z = level_coords(A, a)
+        N = A.global_n(a)
+        s = 2 ** (top - a)
+        for x, y, z in zip(X, Y, Z):
+            g = (int(x), int(y), int(z))
+            if not all(0 <= g[ax] <= N[ax] - 1 for ax in range(dim)):
+                continue
+            key = (g[0] * s, g[1] * s, g[2] * s if dim == 3 else 0)
+            if A.owned(a, *g):
+                owners[key] = owners.get(key, 0) + 1
+            if a == 0 or all((A.boxes[a - 1][0][ax] < g[ax] < A.boxes[a - 1][1][ax])
+                             or (g[ax] == A.boxes[a - 1][0][ax] == 0)
+                             or (g[ax] == A.boxes[a - 1][1][ax] == N[ax] - 1) for ax in range(dim)):
+                region.append(key)
+    assert region and all(owners.get(k, 0) == 1 for k in region)
+
+
+def _uniform_fine(dim, nf, bits, psi_cells, f, u):
     Pf = oracle.Problem(dim, (nf,) * dim, 1.0 / (nf - 1), 1.0, 0.6, 0.5, dirichlet=bits)
-    sl = (slice(1, -1),) * dim
-    def strip(v, comps):
-        shape = (comps,) + tuple(P1.n[::-1][3 - dim:])
-        return v.reshape(shape)[(slice(None),) + sl[::-1]].reshape(-1)
-    cells = psis[1].reshape(tuple(n - 1 for n in P1.n[::-1][3 - dim:]))[sl[::-1]].reshape(-1)
-    ref = oracle.direct_solve(Pf, cells, strip(fs[1], dim), strip(us[1], dim))
-    assert np.abs(strip(sol[1], dim) - ref).max() <= 1e-11 * np.abs(ref).max()
+    return oracle.direct_solve(Pf, psi_cells, f, u)
+
+
+def _strip(P, v, comps):
+    """drop the padding layer of a level array (nodes: comps > 0; cells: comps = 0)"""
+    d = P.dim
+    sl = (slice(1, -1),) * d
+    if comps == 0:
+        shape = tuple(n - 1 for n in P.n[::-1][3 - d:])
+        return v.reshape(shape)[sl].reshape(-1)
+    shape = (comps,) + tuple(P.n[::-1][3 - d:])
+    return v.reshape(shape)[(slice(None),) + sl].reshape(-1)
+
+
+@pytest.mark.parametrize("dim,n0,nest", [(2, 9, 1), (3, 5, 1), (2, 5, 2), (3, 3, 2)])
+def test_P10_patches_over_whole_domain_equal_uniform_fine_solution(oracle_lib, dim, n0, nest):
+    """One patch (nest = 1) or two nested patches (nest = 2) covering the whole
+    domain: the finest level holds the uniformly refined solution and every
+    coarser level its injection.  Padding cells beyond the domain carry psi = 5,
+    which must not enter the composite problem."""
+    nf = (n0 - 1) * 2 ** nest + 1
+    boxes = [((0,) * dim, ((n0 - 1) * 2 ** a,) * dim) for a in range(1, nest + 1)]
+    bits = (4, 4 | 8, 4) if dim == 2 else (16, 16, 16 | 32)
+    A = _amr(dim, n0, boxes, bits=bits)
+    rng_psi = lambda X, Y, Z: 0.05 + 0.95 * (0.5 + 0.5 * np.sin(7 * X + 3 * Y + 5 * Z))
+    psis = []
+    for a in range(A.nlev):
+        from _amr import level_cell_centres
+        v = rng_psi(*level_cell_centres(A, a))
+        if a > 0:
+            v = np.where(cells_inside_domain(A, a), v, 5.0)
+        psis.append(np.ascontiguousarray(v))
+    psis = oracle.amr_coarsen_psi(A, psis)
+    us, fs = _zeros(A), _zeros(A)
+    Pt = A.level_problem(nest)
+    for a in range(A.nlev):
+        P = A.level_problem(a)
+        X, Y, Z = level_coords(A, a)
+        Na = A.global_n(a)
+        top = (Y == Na[1] - 1) if dim == 2 else (Z == Na[2] - 1)
+        us[a][(dim - 1) * P.nnodes:dim * P.nnodes][top] = 0.01
+    fs[nest][:Pt.nnodes] = W.uniform(5, Pt.nnodes, -1, 1)
+    sol = dense_solve(A, psis, fs, us)
+    ref = _uniform_fine(dim, nf, bits, _strip(Pt, psis[nest], 0), _strip(Pt, fs[nest], dim), _strip(Pt, us[nest], dim))
+    scale = np.abs(ref).max()
+    assert np.abs(_strip(Pt, sol[nest], dim) - ref).max() <= 1e-11 * scale
+    # coarser levels hold the injection of the fine solution
+    R = ref.reshape((dim,) + (nf,) * dim)
+    for a in range(nest):
+        P = A.level_problem(a)
+        s = 2 ** (nest - a)
+        sub = (slice(None),) + (slice(None, None, s),) * dim
+        got = sol[a] if a == 0 else _strip(P, sol[a], dim)
+        assert np.abs(got - R[sub].reshape(-1)).max() <= 1e-11 * scale, a
 
 
 @pytest.mark.parametrize("dim,n0,boxes", [
