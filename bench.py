@@ -52,10 +52,11 @@ def workload(name: str):
     raise SystemExit(f"unknown workload {name}")
 
 
-def workload_config(wk, precision):
+def workload_config(wk, precision, inner=1):
     return {"workload": f"{wk.name} {'x'.join(str(v) for v in wk.n[:wk.dim])} nodes",
             "dofs": wk.ndofs, "moduli_c11_c12_c44": list(wk.moduli), "psi_min": wk.psi_min,
             "precision": precision, "tol": 1e-10, "cycle": "V(2,2) damped Jacobi",
+            "fp32_vcycles_per_fp64_residual": inner if precision == "mixed" else None,
             "omega": wk.omega, "l2": "flushed (256 MB write) between timed steps"}
 
 
@@ -68,7 +69,7 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 100 ms."""
+    """nvidia-smi clocks and throttle reasons sampled every 50 ms."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -78,7 +79,7 @@ class ClockSampler:
         self.proc = None
         try:
             self.proc = subprocess.Popen(
-                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100",
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "50",
                  "-i", str(gpu_index)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except (OSError, FileNotFoundError):
             return
@@ -165,6 +166,20 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def aggregate_replicas(total_ms, ndofs, steps, dist=None, device="cpu"):
+    """Replicas only: every rank solved ``steps`` copies of its own problem in
+    ``total_ms``.  The job time is the maximum over ranks (one float64 all-reduce,
+    outside the data path) and the value is the dofs solved by all ranks per
+    second, in MDOF/s.  Returns (job time in ms, value)."""
+    import torch
+    world = dist.get_world_size() if dist else 1
+    t = torch.tensor([total_ms], device=device, dtype=torch.float64)
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    job_ms = float(t.item())
+    return job_ms, world * ndofs * steps / (job_ms / 1e3) / 1e6
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     torch.cuda.set_device(local_rank)
@@ -191,7 +206,7 @@ def run_ours(args, rank, world, local_rank):
 
     psi_d, f_d, u0_d = t64(wk.psi), t64(wk.f), t64(wk.u0)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    opts = {"omega": wk.omega, "tol": 1e-10}
+    opts = {"omega": wk.omega, "tol": 1e-10, "inner_cycles": args.inner if args.precision == "mixed" else 1}
 
     def timed_solves(g, nsteps, nwarm):
         with torch.cuda.stream(stream):
@@ -229,13 +244,8 @@ def run_ours(args, rank, world, local_rank):
     t_wall1 = time.time()
     if dist:
         dist.barrier()
-    total_ms = sum(ms)
-    tmax = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-    if dist:
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-    total_ms = float(tmax.item())
+    total_ms, value = aggregate_replicas(sum(ms), wk.ndofs, args.steps, dist, dev)
     ms_per_step = total_ms / args.steps
-    value = world * wk.ndofs * args.steps / (total_ms / 1e3) / 1e6
     cycles = infos[-1].cycles
     launches = sum(i_.launches for i_ in infos)
 
@@ -243,19 +253,22 @@ def run_ours(args, rank, world, local_rank):
     ms_k, bytes_k, flops_k = C.c_double(), C.c_double(), C.c_double()
     kid = {"residual64": _capi.SBM_K_RESIDUAL64, "jacobi": _capi.SBM_K_JACOBI}[args.roofline_kernel]
     with torch.cuda.stream(stream):
-        _capi.check(sbm.lib().sbm_time_kernel(gmix._h, kid, 20, C.byref(ms_k), C.byref(bytes_k), C.byref(flops_k)),
-                    gmix._h)
+        _capi.check(sbm.lib().sbm_time_kernel(gmix._h, kid, 20, 1, C.byref(ms_k), C.byref(bytes_k),
+                                              C.byref(flops_k)), gmix._h)
+        ms_w, _, _ = C.c_double(), None, None
+        _capi.check(sbm.lib().sbm_time_kernel(gmix._h, kid, 20, 0, C.byref(ms_w), C.byref(bytes_k),
+                                              C.byref(flops_k)), gmix._h)
     hbm_peak, peak_kind = peaks()
     if args.roofline_kernel == "residual64":
         achieved = flops_k.value / (ms_k.value * 1e-3) / 1e9
-        roof = {"bound": "alu", "kernel": "k_sweep3<double,float,residual> (FP64 defect residual)",
+        roof = {"bound": "alu", "kernel": "k_sweep3_dp<residual> (FP64 defect residual, finest level)",
                 "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
                 "frac": achieved / FP64_PEAK_GFLOPS, "peak_kind": "nominal FP64 rate of the hardware table",
                 "algorithmic_flops": flops_k.value, "algorithmic_bytes": bytes_k.value,
-                "ms_per_launch": ms_k.value, "traffic": None}
+                "ms_per_launch": ms_k.value, "ms_per_launch_l2_warm": ms_w.value, "traffic": None}
     else:
         achieved = bytes_k.value / (ms_k.value * 1e-3) / 1e9
-        roof = {"bound": "hbm", "kernel": "k_sweep3<float,float,jacobi> (FP32 Jacobi sweep, finest level)",
+        roof = {"bound": "hbm", "kernel": "k_sweep3_f2<Jacobi> (FP32 TMA-staged Jacobi sweep, finest level)",
                 "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
                 "peak_kind": f"{peak_kind} (copy bandwidth)", "algorithmic_bytes": bytes_k.value,
                 "algorithmic_flops": flops_k.value, "ms_per_launch": ms_k.value, "traffic": None,
@@ -268,7 +281,10 @@ def run_ours(args, rank, world, local_rank):
     if args.precision == "mixed" and not args.skip_fp64:
         g64 = make_grid("fp64")
         timed_solves(g64, 0, 1)
+        opts_mixed = dict(opts)
+        opts["inner_cycles"] = 1
         i64, ms64, u64 = timed_solves(g64, max(1, min(args.steps, 2)), 0)
+        opts.update(opts_mixed)
         fp64 = {"ms_per_step": statistics.mean(ms64), "value": wk.ndofs / (statistics.mean(ms64) / 1e3) / 1e6,
                 "cycles": i64[-1].cycles,
                 "max_rel_diff_vs_mixed": float((u64 - u).abs().max() / u64.abs().max())}
@@ -308,19 +324,19 @@ def run_ours(args, rank, world, local_rank):
 
     cpu = None
     if rank == 0 and world == 1 and not args.skip_cpu:
-        per_cycle = oracle_cycle_sample(wk, 1)
+        per_cycle = oracle_cycle_sample(wk, 2)
         ncyc, src = oracle_cycles_to_tol(args.workload)
         if ncyc is None:
             ncyc, src = (fp64 or {}).get("cycles", cycles), "GPU FP64 cycle count"
         cpu = {"value": wk.ndofs / (per_cycle * ncyc) / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"1 full-size oracle V-cycle ({per_cycle:.2f} s, single thread) x {ncyc} cycles to "
+               "sample": f"2 full-size oracle V-cycles ({per_cycle:.2f} s each, single thread); x {ncyc} cycles to "
                          f"1e-10 ({src})"}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64",
-                "data": "synthetic (seeded damage field)", "config": workload_config(wk, args.precision),
+                "data": "synthetic (seeded damage field)", "config": workload_config(wk, args.precision, args.inner),
                 "cycles_to_tol": cycles, "vcycles_per_s": cycles / (ms_per_step / 1e3),
                 "fp64_solve": fp64, "roofline": roof, "cpu_baseline": cpu,
                 "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
@@ -335,11 +351,12 @@ def run_ours(args, rank, world, local_rank):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="damage_3d_129")
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--inner", type=int, default=8, help="FP32 V-cycles per FP64 defect residual (mixed)")
     ap.add_argument("--roofline-kernel", choices=["residual64", "jacobi"], default="jacobi")
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per launch of the roofline kernel from an ncu capture")

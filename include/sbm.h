@@ -189,9 +189,53 @@ enum { SBM_K_RESIDUAL64 = 0, SBM_K_JACOBI = 1, SBM_K_RESIDUAL = 2 };
  *   SBM_K_RESIDUAL    the V-cycle residual in the V-cycle precision
  * Bytes count one read of u, f and psi and one write of the output per node;
  * flops count the sum-factorised cell arithmetic per cell plus the per-node
- * gather and update.  Uses the level's work buffers (overwrites them). */
-sbm_status sbm_time_kernel(sbm_grid grid, int which, int reps, double *ms_per_launch,
+ * gather and update.  flush_l2 != 0: before every launch a 256 MB scratch buffer
+ * (allocated for the call) is written so that the launch reads its inputs from
+ * HBM, and each launch is timed by its own pair of events.  Uses the level's work
+ * buffers (overwrites them). */
+sbm_status sbm_time_kernel(sbm_grid grid, int which, int reps, int flush_l2, double *ms_per_launch,
                            double *bytes_per_launch, double *flops_per_launch);
+
+/* ---- block-structured refinement (Sec. 2.2) ----
+ * A grid may carry up to 8 refinement patches, level a refining level a-1 by 2
+ * on one node box.  The composite problem: a patch node inside the box (or on a
+ * box face lying on the domain boundary) obeys the fine equation; the parent node
+ * under it is covered (it takes the injected fine value); the patch's other nodes
+ * (its faces inside the domain, and one layer of padding nodes around the box) are
+ * ghosts interpolated from the parent; parent cells under the patch hold the mean
+ * of their fine cells (Sec. 2.4).  Every fine stencil of an owned node and every
+ * full-weighting stencil of a covered node is complete, so no coarse/fine flux
+ * correction ("reflux") is applied.  Patch arrays cover the box grown by one
+ * padding node per side: nodes [lo-1, hi+1], cells [lo-1, hi], packed x fastest,
+ * component-major; values at padding nodes are outputs only. */
+typedef struct {
+    int lo[3], hi[3];      /* node box in the new level's indices; even corners; 2D: lo[2] = hi[2] = 0 */
+} sbm_box;
+
+/* Append patch level a = (patches so far) + 1.  The box must lie inside the parent
+ * patch with at least one parent cell to spare on every side that is not on the
+ * domain boundary.  Allocates the patch storage; SBM_ERR_ARG on a bad box. */
+sbm_status sbm_amr_add_level(sbm_grid grid, const sbm_box *box);
+/* psi of patch level a (device, FP64) on the cells of the padded box, floored at
+ * psi_min.  Covered parent cells are replaced by fine means at the next solve. */
+sbm_status sbm_amr_set_psi(sbm_grid grid, int a, const double *psi_cells, double psi_min);
+/* Right-hand side of patch level a (device, FP64, padded-box nodes). */
+sbm_status sbm_amr_set_source(sbm_grid grid, int a, const double *f_nodes);
+/* Composite solve.  u[0]: base level nodes (packed, device); u[a], a >= 1: padded
+ * box nodes of patch a (device).  In: initial guess with the Dirichlet values (the
+ * face values of sbm_set_bc are written on the base level; patch Dirichlet values
+ * are taken from u[a]).  Out: the composite solution with ghosts filled.  Each
+ * cycle: FP64 composite residual; patches top-down (smoothing of the correction,
+ * full-weighting of its residual onto the covered parent nodes); the base
+ * multigrid V-cycle; patches bottom-up (parent correction prolongated and ghosts
+ * filled, smoothing); u += e on owned dofs.  SBM_MIXED runs the cycle in FP32.
+ * opts->inner_cycles is ignored.  Status as for sbm_solve. */
+sbm_status sbm_amr_solve(sbm_grid grid, double *const *u, const sbm_opts *opts, sbm_info *info);
+/* Composite residual of u (layouts as sbm_amr_solve): r[a] = f_a - K_a u_a on the
+ * owned free dofs of level a, 0 on ghost, covered and Dirichlet dofs; *norm (host)
+ * = its 2-norm over all levels.  u is not modified.  SBM_ERR_STATE when no patch
+ * level has been added (use sbm_residual). */
+sbm_status sbm_amr_residual(sbm_grid grid, double *const *u, double *const *r, double *norm);
 
 /* ---- allocation-free entry point ---- */
 

@@ -171,6 +171,40 @@ class Grid:
         return SolveInfo(info.status, info.cycles, info.vcycles, info.levels, info.r0, info.relres,
                          [hist[i] for i in range(n)], info.solve_ms, info.launches)
 
+    # -- block-structured refinement
+    def amr_add_level(self, lo, hi):
+        b = _capi.sbm_box()
+        b.lo[:] = (list(lo) + [0, 0, 0])[:3]
+        b.hi[:] = (list(hi) + [0, 0, 0])[:3]
+        self._check(lib().sbm_amr_add_level(self._h, C.byref(b)))
+        self.boxes = getattr(self, "boxes", []) + [(tuple(b.lo), tuple(b.hi))]
+
+    def amr_set_psi(self, a: int, psi: torch.Tensor, psi_min: float):
+        self._check(lib().sbm_amr_set_psi(self._h, a, _ptr(psi), psi_min))
+
+    def amr_set_source(self, a: int, f: torch.Tensor):
+        self._check(lib().sbm_amr_set_source(self._h, a, _ptr(f)))
+
+    @staticmethod
+    def _ptr_array(ts):
+        arr = (C.c_void_p * len(ts))()
+        for i, t in enumerate(ts):
+            arr[i] = _ptr(t)
+        return arr
+
+    def amr_solve(self, us, raise_on_fail: bool = True, **opts) -> SolveInfo:
+        o = make_opts(**opts)
+        info, hist = self._info(o.max_cycles)
+        st = lib().sbm_amr_solve(self._h, self._ptr_array(us), C.byref(o), C.byref(info))
+        self._check(st, allow=(SBM_OK,) if raise_on_fail else (SBM_OK, SBM_ERR_NOCONV, SBM_ERR_DIVERGED))
+        return self._to_info(info, hist)
+
+    def amr_residual(self, us):
+        rs = [torch.empty_like(u) for u in us]
+        nrm = C.c_double()
+        self._check(lib().sbm_amr_residual(self._h, self._ptr_array(us), self._ptr_array(rs), C.byref(nrm)))
+        return rs, nrm.value
+
     # -- single steps of the hot path
     def apply(self, level: int, u: torch.Tensor, fp32: bool = False) -> torch.Tensor:
         out = torch.empty_like(u)

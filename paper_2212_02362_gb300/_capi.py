@@ -31,6 +31,10 @@ class sbm_opts(C.Structure):
                 ("use_graph", C.c_int)]
 
 
+class sbm_box(C.Structure):
+    _fields_ = [("lo", C.c_int * 3), ("hi", C.c_int * 3)]
+
+
 class sbm_info(C.Structure):
     _fields_ = [("status", C.c_int), ("cycles", C.c_int), ("vcycles", C.c_int), ("levels", C.c_int),
                 ("r0", C.c_double), ("relres", C.c_double), ("history", C.POINTER(C.c_double)),
@@ -65,8 +69,13 @@ _SIGS = {
     "sbm_get_psi": (C.c_int, [_grid, C.c_int, _dptr]),
     "sbm_bottom_correct": (C.c_int, [_grid, C.c_int, _dptr, _dptr]),
     "sbm_dJdpsi": (C.c_int, [_grid, _dptr, _dptr, _dptr]),
-    "sbm_time_kernel": (C.c_int, [_grid, C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
+    "sbm_time_kernel": (C.c_int, [_grid, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                   C.POINTER(C.c_double)]),
+    "sbm_amr_add_level": (C.c_int, [_grid, C.POINTER(sbm_box)]),
+    "sbm_amr_set_psi": (C.c_int, [_grid, C.c_int, _dptr, C.c_double]),
+    "sbm_amr_set_source": (C.c_int, [_grid, C.c_int, _dptr]),
+    "sbm_amr_solve": (C.c_int, [_grid, C.POINTER(C.c_void_p), C.POINTER(sbm_opts), C.POINTER(sbm_info)]),
+    "sbm_amr_residual": (C.c_int, [_grid, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.POINTER(C.c_double)]),
     "sbm_residual_noalloc": (C.c_int, [C.c_int, C.POINTER(C.c_int), C.c_double, C.POINTER(C.c_double),
                                        C.POINTER(C.c_uint), _dptr, _dptr, _dptr, _dptr, C.POINTER(C.c_double),
                                        C.c_void_p]),

@@ -1,0 +1,353 @@
+// k_amr.cu — kernels of the block-structured refinement (Sec. 2.2): ownership
+// masks of the composite problem, injection of fine values into covered coarse
+// nodes, ghost fill of a patch's interface and padding nodes from its parent
+// level (coarse-to-fine interpolation), full-weighting restriction of a patch's
+// residual onto the covered parent nodes, prolongation of a parent correction
+// into a patch, the owned-dof update and the composite norm.
+//
+// A patch of level a refines level a-1 by 2 on one node box [lo, hi] (level-a
+// indices).  Its storage is the box grown by one padding node per side; `AmrInfo`
+// carries the global extents, the box, the storage origin, the child box and the
+// domain Dirichlet faces, from which every node's role follows:
+//   owned   - inside the box on every axis, or on a box face lying on the domain
+//             boundary, and not covered by an owned node of the child patch;
+//   covered - coincident with an owned node of the child: carries the injected
+//             fine value and no equation of its own;
+//   ghost   - the other storage nodes: interpolated from the parent level.
+#include "sbm_common.cuh"
+
+namespace sbm {
+
+namespace {
+
+__host__ __device__ __forceinline__ bool axes_owned(const AmrInfo &L, const int g[3])
+{
+    for (int ax = 0; ax < L.dim; ++ax) {
+        if (L.is_base) {
+            if (g[ax] < 0 || g[ax] > L.N[ax] - 1) return false;
+        } else {
+            const bool in = (g[ax] > L.lo[ax] && g[ax] < L.hi[ax]) || (g[ax] == L.lo[ax] && L.lo[ax] == 0) ||
+                            (g[ax] == L.hi[ax] && L.hi[ax] == L.N[ax] - 1);
+            if (!in) return false;
+        }
+    }
+    return true;
+}
+
+// child-level coordinates g2 owned by the child's axes rule
+__host__ __device__ __forceinline__ bool child_axes_owned(const AmrInfo &L, const int g2[3])
+{
+    for (int ax = 0; ax < L.dim; ++ax) {
+        const int Nc = 2 * (L.N[ax] - 1) + 1;
+        const bool in = (g2[ax] > L.clo[ax] && g2[ax] < L.chi[ax]) || (g2[ax] == L.clo[ax] && L.clo[ax] == 0) ||
+                        (g2[ax] == L.chi[ax] && L.chi[ax] == Nc - 1);
+        if (!in) return false;
+    }
+    return true;
+}
+
+__host__ __device__ __forceinline__ bool covered(const AmrInfo &L, const int g[3])
+{
+    if (!L.has_child) return false;
+    const int g2[3] = {2 * g[0], 2 * g[1], L.dim == 3 ? 2 * g[2] : 0};
+    return child_axes_owned(L, g2);
+}
+
+__host__ __device__ __forceinline__ bool owned(const AmrInfo &L, const int g[3])
+{
+    return axes_owned(L, g) && !covered(L, g);
+}
+
+__host__ __device__ __forceinline__ bool domain_dirichlet(const AmrInfo &L, const int g[3], int p)
+{
+    const unsigned m = L.dm[p];
+    for (int ax = 0; ax < L.dim; ++ax) {
+        if ((m >> (2 * ax)) & 1u && g[ax] == 0) return true;
+        if ((m >> (2 * ax + 1)) & 1u && g[ax] == L.N[ax] - 1) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ bool inside_domain(const AmrInfo &L, const int g[3])
+{
+    for (int ax = 0; ax < L.dim; ++ax)
+        if (g[ax] < 0 || g[ax] > L.N[ax] - 1) return false;
+    return true;
+}
+
+// Storage node of the current thread: (i,j,k) local, g global.
+__device__ __forceinline__ bool thread_node(const Geom &s, const AmrInfo &L, int &i, int &j, int &k, int g[3])
+{
+    i = blockIdx.x * blockDim.x + threadIdx.x;
+    j = blockIdx.y * blockDim.y + threadIdx.y;
+    k = blockIdx.z * blockDim.z + threadIdx.z;
+    if (i >= s.nx || j >= s.ny || k >= s.nz) return false;
+    g[0] = i + L.org[0];
+    g[1] = j + L.org[1];
+    g[2] = k + L.org[2];
+    return true;
+}
+
+// Value of a parent-level field at child global coordinates g (linear
+// interpolation; coincident nodes copy); 0 outside the parent's storage.
+template <typename T>
+__device__ __forceinline__ T parent_interp(const Geom &sp, const AmrInfo &Lp, const T *up, int p, const int g[3])
+{
+    T s = T(0);
+    int nodd = 0;
+    for (int ax = 0; ax < Lp.dim; ++ax) nodd += g[ax] & 1;
+    for (int c = 0; c < (1 << Lp.dim); ++c) {
+        int l[3] = {0, 0, 0};
+        bool skip = false;
+        for (int ax = 0; ax < Lp.dim; ++ax) {
+            const int bit = (c >> ax) & 1;
+            if (!(g[ax] & 1) && bit) skip = true;
+            l[ax] = (g[ax] >> 1) + ((g[ax] & 1) ? bit : 0) - Lp.org[ax];
+        }
+        if (skip) continue;
+        if (l[0] < 0 || l[1] < 0 || l[2] < 0 || l[0] >= sp.nx || l[1] >= sp.ny || l[2] >= sp.nz) continue;
+        s += up[p * sp.cs + gidx(sp, l[0], l[1], l[2])];
+    }
+    return s * (T(1) / T(1 << nodd));
+}
+
+__global__ void k_amr_mask(const Geom s, const AmrInfo L, double *r)
+{
+    int i, j, k, g[3];
+    if (!thread_node(s, L, i, j, k, g)) return;
+    const bool own = owned(L, g);
+    const long long o = gidx(s, i, j, k);
+    for (int p = 0; p < L.dim; ++p)
+        if (!own || domain_dirichlet(L, g, p)) r[p * s.cs + o] = 0.0;
+}
+
+__global__ void k_amr_inject(const Geom sc, const AmrInfo Lc, const Geom sp, const AmrInfo Lp, const double *uc,
+                             double *up)
+{
+    int i, j, k, g[3];
+    if (!thread_node(sc, Lc, i, j, k, g)) return;
+    for (int ax = 0; ax < Lc.dim; ++ax)
+        if (g[ax] & 1) return;
+    if (!axes_owned(Lc, g)) return;
+    const int lp[3] = {g[0] / 2 - Lp.org[0], g[1] / 2 - Lp.org[1], Lc.dim == 3 ? g[2] / 2 - Lp.org[2] : 0};
+    if (lp[0] < 0 || lp[1] < 0 || lp[2] < 0 || lp[0] >= sp.nx || lp[1] >= sp.ny || lp[2] >= sp.nz) return;
+    const long long oc = gidx(sc, i, j, k), op = gidx(sp, lp[0], lp[1], lp[2]);
+    for (int p = 0; p < Lc.dim; ++p) up[p * sp.cs + op] = uc[p * sc.cs + oc];
+}
+
+// mode 0: ghosts <- interpolated parent values (owned/active nodes untouched).
+// mode 1: correction prolongation: nodes solved on this level (inside the box or
+//         on a domain face) += interpolated parent correction; ghosts <- it.
+template <typename T>
+__global__ void k_amr_ghost(const Geom sc, const AmrInfo Lc, const Geom sp, const AmrInfo Lp, T *uc, const T *up,
+                            int mode)
+{
+    int i, j, k, g[3];
+    if (!thread_node(sc, Lc, i, j, k, g)) return;
+    const long long o = gidx(sc, i, j, k);
+    const bool solved = axes_owned(Lc, g);
+    const bool in = inside_domain(Lc, g);
+    for (int p = 0; p < Lc.dim; ++p) {
+        const T v = in ? parent_interp<T>(sp, Lp, up, p, g) : T(0);
+        if (!solved) uc[p * sc.cs + o] = v;
+        else if (mode == 1 && !domain_dirichlet(Lc, g, p)) uc[p * sc.cs + o] += v;
+    }
+}
+
+// rhs_parent at covered parent nodes <- full weighting of the child residual
+// (the child nodes of the stencil are all inside the child box).
+template <typename T>
+__global__ void k_amr_restrict(const Geom sc, const AmrInfo Lc, const Geom sp, const AmrInfo Lp, const T *rc, T *rhsp)
+{
+    int i, j, k, g[3];
+    if (!thread_node(sp, Lp, i, j, k, g)) return;
+    if (!covered(Lp, g)) return;
+    const bool d3 = Lp.dim == 3;
+    const T w[3] = {T(0.5), T(1), T(0.5)};
+    const T scale = d3 ? T(0.125) : T(0.25);
+    const long long op = gidx(sp, i, j, k);
+    for (int p = 0; p < Lp.dim; ++p) {
+        T s = T(0);
+        if (!domain_dirichlet(Lp, g, p)) {
+            for (int dk = (d3 ? -1 : 0); dk <= (d3 ? 1 : 0); ++dk)
+                for (int dj = -1; dj <= 1; ++dj)
+                    for (int di = -1; di <= 1; ++di) {
+                        const int li = 2 * g[0] + di - Lc.org[0], lj = 2 * g[1] + dj - Lc.org[1];
+                        const int lk = d3 ? 2 * g[2] + dk - Lc.org[2] : 0;
+                        if (li < 0 || lj < 0 || lk < 0 || li >= sc.nx || lj >= sc.ny || lk >= sc.nz) continue;
+                        s += w[di + 1] * w[dj + 1] * (d3 ? w[dk + 1] : T(1)) * rc[p * sc.cs + gidx(sc, li, lj, lk)];
+                    }
+            s *= scale;
+        }
+        rhsp[p * sp.cs + op] = s;
+    }
+}
+
+// u += e on owned free dofs.
+template <typename T>
+__global__ void k_amr_update(const Geom s, const AmrInfo L, const T *e, double *u)
+{
+    int i, j, k, g[3];
+    if (!thread_node(s, L, i, j, k, g)) return;
+    if (!owned(L, g)) return;
+    const long long o = gidx(s, i, j, k);
+    for (int p = 0; p < L.dim; ++p)
+        if (!domain_dirichlet(L, g, p)) u[p * s.cs + o] += double(e[p * s.cs + o]);
+}
+
+// per-block sums of squares of a masked residual (fixed order), then rounded to T
+template <typename TO>
+__global__ void k_amr_sumsq_round(const Geom s, const AmrInfo L, const double *r, TO *out, double *part)
+{
+    __shared__ double red[256];
+    int i, j, k, g[3];
+    double acc = 0.0;
+    if (thread_node(s, L, i, j, k, g)) {
+        const long long o = gidx(s, i, j, k);
+        for (int p = 0; p < L.dim; ++p) {
+            const double v = r[p * s.cs + o];
+            acc += v * v;
+            if (out) out[p * s.cs + o] = TO(v);
+        }
+    }
+    const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    red[tid] = acc;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (tid < w) red[tid] += red[tid + w];
+        __syncthreads();
+    }
+    if (tid == 0) part[blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)] = red[0];
+}
+
+// Parent cells inside the child box <- mean of their 2^d child cells.
+__global__ void k_amr_coarsen_psi(const Geom sc, const AmrInfo Lc, const Geom sp, const AmrInfo Lp,
+                                  const double *psic, double *psip)
+{
+    int i, j, k, g[3];
+    if (!thread_node(sp, Lp, i, j, k, g)) return;     // g = global index of the parent cell
+    if (i >= sp.nx - 1 || j >= sp.ny - 1 || (Lp.dim == 3 && k >= sp.nz - 1)) return;
+    for (int ax = 0; ax < Lp.dim; ++ax)
+        if (2 * g[ax] < Lc.lo[ax] || 2 * g[ax] + 2 > Lc.hi[ax]) return;
+    double s = 0.0;
+    const int nc = 1 << Lp.dim;
+    for (int c = 0; c < nc; ++c) {
+        const int li = 2 * g[0] + (c & 1) - Lc.org[0], lj = 2 * g[1] + ((c >> 1) & 1) - Lc.org[1];
+        const int lk = Lp.dim == 3 ? 2 * g[2] + ((c >> 2) & 1) - Lc.org[2] : 0;
+        s += psic[gidx(sc, li, lj, lk)];
+    }
+    psip[gidx(sp, i, j, k)] = s / nc;
+}
+
+// cells of a padded box: packed (i + (nx-1)*(j + (ny-1)*k)) -> node-indexed storage
+__global__ void k_amr_set_cells(const Geom s, const double *packed, double psi_min, double *lev, int *bad)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z * blockDim.z + threadIdx.z;
+    const int ncx = s.nx - 1, ncy = s.ny - 1, ncz = s.dim == 3 ? s.nz - 1 : 1;
+    if (i >= ncx || j >= ncy || k >= ncz) return;
+    const double v = packed[i + (long long)ncx * (j + (long long)ncy * k)];
+    if (!isfinite(v)) atomicAdd(bad, 1);
+    lev[gidx(s, i, j, k)] = fmax(v, psi_min);
+}
+
+const dim3 kAmrBlock(32, 4, 2);
+inline dim3 amr_grid(const Geom &s) { return dim3((s.nx + 31) / 32, (s.ny + 3) / 4, (s.nz + 1) / 2); }
+
+}  // namespace
+
+long long amr_blocks(const Geom &s)
+{
+    const dim3 g = amr_grid(s);
+    return (long long)g.x * g.y * g.z;
+}
+
+bool amr_owned_host(const AmrInfo &L, int i, int j, int k)
+{
+    const int g[3] = {i, j, k};
+    return owned(L, g);
+}
+
+cudaError_t launch_amr_mask(const Geom &s, const AmrInfo &L, double *r, cudaStream_t st)
+{
+    k_amr_mask<<<amr_grid(s), kAmrBlock, 0, st>>>(s, L, r);
+    ++g_launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_amr_inject(const Geom &sc, const AmrInfo &Lc, const Geom &sp, const AmrInfo &Lp, const double *uc,
+                              double *up, cudaStream_t st)
+{
+    k_amr_inject<<<amr_grid(sc), kAmrBlock, 0, st>>>(sc, Lc, sp, Lp, uc, up);
+    ++g_launches;
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_amr_ghost(const Geom &sc, const AmrInfo &Lc, const Geom &sp, const AmrInfo &Lp, T *uc, const T *up,
+                             int mode, cudaStream_t st)
+{
+    k_amr_ghost<T><<<amr_grid(sc), kAmrBlock, 0, st>>>(sc, Lc, sp, Lp, uc, up, mode);
+    ++g_launches;
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_amr_restrict(const Geom &sc, const AmrInfo &Lc, const Geom &sp, const AmrInfo &Lp, const T *rc,
+                                T *rhsp, cudaStream_t st)
+{
+    k_amr_restrict<T><<<amr_grid(sp), kAmrBlock, 0, st>>>(sc, Lc, sp, Lp, rc, rhsp);
+    ++g_launches;
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_amr_update(const Geom &s, const AmrInfo &L, const T *e, double *u, cudaStream_t st)
+{
+    k_amr_update<T><<<amr_grid(s), kAmrBlock, 0, st>>>(s, L, e, u);
+    ++g_launches;
+    return cudaGetLastError();
+}
+
+template <typename TO>
+cudaError_t launch_amr_sumsq_round(const Geom &s, const AmrInfo &L, const double *r, TO *out, double *part,
+                                   cudaStream_t st)
+{
+    k_amr_sumsq_round<TO><<<amr_grid(s), kAmrBlock, 0, st>>>(s, L, r, out, part);
+    ++g_launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_amr_coarsen_psi(const Geom &sc, const AmrInfo &Lc, const Geom &sp, const AmrInfo &Lp,
+                                   const double *psic, double *psip, cudaStream_t st)
+{
+    k_amr_coarsen_psi<<<amr_grid(sp), kAmrBlock, 0, st>>>(sc, Lc, sp, Lp, psic, psip);
+    ++g_launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_amr_set_cells(const Geom &s, const double *packed, double psi_min, double *lev, int *bad,
+                                 cudaStream_t st)
+{
+    k_amr_set_cells<<<amr_grid(s), kAmrBlock, 0, st>>>(s, packed, psi_min, lev, bad);
+    ++g_launches;
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_amr_ghost<double>(const Geom &, const AmrInfo &, const Geom &, const AmrInfo &, double *,
+                                              const double *, int, cudaStream_t);
+template cudaError_t launch_amr_ghost<float>(const Geom &, const AmrInfo &, const Geom &, const AmrInfo &, float *,
+                                             const float *, int, cudaStream_t);
+template cudaError_t launch_amr_restrict<double>(const Geom &, const AmrInfo &, const Geom &, const AmrInfo &,
+                                                 const double *, double *, cudaStream_t);
+template cudaError_t launch_amr_restrict<float>(const Geom &, const AmrInfo &, const Geom &, const AmrInfo &,
+                                                const float *, float *, cudaStream_t);
+template cudaError_t launch_amr_update<double>(const Geom &, const AmrInfo &, const double *, double *, cudaStream_t);
+template cudaError_t launch_amr_update<float>(const Geom &, const AmrInfo &, const float *, double *, cudaStream_t);
+template cudaError_t launch_amr_sumsq_round<double>(const Geom &, const AmrInfo &, const double *, double *, double *,
+                                                    cudaStream_t);
+template cudaError_t launch_amr_sumsq_round<float>(const Geom &, const AmrInfo &, const double *, float *, double *,
+                                                   cudaStream_t);
+
+}  // namespace sbm

@@ -24,15 +24,23 @@ __device__ __forceinline__ void node_of(const Geom &g, long long t, int &i, int 
 
 // ---------------------------------------------------------------- transfers
 
+// Launch geometry of the node-wise kernels: a 3D grid of (32, 4, 2) blocks covers
+// (nx, ny, nz) directly, so no index decoding by division is needed.
+const dim3 kNodeBlock(32, 4, 2);
+inline dim3 node_grid(const Geom &g)
+{
+    return dim3((g.nx + 31) / 32, (g.ny + 3) / 4, (g.nz + 1) / 2);
+}
+
 // r_c = P^T r_f / 2^d on free coarse dofs (Sec. 2.2 level transfers); coarse
 // node (I,J,K) sits on fine node (2I,2J,2K), the linear weights are 1, 1/2.
 template <typename T>
 __global__ void k_restrict(const Geom gf, const Geom gc, const T *__restrict__ rf, T *__restrict__ fc)
 {
-    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (t >= (long long)gc.nx * gc.ny * gc.nz) return;
-    int I, J, K;
-    node_of(gc, t, I, J, K);
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    const int J = blockIdx.y * blockDim.y + threadIdx.y;
+    const int K = blockIdx.z * blockDim.z + threadIdx.z;
+    if (I >= gc.nx || J >= gc.ny || K >= gc.nz) return;
     const bool d3 = gf.dim == 3;
     const T w[3] = {T(0.5), T(1), T(0.5)};
     const T scale = d3 ? T(0.125) : T(0.25);
@@ -65,10 +73,10 @@ __global__ void k_restrict(const Geom gf, const Geom gc, const T *__restrict__ r
 template <typename T>
 __global__ void k_prolong_add(const Geom gf, const Geom gc, const T *__restrict__ ec, T *__restrict__ uf)
 {
-    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (t >= (long long)gf.nx * gf.ny * gf.nz) return;
-    int i, j, k;
-    node_of(gf, t, i, j, k);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z * blockDim.z + threadIdx.z;
+    if (i >= gf.nx || j >= gf.ny || k >= gf.nz) return;
     const int I0 = i >> 1, I1 = (i + 1) >> 1, J0 = j >> 1, J1 = (j + 1) >> 1;
     const int K0 = k >> 1, K1 = (gf.dim == 3) ? (k + 1) >> 1 : K0;
     const T wi = (I0 == I1) ? T(1) : T(0.5), wj = (J0 == J1) ? T(1) : T(0.5), wk = (K0 == K1) ? T(1) : T(0.5);
@@ -114,25 +122,25 @@ __global__ void k_coarsen_psi(const Geom gf, const Geom gc, const double *__rest
 template <typename TS, typename TD>
 __global__ void k_pack(const Geom g, int ncomp, const TS *__restrict__ packed, TD *__restrict__ lev)
 {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z * blockDim.z + threadIdx.z;
+    if (i >= g.nx || j >= g.ny || k >= g.nz) return;
     const long long N = (long long)g.nx * g.ny * g.nz;
-    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (t >= N * ncomp) return;
-    const int p = (int)(t / N);
-    int i, j, k;
-    node_of(g, t % N, i, j, k);
-    lev[p * g.cs + gidx(g, i, j, k)] = TD(packed[t]);
+    const long long t = i + (long long)g.nx * (j + (long long)g.ny * k), o = gidx(g, i, j, k);
+    for (int p = 0; p < ncomp; ++p) lev[p * g.cs + o] = TD(packed[p * N + t]);
 }
 
 template <typename TS, typename TD>
 __global__ void k_unpack(const Geom g, int ncomp, const TS *__restrict__ lev, TD *__restrict__ packed)
 {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z * blockDim.z + threadIdx.z;
+    if (i >= g.nx || j >= g.ny || k >= g.nz) return;
     const long long N = (long long)g.nx * g.ny * g.nz;
-    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (t >= N * ncomp) return;
-    const int p = (int)(t / N);
-    int i, j, k;
-    node_of(g, t % N, i, j, k);
-    packed[t] = TD(lev[p * g.cs + gidx(g, i, j, k)]);
+    const long long t = i + (long long)g.nx * (j + (long long)g.ny * k), o = gidx(g, i, j, k);
+    for (int p = 0; p < ncomp; ++p) packed[p * N + t] = TD(lev[p * g.cs + o]);
 }
 
 __device__ __forceinline__ void cell_of(const Geom &g, long long t, int &i, int &j, int &k)
@@ -400,8 +408,7 @@ __global__ void k_dJdpsi(const Geom g, const Coef<double> c, const double *__res
 template <typename T>
 cudaError_t launch_restrict(const Geom &gf, const Geom &gc, const T *rf, T *fc, cudaStream_t s)
 {
-    const long long n = (long long)gc.nx * gc.ny * gc.nz;
-    k_restrict<T><<<nblk(n), kThreads, 0, s>>>(gf, gc, rf, fc);
+    k_restrict<T><<<node_grid(gc), kNodeBlock, 0, s>>>(gf, gc, rf, fc);
     ++g_launches;
     return cudaGetLastError();
 }
@@ -411,8 +418,7 @@ template cudaError_t launch_restrict<float>(const Geom &, const Geom &, const fl
 template <typename T>
 cudaError_t launch_prolong_add(const Geom &gf, const Geom &gc, const T *ec, T *uf, cudaStream_t s)
 {
-    const long long n = (long long)gf.nx * gf.ny * gf.nz;
-    k_prolong_add<T><<<nblk(n), kThreads, 0, s>>>(gf, gc, ec, uf);
+    k_prolong_add<T><<<node_grid(gf), kNodeBlock, 0, s>>>(gf, gc, ec, uf);
     ++g_launches;
     return cudaGetLastError();
 }
@@ -429,8 +435,7 @@ cudaError_t launch_coarsen_psi(const Geom &gf, const Geom &gc, const double *pf,
 template <typename TS, typename TD>
 cudaError_t launch_pack(const Geom &g, int ncomp, const TS *packed, TD *lev, cudaStream_t s)
 {
-    const long long n = (long long)g.nx * g.ny * g.nz * ncomp;
-    k_pack<TS, TD><<<nblk(n), kThreads, 0, s>>>(g, ncomp, packed, lev);
+    k_pack<TS, TD><<<node_grid(g), kNodeBlock, 0, s>>>(g, ncomp, packed, lev);
     ++g_launches;
     return cudaGetLastError();
 }
@@ -440,8 +445,7 @@ template cudaError_t launch_pack<double, float>(const Geom &, int, const double 
 template <typename TS, typename TD>
 cudaError_t launch_unpack(const Geom &g, int ncomp, const TS *lev, TD *packed, cudaStream_t s)
 {
-    const long long n = (long long)g.nx * g.ny * g.nz * ncomp;
-    k_unpack<TS, TD><<<nblk(n), kThreads, 0, s>>>(g, ncomp, lev, packed);
+    k_unpack<TS, TD><<<node_grid(g), kNodeBlock, 0, s>>>(g, ncomp, lev, packed);
     ++g_launches;
     return cudaGetLastError();
 }

@@ -180,6 +180,119 @@ __global__ void __launch_bounds__((TX3 + 1) * (TY3 + 1)) k_sweep3(const SweepArg
     if (MODE == kResidual && a.part) block_partial<NT>(ssq, a.part, red);
 }
 
+// FP64 3D sweep.  FP64 runs at 1/64 of the FP32 rate on this GPU, so the kernel is
+// bound by FP64 instruction issue and is organised to minimise FP64 operations:
+// a node plane's in-plane transform is computed once and shared by the two cell
+// layers it bounds, the forces a layer sends to its top plane are carried in the
+// transformed basis (one transposed in-plane butterfly per plane), and the 32 x 12
+// tile keeps the recomputed halo ring small.  The last node plane of the grid is
+// finalised by one extra step over an empty (psi = 0) layer.
+constexpr int TXD = 32, TYD = 12;
+
+template <typename TO, int MODE>
+__global__ void __launch_bounds__((TXD + 1) * (TYD + 1)) k_sweep3_dp(const SweepArgs<double, TO> a)
+{
+    constexpr int BX = TXD + 1, BY = TYD + 1, NT = BX * BY;
+    constexpr int PX = TXD + 2, PY = TYD + 2, PP = PX * PY;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double *up = reinterpret_cast<double *>(smem_raw);   // [2][3][PP] node planes
+    double *fc = up + 2 * 3 * PP;                         // [3][4][PP] corner forces of one plane
+    double *ps = fc + 12 * PP;                            // [PP] psi of the cells below + above
+    __shared__ double red[((NT + 31) / 32) * 32];
+
+    const Geom &g = a.g;
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + BX * ty;
+    const int x0 = blockIdx.x * TXD, y0 = blockIdx.y * TYD;
+    const int kz0 = blockIdx.z * a.kchunk;
+    const int kz1 = min(kz0 + a.kchunk, g.nz - 1);
+    const int kend = (kz1 == g.nz - 1) ? g.nz - 1 : kz1 - 1;
+    const int kfirst = kz0 > 0 ? kz0 - 1 : 0;
+
+    for (int s = tid; s < PP; s += NT) {
+        const int lx = s % PX, ly = s / PX;
+        if (lx == BX || ly == BY) {
+            for (int q = 0; q < 12; ++q) fc[q * PP + s] = 0.0;
+            ps[s] = 0.0;
+        }
+    }
+    auto load_plane = [&](int k, int buf) {
+        double *dst = up + buf * 3 * PP;
+        for (int s = tid; s < PP; s += NT) {
+            const int lx = s % PX, ly = s / PX;
+            const int gx = x0 - 1 + lx, gy = y0 - 1 + ly;
+            const bool ok = gx >= 0 && gx < g.nx && gy >= 0 && gy < g.ny && k >= 0 && k < g.nz;
+            const long long o = gidx(g, gx, gy, k);
+#pragma unroll
+            for (int p = 0; p < 3; ++p) dst[p * PP + s] = ok ? a.u[p * g.cs + o] : 0.0;
+        }
+    };
+    const int gx = x0 + tx, gy = y0 + ty;
+    const bool own = gx < g.nx && gy < g.ny && (tx < TXD || gx == g.nx - 1) && (ty < TYD || gy == g.ny - 1);
+    const int cx = gx - 1, cy = gy - 1;
+    const bool cell_ok = cx >= 0 && cx < g.nx - 1 && cy >= 0 && cy < g.ny - 1;
+    const int me = ty * PX + tx;
+    auto corners = [&](int buf, double (&T)[3][4]) {
+        const double *pl = up + buf * 3 * PP;
+#pragma unroll
+        for (int p = 0; p < 3; ++p) {
+            T[p][0] = pl[p * PP + me];
+            T[p][1] = pl[p * PP + me + 1];
+            T[p][2] = pl[p * PP + me + PX];
+            T[p][3] = pl[p * PP + me + PX + 1];
+            bfly4xy(T[p]);
+        }
+    };
+
+    double Tb[3][4], Cf[3][4];
+#pragma unroll
+    for (int p = 0; p < 3; ++p)
+#pragma unroll
+        for (int s = 0; s < 4; ++s) Cf[p][s] = 0.0;
+    double psi_prev = 0.0, ssq = 0.0;
+    load_plane(kfirst, kfirst & 1);
+    __syncthreads();
+    corners(kfirst & 1, Tb);
+    for (int lz = kfirst; lz <= kend; ++lz) {
+        load_plane(lz + 1, (lz + 1) & 1);
+        __syncthreads();
+        const double psi = (cell_ok && lz <= g.nz - 2) ? a.psi[gidx(g, cx, cy, lz)] : 0.0;
+        double Tt[3][4], Fb[3][4], Ft[3][4];
+        corners((lz + 1) & 1, Tt);
+        cell_faces3<double>(Tb, Tt, psi, a.c, Fb, Ft);
+#pragma unroll
+        for (int p = 0; p < 3; ++p) {
+#pragma unroll
+            for (int s = 0; s < 4; ++s) {
+                Fb[p][s] += Cf[p][s];       // plane lz: top face of layer lz-1 + bottom face of layer lz
+                Cf[p][s] = Ft[p][s];
+                Tb[p][s] = Tt[p][s];
+            }
+            bfly4xyT(Fb[p]);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) fc[(p * 4 + q) * PP + me] = Fb[p][q];
+        }
+        ps[me] = psi_prev + psi;
+        psi_prev = psi;
+        __syncthreads();
+        if (own && lz >= kz0) {
+            double Ku[3], uv[3];
+            const double *pl = up + (lz & 1) * 3 * PP;
+#pragma unroll
+            for (int p = 0; p < 3; ++p) {
+                Ku[p] = (fc[(p * 4 + 3) * PP + me] + fc[(p * 4 + 2) * PP + me + 1]) +
+                        (fc[(p * 4 + 1) * PP + me + PX] + fc[(p * 4 + 0) * PP + me + PX + 1]);
+                uv[p] = pl[p * PP + me + PX + 1];
+            }
+            const double pss = (ps[me] + ps[me + 1]) + (ps[me + PX] + ps[me + PX + 1]);
+            finalize<double, TO, MODE>(a, gx, gy, lz, Ku, pss, uv, ssq);
+        }
+        __syncthreads();
+    }
+    if (MODE == kResidual && a.part) block_partial<NT>(ssq, a.part, red);
+}
+
+constexpr size_t smem_dp() { return sizeof(double) * (2 * 3 + 12 + 1) * (TXD + 2) * (TYD + 2); }
+
 template <typename T, typename TO, int MODE>
 __global__ void __launch_bounds__((TX2 + 1) * (TY2 + 1)) k_sweep2(const SweepArgs<T, TO> a)
 {
@@ -306,18 +419,26 @@ __global__ void k_gs(const Geom g, const T *__restrict__ psi, const T *__restric
 
 }  // namespace
 
+static void sweep_grid_dp(const Geom &g, int *grid, int *kchunk)
+{
+    grid[0] = (g.nx - 1 + TXD - 1) / TXD;
+    grid[1] = (g.ny - 1 + TYD - 1) / TYD;
+    const int nzc = g.nz - 1;
+    const int nc = choose_chunks((long long)grid[0] * grid[1], nzc, 152, false);   // one block per SM
+    const int ch = (nzc + nc - 1) / nc;
+    grid[2] = (nzc + ch - 1) / ch;
+    *kchunk = ch;
+}
+
 void sweep_grid(const Geom &g, int *grid, int *kchunk)
 {
     if (g.dim == 3) {
         grid[0] = (g.nx - 1 + TX3 - 1) / TX3;
         grid[1] = (g.ny - 1 + TY3 - 1) / TY3;
-        const int xy = grid[0] * grid[1];
-        const int target = 4 * 152;                       // blocks wanted to fill the SMs
-        int nchunks = (target + xy - 1) / xy;
-        int ch = (g.nz - 1 + nchunks - 1) / nchunks;
-        if (ch < 2) ch = 2;
-        if (ch > g.nz - 1) ch = g.nz - 1;
-        grid[2] = (g.nz - 1 + ch - 1) / ch;
+        const int nzc = g.nz - 1;
+        const int nc = choose_chunks((long long)grid[0] * grid[1], nzc, 2 * 152, false);
+        const int ch = (nzc + nc - 1) / nc;
+        grid[2] = (nzc + ch - 1) / ch;
         *kchunk = ch;
     } else {
         grid[0] = (g.nx - 1 + TX2 - 1) / TX2;
@@ -327,10 +448,11 @@ void sweep_grid(const Geom &g, int *grid, int *kchunk)
     }
 }
 
-long long sweep_blocks(const Geom &g)
+long long sweep_blocks(const Geom &g, bool fp64)
 {
     int grid[3], ch;
-    sweep_grid(g, grid, &ch);
+    if (fp64 && g.dim == 3) sweep_grid_dp(g, grid, &ch);
+    else sweep_grid(g, grid, &ch);
     return (long long)grid[0] * grid[1] * grid[2];
 }
 
@@ -339,6 +461,20 @@ static cudaError_t launch_mode(const SweepArgs<T, TO> &a0, cudaStream_t s)
 {
     SweepArgs<T, TO> a = a0;
     int grid[3];
+    if (a.g.dim == 3 && sizeof(T) == 8) {
+        sweep_grid_dp(a.g, grid, &a.kchunk);
+        const size_t sm = smem_dp();
+        static bool attr_dp = false;
+        if (!attr_dp) {
+            cudaError_t e = cudaFuncSetAttribute(k_sweep3_dp<TO, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            if (e != cudaSuccess) return e;
+            attr_dp = true;
+        }
+        k_sweep3_dp<TO, MODE><<<dim3(grid[0], grid[1], grid[2]), dim3(TXD + 1, TYD + 1), sm, s>>>(
+            reinterpret_cast<const SweepArgs<double, TO> &>(a));
+        ++g_launches;
+        return cudaGetLastError();
+    }
     sweep_grid(a.g, grid, &a.kchunk);
     if (a.g.dim == 3) {
         const size_t sm = smem3<T>();

@@ -6,9 +6,11 @@
 // row/column being the one-cell halo), streaming a chunk of z.  Each step handles
 // two cell layers (k, k+1) at once: every thread evaluates its two cells in the
 // two lanes of the packed type, so one packed instruction does the work of two.
-// Node planes of u are fetched by the Tensor Memory Accelerator into a 6-deep
-// shared-memory ring (one 40 x 10 x 3 box per plane, out-of-range elements zero
-// filled), two pairs ahead of use, completion signalled by mbarriers.  Corner
+// Node planes of u and f and cell layers of psi are fetched by the Tensor Memory
+// Accelerator into a 6-deep shared-memory ring (40 x 10 x 3 boxes of u and f and a
+// 40 x 10 box of psi per slot, out-of-range elements zero filled), two pairs ahead
+// of use, completion signalled by one mbarrier per slot; the compute loop issues
+// no global loads.  Corner
 // forces of both node planes a cell touches in this step are exchanged as one
 // float2 per corner and component; the top-plane forces of layer k+1 stay in
 // registers and join the next step.  Every mbarrier wait is bounded: on timeout
@@ -29,8 +31,15 @@ constexpr int PXF = TXP + 2, PYF = TYP + 2, PPF = PXF * PYF;   // exchange tiles
 constexpr int WX = 40;                           // TMA box width: nodes x0-4 .. x0+35
 constexpr int XOFF = 3;                          // box-local x of node x0-1
 constexpr int PLANE_FLOATS = 3 * PYF * WX;       // one staged plane: 3 comps x 10 rows x 40
-constexpr int PLANE_BYTES = PLANE_FLOATS * 4;
-constexpr int SLOT_FLOATS = (PLANE_BYTES + 127) / 128 * 128 / 4;
+constexpr int PSI_FLOATS = PYF * WX;             // one staged cell layer of psi
+// A ring slot holds node plane p of u, node plane p of f and cell layer p of psi.
+// Every TMA destination starts on a 128-byte boundary.
+constexpr int PLANE_STRIDE = (PLANE_FLOATS * 4 + 127) / 128 * 128 / 4;   // floats
+constexpr int F_OFF = PLANE_STRIDE, PSI_OFF = 2 * PLANE_STRIDE;
+constexpr int SLOT_FLOATS = ((PSI_OFF + PSI_FLOATS) * 4 + 127) / 128 * 128 / 4;
+constexpr int TX_BYTES = (2 * PLANE_FLOATS + PSI_FLOATS) * 4;           // bytes the three copies deliver
+static_assert((F_OFF * 4) % 128 == 0 && (PSI_OFF * 4) % 128 == 0 && (SLOT_FLOATS * 4) % 128 == 0,
+              "TMA destinations must be 128-byte aligned");
 constexpr int RING = 6;
 constexpr long long kSpinLimit = 1LL << 24;      // mbarrier polls before giving up
 
@@ -69,6 +78,15 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
     return false;
 }
 
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, int x, int y, int z, uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
+        : "memory");
+}
+
 __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map, int x, int y, int z, int c,
                                             uint32_t bar)
 {
@@ -97,7 +115,7 @@ __device__ __forceinline__ void block_partial_f(double ssq, double *part, double
 
 template <int MODE>
 __device__ __forceinline__ void finalize_f(const SweepArgs<float, float> &a, int gx, int gy, int gz, const float *Ku,
-                                           float pss, const float *uv, double &ssq)
+                                           float pss, const float *uv, const float *fv, double &ssq)
 {
     const Geom &g = a.g;
     const long long o = gidx(g, gx, gy, gz);
@@ -106,13 +124,13 @@ __device__ __forceinline__ void finalize_f(const SweepArgs<float, float> &a, int
 #pragma unroll
         for (int p = 0; p < 3; ++p) {
             float v = uv[p];
-            if (!is_dir(g, p, gx, gy, gz)) v = madd((a.f[p * g.cs + o] - Ku[p]) * ip, a.wk[p], v);
+            if (!is_dir(g, p, gx, gy, gz)) v = madd((fv[p] - Ku[p]) * ip, a.wk[p], v);
             a.out[p * g.cs + o] = v;
         }
     } else if (MODE == kResidual) {
 #pragma unroll
         for (int p = 0; p < 3; ++p) {
-            const float r = is_dir(g, p, gx, gy, gz) ? 0.0f : a.f[p * g.cs + o] - Ku[p];
+            const float r = is_dir(g, p, gx, gy, gz) ? 0.0f : fv[p] - Ku[p];
             a.out[p * g.cs + o] = r;
             ssq += double(r) * double(r);
         }
@@ -124,6 +142,8 @@ __device__ __forceinline__ void finalize_f(const SweepArgs<float, float> &a, int
 
 template <int MODE>
 __global__ void __launch_bounds__(NTP) k_sweep3_f2(const __grid_constant__ CUtensorMap tmap,
+                                                    const __grid_constant__ CUtensorMap tmap_f,
+                                                    const __grid_constant__ CUtensorMap tmap_psi,
                                                     const SweepArgs<float, float> a, int *err)
 {
     extern __shared__ unsigned char smem_raw[];
@@ -163,8 +183,11 @@ __global__ void __launch_bounds__(NTP) k_sweep3_f2(const __grid_constant__ CUten
         if (p > pmax) return;
         const int s = slot_of(p);
         const uint32_t b = smem_addr(&bar[s]);
-        mbar_expect_tx(b, PLANE_BYTES);
-        tma_load_4d(smem_addr(ring + s * SLOT_FLOATS), &tmap, x0 - 4, y0 - 1, p, 0, b);
+        mbar_expect_tx(b, TX_BYTES);
+        float *slot = ring + s * SLOT_FLOATS;
+        tma_load_4d(smem_addr(slot), &tmap, x0 - 4, y0 - 1, p, 0, b);
+        tma_load_4d(smem_addr(slot + F_OFF), &tmap_f, x0 - 4, y0 - 1, p, 0, b);
+        tma_load_3d(smem_addr(slot + PSI_OFF), &tmap_psi, x0 - 4, y0 - 1, p, b);
     };
     if (tid == 0)
         for (int j = 0; j < RING; ++j) issue(kfirst + j);
@@ -176,8 +199,6 @@ __global__ void __launch_bounds__(NTP) k_sweep3_f2(const __grid_constant__ CUten
 
     const int gx = x0 + tx, gy = y0 + ty;
     const bool own = gx < g.nx && gy < g.ny && (tx < TXP || gx == g.nx - 1) && (ty < TYP || gy == g.ny - 1);
-    const int cx = gx - 1, cy = gy - 1;
-    const bool cell_ok = cx >= 0 && cx < g.nx - 1 && cy >= 0 && cy < g.ny - 1;
     const int me = ty * PXF + tx;
     float carry[3][4];
 #pragma unroll
@@ -188,20 +209,33 @@ __global__ void __launch_bounds__(NTP) k_sweep3_f2(const __grid_constant__ CUten
     double ssq = 0.0;
     bool failed = false;
 
+    // lanes of this thread's warp (the last warp of the block is partial)
+    const int lane = tid & 31, wlanes = min(32, NTP - (tid & ~31));
+    const unsigned wmask = wlanes == 32 ? 0xffffffffu : ((1u << wlanes) - 1u);
     for (int it = 0; it < npairs; ++it) {
         const int k = kfirst + 2 * it;
-        bool ok = mbar_wait(smem_addr(&bar[slot_of(k)]), parity_of(k)) &&
-                  mbar_wait(smem_addr(&bar[slot_of(k + 1)]), parity_of(k + 1)) &&
-                  mbar_wait(smem_addr(&bar[slot_of(k + 2)]), parity_of(k + 2));
-        if (__syncthreads_or(!ok)) {
-            failed = true;
-            break;
-        }
+        // one lane per warp polls the barriers of planes k..k+2 (bounded); the warp
+        // proceeds when its lane 0 has seen them complete
+        int ok = 1;
+        if (lane == 0)
+            ok = mbar_wait(smem_addr(&bar[slot_of(k)]), parity_of(k)) &&
+                 mbar_wait(smem_addr(&bar[slot_of(k + 1)]), parity_of(k + 1)) &&
+                 mbar_wait(smem_addr(&bar[slot_of(k + 2)]), parity_of(k + 2));
+        ok = __shfl_sync(wmask, ok, 0);
+        // every lane then observes the completed phases itself (acquiring the copied
+        // data); a timed-out wait is reported at the exchange barrier below and
+        // this warp's values are then never used
+        if (ok)
+            ok = mbar_try(smem_addr(&bar[slot_of(k)]), parity_of(k)) &&
+                 mbar_try(smem_addr(&bar[slot_of(k + 1)]), parity_of(k + 1)) &&
+                 mbar_try(smem_addr(&bar[slot_of(k + 2)]), parity_of(k + 2));
         const float *P0 = ring + slot_of(k) * SLOT_FLOATS;
         const float *P1 = ring + slot_of(k + 1) * SLOT_FLOATS;
         const float *P2 = ring + slot_of(k + 2) * SLOT_FLOATS;
-        const float p0 = (cell_ok && k <= g.nz - 2) ? a.psi[gidx(g, cx, cy, k)] : 0.f;
-        const float p1 = (cell_ok && k + 1 <= g.nz - 2) ? a.psi[gidx(g, cx, cy, k + 1)] : 0.f;
+        // cell (x0+tx-1, y0+ty-1) of layers k, k+1; the tensor map zero-fills cells
+        // outside the grid, so no bounds test is needed
+        const float p0 = P0[PSI_OFF + ty * WX + tx + XOFF];
+        const float p1 = P1[PSI_OFF + ty * WX + tx + XOFF];
         F2 U[3][8];
 #pragma unroll
         for (int p = 0; p < 3; ++p)
@@ -224,7 +258,10 @@ __global__ void __launch_bounds__(NTP) k_sweep3_f2(const __grid_constant__ CUten
             }
         ps[me] = make_float2(psi_prev + p0, p0 + p1);
         psi_prev = p1;
-        __syncthreads();
+        if (__syncthreads_or(!ok)) {
+            failed = true;
+            break;
+        }
         if (own) {
             // node = corner 3 of cell (tx,ty), 2 of (tx+1,ty), 1 of (tx,ty+1), 0 of (tx+1,ty+1)
             F2 Ku2[3];
@@ -247,12 +284,14 @@ __global__ void __launch_bounds__(NTP) k_sweep3_f2(const __grid_constant__ CUten
             if (k >= kz0 && k <= kend) {
                 const float Ku[3] = {Ku2[0].v.x, Ku2[1].v.x, Ku2[2].v.x};
                 const float uv[3] = {P0[onode], P0[PYF * WX + onode], P0[2 * PYF * WX + onode]};
-                finalize_f<MODE>(a, gx, gy, k, Ku, pss.v.x, uv, ssq);
+                const float fv[3] = {P0[F_OFF + onode], P0[F_OFF + PYF * WX + onode], P0[F_OFF + 2 * PYF * WX + onode]};
+                finalize_f<MODE>(a, gx, gy, k, Ku, pss.v.x, uv, fv, ssq);
             }
             if (k + 1 >= kz0 && k + 1 <= kend) {
                 const float Ku[3] = {Ku2[0].v.y, Ku2[1].v.y, Ku2[2].v.y};
                 const float uv[3] = {P1[onode], P1[PYF * WX + onode], P1[2 * PYF * WX + onode]};
-                finalize_f<MODE>(a, gx, gy, k + 1, Ku, pss.v.y, uv, ssq);
+                const float fv[3] = {P1[F_OFF + onode], P1[F_OFF + PYF * WX + onode], P1[F_OFF + 2 * PYF * WX + onode]};
+                finalize_f<MODE>(a, gx, gy, k + 1, Ku, pss.v.y, uv, fv, ssq);
             }
         }
         __syncthreads();
@@ -288,13 +327,10 @@ void sweep_grid_f2(const Geom &g, int *grid, int *kchunk)
 {
     grid[0] = (g.nx - 1 + TXP - 1) / TXP;
     grid[1] = (g.ny - 1 + TYP - 1) / TYP;
-    const int xy = grid[0] * grid[1];
-    const int target = 4 * 152;
-    const int nchunks = (target + xy - 1) / xy;
-    int ch = (g.nz - 1 + nchunks - 1) / nchunks;
-    if (ch < 3) ch = 3;
-    if (ch > g.nz - 1) ch = g.nz - 1;
-    grid[2] = (g.nz - 1 + ch - 1) / ch;
+    const int nzc = g.nz - 1;
+    const int nc = choose_chunks((long long)grid[0] * grid[1], nzc, 2 * 152, true);   // two blocks per SM
+    const int ch = (nzc + nc - 1) / nc;
+    grid[2] = (nzc + ch - 1) / ch;
     *kchunk = ch;
 }
 
@@ -311,7 +347,7 @@ static cudaError_t launch_f2_mode(const SweepArgs<float, float> &a0, const CUten
         if (e != cudaSuccess) return e;
         attr_done = true;
     }
-    k_sweep3_f2<MODE><<<dim3(grid[0], grid[1], grid[2]), dim3(BXP, BYP), sm, s>>>(*tmap, a, err);
+    k_sweep3_f2<MODE><<<dim3(grid[0], grid[1], grid[2]), dim3(BXP, BYP), sm, s>>>(tmap[0], tmap[1], tmap[2], a, err);
     ++g_launches;
     return cudaGetLastError();
 }

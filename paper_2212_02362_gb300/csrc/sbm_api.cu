@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cstring>
 #include <algorithm>
+#include <type_traits>
 #include <string>
 #include <vector>
 
@@ -33,8 +34,28 @@ struct Level {
     Coef<float> c32{};
     double *Ke64 = nullptr;   // unit-psi cell matrix (GS smoother)
     float *Ke32 = nullptr;
-    CUtensorMap tm32[2];      // TMA descriptors of su[0], su[1] (3D levels)
+    CUtensorMap tm32[2][3];   // TMA descriptors {su[i], sf, psi32} for input su[i] (3D levels)
     bool has_tm = false;
+};
+
+// One refinement patch (block-structured AMR level a >= 1): node box [lo, hi] in
+// level-a indices, stored with one padding node per side.
+struct Patch {
+    int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+    Geom s{};                 // padded storage (no Dirichlet faces)
+    Geom v{};                 // view of the box: interface faces fixed, domain faces as the domain
+    long long voff = 0;       // element offset of the view origin in the storage
+    double h = 0;
+    AmrInfo info{};
+    double *psi64 = nullptr;
+    float *psi32 = nullptr;
+    double *u64 = nullptr, *f64 = nullptr, *r64 = nullptr;
+    double *de[2] = {nullptr, nullptr}, *drhs = nullptr, *dres = nullptr;
+    float *se[2] = {nullptr, nullptr}, *srhs = nullptr, *sres = nullptr;
+    Coef<double> c64{};
+    Coef<float> c32{};
+    double *Ke64 = nullptr;
+    float *Ke32 = nullptr;
 };
 
 struct GraphSlot {
@@ -79,6 +100,13 @@ struct sbm_grid_s {
     GraphSlot slots[2];
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     std::string err;
+    int npatch = 0;
+    Patch P[8];
+    AmrInfo base_info{};
+    bool amr_psi_dirty = false;
+    double *amr_part = nullptr;   // partial sums of the composite norm
+    long long amr_npart = 0;
+    double *amr_u0 = nullptr, *amr_r0 = nullptr;   // composite solution / residual on the base level
 };
 
 namespace {
@@ -176,16 +204,16 @@ cudaError_t sweep<float>(sbm_grid G, int l, int mode, const float *u, const floa
     a.c = L.c32;
     for (int p = 0; p < 3; ++p) a.wk[p] = (L.c64.kdiag[p] != 0.0) ? float(omega / L.c64.kdiag[p]) : 0.f;
     a.kchunk = 0;
-    if (L.has_tm && (u == L.su[0] || u == L.su[1]))
-        return launch_sweep_f2(mode, a, &L.tm32[u == L.su[0] ? 0 : 1], G->derr, G->st);
+    if (L.has_tm && (u == L.su[0] || u == L.su[1]) && (mode == kApply || f == L.sf))
+        return launch_sweep_f2(mode, a, L.tm32[u == L.su[0] ? 0 : 1], G->derr, G->st);
     return launch_sweep<float, float>(mode, a, G->st);
 }
 
-long long sweep_nblocks(sbm_grid G, int l, bool fp32, const void *u)
+long long sweep_nblocks(sbm_grid G, int l, bool fp32, const void *u, const void *f)
 {
     Level &L = G->L[l];
-    if (fp32 && L.has_tm && (u == L.su[0] || u == L.su[1])) return sweep_blocks_f2(L.g);
-    return sweep_blocks(L.g);
+    if (fp32 && L.has_tm && (u == L.su[0] || u == L.su[1]) && f == L.sf) return sweep_blocks_f2(L.g);
+    return sweep_blocks(L.g, !fp32);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
@@ -201,6 +229,20 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
             cudaGetLastError();
     }
     return fn;
+}
+
+// 3D map of an FP32 cell array (cells at the node index of their lower corner);
+// box = 40 x 10 x 1 cells, zero fill outside the grid's cells.
+bool encode_cell_map(CUtensorMap *m, float *buf, const Geom &g)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return false;
+    cuuint64_t dims[3] = {(cuuint64_t)(g.nx - 1), (cuuint64_t)(g.ny - 1), (cuuint64_t)(g.nz - 1)};
+    cuuint64_t strides[2] = {(cuuint64_t)g.sx * 4, (cuuint64_t)g.sy * 4};
+    cuuint32_t box[3] = {40, 10, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, buf, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 // 4D (x, y, z, component) map of one FP32 level buffer; box = 40 x 10 x 1 x 3 nodes
@@ -285,7 +327,7 @@ cudaError_t residual64(sbm_grid G, const double *rhs, int mixed, int which)
         e = sweep<double>(G, G->nl - 1, kResidual, L.du[0], rhs, L.dr, G->part, 0.0);
     }
     if (e != cudaSuccess) return e;
-    return launch_norm_final(G->part, (int)sweep_blocks(L.g), G->scal, which, G->st);
+    return launch_norm_final(G->part, (int)sweep_blocks(L.g, true), G->scal, which, G->st);
 }
 
 // One outer iteration: V-cycle(s) and the FP64 residual + norm of the result.
@@ -494,6 +536,338 @@ sbm_status check_level(sbm_grid G, int level)
     return SBM_OK;
 }
 
+
+// ===================================================== block-structured refinement
+
+int level_N(sbm_grid G, int a, int ax)
+{
+    if (ax >= G->desc.dim) return 1;
+    return (G->desc.n[ax] - 1) * (1 << a) + 1;
+}
+
+void amr_refresh_infos(sbm_grid G)
+{
+    const int d = G->desc.dim;
+    unsigned dm[3] = {0, 0, 0};
+    for (int p = 0; p < 3; ++p)
+        for (int f = 0; f < 6; ++f)
+            if (p < d && G->bct[f][p] != SBM_FREE) dm[p] |= 1u << f;
+    AmrInfo &B = G->base_info;
+    B = AmrInfo{};
+    B.dim = d;
+    for (int ax = 0; ax < 3; ++ax) {
+        B.N[ax] = level_N(G, 0, ax);
+        B.dm[ax] = dm[ax];
+    }
+    B.is_base = 1;
+    for (int a = 1; a <= G->npatch; ++a) {
+        Patch &Pt = G->P[a - 1];
+        AmrInfo &L = Pt.info;
+        L = AmrInfo{};
+        L.dim = d;
+        for (int ax = 0; ax < 3; ++ax) {
+            L.N[ax] = level_N(G, a, ax);
+            L.lo[ax] = Pt.lo[ax];
+            L.hi[ax] = Pt.hi[ax];
+            L.org[ax] = ax < d ? Pt.lo[ax] - 1 : 0;
+            L.dm[ax] = dm[ax];
+        }
+        // view faces: interface faces fixed for every component, domain faces as the domain
+        unsigned vdm[3] = {0, 0, 0};
+        for (int ax = 0; ax < d; ++ax)
+            for (int side = 0; side < 2; ++side) {
+                const int f = 2 * ax + side;
+                const bool on_domain = side == 0 ? Pt.lo[ax] == 0 : Pt.hi[ax] == L.N[ax] - 1;
+                for (int p = 0; p < d; ++p)
+                    if (!on_domain || ((dm[p] >> f) & 1u)) vdm[p] |= 1u << f;
+            }
+        for (int p = 0; p < 3; ++p) Pt.v.dm[p] = vdm[p];
+    }
+    for (int a = 0; a < G->npatch; ++a) {
+        AmrInfo &L = a == 0 ? G->base_info : G->P[a - 1].info;
+        const Patch &C = G->P[a];
+        L.has_child = 1;
+        for (int ax = 0; ax < 3; ++ax) {
+            L.clo[ax] = C.lo[ax];
+            L.chi[ax] = C.hi[ax];
+        }
+    }
+}
+
+template <typename T> struct PP;
+template <> struct PP<double> {
+    static double *e(Patch &P, int i) { return P.de[i]; }
+    static double *rhs(Patch &P) { return P.drhs; }
+    static double *res(Patch &P) { return P.dres; }
+    static const double *psi(Patch &P) { return P.psi64; }
+    static const Coef<double> &c(Patch &P) { return P.c64; }
+    static const double *Ke(Patch &P) { return P.Ke64; }
+};
+template <> struct PP<float> {
+    static float *e(Patch &P, int i) { return P.se[i]; }
+    static float *rhs(Patch &P) { return P.srhs; }
+    static float *res(Patch &P) { return P.sres; }
+    static const float *psi(Patch &P) { return P.psi32; }
+    static const Coef<float> &c(Patch &P) { return P.c32; }
+    static const float *Ke(Patch &P) { return P.Ke32; }
+};
+
+template <typename T>
+cudaError_t sweep_view(sbm_grid G, Patch &Pt, int mode, const T *u, const T *f, T *out, double omega)
+{
+    SweepArgs<T, T> a;
+    a.g = Pt.v;
+    a.u = u + Pt.voff;
+    a.f = f ? f + Pt.voff : nullptr;
+    a.psi = PP<T>::psi(Pt) + Pt.voff;
+    a.out = out + Pt.voff;
+    a.part = nullptr;
+    a.c = PP<T>::c(Pt);
+    for (int p = 0; p < 3; ++p) a.wk[p] = (Pt.c64.kdiag[p] != 0.0) ? T(omega / Pt.c64.kdiag[p]) : T(0);
+    a.kchunk = 0;
+    return launch_sweep<T, T>(mode, a, G->st);
+}
+
+template <typename T>
+cudaError_t patch_smooth(sbm_grid G, Patch &Pt, int &cur, const sbm_opts &o, int n, bool desc)
+{
+    const int ncol = 1 << Pt.v.dim;
+    for (int s = 0; s < n; ++s) {
+        if (o.smoother == SBM_MCGS) {
+            for (int c = 0; c < ncol; ++c)
+                CKE(launch_gs<T>(Pt.v, PP<T>::psi(Pt) + Pt.voff, PP<T>::Ke(Pt), PP<T>::rhs(Pt) + Pt.voff,
+                                 PP<T>::e(Pt, cur) + Pt.voff, desc ? ncol - 1 - c : c, G->st));
+        } else {
+            CKE(sweep_view<T>(G, Pt, kJacobi, PP<T>::e(Pt, cur), PP<T>::rhs(Pt), PP<T>::e(Pt, 1 - cur), o.omega));
+            cur ^= 1;
+        }
+    }
+    return cudaSuccess;
+}
+
+size_t patch_bytes(const Patch &Pt, size_t elem) { return (size_t)Pt.s.dim * Pt.s.cs * elem; }
+
+// Injection into covered parents (finest first), then ghost fill (coarsest first).
+cudaError_t amr_fill(sbm_grid G)
+{
+    Level &B = G->L[G->nl - 1];
+    for (int a = G->npatch; a >= 1; --a) {
+        Patch &Pt = G->P[a - 1];
+        if (a == 1) CKE(launch_amr_inject(Pt.s, Pt.info, B.g, G->base_info, Pt.u64, G->amr_u0, G->st));
+        else CKE(launch_amr_inject(Pt.s, Pt.info, G->P[a - 2].s, G->P[a - 2].info, Pt.u64, G->P[a - 2].u64, G->st));
+    }
+    for (int a = 1; a <= G->npatch; ++a) {
+        Patch &Pt = G->P[a - 1];
+        if (a == 1) CKE(launch_amr_ghost<double>(Pt.s, Pt.info, B.g, G->base_info, Pt.u64, G->amr_u0, 0, G->st));
+        else CKE(launch_amr_ghost<double>(Pt.s, Pt.info, G->P[a - 2].s, G->P[a - 2].info, Pt.u64, G->P[a - 2].u64, 0, G->st));
+    }
+    return cudaSuccess;
+}
+
+// Composite FP64 residual of every level, its norm into scal[which..] and the
+// residual rounded to T as the right-hand side of the correction cycle.
+template <typename T>
+cudaError_t amr_residual(sbm_grid G, int which)
+{
+    Level &B = G->L[G->nl - 1];
+    CKE(amr_fill(G));
+    CKE(sweep<double>(G, G->nl - 1, kResidual, G->amr_u0, G->fsrc, G->amr_r0, nullptr, 0.0));
+    CKE(launch_amr_mask(B.g, G->base_info, G->amr_r0, G->st));
+    T *base_rhs = std::is_same<T, double>::value ? (T *)B.df : (T *)B.sf;
+    long long off = 0;
+    CKE(launch_amr_sumsq_round<T>(B.g, G->base_info, G->amr_r0, base_rhs, G->amr_part, G->st));
+    off += amr_blocks(B.g);
+    for (int a = 1; a <= G->npatch; ++a) {
+        Patch &Pt = G->P[a - 1];
+        CKE(sweep_view<double>(G, Pt, kResidual, Pt.u64, Pt.f64, Pt.r64, 0.0));
+        CKE(launch_amr_mask(Pt.s, Pt.info, Pt.r64, G->st));
+        CKE(launch_amr_sumsq_round<T>(Pt.s, Pt.info, Pt.r64, PP<T>::rhs(Pt), G->amr_part + off, G->st));
+        off += amr_blocks(Pt.s);
+    }
+    return launch_norm_final(G->amr_part, (int)off, G->scal, which, G->st);
+}
+
+// One correction cycle: patches top-down (smooth, residual, restrict to covered
+// parent nodes), the base multigrid V-cycle, patches bottom-up (prolongate the
+// parent correction, fill ghosts, smooth), then u += e on owned dofs.
+template <typename T>
+cudaError_t amr_cycle(sbm_grid G, const sbm_opts &o)
+{
+    const int A = G->npatch;
+    Level &B = G->L[G->nl - 1];
+    int cur[9] = {0};
+    for (int a = A; a >= 1; --a) {
+        Patch &Pt = G->P[a - 1];
+        CKE(cudaMemsetAsync(PP<T>::e(Pt, 0), 0, patch_bytes(Pt, sizeof(T)), G->st));
+        CKE(cudaMemsetAsync(PP<T>::e(Pt, 1), 0, patch_bytes(Pt, sizeof(T)), G->st));
+        cur[a] = 0;
+        CKE(patch_smooth<T>(G, Pt, cur[a], o, o.nu1, false));
+        CKE(sweep_view<T>(G, Pt, kResidual, PP<T>::e(Pt, cur[a]), PP<T>::rhs(Pt), PP<T>::res(Pt), 0.0));
+        if (a == 1) {
+            T *base_rhs = std::is_same<T, double>::value ? (T *)B.df : (T *)B.sf;
+            CKE(launch_amr_restrict<T>(Pt.s, Pt.info, B.g, G->base_info, PP<T>::res(Pt), base_rhs, G->st));
+        } else {
+            Patch &Pp = G->P[a - 2];
+            CKE(launch_amr_restrict<T>(Pt.s, Pt.info, Pp.s, Pp.info, PP<T>::res(Pt), PP<T>::rhs(Pp), G->st));
+        }
+    }
+    T *base_rhs = std::is_same<T, double>::value ? (T *)B.df : (T *)B.sf;
+    CKE(cudaMemsetAsync(P<T>::u(B, 0), 0, level_bytes(B, sizeof(T)), G->st));
+    int cb = 0;
+    CKE(vcycle<T>(G, G->nl - 1, cb, o, base_rhs));
+    for (int a = 1; a <= A; ++a) {
+        Patch &Pt = G->P[a - 1];
+        if (a == 1)
+            CKE(launch_amr_ghost<T>(Pt.s, Pt.info, B.g, G->base_info, PP<T>::e(Pt, cur[a]), P<T>::u(B, cb), 1, G->st));
+        else
+            CKE(launch_amr_ghost<T>(Pt.s, Pt.info, G->P[a - 2].s, G->P[a - 2].info, PP<T>::e(Pt, cur[a]),
+                                    PP<T>::e(G->P[a - 2], cur[a - 1]), 1, G->st));
+        CKE(patch_smooth<T>(G, Pt, cur[a], o, o.nu2, true));
+    }
+    CKE(launch_amr_update<T>(B.g, G->base_info, P<T>::u(B, cb), G->amr_u0, G->st));
+    for (int a = 1; a <= A; ++a) {
+        Patch &Pt = G->P[a - 1];
+        CKE(launch_amr_update<T>(Pt.s, Pt.info, PP<T>::e(Pt, cur[a]), Pt.u64, G->st));
+    }
+    return cudaSuccess;
+}
+
+sbm_status amr_prepare(sbm_grid G)
+{
+    amr_refresh_infos(G);
+    for (int a = 1; a <= G->npatch; ++a) {
+        Patch &Pt = G->P[a - 1];
+        Pt.c64 = make_coef<double>(Pt.s.dim, Pt.h, G->mod[0], G->mod[1], G->mod[2]);
+        Pt.c32 = make_coef<float>(Pt.s.dim, Pt.h, G->mod[0], G->mod[1], G->mod[2]);
+        const int d = Pt.s.dim, nc = 1 << d, nd = nc * d;
+        std::vector<double> Ke(nd * nd);
+        std::vector<float> Kf(nd * nd);
+        for (int b = 0; b < nc; ++b)
+            for (int q = 0; q < d; ++q) {
+                if (d == 3) {
+                    double U[3][8] = {};
+                    U[q][b] = 1.0;
+                    cell_forces3<double>(U, 1.0, Pt.c64);
+                    for (int c = 0; c < 8; ++c)
+                        for (int p = 0; p < 3; ++p) Ke[(c * 3 + p) * nd + b * 3 + q] = U[p][c];
+                } else {
+                    double U[2][4] = {};
+                    U[q][b] = 1.0;
+                    cell_forces2<double>(U, 1.0, Pt.c64);
+                    for (int c = 0; c < 4; ++c)
+                        for (int p = 0; p < 2; ++p) Ke[(c * 2 + p) * nd + b * 2 + q] = U[p][c];
+                }
+            }
+        for (int e = 0; e < nd * nd; ++e) Kf[e] = float(Ke[e]);
+        CK(cudaMemcpyAsync(Pt.Ke64, Ke.data(), sizeof(double) * nd * nd, cudaMemcpyHostToDevice, G->st));
+        CK(cudaMemcpyAsync(Pt.Ke32, Kf.data(), sizeof(float) * nd * nd, cudaMemcpyHostToDevice, G->st));
+        CK(cudaStreamSynchronize(G->st));
+    }
+    if (G->amr_psi_dirty) {
+        Level &B = G->L[G->nl - 1];
+        for (int a = G->npatch; a >= 1; --a) {
+            Patch &Pt = G->P[a - 1];
+            if (a == 1) CK(launch_amr_coarsen_psi(Pt.s, Pt.info, B.g, G->base_info, Pt.psi64, B.psi64, G->st));
+            else CK(launch_amr_coarsen_psi(Pt.s, Pt.info, G->P[a - 2].s, G->P[a - 2].info, Pt.psi64, G->P[a - 2].psi64, G->st));
+        }
+        for (int a = 1; a <= G->npatch; ++a)
+            CK(launch_round(G->P[a - 1].s.cs, G->P[a - 1].psi64, G->P[a - 1].psi32, G->st));
+        for (int l = G->nl - 1; l > 0; --l)
+            CK(launch_coarsen_psi(G->L[l].g, G->L[l - 1].g, G->L[l].psi64, G->L[l - 1].psi64, G->st));
+        for (int l = 0; l < G->nl; ++l) CK(launch_round_cells(G->L[l].g, G->L[l].psi64, G->L[l].psi32, G->st));
+        G->bottom_ready = false;
+        G->amr_psi_dirty = false;
+    }
+    return SBM_OK;
+}
+
+template <typename T>
+sbm_status amr_run(sbm_grid G, const sbm_opts &o, sbm_info *info)
+{
+    sbm_status st = setup_bottom(G);
+    if (st != SBM_OK) return st;
+    const long long launches0 = g_launches;
+    CK(cudaEventRecord(G->ev0, G->st));
+    CK(amr_residual<T>(G, 0));
+    CK(cudaMemcpyAsync(G->hscal, G->scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, G->st));
+    CK(cudaStreamSynchronize(G->st));
+    const double r0 = G->hscal[1];
+    if (info) {
+        info->r0 = r0;
+        info->levels = G->nl + G->npatch;
+        if (info->history && info->history_capacity > 0) info->history[0] = 1.0;
+    }
+    int cyc = 0;
+    double rel = 1.0;
+    sbm_status status = SBM_ERR_NOCONV;
+    if (r0 == 0.0) {
+        status = SBM_OK;
+        rel = 0.0;
+    }
+    while (status == SBM_ERR_NOCONV && cyc < o.max_cycles) {
+        CK(amr_cycle<T>(G, o));
+        CK(amr_residual<T>(G, 2));
+        CK(cudaMemcpyAsync(G->hscal + 4, G->scal + 4, sizeof(double), cudaMemcpyDeviceToHost, G->st));
+        CK(cudaStreamSynchronize(G->st));
+        ++cyc;
+        rel = G->hscal[4];
+        if (info && info->history && cyc < info->history_capacity) info->history[cyc] = rel;
+        if (!std::isfinite(rel) || rel > 1e10) status = SBM_ERR_DIVERGED;
+        else if (rel <= o.tol) status = SBM_OK;
+    }
+    CK(amr_fill(G));
+    CK(cudaEventRecord(G->ev1, G->st));
+    CK(cudaEventSynchronize(G->ev1));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, G->ev0, G->ev1);
+    if (info) {
+        info->status = status;
+        info->cycles = cyc;
+        info->vcycles = cyc;
+        info->relres = rel;
+        info->solve_ms = ms;
+        info->launches = g_launches - launches0;
+    }
+    if (status == SBM_ERR_NOCONV) G->err = "max_cycles reached before the tolerance";
+    if (status == SBM_ERR_DIVERGED) G->err = "relative residual not finite or above 1e10";
+    return status;
+}
+
+sbm_status amr_pack_u(sbm_grid G, double *const *u)
+{
+    Level &F = G->L[G->nl - 1];
+    if (!is_dev_ptr(u[0], G->dev)) return fail(G, SBM_ERR_ARG, "u[0] is not a device pointer");
+    CK(launch_pack<double, double>(F.g, F.g.dim, u[0], G->amr_u0, G->st));
+    for (int f = 0; f < 2 * F.g.dim; ++f)
+        for (int p = 0; p < F.g.dim; ++p)
+            if (G->bct[f][p] == SBM_DIRICHLET) CK(launch_set_face(F.g, f, p, G->bcv[f][p], G->amr_u0, G->st));
+    for (int a = 1; a <= G->npatch; ++a) {
+        if (!is_dev_ptr(u[a], G->dev)) return fail(G, SBM_ERR_ARG, "u[a] is not a device pointer");
+        Patch &Pt = G->P[a - 1];
+        CK(launch_pack<double, double>(Pt.s, Pt.s.dim, u[a], Pt.u64, G->st));
+    }
+    return SBM_OK;
+}
+
+sbm_status amr_unpack(sbm_grid G, double *base, double *const *pat, bool residual)
+{
+    Level &F = G->L[G->nl - 1];
+    CK(launch_unpack<double, double>(F.g, F.g.dim, residual ? G->amr_r0 : G->amr_u0, base, G->st));
+    for (int a = 1; a <= G->npatch; ++a) {
+        Patch &Pt = G->P[a - 1];
+        CK(launch_unpack<double, double>(Pt.s, Pt.s.dim, residual ? Pt.r64 : Pt.u64, pat[a], G->st));
+    }
+    return SBM_OK;
+}
+
+void free_patch(Patch &Pt)
+{
+    void *ptrs[] = {Pt.psi64, Pt.psi32, Pt.u64, Pt.f64, Pt.r64, Pt.de[0], Pt.de[1], Pt.drhs, Pt.dres,
+                    Pt.se[0], Pt.se[1], Pt.srhs, Pt.sres, Pt.Ke64, Pt.Ke32};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+}
+
 }  // namespace
 
 void sbm::set_library_error(const char *msg) { g_lib_error = msg; }
@@ -544,8 +918,9 @@ sbm_status sbm_grid_destroy(sbm_grid G)
         for (void *p : ptrs)
             if (p) cudaFree(p);
     }
+    for (int a = 0; a < G->npatch; ++a) free_patch(G->P[a]);
     void *ptrs[] = {G->fsrc, G->fadj, G->psi_raw, G->rho, G->part, G->scal, G->dbad, G->A64, G->A32, G->gjtmp, G->gather,
-                    G->derr};
+                    G->derr, G->amr_part, G->amr_u0, G->amr_r0};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (G->hscal) cudaFreeHost(G->hscal);
@@ -627,8 +1002,12 @@ sbm_status sbm_grid_create(const sbm_grid_desc *d, sbm_grid *out)
             CK(cudaMalloc(p, sizeof(float) * nd));
             CK(cudaMemset(*p, 0, sizeof(float) * nd));
         }
-        if (g.dim == 3)
-            L.has_tm = encode_plane_map(&L.tm32[0], L.su[0], g) && encode_plane_map(&L.tm32[1], L.su[1], g);
+        if (g.dim == 3) {
+            L.has_tm = true;
+            for (int i = 0; i < 2; ++i)
+                L.has_tm = L.has_tm && encode_plane_map(&L.tm32[i][0], L.su[i], g) &&
+                           encode_plane_map(&L.tm32[i][1], L.sf, g) && encode_cell_map(&L.tm32[i][2], L.psi32, g);
+        }
         const int nk = (1 << g.dim) * g.dim;
         CK(cudaMalloc(&L.Ke64, sizeof(double) * nk * nk));
         CK(cudaMalloc(&L.Ke32, sizeof(float) * nk * nk));
@@ -644,7 +1023,8 @@ sbm_status sbm_grid_create(const sbm_grid_desc *d, sbm_grid *out)
     CK(cudaMalloc(&G->rho, sizeof(double) * nc));
     G->npart = 1;
     for (int l = 0; l < G->nl; ++l)
-        G->npart = std::max(G->npart, std::max(sweep_blocks(G->L[l].g), sweep_blocks_f2(G->L[l].g)));
+        G->npart = std::max({G->npart, sweep_blocks(G->L[l].g, false), sweep_blocks(G->L[l].g, true),
+                             sweep_blocks_f2(G->L[l].g)});
     CK(cudaMalloc(&G->part, sizeof(double) * G->npart));
     CK(cudaMalloc(&G->derr, sizeof(int)));
     CK(cudaMemset(G->derr, 0, sizeof(int)));
@@ -732,6 +1112,7 @@ sbm_status sbm_set_psi(sbm_grid G, int level, const double *psi, double psi_min)
     CK(launch_set_psi(F.g, psi, psi_min, F.psi64, G->dbad, G->st));
     G->density = 0;
     G->psi_min = psi_min;
+    if (G->npatch > 0) G->amr_psi_dirty = true;   // covered cells are re-averaged at the next solve
     return finish_psi(G);
 }
 
@@ -896,7 +1277,8 @@ sbm_status sbm_residual(sbm_grid G, int level, int fp32, const double *f, const 
         return fail(G, SBM_ERR_ARG, "f, u and r must be device pointers");
     CK(cudaSetDevice(G->dev));
     Level &L = G->L[level];
-    const int nb = (int)sweep_nblocks(G, level, fp32 != 0, fp32 ? (const void *)L.su[1] : (const void *)L.du[1]);
+    const int nb = (int)sweep_nblocks(G, level, fp32 != 0, fp32 ? (const void *)L.su[1] : (const void *)L.du[1],
+                                      fp32 ? (const void *)L.sf : (const void *)L.df);
     if (fp32) {
         CK(launch_pack<double, float>(L.g, L.g.dim, u, L.su[1], G->st));
         CK(launch_pack<double, float>(L.g, L.g.dim, f, L.sf, G->st));
@@ -1039,7 +1421,7 @@ sbm_status sbm_dJdpsi(sbm_grid G, const double *u, const double *lam, double *g)
     return SBM_OK;
 }
 
-sbm_status sbm_time_kernel(sbm_grid G, int which, int reps, double *ms, double *bytes, double *flops)
+sbm_status sbm_time_kernel(sbm_grid G, int which, int reps, int flush_l2, double *ms, double *bytes, double *flops)
 {
     sbm_status s = check_ready(G);
     if (s != SBM_OK) return s;
@@ -1065,12 +1447,33 @@ sbm_status sbm_time_kernel(sbm_grid G, int which, int reps, double *ms, double *
         return sweep<double>(G, fine, kResidual, L.du[0], L.df, L.dr, nullptr, 0.0);
     };
     CK(launch());
-    CK(cudaEventRecord(G->ev0, G->st));
-    for (int r = 0; r < reps; ++r) CK(launch());
-    CK(cudaEventRecord(G->ev1, G->st));
-    CK(cudaEventSynchronize(G->ev1));
     float t = 0.f;
-    CK(cudaEventElapsedTime(&t, G->ev0, G->ev1));
+    if (flush_l2) {
+        const size_t fb = 256ull << 20;
+        void *flush = nullptr;
+        CK(cudaMalloc(&flush, fb));
+        for (int r = 0; r < reps; ++r) {
+            cudaError_t e = cudaMemsetAsync(flush, r & 0xff, fb, G->st);
+            if (e == cudaSuccess) e = cudaEventRecord(G->ev0, G->st);
+            if (e == cudaSuccess) e = launch();
+            if (e == cudaSuccess) e = cudaEventRecord(G->ev1, G->st);
+            if (e == cudaSuccess) e = cudaEventSynchronize(G->ev1);
+            float tr = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&tr, G->ev0, G->ev1);
+            if (e != cudaSuccess) {
+                cudaFree(flush);
+                return fail(G, SBM_ERR_CUDA, std::string("sbm_time_kernel: ") + cudaGetErrorString(e));
+            }
+            t += tr;
+        }
+        CK(cudaFree(flush));
+    } else {
+        CK(cudaEventRecord(G->ev0, G->st));
+        for (int r = 0; r < reps; ++r) CK(launch());
+        CK(cudaEventRecord(G->ev1, G->st));
+        CK(cudaEventSynchronize(G->ev1));
+        CK(cudaEventElapsedTime(&t, G->ev0, G->ev1));
+    }
     if (ms) *ms = t / reps;
     // per node: read u and f (d values each), psi (one cell per node), write d outputs
     double per_node;
@@ -1078,6 +1481,158 @@ sbm_status sbm_time_kernel(sbm_grid G, int which, int reps, double *ms, double *
     else per_node = (mixed ? 4.0 : 8.0) * (3 * d + 1);
     if (bytes) *bytes = per_node * nn;
     if (flops) *flops = cellf * nc + (which == SBM_K_JACOBI ? nodef : nodef - 11.0) * nn;
+    return SBM_OK;
+}
+
+// ------------------------------------------------------------------- BSAMR
+
+sbm_status sbm_amr_add_level(sbm_grid G, const sbm_box *box)
+{
+    if (!G || !box) return fail(G, SBM_ERR_ARG, "null argument");
+    if (G->npatch >= 8) return fail(G, SBM_ERR_ARG, "at most 8 patch levels");
+    CK(cudaSetDevice(G->dev));
+    const int a = G->npatch + 1, d = G->desc.dim;
+    Patch &Pt = G->P[a - 1];
+    for (int ax = 0; ax < 3; ++ax) {
+        const int lo = box->lo[ax], hi = box->hi[ax], N = level_N(G, a, ax);
+        if (ax >= d) {
+            if (lo != 0 || hi != 0) return fail(G, SBM_ERR_ARG, "2D boxes have lo[2] = hi[2] = 0");
+            continue;
+        }
+        if ((lo & 1) || (hi & 1) || lo < 0 || hi > N - 1 || hi - lo < 2)
+            return fail(G, SBM_ERR_ARG, "box corners must be even, inside the level and at least 2 apart");
+        if (a > 1) {
+            const Patch &Pp = G->P[a - 2];
+            const int Np = level_N(G, a - 1, ax);
+            const bool lo_ok = (lo == 0 && Pp.lo[ax] == 0) || lo >= 2 * Pp.lo[ax] + 2;
+            const bool hi_ok = (hi == N - 1 && Pp.hi[ax] == Np - 1) || hi <= 2 * Pp.hi[ax] - 2;
+            if (!lo_ok || !hi_ok) return fail(G, SBM_ERR_ARG, "box must lie inside the parent patch by one parent cell");
+        }
+    }
+    for (int ax = 0; ax < 3; ++ax) {
+        Pt.lo[ax] = box->lo[ax];
+        Pt.hi[ax] = box->hi[ax];
+    }
+    Pt.h = G->desc.h / (double)(1 << a);
+    Geom &g = Pt.s;
+    g.dim = d;
+    g.nx = Pt.hi[0] - Pt.lo[0] + 3;
+    g.ny = Pt.hi[1] - Pt.lo[1] + 3;
+    g.nz = d == 3 ? Pt.hi[2] - Pt.lo[2] + 3 : 1;
+    g.sx = (g.nx + 7) / 8 * 8;
+    g.sy = (long long)g.sx * g.ny;
+    g.cs = (g.sy * g.nz + 63) / 64 * 64;
+    g.dm[0] = g.dm[1] = g.dm[2] = 0;
+    Pt.v = g;
+    Pt.v.nx = g.nx - 2;
+    Pt.v.ny = g.ny - 2;
+    Pt.v.nz = d == 3 ? g.nz - 2 : 1;
+    Pt.voff = 1 + g.sx + (d == 3 ? g.sy : 0);
+    const size_t nd = (size_t)d * g.cs;
+    CK(cudaMalloc(&Pt.psi64, sizeof(double) * g.cs));
+    CK(cudaMemset(Pt.psi64, 0, sizeof(double) * g.cs));
+    CK(cudaMalloc(&Pt.psi32, sizeof(float) * g.cs));
+    CK(cudaMemset(Pt.psi32, 0, sizeof(float) * g.cs));
+    double **dp[] = {&Pt.u64, &Pt.f64, &Pt.r64, &Pt.de[0], &Pt.de[1], &Pt.drhs, &Pt.dres};
+    for (double **q : dp) {
+        CK(cudaMalloc(q, sizeof(double) * nd));
+        CK(cudaMemset(*q, 0, sizeof(double) * nd));
+    }
+    float **fp[] = {&Pt.se[0], &Pt.se[1], &Pt.srhs, &Pt.sres};
+    for (float **q : fp) {
+        CK(cudaMalloc(q, sizeof(float) * nd));
+        CK(cudaMemset(*q, 0, sizeof(float) * nd));
+    }
+    const int nk = (1 << d) * d;
+    CK(cudaMalloc(&Pt.Ke64, sizeof(double) * nk * nk));
+    CK(cudaMalloc(&Pt.Ke32, sizeof(float) * nk * nk));
+    G->npatch = a;
+    Level &F = G->L[G->nl - 1];
+    if (!G->amr_u0) {
+        const size_t nb = (size_t)F.g.dim * F.g.cs;
+        CK(cudaMalloc(&G->amr_u0, sizeof(double) * nb));
+        CK(cudaMemset(G->amr_u0, 0, sizeof(double) * nb));
+        CK(cudaMalloc(&G->amr_r0, sizeof(double) * nb));
+        CK(cudaMemset(G->amr_r0, 0, sizeof(double) * nb));
+    }
+    long long need = amr_blocks(F.g);
+    for (int b = 1; b <= G->npatch; ++b) need += amr_blocks(G->P[b - 1].s);
+    if (need > G->amr_npart) {
+        if (G->amr_part) cudaFree(G->amr_part);
+        CK(cudaMalloc(&G->amr_part, sizeof(double) * need));
+        G->amr_npart = need;
+    }
+    amr_refresh_infos(G);
+    return SBM_OK;
+}
+
+sbm_status sbm_amr_set_psi(sbm_grid G, int a, const double *psi, double psi_min)
+{
+    if (!G) return fail(nullptr, SBM_ERR_ARG, "null grid");
+    if (a < 1 || a > G->npatch) return fail(G, SBM_ERR_ARG, "patch level out of range");
+    if (!is_dev_ptr(psi, G->dev)) return fail(G, SBM_ERR_ARG, "psi is not a device pointer of the grid's device");
+    if (!(psi_min > 0.0)) return fail(G, SBM_ERR_ARG, "psi_min must be positive");
+    CK(cudaSetDevice(G->dev));
+    Patch &Pt = G->P[a - 1];
+    CK(cudaMemsetAsync(G->dbad, 0, sizeof(int), G->st));
+    CK(launch_amr_set_cells(Pt.s, psi, psi_min, Pt.psi64, G->dbad, G->st));
+    int bad = 0;
+    CK(cudaMemcpyAsync(&bad, G->dbad, sizeof(int), cudaMemcpyDeviceToHost, G->st));
+    CK(cudaStreamSynchronize(G->st));
+    if (bad) return fail(G, SBM_ERR_ARG, "psi contains non-finite values");
+    G->amr_psi_dirty = true;
+    return SBM_OK;
+}
+
+sbm_status sbm_amr_set_source(sbm_grid G, int a, const double *f)
+{
+    if (!G) return fail(nullptr, SBM_ERR_ARG, "null grid");
+    if (a < 1 || a > G->npatch) return fail(G, SBM_ERR_ARG, "patch level out of range");
+    if (!is_dev_ptr(f, G->dev)) return fail(G, SBM_ERR_ARG, "f is not a device pointer of the grid's device");
+    CK(cudaSetDevice(G->dev));
+    Patch &Pt = G->P[a - 1];
+    CK(launch_pack<double, double>(Pt.s, Pt.s.dim, f, Pt.f64, G->st));
+    CK(cudaStreamSynchronize(G->st));
+    return SBM_OK;
+}
+
+sbm_status sbm_amr_solve(sbm_grid G, double *const *u, const sbm_opts *opts, sbm_info *info)
+{
+    sbm_status s = check_ready(G);
+    if (s != SBM_OK) return s;
+    if (!u) return fail(G, SBM_ERR_ARG, "null u");
+    sbm_opts o;
+    sbm_default_opts(&o);
+    if (opts) o = *opts;
+    if ((s = validate_opts(G, o)) != SBM_OK) return s;
+    CK(cudaSetDevice(G->dev));
+    if (G->npatch == 0) return sbm_solve(G, u[0], opts, info);
+    if ((s = amr_prepare(G)) != SBM_OK) return s;
+    if ((s = amr_pack_u(G, u)) != SBM_OK) return s;
+    s = G->desc.precision == SBM_MIXED ? amr_run<float>(G, o, info) : amr_run<double>(G, o, info);
+    if (s != SBM_OK && s != SBM_ERR_NOCONV && s != SBM_ERR_DIVERGED) return s;
+    sbm_status s2 = amr_unpack(G, u[0], u, false);
+    if (s2 != SBM_OK) return s2;
+    CK(cudaStreamSynchronize(G->st));
+    return s;
+}
+
+sbm_status sbm_amr_residual(sbm_grid G, double *const *u, double *const *r, double *norm)
+{
+    sbm_status s = check_ready(G);
+    if (s != SBM_OK) return s;
+    if (!u || !r) return fail(G, SBM_ERR_ARG, "null argument");
+    if (G->npatch == 0) return fail(G, SBM_ERR_STATE, "no patch levels: use sbm_residual");
+    CK(cudaSetDevice(G->dev));
+    if ((s = amr_prepare(G)) != SBM_OK) return s;
+    if ((s = amr_pack_u(G, u)) != SBM_OK) return s;
+    for (int a = 0; a <= G->npatch; ++a)
+        if (!is_dev_ptr(r[a], G->dev)) return fail(G, SBM_ERR_ARG, "r[a] is not a device pointer");
+    CK(amr_residual<double>(G, 5));
+    if ((s = amr_unpack(G, r[0], r, true)) != SBM_OK) return s;
+    CK(cudaMemcpyAsync(G->hscal + 5, G->scal + 5, 2 * sizeof(double), cudaMemcpyDeviceToHost, G->st));
+    CK(cudaStreamSynchronize(G->st));
+    if (norm) *norm = G->hscal[6];
     return SBM_OK;
 }
 

@@ -196,3 +196,83 @@ inline Coef<T> make_coef(int dim, double h, double c11, double c12, double c44)
 }
 
 }  // namespace sbm
+
+namespace sbm {
+
+// ---- plane-shared form of cell_forces3 (used by the FP64 z-streaming kernel) ----
+// A node plane's in-plane transform is shared by the two cell layers it bounds,
+// and the forces a layer sends to its top plane are carried in the transformed
+// basis, so per layer only one in-plane forward and one in-plane transposed
+// butterfly are evaluated.
+
+// In-plane (x then y) transform of the 4 nodal values of one cell face.
+template <typename T>
+__host__ __device__ __forceinline__ void bfly4xy(T (&v)[4])
+{
+    const T a0 = v[0] + v[1], d0 = v[1] - v[0], a1 = v[2] + v[3], d1 = v[3] - v[2];
+    v[0] = a0 + a1;
+    v[2] = a1 - a0;
+    v[1] = d0 + d1;
+    v[3] = d1 - d0;
+}
+
+// Transpose of bfly4xy (y then x).
+template <typename T>
+__host__ __device__ __forceinline__ void bfly4xyT(T (&v)[4])
+{
+    const T w0 = v[0] - v[2], w2 = v[0] + v[2], w1 = v[1] - v[3], w3 = v[1] + v[3];
+    v[0] = w0 - w1;
+    v[1] = w0 + w1;
+    v[2] = w2 - w3;
+    v[3] = w2 + w3;
+}
+
+// One cell given the in-plane transforms of its bottom (Tb) and top (Tt) faces:
+// returns the transformed face forces Fb (to the bottom plane) and Ft (to the top).
+template <typename T>
+__host__ __device__ __forceinline__ void cell_faces3(const T (&Tb)[3][4], const T (&Tt)[3][4], T psi,
+                                                     const Coef<T> &c, T (&Fb)[3][4], T (&Ft)[3][4])
+{
+    T U[3][8];
+#pragma unroll
+    for (int p = 0; p < 3; ++p)
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            U[p][s] = Tb[p][s] + Tt[p][s];
+            U[p][s + 4] = Tt[p][s] - Tb[p][s];
+        }
+    const T ad = psi * c.ad, a12 = psi * c.a12, a44 = psi * c.a44;
+    const T b1 = psi * c.b1, b12 = psi * c.b12, b44 = psi * c.b44, c2 = psi * c.c2;
+    const T ltr = a12 * (U[0][1] + U[1][2] + U[2][4]);
+    const T sxx = madd(ad, U[0][1], ltr), syy = madd(ad, U[1][2], ltr), szz = madd(ad, U[2][4], ltr);
+    const T sxy = a44 * (U[1][1] + U[0][2]);
+    const T sxz = a44 * (U[2][1] + U[0][4]);
+    const T syz = a44 * (U[2][2] + U[1][4]);
+    const T S = U[2][3] + U[1][5] + U[0][6];
+    const T d03 = madd(b1, U[0][3], b12 * U[2][6]);
+    const T d26 = madd(b1, U[2][6], b12 * U[0][3]);
+    const T d13 = madd(b1, U[1][3], b12 * U[2][5]);
+    const T d25 = madd(b1, U[2][5], b12 * U[1][3]);
+    const T d05 = madd(b1, U[0][5], b12 * U[1][6]);
+    const T d16 = madd(b1, U[1][6], b12 * U[0][5]);
+    const T d23 = b44 * (S + U[2][3]);
+    const T d15 = b44 * (S + U[1][5]);
+    const T d06 = b44 * (S + U[0][6]);
+    const T d07 = c2 * U[0][7], d17 = c2 * U[1][7], d27 = c2 * U[2][7];
+    // dU[p][0] = 0; transposed z stage: bottom = dU[s] - dU[s+4], top = dU[s] + dU[s+4]
+    const T dU[3][8] = {{T(0), sxx, sxy, d03, sxz, d05, d06, d07},
+                        {T(0), sxy, syy, d13, syz, d15, d16, d17},
+                        {T(0), sxz, syz, d23, szz, d25, d26, d27}};
+#pragma unroll
+    for (int p = 0; p < 3; ++p) {
+        Fb[p][0] = T(0) - dU[p][4];
+        Ft[p][0] = dU[p][4];
+#pragma unroll
+        for (int s = 1; s < 4; ++s) {
+            Fb[p][s] = dU[p][s] - dU[p][s + 4];
+            Ft[p][s] = dU[p][s] + dU[p][s + 4];
+        }
+    }
+}
+
+}  // namespace sbm

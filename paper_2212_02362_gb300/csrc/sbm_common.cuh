@@ -20,14 +20,16 @@ struct Geom {
     int dim;
     int nx, ny, nz;
     int sx;
-    long long sy;          // sx * ny
+    long long sy;          // plane stride (sx * ny for a full level)
     long long cs;          // component stride (>= sy * nz, multiple of 64)
     unsigned dm[3];        // Dirichlet face bits per component (faces 0..5)
 };
 
+// sy is the plane stride; it equals sx * ny for a full level, and is larger for a
+// view of a sub-box of a padded patch (extents nx, ny, nz, strides of the storage).
 __host__ __device__ __forceinline__ long long gidx(const Geom &g, int i, int j, int k)
 {
-    return (long long)i + (long long)g.sx * ((long long)j + (long long)g.ny * k);
+    return (long long)i + (long long)g.sx * j + g.sy * k;
 }
 
 __host__ __device__ __forceinline__ bool is_dir(const Geom &g, int p, int i, int j, int k)
@@ -52,6 +54,29 @@ struct SweepArgs {
     int kchunk;            // node planes per block along z (3D)
 };
 
+// Number of z chunks for a z-streaming stencil launch: minimises
+// waves x (layers per block), where a wave is `slots` resident blocks (the
+// kernel's blocks per SM x 152 SMs), a block streams ceil(nzc/nc) layers plus one
+// halo layer, and `pair` counts layers two at a time (the packed FP32 kernel).
+inline int choose_chunks(long long xy, int nzc, int slots, bool pair)
+{
+    int best = 1;
+    long long best_cost = -1;
+    for (int nc = 1; nc <= nzc; ++nc) {
+        const int ch = (nzc + nc - 1) / nc;
+        const int nblk_z = (nzc + ch - 1) / ch;
+        if (nblk_z != nc) continue;                       // same chunking as a smaller nc
+        const long long waves = (xy * nc + slots - 1) / slots;
+        const long long layers = ch + (nc > 1 ? 1 : 0);
+        const long long cost = waves * (pair ? (layers + 1) / 2 : layers);
+        if (best_cost < 0 || cost < best_cost) {
+            best_cost = cost;
+            best = nc;
+        }
+    }
+    return best;
+}
+
 // ---- launchers (defined in k_stencil.cu / k_misc.cu) ----------------------
 
 // Number of kernels the launchers have enqueued (graph capture included).
@@ -61,15 +86,17 @@ extern long long g_launches;
 void set_library_error(const char *msg);
 
 // Tile shape of the stencil kernels (cells per block along x and y).
-void sweep_grid(const Geom &g, int *grid, int *kchunk);   // grid[3]; returns blocks
-long long sweep_blocks(const Geom &g);
+void sweep_grid(const Geom &g, int *grid, int *kchunk);   // grid[3] of the generic kernel
+// Blocks (= partial sums written) of launch_sweep in FP64 (fp64) or FP32.
+long long sweep_blocks(const Geom &g, bool fp64);
 
 template <typename T, typename TO>
 cudaError_t launch_sweep(int mode, const SweepArgs<T, TO> &a, cudaStream_t s);
 
 // FP32 3D sweep with TMA plane staging and packed FP32x2 arithmetic
-// (k_stencil_tma.cu).  tmap: CUtensorMap of a.u as 4D (x, y, z, component) with
-// a 40 x 10 x 1 x 3 box; err: device flag set when an mbarrier wait times out.
+// (k_stencil_tma.cu).  tmap: three CUtensorMaps — a.u and a.f as 4D (x, y, z,
+// component) with a 40 x 10 x 1 x 3 box, a.psi as 3D cells with a 40 x 10 x 1 box;
+// err: device flag set when an mbarrier wait times out.
 cudaError_t launch_sweep_f2(int mode, const SweepArgs<float, float> &a, const void *tmap, int *err,
                             cudaStream_t s);
 long long sweep_blocks_f2(const Geom &g);
@@ -122,5 +149,41 @@ cudaError_t launch_bottom_apply(int n, const T *Ainv, const int *gather, const T
 cudaError_t launch_dJdpsi(const Geom &g, const Coef<double> &c, const double *u, const double *lam,
                           double *g_out, double *grho_out, const double *rho, const double *psi_raw,
                           double psi_min, double q, int density, cudaStream_t s);
+
+// ---- block-structured refinement (k_amr.cu) ---------------------------------
+
+// Roles of the nodes of one refinement level (see k_amr.cu).
+struct AmrInfo {
+    int dim;
+    int N[3];              // global nodes per axis at this level
+    int lo[3], hi[3];      // the patch box (level indices); unused on the base level
+    int org[3];            // global index of storage node (0, 0, 0)
+    int is_base;
+    int has_child;
+    int clo[3], chi[3];    // child patch box (child-level indices)
+    unsigned dm[3];        // Dirichlet faces of the domain, per component
+};
+
+long long amr_blocks(const Geom &s);
+bool amr_owned_host(const AmrInfo &L, int i, int j, int k);
+cudaError_t launch_amr_mask(const Geom &s, const AmrInfo &L, double *r, cudaStream_t st);
+cudaError_t launch_amr_inject(const Geom &sc, const AmrInfo &Lc, const Geom &sp, const AmrInfo &Lp, const double *uc,
+                              double *up, cudaStream_t st);
+template <typename T>
+cudaError_t launch_amr_ghost(const Geom &sc, const AmrInfo &Lc, const Geom &sp, const AmrInfo &Lp, T *uc, const T *up,
+                             int mode, cudaStream_t st);
+template <typename T>
+cudaError_t launch_amr_restrict(const Geom &sc, const AmrInfo &Lc, const Geom &sp, const AmrInfo &Lp, const T *rc,
+                                T *rhsp, cudaStream_t st);
+template <typename T>
+cudaError_t launch_amr_update(const Geom &s, const AmrInfo &L, const T *e, double *u, cudaStream_t st);
+template <typename TO>
+cudaError_t launch_amr_sumsq_round(const Geom &s, const AmrInfo &L, const double *r, TO *out, double *part,
+                                   cudaStream_t st);
+cudaError_t launch_amr_coarsen_psi(const Geom &sc, const AmrInfo &Lc, const Geom &sp, const AmrInfo &Lp,
+                                   const double *psic, double *psip, cudaStream_t st);
+// padded-box cells: packed user layout <-> node-indexed storage (floor psi_min)
+cudaError_t launch_amr_set_cells(const Geom &s, const double *packed, double psi_min, double *lev, int *bad,
+                                 cudaStream_t st);
 
 }  // namespace sbm

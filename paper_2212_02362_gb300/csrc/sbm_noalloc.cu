@@ -68,7 +68,7 @@ extern "C" sbm_status sbm_residual_noalloc(int dim, const int n[3], double h, co
     g.sy = (long long)n[0] * n[1];
     g.cs = g.sy * n[2];
     for (int p = 0; p < 3; ++p) g.dm[p] = p < dim ? (dirichlet_faces[p] & (dim == 3 ? 63u : 15u)) : 0u;
-    const long long nblocks = sweep_blocks(g);
+    const long long nblocks = sweep_blocks(g, true);
     if (nblocks > SBM_NOALLOC_MAX_BLOCKS) {
         char msg[160];
         snprintf(msg, sizeof(msg), "grid needs %lld partial sums; the fixed scratch holds %d", nblocks,

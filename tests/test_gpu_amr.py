@@ -1,0 +1,145 @@
+"""Block-structured refinement on the GPU against the oracle's composite problem.
+
+Composite residual parity covers the injection, ghost fill (coarse-to-fine
+interpolation), coarse psi under patches and the ownership masks; the composite
+solve is compared with the oracle's dense composite solve on small hierarchies,
+with the uniformly refined solve when a patch covers the whole domain, and, at
+the 2D (129^2 base + 3 levels, colour Gauss-Seidel, FP64) and 3D (mixed
+precision) test sizes, through the oracle's composite residual of the GPU result.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from _amr import dense_solve
+from _sbm import cuda, host
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2212_02362_gb300 as sbm  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def built():
+    from paper_2212_02362_gb300 import build
+    build.build()
+    oracle.build()
+    return True
+
+
+def _custom(dim, n0, boxes, precision="fp64", smoother="jacobi"):
+    wk = W.voids_amr(dim, n0, len(boxes), count=2, rmin=0.1, rmax=0.2)
+    wk.boxes = boxes
+    wk.precision = precision
+    wk.smoother = smoother
+    return wk
+
+
+def _gpu(wk, precision=None):
+    g = sbm.Grid(wk.dim, wk.n, wk.h, precision=precision or wk.precision)
+    g.set_moduli(sbm.SBM_CUBIC, wk.moduli)
+    for face, comp, _ in wk.bcs:
+        g.set_bc(face, comp, sbm.SBM_DIRICHLET_FROM_U)
+    g.set_psi(cuda(wk.level_psi(0)), wk.psi_min)
+    for lo, hi in wk.boxes:
+        g.amr_add_level(lo, hi)
+    for a in range(1, len(wk.boxes) + 1):
+        g.amr_set_psi(a, cuda(wk.level_psi(a)), wk.psi_min)
+    return g
+
+
+def _oracle(wk):
+    P = oracle.Problem(wk.dim, wk.n, wk.h, *wk.moduli, dirichlet=wk.dirichlet_bits())
+    A = oracle.Amr(P, [(lo[:wk.dim], hi[:wk.dim]) for lo, hi in wk.boxes])
+    psis = [np.ascontiguousarray(np.maximum(wk.level_psi(a), wk.psi_min)) for a in range(A.nlev)]
+    oracle.amr_coarsen_psi(A, psis)
+    return A, psis
+
+
+def _zeros_f(A):
+    return [np.zeros(A.level_problem(a).ndofs) for a in range(A.nlev)]
+
+
+SMALL = {
+    "2d_two_patches": lambda: _custom(2, 9, [((4, 4, 0), (12, 12, 0)), ((10, 10, 0), (22, 22, 0))]),
+    "2d_touching_boundary": lambda: _custom(2, 9, [((0, 4, 0), (12, 16, 0))]),
+    "3d_one_patch": lambda: _custom(3, 5, [((2, 2, 2), (6, 6, 6))]),
+}
+
+
+@pytest.mark.parametrize("case", list(SMALL))
+def test_composite_residual_parity(built, case):
+    wk = SMALL[case]()
+    g = _gpu(wk)
+    A, psis = _oracle(wk)
+    us = [np.ascontiguousarray(wk.level_u0(a) + W.uniform(70 + a, A.level_problem(a).ndofs, -1e-3, 1e-3))
+          for a in range(A.nlev)]
+    fs = _zeros_f(A)
+    ref = oracle.amr_residual(A, psis, fs, [u.copy() for u in us])
+    rs, nrm = g.amr_residual([cuda(u) for u in us])
+    scale = max(np.abs(r).max() for r in ref)
+    for a in range(A.nlev):
+        assert np.abs(host(rs[a]) - ref[a]).max() <= 1e-12 * scale, a
+    assert np.isclose(nrm, np.sqrt(sum((r ** 2).sum() for r in ref)), rtol=1e-12)
+
+
+@pytest.mark.parametrize("case", list(SMALL))
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_composite_solve_matches_dense_oracle(built, case, precision):
+    wk = SMALL[case]()
+    A, psis = _oracle(wk)
+    us0 = [np.ascontiguousarray(wk.level_u0(a)) for a in range(A.nlev)]
+    ref = dense_solve(A, psis, _zeros_f(A), us0)
+    g = _gpu(wk, precision)
+    us = [cuda(u) for u in us0]
+    info = g.amr_solve(us, tol=1e-10, omega=wk.omega, smoother=wk.smoother)
+    assert info.converged
+    num = np.sqrt(sum(((host(us[a]) - ref[a]) ** 2).sum() for a in range(A.nlev)))
+    den = np.sqrt(sum((ref[a] ** 2).sum() for a in range(A.nlev)))
+    assert num <= 1e-8 * den, (num / den, info.cycles)
+
+
+def test_P10_patch_over_domain_equals_uniform_fine_gpu_solve(built):
+    n0 = 17
+    wk = _custom(2, n0, [((0, 0, 0), (32, 32, 0))])
+    g = _gpu(wk)
+    us = [cuda(wk.level_u0(a)) for a in range(2)]
+    g.amr_solve(us, tol=1e-12)
+    # the same fine problem as a single-level grid
+    nf = 2 * (n0 - 1) + 1
+    fine = W.Workload("fine", 2, (nf, nf, 1), wk.h / 2, wk.moduli, wk.bcs,
+                      wk.level_psi(1).reshape(nf + 1, nf + 1)[1:-1, 1:-1].reshape(-1), wk.psi_min,
+                      np.zeros(2 * nf * nf), W.initial_guess(2, (nf, nf, 1), wk.bcs))
+    gf = sbm.Grid(2, fine.n, fine.h)
+    gf.set_moduli(sbm.SBM_CUBIC, fine.moduli)
+    for face, comp, v in fine.bcs:
+        gf.set_bc(face, comp, sbm.SBM_DIRICHLET, float(v))
+    gf.set_psi(cuda(fine.psi), fine.psi_min)
+    uf = cuda(fine.u0)
+    gf.solve(uf, tol=1e-12)
+    patch = host(us[1]).reshape(2, nf + 2, nf + 2)[:, 1:-1, 1:-1].reshape(-1)
+    assert np.linalg.norm(patch - host(uf)) <= 1e-9 * np.linalg.norm(host(uf))
+
+
+@pytest.mark.parametrize("dim,n0,levels,precision", [(2, 129, 3, "fp64"), (3, 33, 2, "mixed")])
+def test_full_hierarchy_converges_with_oracle_residual(built, dim, n0, levels, precision):
+    """The refinement recipes of the 2D (GS, FP64) and 3D (mixed) AMR workloads:
+    the oracle's composite residual of the GPU solution is at the tolerance."""
+    wk = W.voids_amr(dim, n0, levels) if dim == 2 else W.voids_amr(3, n0, levels, count=16, rmin=0.04, rmax=0.12)
+    g = _gpu(wk, precision)
+    A, psis = _oracle(wk)
+    us0 = [np.ascontiguousarray(wk.level_u0(a)) for a in range(A.nlev)]
+    us = [cuda(u) for u in us0]
+    info = g.amr_solve(us, tol=1e-10, omega=wk.omega, smoother=wk.smoother, max_cycles=300)
+    assert info.converged, info
+    fs = _zeros_f(A)
+    r0 = oracle.amr_residual(A, psis, fs, [u.copy() for u in us0])
+    r = oracle.amr_residual(A, psis, fs, [host(u).copy() for u in us])
+    n0_ = np.sqrt(sum((x ** 2).sum() for x in r0))
+    n1_ = np.sqrt(sum((x ** 2).sum() for x in r))
+    assert n1_ / n0_ <= 2e-10, (n1_ / n0_, info.cycles)

@@ -270,6 +270,147 @@ def topopt3d(nx: int = 257, ny: int = 129, nz: int = 129, psi_min: float = 1e-3,
                     initial_guess(dim, nn, bcs), omega=0.5, precision="mixed", rho=rho)
 
 
+@dataclass
+class AmrWorkload:
+    """Base grid + nested refinement boxes (one per level).  psi is the same analytic
+    indicator evaluated at every level's cell centres; patch arrays cover the box
+    grown by one padding node per side (cells outside the domain get psi = 0)."""
+    name: str
+    dim: int
+    n: tuple
+    h: float
+    moduli: tuple
+    bcs: list
+    psi_fn: object
+    psi_min: float
+    boxes: list
+    smoother: str = "jacobi"
+    omega: float = 2.0 / 3.0
+    precision: str = "fp64"
+    notes: dict = field(default_factory=dict)
+
+    def dirichlet_bits(self):
+        bits = [0, 0, 0]
+        for face, comp, _ in self.bcs:
+            bits[comp] |= 1 << FACES[face]
+        return tuple(bits)
+
+    def level_h(self, a):
+        return self.h / 2 ** a
+
+    def level_N(self, a):
+        return tuple((self.n[ax] - 1) * 2 ** a + 1 if ax < self.dim else 1 for ax in range(3))
+
+    def storage_shape(self, a):
+        """nodes per axis of level a's storage (full grid for a = 0)"""
+        if a == 0:
+            return tuple(self.n)
+        lo, hi = self.boxes[a - 1]
+        return tuple(hi[ax] - lo[ax] + 3 if ax < self.dim else 1 for ax in range(3))
+
+    def origin(self, a):
+        if a == 0:
+            return (0, 0, 0)
+        lo = self.boxes[a - 1][0]
+        return tuple(lo[ax] - 1 if ax < self.dim else 0 for ax in range(3))
+
+    def level_psi(self, a):
+        """cell values of level a's storage (padding cells outside the domain: 0)"""
+        n, o, h = self.storage_shape(a), self.origin(a), self.level_h(a)
+        N = self.level_N(a)
+        ncz = n[2] - 1 if self.dim == 3 else 1
+        k, j, i = np.meshgrid(np.arange(ncz), np.arange(n[1] - 1), np.arange(n[0] - 1), indexing="ij")
+        gi, gj, gk = i + o[0], j + o[1], k + o[2]
+        X, Y, Z = (gi + 0.5) * h, (gj + 0.5) * h, ((gk + 0.5) * h if self.dim == 3 else np.zeros(gi.shape))
+        v = self.psi_fn(X, Y, Z)
+        inside = (gi >= 0) & (gi < N[0] - 1) & (gj >= 0) & (gj < N[1] - 1)
+        if self.dim == 3:
+            inside &= (gk >= 0) & (gk < N[2] - 1)
+        return np.where(inside, v, 0.0).reshape(-1)
+
+    def level_u0(self, a):
+        """Dirichlet values on the level's storage nodes on the domain faces, 0 elsewhere"""
+        n, o = self.storage_shape(a), self.origin(a)
+        N = self.level_N(a)
+        Nn = n[0] * n[1] * n[2]
+        u = np.zeros(self.dim * Nn)
+        k, j, i = np.meshgrid(np.arange(n[2]), np.arange(n[1]), np.arange(n[0]), indexing="ij")
+        g = [(i + o[0]).reshape(-1), (j + o[1]).reshape(-1), (k + o[2]).reshape(-1)]
+        for face, comp, value in self.bcs:
+            ax, side = FACES[face] // 2, FACES[face] % 2
+            on = g[ax] == (0 if side == 0 else N[ax] - 1)
+            u[comp * Nn:(comp + 1) * Nn][on] = value
+        return u
+
+
+def tag_boxes(dim, n0, psi_fn, levels, threshold=0.1, grow=2):
+    """One refinement box per level: cells of level a-1 where h |grad psi| (centred
+    differences of cell psi) exceeds ``threshold``, grown by ``grow`` cells, bounded
+    by an even-cornered box in level-a indices, nested one parent cell inside the
+    parent box unless on the domain boundary."""
+    boxes = []
+    h0 = 1.0 / (n0 - 1)
+    for a in range(1, levels + 1):
+        hp = h0 / 2 ** (a - 1)
+        Np = [(n0 - 1) * 2 ** (a - 1) + 1 if ax < dim else 1 for ax in range(3)]
+        nc = [Np[ax] - 1 if ax < dim else 1 for ax in range(3)]
+        axes = [(np.arange(nc[ax]) + 0.5) * hp if ax < dim else np.zeros(1) for ax in range(3)]
+        Z, Y, X = np.meshgrid(axes[2], axes[1], axes[0], indexing="ij")
+        psi = psi_fn(X, Y, Z)
+        grad = np.zeros(psi.shape)
+        for ax in range(dim):
+            axn = 2 - ax
+            d = (np.roll(psi, -1, axn) - np.roll(psi, 1, axn)) / 2.0
+            grad += d ** 2
+        tag = np.sqrt(grad) > threshold
+        if not tag.any():
+            break
+        idx = np.nonzero(tag)
+        lo, hi = [0, 0, 0], [0, 0, 0]
+        for ax in range(dim):
+            c = idx[2 - ax]
+            lo_c = max(int(c.min()) - grow, 0)
+            hi_c = min(int(c.max()) + 1 + grow, nc[ax])
+            lo[ax], hi[ax] = 2 * lo_c, 2 * hi_c                # parent cells -> level-a nodes
+            if a > 1:
+                plo, phi = boxes[-1][0][ax], boxes[-1][1][ax]
+                Npa = Np[ax]
+                lo[ax] = 0 if plo == 0 and lo[ax] <= 2 * plo + 2 else max(lo[ax], 2 * plo + 2)
+                hi[ax] = (2 * (Npa - 1)) if phi == Npa - 1 and hi[ax] >= 2 * phi - 2 else min(hi[ax], 2 * phi - 2)
+        boxes.append((tuple(lo), tuple(hi)))
+    return boxes
+
+
+def voids_amr(dim=2, n0=129, levels=3, count=8, rmin=0.03, rmax=0.10, psi_min=1e-4, seed=2001):
+    """Random non-overlapping voids (circles / spheres), tanh width 2 h_f with h_f the
+    finest spacing, refined by tag_boxes."""
+    st = _Stream(seed)
+    h0 = 1.0 / (n0 - 1)
+    balls = _random_balls(st, count, rmin, rmax, min(4.0 * h0, 0.04), dim)
+    hf = h0 / 2 ** levels
+
+    def psi_fn(X, Y, Z):
+        v = np.ones(np.shape(X))
+        coords = (X, Y, Z)
+        for c, r in balls:
+            dist = np.sqrt(sum((coords[ax] - c[ax]) ** 2 for ax in range(dim)))
+            v = v * _tanh_step(dist - r, 2.0 * hf)
+        return v
+
+    boxes = tag_boxes(dim, n0, psi_fn, levels)
+    if dim == 2:
+        bcs = [("-y", 0, 0.0), ("-y", 1, 0.0), ("+y", 0, 0.0), ("+y", 1, 0.01)]
+        moduli = iso_cubic(1.0, 0.3)
+    else:
+        bcs = [(f, p, (0.005 if f[0] == "+" else -0.005) if p == "xyz".index(f[1]) else 0.0)
+               for f in ("-x", "+x", "-y", "+y", "-z", "+z") for p in range(3)]
+        moduli = iso_cubic(1.0, 0.25)
+    n = (n0, n0, n0 if dim == 3 else 1)
+    return AmrWorkload(f"voids_amr_{dim}d", dim, n, h0, moduli, bcs, psi_fn, psi_min, boxes,
+                       smoother="gs" if dim == 2 else "jacobi", omega=2.0 / 3.0 if dim == 2 else 0.5,
+                       precision="fp64" if dim == 2 else "mixed", notes={"balls": balls})
+
+
 CONFIGS = {
     "plate_hole_2d": plate_hole,
     "damage_3d": damage3d,
