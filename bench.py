@@ -40,7 +40,45 @@ FP64_PEAK_GFLOPS = 1250.0       # GB300 FP64 rate (vector and tensor), from the 
 FP32_PEAK_GFLOPS = 152 * 128 * 2 * 2.070   # 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz
 
 
+AMR_WORKLOADS = {
+    # 2D refinement: 129^2 base + 3 levels around 8 circular voids, FP64, colour GS
+    "voids_amr_2d": lambda: W.voids_amr(2, 129, 3),
+    # 3D refinement: 129^3 base + 2 levels around 16 spherical voids, triaxial loading
+    "voids_amr_3d": lambda: W.voids_amr(3, 129, 2, count=16, rmin=0.04, rmax=0.12),
+}
+
+
+def amr_unknowns(wk):
+    """Composite unknowns: nodes owned by each level (in its box region and not
+    covered by the next level) times the dimension."""
+    def region(a, ax, lo, hi, N, even=False):
+        if a == 0:
+            return (N + 1) // 2 if even else N
+        step = 2 if even else 1
+        inner = len(range(lo + step, hi, step))
+        return inner + (lo == 0) + (hi == N - 1)
+    total = 0
+    nl = len(wk.boxes) + 1
+    for a in range(nl):
+        N = wk.level_N(a)
+        own = 1
+        for ax in range(wk.dim):
+            lo, hi = (wk.boxes[a - 1][0][ax], wk.boxes[a - 1][1][ax]) if a else (0, N[ax] - 1)
+            own *= region(a, ax, lo, hi, N[ax])
+        cov = 0
+        if a + 1 < nl:
+            Nc = wk.level_N(a + 1)
+            cov = 1
+            for ax in range(wk.dim):
+                lo, hi = wk.boxes[a][0][ax], wk.boxes[a][1][ax]
+                cov *= region(a + 1, ax, lo, hi, Nc[ax], even=True)
+        total += (own - cov) * wk.dim
+    return total
+
+
 def workload(name: str):
+    if name in AMR_WORKLOADS:
+        return AMR_WORKLOADS[name]()
     if name == "damage_3d_129":
         return W.damage3d(129)
     if name == "damage_3d_65":
@@ -132,6 +170,20 @@ def oracle_cycle_sample(wk, ncycles=1):
     return (time.perf_counter() - t) / ncycles
 
 
+def oracle_error(name, u):
+    """Relative 2-norm error of u at the stored sample dofs against the oracle's FP64
+    solution converged to 1e-14 (golden record written by the oracle)."""
+    path = os.path.join(ROOT, "tests", "golden", f"{name}_oracle.json")
+    if not os.path.exists(path):
+        return None
+    d = json.load(open(path))
+    idx = np.array(d["sample_index"])
+    ref = np.array(d["sample_u"])
+    got = u.detach().cpu().numpy()[idx]
+    return {"rel_err_at_samples": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
+            "samples": int(len(idx)), "oracle_relres": 1e-14}
+
+
 def oracle_cycles_to_tol(name):
     if name == "damage_3d_129" and os.path.exists(GOLDEN):
         return int(json.load(open(GOLDEN))["cycles_to_1e-10"]), "oracle golden record"
@@ -205,13 +257,21 @@ def run_ours(args, rank, world, local_rank):
         return g
 
     psi_d, f_d, u0_d = t64(wk.psi), t64(wk.f), t64(wk.u0)
+    rho_d = t64(wk.rho) if args.adjoint and wk.rho is not None else None
+    dJdu = f_d * wk.h ** wk.dim
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     opts = {"omega": wk.omega, "tol": 1e-10, "inner_cycles": args.inner if args.precision == "mixed" else 1}
 
     def timed_solves(g, nsteps, nwarm):
         with torch.cuda.stream(stream):
-            g.set_psi(psi_d, wk.psi_min)
-            g.set_source(f_d)
+            if not getattr(g, "_bench_ready", False):
+                # psi set-up and the lazy bottom-level inverse happen in the untimed warm-up
+                if rho_d is not None:
+                    g.set_density(rho_d, wk.psi_min)
+                else:
+                    g.set_psi(psi_d, wk.psi_min)
+                g.set_source(f_d)
+                g._bench_ready = True
             u = torch.empty_like(u0_d)
             infos, ms = [], []
             for i in range(nwarm + nsteps):
@@ -220,6 +280,9 @@ def run_ours(args, rank, world, local_rank):
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
                 info = g.solve(u, **opts)
+                if args.adjoint:
+                    # compliance J = h^d f.u: adjoint solve and dJ/drho
+                    g.adjoint(u, dJdu, want_rho=rho_d is not None, **opts)
                 e1.record(stream)
                 e1.synchronize()
                 if i >= nwarm:
@@ -247,18 +310,35 @@ def run_ours(args, rank, world, local_rank):
     total_ms, value = aggregate_replicas(sum(ms), wk.ndofs, args.steps, dist, dev)
     ms_per_step = total_ms / args.steps
     cycles = infos[-1].cycles
+    vcycles = infos[-1].vcycles
     launches = sum(i_.launches for i_ in infos)
+    # whole solve against HBM: algorithmic bytes per node of each step of the path (3D):
+    # FP64 residual 80 B, FP64 defect update 60 B, FP32 V(2,2) cycle over all levels 270 B
+    hbm_peak, peak_kind = peaks()
+    nodes = wk.ndofs // wk.dim
+    if args.precision == "mixed":
+        solve_bytes = nodes * (80.0 * (cycles + 1) + 60.0 * cycles + 270.0 * vcycles)
+    else:
+        solve_bytes = nodes * (80.0 * (cycles + 1) + 539.0 * cycles)
+    solve_hbm = {"algorithmic_bytes": solve_bytes,
+                 "achieved_gbs": solve_bytes / (ms_per_step * 1e-3) / 1e9,
+                 "frac": solve_bytes / (ms_per_step * 1e-3) / 1e9 / hbm_peak,
+                 "per_node": "80 B per FP64 residual, 60 B per defect update, 270 B per FP32 V(2,2) cycle"
+                             if args.precision == "mixed" else "80 B per FP64 residual, 539 B per FP64 V(2,2) cycle"}
+    err = oracle_error(args.workload, u)
 
     # ---- kernel roofline (dominant kernel, timed live on the grid stream) ----
     ms_k, bytes_k, flops_k = C.c_double(), C.c_double(), C.c_double()
     kid = {"residual64": _capi.SBM_K_RESIDUAL64, "jacobi": _capi.SBM_K_JACOBI}[args.roofline_kernel]
     with torch.cuda.stream(stream):
+        # NVTX range "roofline": lets a profiler select exactly these launches
+        torch.cuda.nvtx.range_push("roofline")
         _capi.check(sbm.lib().sbm_time_kernel(gmix._h, kid, 20, 1, C.byref(ms_k), C.byref(bytes_k),
                                               C.byref(flops_k)), gmix._h)
+        torch.cuda.nvtx.range_pop()
         ms_w, _, _ = C.c_double(), None, None
         _capi.check(sbm.lib().sbm_time_kernel(gmix._h, kid, 20, 0, C.byref(ms_w), C.byref(bytes_k),
                                               C.byref(flops_k)), gmix._h)
-    hbm_peak, peak_kind = peaks()
     if args.roofline_kernel == "residual64":
         achieved = flops_k.value / (ms_k.value * 1e-3) / 1e9
         roof = {"bound": "alu", "kernel": "k_sweep3_dp<residual> (FP64 defect residual, finest level)",
@@ -336,12 +416,147 @@ def run_ours(args, rank, world, local_rank):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64",
-                "data": "synthetic (seeded damage field)", "config": workload_config(wk, args.precision, args.inner),
-                "cycles_to_tol": cycles, "vcycles_per_s": cycles / (ms_per_step / 1e3),
+                "data": f"synthetic (seeded {wk.name} fields)", "config": dict(workload_config(wk, args.precision, args.inner),
+                                                                          adjoint_in_step=bool(args.adjoint)),
+                "cycles_to_tol": cycles, "vcycles_to_tol": vcycles, "vcycles_per_s": vcycles / (ms_per_step / 1e3),
+                "solve_hbm": solve_hbm, "err_vs_oracle": err,
                 "fp64_solve": fp64, "roofline": roof, "cpu_baseline": cpu,
                 "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                         "note": "host->device inputs, psi set-up (coarsening, bottom inverse), solve, result->host"},
                 "gpu_launches": launches, "clocks": clocks,
+                "wall_s_timed": t_wall1 - t_wall0}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def run_amr(args, rank, world, local_rank):
+    """Composite (block-structured refinement) solves: one step = one solve of the
+    composite problem from the initial guess to relres 1e-10."""
+    import torch
+    torch.cuda.set_device(local_rank)
+    import paper_2212_02362_gb300 as sbm
+    from paper_2212_02362_gb300 import _capi
+    import ctypes as C
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    wk = workload(args.workload)
+    precision = args.precision or wk.precision
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.Stream(device=dev)
+    nl = len(wk.boxes) + 1
+    psi_h = [torch.from_numpy(np.ascontiguousarray(wk.level_psi(a))) for a in range(nl)]
+    u0_h = [torch.from_numpy(np.ascontiguousarray(wk.level_u0(a))) for a in range(nl)]
+    psi_d = [t.to(dev) for t in psi_h]
+    u0_d = [t.to(dev) for t in u0_h]
+    unknowns = amr_unknowns(wk)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    opts = {"omega": wk.omega, "tol": 1e-10, "smoother": wk.smoother, "max_cycles": 500}
+
+    def make_grid(prec):
+        g = sbm.Grid(wk.dim, wk.n, wk.h, precision=prec, device=local_rank, stream=stream.cuda_stream)
+        g.set_moduli(sbm.SBM_CUBIC, wk.moduli)
+        for face, comp, _ in wk.bcs:
+            g.set_bc(face, comp, sbm.SBM_DIRICHLET_FROM_U)
+        with torch.cuda.stream(stream):
+            g.set_psi(psi_d[0], wk.psi_min)
+            for lo, hi in wk.boxes:
+                g.amr_add_level(lo, hi)
+            for a in range(1, nl):
+                g.amr_set_psi(a, psi_d[a], wk.psi_min)
+        return g
+
+    def timed(g, nsteps, nwarm):
+        infos, ms = [], []
+        with torch.cuda.stream(stream):
+            us = [torch.empty_like(u) for u in u0_d]
+            for i in range(nwarm + nsteps):
+                flush.zero_()
+                for u, u0 in zip(us, u0_d):
+                    u.copy_(u0)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                info = g.amr_solve(us, **opts)
+                e1.record(stream)
+                e1.synchronize()
+                if i >= nwarm:
+                    infos.append(info)
+                    ms.append(e0.elapsed_time(e1))
+        return infos, ms, us
+
+    g = make_grid(precision)
+    timed(g, 0, args.warmup)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local_rank) if rank == 0 else None
+    time.sleep(0.3 if sampler else 0)
+    t_wall0 = time.time()
+    infos, ms, us = timed(g, args.steps, 0)
+    torch.cuda.synchronize()
+    t_wall1 = time.time()
+    if dist:
+        dist.barrier()
+    total_ms, value = aggregate_replicas(sum(ms), unknowns, args.steps, dist, dev)
+    ms_per_step = total_ms / args.steps
+    fp64 = None
+    if precision == "mixed" and not args.skip_fp64:
+        g64 = make_grid("fp64")
+        timed(g64, 0, 1)
+        i64, ms64, u64 = timed(g64, 1, 0)
+        num = sum(float(((a - b) ** 2).sum()) for a, b in zip(u64, us))
+        den = sum(float((b ** 2).sum()) for b in u64)
+        fp64 = {"ms_per_step": ms64[0], "value": unknowns / (ms64[0] / 1e3) / 1e6, "cycles": i64[0].cycles,
+                "rel_diff_vs_mixed": (num / den) ** 0.5}
+        del g64
+    # end to end: host psi and initial guess in, solution out
+    out_h = [torch.empty_like(u).pin_memory() for u in u0_h]
+    psi_p = [t.pin_memory() for t in psi_h]
+    u0_p = [t.pin_memory() for t in u0_h]
+    e2e_ms = []
+    with torch.cuda.stream(stream):
+        pe = [torch.empty_like(t) for t in psi_d]
+        ue = [torch.empty_like(t) for t in u0_d]
+        for i in range(1 + min(args.steps, 2)):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for dst, src in zip(pe + ue, psi_p + u0_p):
+                dst.copy_(src, non_blocking=True)
+            g.set_psi(pe[0], wk.psi_min)
+            for a in range(1, nl):
+                g.amr_set_psi(a, pe[a], wk.psi_min)
+            g.amr_solve(ue, **opts)
+            for dst, src in zip(out_h, ue):
+                dst.copy_(src, non_blocking=True)
+            e1.record(stream)
+            e1.synchronize()
+            if i > 0:
+                e2e_ms.append(e0.elapsed_time(e1))
+    clocks = None
+    if sampler:
+        sampler.stop()
+        clocks = sampler.summary(t_wall0, t_wall1)
+    if rank == 0:
+        cyc = infos[-1].cycles
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32+f64" if precision == "mixed" else "f64",
+                "data": "synthetic (seeded voids)",
+                "config": {"workload": f"{wk.name} base {'x'.join(str(v) for v in wk.n[:wk.dim])} + "
+                                       f"{len(wk.boxes)} levels", "boxes": [list(map(list, b)) for b in wk.boxes],
+                           "composite_unknowns": unknowns, "precision": precision, "tol": 1e-10,
+                           "smoother": wk.smoother, "omega": wk.omega,
+                           "l2": "flushed (256 MB write) between timed steps"},
+                "cycles_to_tol": cyc, "cycles_per_s": cyc / (ms_per_step / 1e3), "fp64_solve": fp64,
+                "roofline": None, "cpu_baseline": None,
+                "e2e": {"value": world * unknowns / (statistics.mean(e2e_ms) / 1e3) / 1e6, "unit": UNIT,
+                        "h2d_bytes_per_step": sum(t.numel() * 8 for t in psi_h + u0_h),
+                        "d2h_bytes_per_step": sum(t.numel() * 8 for t in out_h)},
+                "gpu_launches": sum(i_.launches for i_ in infos), "clocks": clocks,
                 "wall_s_timed": t_wall1 - t_wall0}
         print(json.dumps(line), flush=True)
     if dist:
@@ -355,11 +570,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="damage_3d_129")
-    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--precision", choices=["mixed", "fp64"], default=None,
+                    help="default: the workload's (mixed for the 3D configurations)")
     ap.add_argument("--inner", type=int, default=8, help="FP32 V-cycles per FP64 defect residual (mixed)")
     ap.add_argument("--roofline-kernel", choices=["residual64", "jacobi"], default="jacobi")
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per launch of the roofline kernel from an ncu capture")
+    ap.add_argument("--adjoint", action="store_true",
+                    help="each step also runs the adjoint solve and dJ/drho of the compliance (topology optimisation)")
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     args = ap.parse_args()
@@ -371,6 +589,14 @@ def main():
     if args.impl == "reference":
         run_reference(args, rank, world)
         return
+    if args.workload in AMR_WORKLOADS:
+        from paper_2212_02362_gb300 import build
+        if rank == 0:
+            build.build()
+        run_amr(args, rank, world, local_rank)
+        return
+    if args.precision is None:
+        args.precision = "fp64" if args.workload == "plate_hole_2d" else "mixed"
     from paper_2212_02362_gb300 import build
     if rank == 0:
         build.build()

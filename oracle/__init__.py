@@ -357,6 +357,20 @@ def amr_fill(A: Amr, us):
     return us
 
 
+def amr_residual_at(A: Amr, psis, fs, us, lev, nodes, comps):
+    """Composite residual at sampled dofs: lev[s], global level node nodes[s] (3
+    ints), component comps[s]; the arrays are not filled or modified."""
+    lev = np.ascontiguousarray(lev, dtype=np.int32)
+    nodes = np.ascontiguousarray(nodes, dtype=np.int32).reshape(-1, 3)
+    comps = np.ascontiguousarray(comps, dtype=np.int32)
+    r = np.zeros(len(lev))
+    ip = C.POINTER(C.c_int)
+    _La().orc_amr_residual_at(C.byref(A.c()), _ptrs(psis), _ptrs(fs), _ptrs(us), C.c_long(len(lev)),
+                              lev.ctypes.data_as(ip), nodes.ctypes.data_as(ip), comps.ctypes.data_as(ip),
+                              r.ctypes.data_as(C.POINTER(C.c_double)))
+    return r
+
+
 def amr_residual(A: Amr, psis, fs, us):
     """Composite residual per level (u is filled in place)."""
     rs = [np.zeros_like(u) for u in us]

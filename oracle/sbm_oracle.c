@@ -828,3 +828,76 @@ void orc_amr_residual(const orc_amr *A, double *const *psi, double *const *f, do
         free(Ku);
     }
 }
+
+/* Filled value of component p at level-a node g (global level-a indices): the
+ * stored value on the level's own solve region (owned nodes), the value of the
+ * next finer level at the coincident node on covered nodes (recursively, so the
+ * finest owner's value), the (bi/tri)linear interpolation of the parent's filled
+ * values on ghosts, and 0 outside the domain.  This is what orc_amr_fill leaves
+ * in the arrays, evaluated at one node. */
+static double amr_value(const orc_amr *A, double *const *u, int a, const int g[3], int p)
+{
+    const int d = A->base.dim;
+    for (int ax = 0; ax < d; ++ax)
+        if (g[ax] < 0 || g[ax] > amr_N(A, a, ax) - 1) return 0.0;
+    if (amr_box_owned(A, a, g)) {
+        if (amr_covered(A, a, g)) {
+            const int g2[3] = {2 * g[0], 2 * g[1], d == 3 ? 2 * g[2] : 0};
+            return amr_value(A, u, a + 1, g2, p);
+        }
+        orc_problem P;
+        orc_amr_level_problem(A, a, &P);
+        return u[a][p * orc_nnodes(&P) + amr_local(A, a, (int *)g)];
+    }
+    int nodd = 0;
+    for (int ax = 0; ax < d; ++ax) nodd += g[ax] & 1;
+    double s = 0.0;
+    for (int c = 0; c < (1 << d); ++c) {
+        int gc[3] = {0, 0, 0}, skip = 0;
+        for (int ax = 0; ax < d; ++ax) {
+            const int bit = (c >> ax) & 1;
+            if (!(g[ax] & 1) && bit) skip = 1;
+            gc[ax] = (g[ax] >> 1) + ((g[ax] & 1) ? bit : 0);
+        }
+        if (skip) continue;
+        s += amr_value(A, u, a - 1, gc, p);
+    }
+    return s / (double)(1 << nodd);
+}
+
+void orc_amr_residual_at(const orc_amr *A, double *const *psi, double *const *f, double *const *u, long n,
+                         const int *lev, const int *node, const int *comp, double *r)
+{
+    const int d = A->base.dim, nc = 1 << d, nd = nc * d;
+    double Ke[24 * 24];
+    for (long s = 0; s < n; ++s) {
+        const int a = lev[s], p = comp[s];
+        const int g[3] = {node[3 * s], node[3 * s + 1], d == 3 ? node[3 * s + 2] : 0};
+        if (!orc_amr_owned(A, a, g[0], g[1], g[2]) || amr_dirichlet(A, a, (int *)g, p)) {
+            r[s] = 0.0;
+            continue;
+        }
+        orc_problem P;
+        orc_amr_level_problem(A, a, &P);
+        orc_element_matrix(&P, Ke);
+        const int ncx = P.n[0] - 1, ncy = P.n[1] - 1;
+        double Ku = 0.0;
+        for (int b = 0; b < nc; ++b) {        /* g is corner b of cell g - offset(b) */
+            int C[3] = {g[0] - (b & 1), g[1] - ((b >> 1) & 1), d == 3 ? g[2] - ((b >> 2) & 1) : 0};
+            int inside = 1, lc[3] = {0, 0, 0};
+            for (int ax = 0; ax < d; ++ax) {
+                if (C[ax] < 0 || C[ax] > amr_N(A, a, ax) - 2) inside = 0;
+                lc[ax] = a ? C[ax] - A->lo[a][ax] + 1 : C[ax];
+            }
+            if (!inside) continue;
+            const double pc = psi[a][lc[0] + (long)ncx * (lc[1] + (long)ncy * lc[2])];
+            for (int e = 0; e < nc; ++e) {
+                const int ge[3] = {C[0] + (e & 1), C[1] + ((e >> 1) & 1), d == 3 ? C[2] + ((e >> 2) & 1) : 0};
+                for (int q = 0; q < d; ++q)
+                    Ku += pc * Ke[(b * d + p) * nd + e * d + q] * amr_value(A, u, a, ge, q);
+            }
+        }
+        r[s] = f[a][p * orc_nnodes(&P) + amr_local(A, a, (int *)g)] - Ku;
+    }
+}
+

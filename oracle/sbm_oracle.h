@@ -139,6 +139,12 @@ void orc_amr_fill(const orc_amr *A, double *const *u);
  * ghost, covered and Dirichlet dofs.  u is filled (injection + ghosts) in place. */
 void orc_amr_residual(const orc_amr *A, double *const *psi, double *const *f, double *const *u,
                       double *const *r);
+/* The composite residual at n sampled dofs (level lev[s], global level indices
+ * node[3s..3s+2], component comp[s]) without filling or touching the arrays:
+ * ghost and covered values are evaluated on the fly.  Equals orc_amr_residual at
+ * those dofs; for checking hierarchies too large to fill and sweep whole. */
+void orc_amr_residual_at(const orc_amr *A, double *const *psi, double *const *f, double *const *u, long n,
+                         const int *lev, const int *node, const int *comp, double *r);
 
 #ifdef __cplusplus
 }

@@ -32,8 +32,35 @@ inline dim3 node_grid(const Geom &g)
     return dim3((g.nx + 31) / 32, (g.ny + 3) / 4, (g.nz + 1) / 2);
 }
 
+template <typename T> struct Vec2;
+template <> struct Vec2<float> { using type = float2; };
+template <> struct Vec2<double> { using type = double2; };
+
+// Fine values x = 2I-1, 2I, 2I+1 of one row, with weights 1/2, 1, 1/2 (missing
+// neighbours beyond the row weigh 0).  2I is even and rows start on 8-element
+// boundaries, so (2I, 2I+1) is one aligned vector load when 2I+1 is in the row.
+template <typename T>
+__device__ __forceinline__ T fw_row(const T *__restrict__ row, int I, int nx)
+{
+    using V = typename Vec2<T>::type;
+    const int i = 2 * I;
+    const T lo = (i > 0) ? row[i - 1] : T(0);
+    T c, hi;
+    if (i + 1 < nx) {
+        const V v = *reinterpret_cast<const V *>(row + i);
+        c = v.x;
+        hi = v.y;
+    } else {
+        c = row[i];
+        hi = T(0);
+    }
+    return c + T(0.5) * (lo + hi);
+}
+
 // r_c = P^T r_f / 2^d on free coarse dofs (Sec. 2.2 level transfers); coarse
 // node (I,J,K) sits on fine node (2I,2J,2K), the linear weights are 1, 1/2.
+// The 3^d fine rows are read with independent loads (clamped index, zero weight
+// outside the grid) so they are all in flight together.
 template <typename T>
 __global__ void k_restrict(const Geom gf, const Geom gc, const T *__restrict__ rf, T *__restrict__ fc)
 {
@@ -42,25 +69,27 @@ __global__ void k_restrict(const Geom gf, const Geom gc, const T *__restrict__ r
     const int K = blockIdx.z * blockDim.z + threadIdx.z;
     if (I >= gc.nx || J >= gc.ny || K >= gc.nz) return;
     const bool d3 = gf.dim == 3;
-    const T w[3] = {T(0.5), T(1), T(0.5)};
     const T scale = d3 ? T(0.125) : T(0.25);
     const long long oc = gidx(gc, I, J, K);
+    const int nz_rows = d3 ? 3 : 1;
     for (int p = 0; p < gf.dim; ++p) {
         T s = T(0);
         if (!is_dir(gc, p, I, J, K)) {
-            for (int dk = (d3 ? -1 : 0); dk <= (d3 ? 1 : 0); ++dk) {
-                const int k = 2 * K + dk;
-                if (k < 0 || k >= gf.nz) continue;
-                for (int dj = -1; dj <= 1; ++dj) {
-                    const int j = 2 * J + dj;
-                    if (j < 0 || j >= gf.ny) continue;
-                    T sr = T(0);
-                    for (int di = -1; di <= 1; ++di) {
-                        const int i = 2 * I + di;
-                        if (i < 0 || i >= gf.nx) continue;
-                        sr += w[di + 1] * rf[p * gf.cs + gidx(gf, i, j, k)];
-                    }
-                    s += (d3 ? w[dk + 1] : T(1)) * w[dj + 1] * sr;
+            const T *base = rf + p * gf.cs;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                if (a >= nz_rows) break;
+                const int k = d3 ? 2 * K + a - 1 : 0;
+                const bool kin = k >= 0 && k < gf.nz;
+                const T wk = !d3 ? T(1) : (kin ? (a == 1 ? T(1) : T(0.5)) : T(0));
+                const int kc = kin ? k : 2 * K;
+#pragma unroll
+                for (int b = 0; b < 3; ++b) {
+                    const int j = 2 * J + b - 1;
+                    const bool jin = j >= 0 && j < gf.ny;
+                    const T w = wk * (jin ? (b == 1 ? T(1) : T(0.5)) : T(0));
+                    const int jc = jin ? j : 2 * J;
+                    s += w * fw_row<T>(base + gidx(gf, 0, jc, kc), I, gf.nx);
                 }
             }
             s *= scale;
@@ -69,33 +98,71 @@ __global__ void k_restrict(const Geom gf, const Geom gc, const T *__restrict__ r
     }
 }
 
-// u_f += P e_c on free fine dofs.
+// u_f += P e_c on free fine dofs.  One thread per coarse node (I,J,K) writes the
+// fine nodes (2I+a, 2J+b, 2K+c), a, b, c in {0, 1}, that exist: the coincident
+// node copies e_c, the others average the 2, 4 or 8 coarse neighbours.  The x
+// pair (2I, 2I+1) is read and written as one aligned vector.
 template <typename T>
 __global__ void k_prolong_add(const Geom gf, const Geom gc, const T *__restrict__ ec, T *__restrict__ uf)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    const int k = blockIdx.z * blockDim.z + threadIdx.z;
-    if (i >= gf.nx || j >= gf.ny || k >= gf.nz) return;
-    const int I0 = i >> 1, I1 = (i + 1) >> 1, J0 = j >> 1, J1 = (j + 1) >> 1;
-    const int K0 = k >> 1, K1 = (gf.dim == 3) ? (k + 1) >> 1 : K0;
-    const T wi = (I0 == I1) ? T(1) : T(0.5), wj = (J0 == J1) ? T(1) : T(0.5), wk = (K0 == K1) ? T(1) : T(0.5);
-    const long long of = gidx(gf, i, j, k);
+    using V = typename Vec2<T>::type;
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    const int J = blockIdx.y * blockDim.y + threadIdx.y;
+    const int K = blockIdx.z * blockDim.z + threadIdx.z;
+    if (I >= gc.nx || J >= gc.ny || K >= gc.nz) return;
+    const bool d3 = gf.dim == 3;
+    const bool hx = I + 1 < gc.nx, hy = J + 1 < gc.ny, hz = d3 && K + 1 < gc.nz;
+    const int I1 = hx ? I + 1 : I, J1 = hy ? J + 1 : J, K1 = hz ? K + 1 : K;
+    const int i0 = 2 * I, j0 = 2 * J, k0 = d3 ? 2 * K : 0;
     for (int p = 0; p < gf.dim; ++p) {
-        if (is_dir(gf, p, i, j, k)) continue;
         const T *e = ec + p * gc.cs;
-        T s = wi * wj * e[gidx(gc, I0, J0, K0)];
-        if (I1 != I0) s += wi * wj * e[gidx(gc, I1, J0, K0)];
-        if (J1 != J0) s += wi * wj * e[gidx(gc, I0, J1, K0)];
-        if (I1 != I0 && J1 != J0) s += wi * wj * e[gidx(gc, I1, J1, K0)];
-        if (K1 != K0) {
-            T s2 = e[gidx(gc, I0, J0, K1)];
-            if (I1 != I0) s2 += e[gidx(gc, I1, J0, K1)];
-            if (J1 != J0) s2 += e[gidx(gc, I0, J1, K1)];
-            if (I1 != I0 && J1 != J0) s2 += e[gidx(gc, I1, J1, K1)];
-            s = wk * (s + wi * wj * s2);
+        // coarse values of the cell above (I,J,K): [z][y][x]
+        T c[2][2][2];
+        c[0][0][0] = e[gidx(gc, I, J, K)];
+        c[0][0][1] = e[gidx(gc, I1, J, K)];
+        c[0][1][0] = e[gidx(gc, I, J1, K)];
+        c[0][1][1] = e[gidx(gc, I1, J1, K)];
+        c[1][0][0] = e[gidx(gc, I, J, K1)];
+        c[1][0][1] = e[gidx(gc, I1, J, K1)];
+        c[1][1][0] = e[gidx(gc, I, J1, K1)];
+        c[1][1][1] = e[gidx(gc, I1, J1, K1)];
+        T *u = uf + p * gf.cs;
+#pragma unroll
+        for (int zc = 0; zc < 2; ++zc) {
+            if (zc == 1 && !hz) break;
+#pragma unroll
+            for (int yc = 0; yc < 2; ++yc) {
+                if (yc == 1 && !hy) break;
+                // values at x = 2I (even) and 2I+1 (odd) on this fine row
+                T ev, od;
+                if (zc == 0 && yc == 0) {
+                    ev = c[0][0][0];
+                    od = T(0.5) * (c[0][0][0] + c[0][0][1]);
+                } else if (zc == 0) {
+                    ev = T(0.5) * (c[0][0][0] + c[0][1][0]);
+                    od = T(0.25) * ((c[0][0][0] + c[0][0][1]) + (c[0][1][0] + c[0][1][1]));
+                } else if (yc == 0) {
+                    ev = T(0.5) * (c[0][0][0] + c[1][0][0]);
+                    od = T(0.25) * ((c[0][0][0] + c[0][0][1]) + (c[1][0][0] + c[1][0][1]));
+                } else {
+                    ev = T(0.25) * ((c[0][0][0] + c[0][1][0]) + (c[1][0][0] + c[1][1][0]));
+                    od = T(0.125) * (((c[0][0][0] + c[0][0][1]) + (c[0][1][0] + c[0][1][1])) +
+                                     ((c[1][0][0] + c[1][0][1]) + (c[1][1][0] + c[1][1][1])));
+                }
+                const int j = j0 + yc, k = k0 + zc;
+                T *row = u + gidx(gf, 0, j, k);
+                const T me = is_dir(gf, p, i0, j, k) ? T(0) : T(1);
+                if (hx) {
+                    const T mo = is_dir(gf, p, i0 + 1, j, k) ? T(0) : T(1);
+                    V v = *reinterpret_cast<V *>(row + i0);
+                    v.x += me * ev;
+                    v.y += mo * od;
+                    *reinterpret_cast<V *>(row + i0) = v;
+                } else {
+                    row[i0] += me * ev;
+                }
+            }
         }
-        uf[p * gf.cs + of] += s;
     }
 }
 
@@ -309,30 +376,89 @@ __global__ void k_bottom_dirichlet(const Geom g, double *A)
     }
 }
 
-// Gauss-Jordan inversion without pivoting (SPD matrix), pivot k:
-//   stage 1: tmp[0..n) = row k / a_kk with the pivot entry replaced by 1/a_kk,
-//            tmp[n..2n) = column k (the multipliers);
-//   stage 2: every row i != k subtracts multiplier_i * tmp; row k becomes tmp.
-__global__ void k_gj_stage1(int n, int k, const double *A, double *tmp)
+// Gauss-Jordan inversion without pivoting (SPD matrix; Dirichlet rows and
+// columns are identity and are skipped as pivots).  For pivot k with p = a_kk:
+//   a_kk <- 1/p,  a_kj <- a_kj/p,  a_ik <- -a_ik/p,  a_ij <- a_ij - a_ik a_kj/p.
+// One cooperative launch runs every pivot: the grid updates the matrix row by
+// row (block per row, threads over columns), and while doing so copies the next
+// pivot's row and column into the other half of a double buffer, so one grid
+// barrier per pivot suffices.  The barrier is a counter + generation in global
+// memory; every wait is bounded (on timeout bar[2] is set and the kernel ends).
+constexpr long long kGridSpinLimit = 1LL << 22;
+
+__device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned nblocks)
 {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n) return;
-    const double ip = 1.0 / A[(long long)k * n + k];
-    tmp[t] = (t == k) ? ip : A[(long long)k * n + t] * ip;
-    tmp[n + t] = A[(long long)t * n + k];
+    __syncthreads();
+    int ok = 1;
+    if (threadIdx.x == 0) {
+        volatile unsigned *gen = bar + 1;
+        const unsigned g0 = *gen;
+        __threadfence();
+        if (atomicAdd(bar, 1u) == nblocks - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            long long it = 0;
+            while (*gen == g0) {
+                if (++it > kGridSpinLimit || *(volatile unsigned *)(bar + 2)) {
+                    atomicExch(bar + 2, 1u);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        __threadfence();
+    }
+    return __syncthreads_and(ok) != 0;
 }
 
-__global__ void k_gj_stage2(int n, int k, double *A, const double *tmp)
+__device__ __forceinline__ int next_pivot(const Geom &g, long long N, int k, int n)
 {
-    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (t >= (long long)n * n) return;
-    const int i = (int)(t / n), j = (int)(t % n);
-    if (i == k) {
-        A[t] = tmp[j];
-    } else {
-        const double m = tmp[n + i];
-        const double akj = (j == k) ? 0.0 : A[t];
-        A[t] = ((j == k) ? 0.0 : akj) - m * tmp[j];
+    for (; k < n; ++k) {
+        int i, j, kk;
+        node_of(g, k % N, i, j, kk);
+        if (!is_dir(g, (int)(k / N), i, j, kk)) return k;
+    }
+    return n;
+}
+
+__global__ void k_gauss_jordan(const Geom g, int n, double *A, double *tmp, unsigned *bar)
+{
+    const long long N = (long long)g.nx * g.ny * g.nz;
+    const unsigned nb = gridDim.x;
+    // tmp[b * 2n + j]: row of the pivot; tmp[b * 2n + n + i]: its column (both unscaled)
+    int k = next_pivot(g, N, 0, n);
+    if (k >= n) return;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+        tmp[t] = A[(long long)k * n + t];
+        tmp[n + t] = A[(long long)t * n + k];
+    }
+    if (!grid_barrier(bar, nb)) return;
+    int cur = 0;
+    while (k < n) {
+        const int kn = next_pivot(g, N, k + 1, n);
+        const double *R = tmp + (long long)cur * 2 * n, *Cc = R + n;
+        double *Rn = tmp + (long long)(1 - cur) * 2 * n, *Cn = Rn + n;
+        // the pivot row and column were written by other blocks: read them from L2
+        const double ip = 1.0 / __ldcg(R + k);
+        for (int i = blockIdx.x; i < n; i += gridDim.x) {
+            double *row = A + (long long)i * n;
+            const double m = __ldcg(Cc + i);
+            for (int j = threadIdx.x; j < n; j += blockDim.x) {
+                const double rkj = (j == k) ? ip : __ldcg(R + j) * ip;
+                double v;
+                if (i == k) v = rkj;
+                else v = ((j == k) ? 0.0 : row[j]) - m * rkj;
+                row[j] = v;
+                if (i == kn) Rn[j] = v;
+                if (j == kn) Cn[i] = v;
+            }
+        }
+        if (!grid_barrier(bar, nb)) return;
+        cur ^= 1;
+        k = kn;
     }
 }
 
@@ -418,7 +544,7 @@ template cudaError_t launch_restrict<float>(const Geom &, const Geom &, const fl
 template <typename T>
 cudaError_t launch_prolong_add(const Geom &gf, const Geom &gc, const T *ec, T *uf, cudaStream_t s)
 {
-    k_prolong_add<T><<<node_grid(gf), kNodeBlock, 0, s>>>(gf, gc, ec, uf);
+    k_prolong_add<T><<<node_grid(gc), kNodeBlock, 0, s>>>(gf, gc, ec, uf);
     ++g_launches;
     return cudaGetLastError();
 }
@@ -523,15 +649,24 @@ cudaError_t launch_bottom_dirichlet(const Geom &g, double *A, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_gauss_jordan(int n, double *A, double *tmp, cudaStream_t s)
+cudaError_t launch_gauss_jordan(const Geom &g, int n, double *A, double *tmp, unsigned *bar, cudaStream_t s)
 {
-    for (int k = 0; k < n; ++k) {
-        k_gj_stage1<<<nblk(n), kThreads, 0, s>>>(n, k, A, tmp);
-        k_gj_stage2<<<nblk((long long)n * n), kThreads, 0, s>>>(n, k, A, tmp);
-    }
-    g_launches += 2LL * n - 1;
+    int dev = 0, nsm = 0, per_sm = 0, coop = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gauss_jordan, kThreads, 0);
+    if (e != cudaSuccess) return e;
+    if (!coop || per_sm < 1) return cudaErrorNotSupported;
+    int nblocks = nsm;                      // one block per SM, all co-resident
+    if (nblocks > n) nblocks = n;
+    e = cudaMemsetAsync(bar, 0, 4 * sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    Geom gg = g;
+    void *args[] = {&gg, &n, &A, &tmp, &bar};
+    e = cudaLaunchCooperativeKernel((const void *)k_gauss_jordan, dim3(nblocks), dim3(kThreads), args, 0, s);
     ++g_launches;
-    return cudaGetLastError();
+    return e;
 }
 
 cudaError_t launch_round(long long n, const double *src, float *dst, cudaStream_t s)

@@ -456,6 +456,66 @@ long long sweep_blocks(const Geom &g, bool fp64)
     return (long long)grid[0] * grid[1] * grid[2];
 }
 
+// Small 3D levels (FP32): one thread per node gathers its 3x3x3 neighbourhood and
+// evaluates the 2^3 cells around it, keeping its own corner's force.  Every cell
+// is evaluated by each of its 8 corner nodes (8x the arithmetic), but the kernel
+// has no shared memory, no barriers and no z streaming: on coarse levels, whose
+// cost is latency, it finishes in a fraction of the time of the tiled kernels.
+template <int MODE>
+__global__ void __launch_bounds__(128) k_sweep3_node(const SweepArgs<float, float> a)
+{
+    const Geom &g = a.g;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z * blockDim.z + threadIdx.z;
+    if (i >= g.nx || j >= g.ny || k >= g.nz) return;
+    float nb[3][27];
+#pragma unroll
+    for (int q = 0; q < 27; ++q) {
+        const int x = i + q % 3 - 1, y = j + (q / 3) % 3 - 1, z = k + q / 9 - 1;
+        const bool in = x >= 0 && x < g.nx && y >= 0 && y < g.ny && z >= 0 && z < g.nz;
+        const long long o = in ? gidx(g, x, y, z) : 0;
+#pragma unroll
+        for (int p = 0; p < 3; ++p) nb[p][q] = in ? a.u[p * g.cs + o] : 0.f;
+    }
+    float Ku[3] = {0.f, 0.f, 0.f}, psisum = 0.f;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        // cell with lower corner (i - cx, j - cy, k - cz); this node is its corner (cx, cy, cz)
+        const int cx = c & 1, cy = (c >> 1) & 1, cz = (c >> 2) & 1;
+        const int ci = i - cx, cj = j - cy, ck = k - cz;
+        if (ci < 0 || cj < 0 || ck < 0 || ci >= g.nx - 1 || cj >= g.ny - 1 || ck >= g.nz - 1) continue;
+        const float ps = a.psi[gidx(g, ci, cj, ck)];
+        psisum += ps;
+        float U[3][8];
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+            const int q = ((b & 1) - cx + 1) + 3 * (((b >> 1) & 1) - cy + 1) + 9 * (((b >> 2) & 1) - cz + 1);
+#pragma unroll
+            for (int p = 0; p < 3; ++p) U[p][b] = nb[p][q];
+        }
+        cell_forces3<float>(U, ps, a.c);
+#pragma unroll
+        for (int p = 0; p < 3; ++p) Ku[p] += U[p][c];
+    }
+    double ssq = 0.0;
+    const float uv[3] = {nb[0][13], nb[1][13], nb[2][13]};
+    finalize<float, float, MODE>(a, i, j, k, Ku, psisum, uv, ssq);
+}
+
+cudaError_t launch_sweep_node(int mode, const SweepArgs<float, float> &a, cudaStream_t s)
+{
+    const dim3 b(32, 4, 1), gr((a.g.nx + 31) / 32, (a.g.ny + 3) / 4, a.g.nz);
+    switch (mode) {
+    case kApply: k_sweep3_node<kApply><<<gr, b, 0, s>>>(a); break;
+    case kResidual: k_sweep3_node<kResidual><<<gr, b, 0, s>>>(a); break;
+    case kJacobi: k_sweep3_node<kJacobi><<<gr, b, 0, s>>>(a); break;
+    default: return cudaErrorInvalidValue;
+    }
+    ++g_launches;
+    return cudaGetLastError();
+}
+
 template <typename T, typename TO, int MODE>
 static cudaError_t launch_mode(const SweepArgs<T, TO> &a0, cudaStream_t s)
 {

@@ -93,6 +93,7 @@ struct sbm_grid_s {
     int *dbad = nullptr;
     int nb = 0;                 // bottom dofs
     double *A64 = nullptr, *gjtmp = nullptr;
+    unsigned *gjbar = nullptr;  // grid-barrier words of the bottom-level inversion
     float *A32 = nullptr;
     int *gather = nullptr;
     bool bottom_ready = false;
@@ -187,8 +188,9 @@ cudaError_t sweep(sbm_grid G, int l, int mode, const T *u, const T *f, T *out, d
     return launch_sweep<T, T>(mode, a, G->st);
 }
 
-// FP32 3D sweeps whose input is one of the level's TMA-described buffers use the
-// TMA + packed-FP32x2 kernel; everything else the generic kernel.
+// FP32 3D sweeps: small levels (no norm wanted) use the per-node kernel; larger
+// ones whose input is one of the level's TMA-described buffers the TMA +
+// packed-FP32x2 block kernel; everything else the generic kernel.
 template <>
 cudaError_t sweep<float>(sbm_grid G, int l, int mode, const float *u, const float *f, float *out, double *part,
                          double omega)
@@ -204,6 +206,8 @@ cudaError_t sweep<float>(sbm_grid G, int l, int mode, const float *u, const floa
     a.c = L.c32;
     for (int p = 0; p < 3; ++p) a.wk[p] = (L.c64.kdiag[p] != 0.0) ? float(omega / L.c64.kdiag[p]) : 0.f;
     a.kchunk = 0;
+    if (L.g.dim == 3 && part == nullptr && (long long)L.g.nx * L.g.ny * L.g.nz <= kNodeKernelMaxNodes)
+        return launch_sweep_node(mode, a, G->st);
     if (L.has_tm && (u == L.su[0] || u == L.su[1]) && (mode == kApply || f == L.sf))
         return launch_sweep_f2(mode, a, L.tm32[u == L.su[0] ? 0 : 1], G->derr, G->st);
     return launch_sweep<float, float>(mode, a, G->st);
@@ -356,7 +360,13 @@ sbm_status setup_bottom(sbm_grid G)
     CK(cudaMemsetAsync(G->A64, 0, sizeof(double) * n * n, G->st));
     CK(launch_bottom_assemble(B.g, B.psi64, B.c64, G->A64, G->st));
     CK(launch_bottom_dirichlet(B.g, G->A64, G->st));
-    CK(launch_gauss_jordan((int)n, G->A64, G->gjtmp, G->st));
+    CK(launch_gauss_jordan(B.g, (int)n, G->A64, G->gjtmp, G->gjbar, G->st));
+    {
+        unsigned hbar[4] = {0, 0, 0, 0};
+        CK(cudaMemcpyAsync(hbar, G->gjbar, sizeof(hbar), cudaMemcpyDeviceToHost, G->st));
+        CK(cudaStreamSynchronize(G->st));
+        if (hbar[2]) return fail(G, SBM_ERR_CUDA, "a grid barrier of the bottom-level inversion timed out");
+    }
     CK(launch_round(n * n, G->A64, G->A32, G->st));
     G->bottom_ready = true;
     return SBM_OK;
@@ -919,7 +929,7 @@ sbm_status sbm_grid_destroy(sbm_grid G)
             if (p) cudaFree(p);
     }
     for (int a = 0; a < G->npatch; ++a) free_patch(G->P[a]);
-    void *ptrs[] = {G->fsrc, G->fadj, G->psi_raw, G->rho, G->part, G->scal, G->dbad, G->A64, G->A32, G->gjtmp, G->gather,
+    void *ptrs[] = {G->fsrc, G->fadj, G->psi_raw, G->rho, G->part, G->scal, G->dbad, G->A64, G->A32, G->gjtmp, G->gjbar, G->gather,
                     G->derr, G->amr_part, G->amr_u0, G->amr_r0};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -1041,7 +1051,8 @@ sbm_status sbm_grid_create(const sbm_grid_desc *d, sbm_grid *out)
     }
     CK(cudaMalloc(&G->A64, sizeof(double) * G->nb * G->nb));
     CK(cudaMalloc(&G->A32, sizeof(float) * G->nb * G->nb));
-    CK(cudaMalloc(&G->gjtmp, sizeof(double) * 2 * G->nb));
+    CK(cudaMalloc(&G->gjtmp, sizeof(double) * 4 * G->nb));
+    CK(cudaMalloc(&G->gjbar, sizeof(unsigned) * 4));
     CK(cudaMalloc(&G->gather, sizeof(int) * G->nb));
     {
         std::vector<int> gi(G->nb);

@@ -139,7 +139,14 @@ cudaError_t launch_norm_final(const double *part, int nparts, double *scal, int 
 cudaError_t launch_bottom_assemble(const Geom &g, const double *psi, const Coef<double> &c,
                                    double *A, cudaStream_t s);
 cudaError_t launch_bottom_dirichlet(const Geom &g, double *A, cudaStream_t s);
-cudaError_t launch_gauss_jordan(int n, double *A, double *tmp, cudaStream_t s);
+// FP32 3D sweep, one thread per node (small levels; no partial sums).
+cudaError_t launch_sweep_node(int mode, const SweepArgs<float, float> &a, cudaStream_t s);
+// Levels with at most this many nodes use the per-node FP32 kernel.
+constexpr long long kNodeKernelMaxNodes = 80000;
+
+// Inverse of the coarsest-level matrix in place (one cooperative launch);
+// bar: 4 device words, bar[2] != 0 afterwards if a grid barrier timed out.
+cudaError_t launch_gauss_jordan(const Geom &g, int n, double *A, double *tmp, unsigned *bar, cudaStream_t s);
 cudaError_t launch_round(long long n, const double *src, float *dst, cudaStream_t s);
 template <typename T>
 cudaError_t launch_bottom_apply(int n, const T *Ainv, const int *gather, const T *b, T *u,

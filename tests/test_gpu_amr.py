@@ -143,3 +143,79 @@ def test_full_hierarchy_converges_with_oracle_residual(built, dim, n0, levels, p
     n0_ = np.sqrt(sum((x ** 2).sum() for x in r0))
     n1_ = np.sqrt(sum((x ** 2).sum() for x in r))
     assert n1_ / n0_ <= 2e-10, (n1_ / n0_, info.cycles)
+
+
+def _samples(wk, A, count, seed):
+    """Random owned-or-not dofs of every level plus dofs next to each patch's
+    coarse/fine interface (global level indices)."""
+    rng = np.random.default_rng(seed)
+    lev, nodes, comps = [], [], []
+    for a in range(A.nlev):
+        n = wk.storage_shape(a)
+        o = wk.origin(a)
+        pts = rng.integers(0, n, size=(count, 3))
+        if a > 0:                        # rows on and next to the interface
+            lo, hi = wk.boxes[a - 1]
+            face = pts.copy()
+            ax = rng.integers(0, wk.dim, size=count)
+            side = rng.integers(0, 2, size=count)
+            off = rng.integers(-1, 3, size=count)
+            for s_ in range(count):
+                x = ax[s_]
+                face[s_, x] = (lo[x] - o[x] + off[s_]) if side[s_] == 0 else (hi[x] - o[x] - off[s_])
+            pts = np.concatenate([pts, np.clip(face, 0, np.array(n) - 1)])
+        g = pts + np.array(o)
+        lev += [a] * len(g)
+        nodes.append(g)
+        comps.append(rng.integers(0, wk.dim, size=len(g)))
+    return np.array(lev), np.concatenate(nodes), np.concatenate(comps)
+
+
+def _at(wk, arrs, lev, nodes, comps):
+    out = np.empty(len(lev))
+    for i, (a, g, p) in enumerate(zip(lev, nodes, comps)):
+        n, o = wk.storage_shape(a), wk.origin(a)
+        loc = (g[0] - o[0]) + n[0] * ((g[1] - o[1]) + n[1] * (g[2] - o[2]))
+        out[i] = arrs[a][p * n[0] * n[1] * n[2] + loc]
+    return out
+
+
+def test_C5_full_size_sampled_parity(built):
+    """3D refinement at full size (129^3 base + 2 levels around 16 spherical voids,
+    triaxial loading, mixed precision): at sampled dofs of every level (random and
+    next to the interfaces) the GPU composite residual of the initial guess equals
+    the oracle's, and the oracle's composite residual of the GPU solution is at the
+    tolerance relative to the initial residual."""
+    wk = W.voids_amr(3, 129, 2, count=16, rmin=0.04, rmax=0.12)
+    raw = [np.ascontiguousarray(wk.level_psi(a)) for a in range(3)]
+    g = sbm.Grid(3, wk.n, wk.h, precision="mixed")
+    g.set_moduli(sbm.SBM_CUBIC, wk.moduli)
+    for face, comp, _ in wk.bcs:
+        g.set_bc(face, comp, sbm.SBM_DIRICHLET_FROM_U)
+    g.set_psi(cuda(raw[0]), wk.psi_min)
+    for lo, hi in wk.boxes:
+        g.amr_add_level(lo, hi)
+    for a in (1, 2):
+        g.amr_set_psi(a, cuda(raw[a]), wk.psi_min)
+    P = oracle.Problem(3, wk.n, wk.h, *wk.moduli, dirichlet=wk.dirichlet_bits())
+    A = oracle.Amr(P, [(lo, hi) for lo, hi in wk.boxes])
+    psis = [np.ascontiguousarray(np.maximum(r, wk.psi_min)) for r in raw]
+    del raw
+    oracle.amr_coarsen_psi(A, psis)
+    fs = [np.zeros(A.level_problem(a).ndofs) for a in range(3)]
+    us0 = [np.ascontiguousarray(wk.level_u0(a)) for a in range(3)]
+    lev, nodes, comps = _samples(wk, A, 1500, 77)
+    # residual of the initial guess
+    rs, nrm0 = g.amr_residual([cuda(u) for u in us0])
+    got = _at(wk, [host(r) for r in rs], lev, nodes, comps)
+    del rs
+    ref = oracle.amr_residual_at(A, psis, fs, us0, lev, nodes, comps)
+    assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
+    # solve, then the oracle's residual of the GPU solution
+    us = [cuda(u) for u in us0]
+    info = g.amr_solve(us, tol=1e-10, omega=wk.omega, smoother=wk.smoother, max_cycles=200)
+    assert info.converged, info
+    sol = [host(u) for u in us]
+    r = oracle.amr_residual_at(A, psis, fs, sol, lev, nodes, comps)
+    assert np.abs(r).max() <= 2e-10 * nrm0, (np.abs(r).max() / nrm0, info.cycles)
+

@@ -29,6 +29,11 @@ CASES = {
     "ragged2d": lambda: random_workload(2, (73, 45), 101),
     "damage33": lambda: W.damage3d(33),
     "ragged3d": lambda: random_workload(3, (73, 45, 21), 202),
+    # large enough for the warp-specialised FP32 kernel: ragged x tile (97 = 3 x 31 + 4),
+    # a one-row last block row (65 = 2 x 32 + 1), Dirichlet data on several faces
+    "col_ragged3d": lambda: random_workload(3, (97, 65, 33), 303, bits=(1 | 2 | 16, 4 | 8, 32)),
+    # nx - 1 = 4 x 31: the last node of each row falls to lane 31 of the last tile
+    "col_lastlane3d": lambda: random_workload(3, (125, 49, 17), 404, bits=(2 | 32, 1 | 16, 8)),
 }
 
 

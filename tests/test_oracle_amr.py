@@ -201,3 +201,28 @@ def test_composite_reproduces_affine_fields(oracle_lib, dim, n0, boxes):
         inside = np.all([(c >= 0) & (c <= n - 1) for c, n in zip((X, Y, Z)[:dim], N)], axis=0)
         mask = np.tile(inside, dim)
         assert np.abs(sol[a][mask] - exact[a][mask]).max() <= 1e-12
+
+
+@pytest.mark.parametrize("dim,n0,boxes", [
+    (2, 9, [((4, 4), (12, 12)), ((10, 10), (22, 22)), ((22, 22), (42, 42))]),
+    (2, 9, [((0, 4), (12, 16)), ((0, 10), (14, 30))]),
+    (3, 5, [((2, 2, 2), (6, 6, 6)), ((6, 6, 4), (10, 10, 10))]),
+])
+def test_sampled_composite_residual_equals_full(oracle_lib, dim, n0, boxes):
+    """The sampled composite residual (ghost and covered values evaluated on the
+    fly) equals the full composite residual at every dof of every level."""
+    bits = (1 | 4, 2 | 8, 16) if dim == 3 else (1 | 4, 8)
+    A = _amr(dim, n0, boxes, bits=bits + (0,) * (3 - len(bits)))
+    psis = oracle.amr_coarsen_psi(A, _psi(A, lambda X, Y, Z: 0.1 + 0.9 * (0.5 + 0.5 * np.cos(5 * X - 2 * Y + 3 * Z))))
+    us = [W.uniform(300 + a, A.level_problem(a).ndofs, -1, 1) for a in range(A.nlev)]
+    fs = [W.uniform(400 + a, A.level_problem(a).ndofs, -1, 1) for a in range(A.nlev)]
+    full = oracle.amr_residual(A, psis, fs, [u.copy() for u in us])
+    for a in range(A.nlev):
+        P = A.level_problem(a)
+        X, Y, Z = level_coords(A, a)
+        nodes = np.stack([X, Y, Z], axis=1)
+        for p in range(dim):
+            got = oracle.amr_residual_at(A, psis, fs, us, np.full(P.nnodes, a), nodes, np.full(P.nnodes, p))
+            ref = full[a][p * P.nnodes:(p + 1) * P.nnodes]
+            assert np.abs(got - ref).max() <= 1e-13 * max(1.0, np.abs(ref).max()), (a, p)
+

@@ -288,6 +288,7 @@ class AmrWorkload:
     omega: float = 2.0 / 3.0
     precision: str = "fp64"
     notes: dict = field(default_factory=dict)
+    affine: float = None      # Dirichlet data u_p = affine * (x_p - 1/2) instead of the bcs values
 
     def dirichlet_bits(self):
         bits = [0, 0, 0]
@@ -336,9 +337,12 @@ class AmrWorkload:
         u = np.zeros(self.dim * Nn)
         k, j, i = np.meshgrid(np.arange(n[2]), np.arange(n[1]), np.arange(n[0]), indexing="ij")
         g = [(i + o[0]).reshape(-1), (j + o[1]).reshape(-1), (k + o[2]).reshape(-1)]
+        h = self.level_h(a)
         for face, comp, value in self.bcs:
             ax, side = FACES[face] // 2, FACES[face] % 2
             on = g[ax] == (0 if side == 0 else N[ax] - 1)
+            if self.affine is not None:
+                value = (self.affine * (g[comp] * h - 0.5))[on]
             u[comp * Nn:(comp + 1) * Nn][on] = value
         return u
 
@@ -402,13 +406,15 @@ def voids_amr(dim=2, n0=129, levels=3, count=8, rmin=0.03, rmax=0.10, psi_min=1e
         bcs = [("-y", 0, 0.0), ("-y", 1, 0.0), ("+y", 0, 0.0), ("+y", 1, 0.01)]
         moduli = iso_cubic(1.0, 0.3)
     else:
-        bcs = [(f, p, (0.005 if f[0] == "+" else -0.005) if p == "xyz".index(f[1]) else 0.0)
-               for f in ("-x", "+x", "-y", "+y", "-z", "+z") for p in range(3)]
+        # triaxial loading: every component fixed on every face to the affine field
+        # u = 0.01 (x - 1/2), so each face moves 0.005 outward
+        bcs = [(f, p, None) for f in ("-x", "+x", "-y", "+y", "-z", "+z") for p in range(3)]
         moduli = iso_cubic(1.0, 0.25)
     n = (n0, n0, n0 if dim == 3 else 1)
     return AmrWorkload(f"voids_amr_{dim}d", dim, n, h0, moduli, bcs, psi_fn, psi_min, boxes,
                        smoother="gs" if dim == 2 else "jacobi", omega=2.0 / 3.0 if dim == 2 else 0.5,
-                       precision="fp64" if dim == 2 else "mixed", notes={"balls": balls})
+                       precision="fp64" if dim == 2 else "mixed", notes={"balls": balls},
+                       affine=None if dim == 2 else 0.01)
 
 
 CONFIGS = {
