@@ -279,6 +279,10 @@ _AMR_SIGS = {
     "orc_amr_coarsen_psi": (None, [C.POINTER(_Amr), C.POINTER(C.POINTER(C.c_double))]),
     "orc_amr_fill": (None, [C.POINTER(_Amr), C.POINTER(C.POINTER(C.c_double))]),
     "orc_amr_residual": (None, [C.POINTER(_Amr)] + [C.POINTER(C.POINTER(C.c_double))] * 4),
+    "orc_amr_residual_at": (None, [C.POINTER(_Amr)] + [C.POINTER(C.POINTER(C.c_double))] * 3 +
+                            [C.c_long, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                             C.POINTER(C.c_double)]),
+    "orc_amr_dJdpsi": (None, [C.POINTER(_Amr)] + [C.POINTER(C.POINTER(C.c_double))] * 3),
 }
 
 
@@ -355,6 +359,13 @@ def amr_fill(A: Amr, us):
     ghost fill of every patch from its parent level."""
     _La().orc_amr_fill(C.byref(A.c()), _ptrs(us))
     return us
+
+
+def amr_dJdpsi(A: Amr, us, lams):
+    """Per-level cell gradients for the composite problem (see sbm_oracle.h)."""
+    gs = [np.zeros(A.level_problem(a).ncells) for a in range(A.nlev)]
+    _La().orc_amr_dJdpsi(C.byref(A.c()), _ptrs(us), _ptrs(lams), _ptrs(gs))
+    return gs
 
 
 def amr_residual_at(A: Amr, psis, fs, us, lev, nodes, comps):

@@ -901,3 +901,69 @@ void orc_amr_residual_at(const orc_amr *A, double *const *psi, double *const *f,
     }
 }
 
+void orc_amr_dJdpsi(const orc_amr *A, double *const *u, double *const *lam, double *const *g)
+{
+    const int d = A->base.dim, nc = 1 << d, nd = nc * d;
+    double Ke[24 * 24], ue[24], le[24];
+    for (int a = 0; a < A->nlev; ++a) {
+        orc_problem P;
+        orc_amr_level_problem(A, a, &P);
+        orc_element_matrix(&P, Ke);
+        const long N = orc_nnodes(&P);
+        const int ncx = P.n[0] - 1, ncy = P.n[1] - 1, ncz = d == 3 ? P.n[2] - 1 : 1;
+        for (int ck = 0; ck < ncz; ++ck)
+            for (int cj = 0; cj < ncy; ++cj)
+                for (int ci = 0; ci < ncx; ++ci) {
+                    const long cidx = ci + (long)ncx * (cj + (long)ncy * ck);
+                    const int C[3] = {a ? ci + A->lo[a][0] - 1 : ci, a ? cj + A->lo[a][1] - 1 : cj,
+                                      (a && d == 3) ? ck + A->lo[a][2] - 1 : ck};
+                    int inside = 1;
+                    for (int ax = 0; ax < d; ++ax)
+                        if (C[ax] < 0 || C[ax] > amr_N(A, a, ax) - 2) inside = 0;
+                    if (!inside) {
+                        g[a][cidx] = 0.0;
+                        continue;
+                    }
+                    for (int b = 0; b < nc; ++b) {
+                        const long n = (ci + (b & 1)) + (long)P.n[0] * ((cj + ((b >> 1) & 1)) +
+                                       (long)P.n[1] * (d == 3 ? ck + ((b >> 2) & 1) : 0));
+                        for (int q = 0; q < d; ++q) {
+                            ue[b * d + q] = u[a][q * N + n];
+                            le[b * d + q] = lam[a][q * N + n];
+                        }
+                    }
+                    double s = 0.0;
+                    for (int r = 0; r < nd; ++r)
+                        for (int c = 0; c < nd; ++c) s += le[r] * Ke[r * nd + c] * ue[c];
+                    g[a][cidx] = -s;
+                }
+    }
+    /* coarse cells under a patch hold the mean of their fine cells: their gradient
+     * passes to those cells (coarse to fine) and they keep none of their own */
+    for (int a = 0; a + 1 < A->nlev; ++a) {
+        orc_problem Pc, Pf;
+        orc_amr_level_problem(A, a, &Pc);
+        orc_amr_level_problem(A, a + 1, &Pf);
+        const int ncx = Pc.n[0] - 1, ncy = Pc.n[1] - 1, ncz = d == 3 ? Pc.n[2] - 1 : 1;
+        for (int ck = 0; ck < ncz; ++ck)
+            for (int cj = 0; cj < ncy; ++cj)
+                for (int ci = 0; ci < ncx; ++ci) {
+                    int C[3] = {ci, cj, ck};
+                    if (a > 0)
+                        for (int ax = 0; ax < d; ++ax) C[ax] += A->lo[a][ax] - 1;
+                    int in = 1;
+                    for (int ax = 0; ax < d; ++ax)
+                        if (2 * C[ax] < A->lo[a + 1][ax] || 2 * C[ax] + 2 > A->hi[a + 1][ax]) in = 0;
+                    if (!in) continue;
+                    const long cidx = ci + (long)ncx * (cj + (long)ncy * ck);
+                    const double share = g[a][cidx] / nc;
+                    for (int c = 0; c < nc; ++c) {
+                        int fl[3] = {0, 0, 0};
+                        for (int ax = 0; ax < d; ++ax) fl[ax] = 2 * C[ax] + ((c >> ax) & 1) - A->lo[a + 1][ax] + 1;
+                        g[a + 1][fl[0] + (long)(Pf.n[0] - 1) * (fl[1] + (long)(Pf.n[1] - 1) * fl[2])] += share;
+                    }
+                    g[a][cidx] = 0.0;
+                }
+    }
+}
+

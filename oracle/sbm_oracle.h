@@ -143,6 +143,13 @@ void orc_amr_residual(const orc_amr *A, double *const *psi, double *const *f, do
  * node[3s..3s+2], component comp[s]) without filling or touching the arrays:
  * ghost and covered values are evaluated on the fly.  Equals orc_amr_residual at
  * those dofs; for checking hierarchies too large to fill and sweep whole. */
+/* Gradient of J(psi) for the composite problem (Sec. 2.4 averaging of psi under
+ * patches, reading D10 on every level): u = the filled composite solution, lam = the
+ * adjoint solution of A^T lam = dJ/dx scattered to the owned free dofs (0
+ * elsewhere).  g[a] (level-a storage cells) = -lam_c^T S_c u_c for cells inside the
+ * domain; then each coarse cell under a patch passes g / 2^d to its fine cells
+ * (coarse to fine) and is set to 0 (its psi is the fine mean, not a parameter). */
+void orc_amr_dJdpsi(const orc_amr *A, double *const *u, double *const *lam, double *const *g);
 void orc_amr_residual_at(const orc_amr *A, double *const *psi, double *const *f, double *const *u, long n,
                          const int *lev, const int *node, const int *comp, double *r);
 

@@ -66,12 +66,12 @@ def unknowns(A):
     return out
 
 
-def dense_solve(A, psis, fs, us0):
-    """Solve the composite problem by probing its (affine) residual column by
-    column and a numpy dense solve."""
+def dense_system(A, psis, fs, us0):
+    """The composite operator M (d residual / d unknowns, negated) and the residual
+    b of us0, by probing the oracle's (affine) composite residual column by column:
+    the composite problem is M x = b for the correction x of the unknowns."""
     unk = unknowns(A)
-    us = [u.copy() for u in us0]
-    r0 = oracle.amr_residual(A, psis, fs, [u.copy() for u in us])
+    r0 = oracle.amr_residual(A, psis, fs, [u.copy() for u in us0])
 
     def vec(rs):
         return np.array([rs[a][e] for a, e in unk])
@@ -79,9 +79,17 @@ def dense_solve(A, psis, fs, us0):
     b = vec(r0)
     M = np.zeros((len(unk), len(unk)))
     for col, (a, e) in enumerate(unk):
-        ue = [u.copy() for u in us]
+        ue = [u.copy() for u in us0]
         ue[a][e] += 1.0
         M[:, col] = b - vec(oracle.amr_residual(A, psis, fs, ue))
+    return unk, M, b
+
+
+def dense_solve(A, psis, fs, us0):
+    """Solve the composite problem by probing its (affine) residual column by
+    column and a numpy dense solve."""
+    unk, M, b = dense_system(A, psis, fs, us0)
+    us = [u.copy() for u in us0]
     x = np.linalg.solve(M, b)
     for (a, e), v in zip(unk, x):
         us[a][e] += v

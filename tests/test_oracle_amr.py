@@ -10,7 +10,7 @@ import pytest
 
 import oracle
 import workloads as W
-from _amr import cells_inside_domain, dense_solve, level_coords
+from _amr import cells_inside_domain, dense_solve, dense_system, level_coords
 
 
 def _amr(dim, n0, boxes, moduli=(1.0, 0.6, 0.5), bits=(0, 0, 0)):
@@ -225,4 +225,67 @@ def test_sampled_composite_residual_equals_full(oracle_lib, dim, n0, boxes):
             got = oracle.amr_residual_at(A, psis, fs, us, np.full(P.nnodes, a), nodes, np.full(P.nnodes, p))
             ref = full[a][p * P.nnodes:(p + 1) * P.nnodes]
             assert np.abs(got - ref).max() <= 1e-13 * max(1.0, np.abs(ref).max()), (a, p)
+
+
+@pytest.mark.parametrize("dim,n0,boxes,bits", [
+    (2, 9, [((4, 4), (12, 12)), ((10, 10), (22, 22))], (4 | 8, 4, 0)),
+    (2, 9, [((0, 4), (12, 16))], (1 | 4, 4 | 8, 0)),
+    (3, 5, [((2, 2, 2), (6, 6, 6))], (16, 16 | 32, 16)),
+])
+def test_composite_gradient_matches_central_differences(oracle_lib, dim, n0, boxes, bits):
+    """dJ/dpsi of J = g.x (x the composite unknowns) from the adjoint A^T lam = g and
+    the per-level cell formula with the coarse-to-fine chain rule, against central
+    differences of dense composite solves, for cells on every level: outside the
+    patches, under them (whose psi is overwritten by the fine mean: gradient 0) and
+    on the fine levels."""
+    A = _amr(dim, n0, boxes, bits=bits)
+    raw = _psi(A, lambda X, Y, Z: 0.2 + 0.8 * (0.5 + 0.5 * np.sin(6 * X + 4 * Y + 3 * Z)))
+    us0, fs = _zeros(A), []
+    for a in range(A.nlev):
+        P = A.level_problem(a)
+        X, Y, Z = level_coords(A, a)
+        Na = A.global_n(a)
+        top = (Y == Na[1] - 1) if dim == 2 else (Z == Na[2] - 1)
+        us0[a][(dim - 1) * P.nnodes:dim * P.nnodes][top] = 0.01
+        fs.append(W.uniform(500 + a, P.ndofs, -1, 1))
+
+    def solve(raw_psis):
+        psis = oracle.amr_coarsen_psi(A, [p.copy() for p in raw_psis])
+        unk, M, b = dense_system(A, psis, fs, us0)
+        x = np.linalg.solve(M, b)
+        return psis, unk, M, x
+
+    psis, unk, M, x = solve(raw)
+    gvec = W.uniform(600, len(unk), -1, 1)
+    base = np.array([us0[a][e] for a, e in unk])
+    J = lambda xx: float(gvec @ (base + xx))
+    lam = np.linalg.solve(M.T, gvec)
+    lams = [np.zeros_like(u) for u in us0]
+    us = [u.copy() for u in us0]
+    for (a, e), v, xv in zip(unk, lam, x):
+        lams[a][e] = v
+        us[a][e] += xv
+    oracle.amr_fill(A, us)
+    grads = oracle.amr_dJdpsi(A, us, lams)
+    scale = max(np.abs(gg).max() for gg in grads)
+    rng = np.random.default_rng(7)
+    checked = 0
+    for a in range(A.nlev):
+        inside = np.nonzero(cells_inside_domain(A, a))[0]
+        for c in rng.choice(inside, size=min(4, len(inside)), replace=False):
+            eps = 1e-6 * raw[a][c]
+            plus = [p.copy() for p in raw]
+            minus = [p.copy() for p in raw]
+            plus[a][c] += eps
+            minus[a][c] -= eps
+            fd = (J(solve(plus)[3]) - J(solve(minus)[3])) / (2 * eps)
+            assert abs(fd - grads[a][c]) <= 1e-6 * scale, (a, c, fd, grads[a][c])
+            checked += 1
+    # a coarse cell under the first patch: its psi is overwritten, its gradient is 0
+    lo, hi = A.boxes[0]
+    C0 = [lo[ax] // 2 for ax in range(dim)] + [0] * (3 - dim)
+    P0 = A.level_problem(0)
+    cid = C0[0] + (P0.n[0] - 1) * (C0[1] + (P0.n[1] - 1) * C0[2])
+    assert grads[0][cid] == 0.0
+    assert checked >= 2 * A.nlev
 
