@@ -61,18 +61,19 @@ __device__ __forceinline__ T fw_row(const T *__restrict__ row, int I, int nx)
 // node (I,J,K) sits on fine node (2I,2J,2K), the linear weights are 1, 1/2.
 // The 3^d fine rows are read with independent loads (clamped index, zero weight
 // outside the grid) so they are all in flight together.
-template <typename T>
+template <typename T, int D>
 __global__ void k_restrict(const Geom gf, const Geom gc, const T *__restrict__ rf, T *__restrict__ fc)
 {
     const int I = blockIdx.x * blockDim.x + threadIdx.x;
     const int J = blockIdx.y * blockDim.y + threadIdx.y;
     const int K = blockIdx.z * blockDim.z + threadIdx.z;
     if (I >= gc.nx || J >= gc.ny || K >= gc.nz) return;
-    const bool d3 = gf.dim == 3;
+    constexpr bool d3 = D == 3;
     const T scale = d3 ? T(0.125) : T(0.25);
     const long long oc = gidx(gc, I, J, K);
-    const int nz_rows = d3 ? 3 : 1;
-    for (int p = 0; p < gf.dim; ++p) {
+    constexpr int nz_rows = d3 ? 3 : 1;
+#pragma unroll
+    for (int p = 0; p < D; ++p) {
         T s = T(0);
         if (!is_dir(gc, p, I, J, K)) {
             const T *base = rf + p * gf.cs;
@@ -102,7 +103,7 @@ __global__ void k_restrict(const Geom gf, const Geom gc, const T *__restrict__ r
 // fine nodes (2I+a, 2J+b, 2K+c), a, b, c in {0, 1}, that exist: the coincident
 // node copies e_c, the others average the 2, 4 or 8 coarse neighbours.  The x
 // pair (2I, 2I+1) is read and written as one aligned vector.
-template <typename T>
+template <typename T, int D>
 __global__ void k_prolong_add(const Geom gf, const Geom gc, const T *__restrict__ ec, T *__restrict__ uf)
 {
     using V = typename Vec2<T>::type;
@@ -110,11 +111,12 @@ __global__ void k_prolong_add(const Geom gf, const Geom gc, const T *__restrict_
     const int J = blockIdx.y * blockDim.y + threadIdx.y;
     const int K = blockIdx.z * blockDim.z + threadIdx.z;
     if (I >= gc.nx || J >= gc.ny || K >= gc.nz) return;
-    const bool d3 = gf.dim == 3;
+    constexpr bool d3 = D == 3;
     const bool hx = I + 1 < gc.nx, hy = J + 1 < gc.ny, hz = d3 && K + 1 < gc.nz;
     const int I1 = hx ? I + 1 : I, J1 = hy ? J + 1 : J, K1 = hz ? K + 1 : K;
     const int i0 = 2 * I, j0 = 2 * J, k0 = d3 ? 2 * K : 0;
-    for (int p = 0; p < gf.dim; ++p) {
+#pragma unroll
+    for (int p = 0; p < D; ++p) {
         const T *e = ec + p * gc.cs;
         // coarse values of the cell above (I,J,K): [z][y][x]
         T c[2][2][2];
@@ -534,7 +536,8 @@ __global__ void k_dJdpsi(const Geom g, const Coef<double> c, const double *__res
 template <typename T>
 cudaError_t launch_restrict(const Geom &gf, const Geom &gc, const T *rf, T *fc, cudaStream_t s)
 {
-    k_restrict<T><<<node_grid(gc), kNodeBlock, 0, s>>>(gf, gc, rf, fc);
+    if (gf.dim == 3) k_restrict<T, 3><<<node_grid(gc), kNodeBlock, 0, s>>>(gf, gc, rf, fc);
+    else k_restrict<T, 2><<<node_grid(gc), kNodeBlock, 0, s>>>(gf, gc, rf, fc);
     ++g_launches;
     return cudaGetLastError();
 }
@@ -544,7 +547,8 @@ template cudaError_t launch_restrict<float>(const Geom &, const Geom &, const fl
 template <typename T>
 cudaError_t launch_prolong_add(const Geom &gf, const Geom &gc, const T *ec, T *uf, cudaStream_t s)
 {
-    k_prolong_add<T><<<node_grid(gc), kNodeBlock, 0, s>>>(gf, gc, ec, uf);
+    if (gf.dim == 3) k_prolong_add<T, 3><<<node_grid(gc), kNodeBlock, 0, s>>>(gf, gc, ec, uf);
+    else k_prolong_add<T, 2><<<node_grid(gc), kNodeBlock, 0, s>>>(gf, gc, ec, uf);
     ++g_launches;
     return cudaGetLastError();
 }

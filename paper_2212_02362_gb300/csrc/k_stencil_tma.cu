@@ -113,30 +113,61 @@ __device__ __forceinline__ void block_partial_f(double ssq, double *part, double
     }
 }
 
+// Dirichlet bits (bit p = component p) of node (gx, gy, *) from the x and y faces;
+// the z faces are added per plane.
+__device__ __forceinline__ unsigned dir_xy(const Geom &g, int gx, int gy)
+{
+    unsigned b = 0;
+#pragma unroll
+    for (int p = 0; p < 3; ++p) {
+        const unsigned m = g.dm[p];
+        if (((m & 1u) && gx == 0) || ((m & 2u) && gx == g.nx - 1) || ((m & 4u) && gy == 0) ||
+            ((m & 8u) && gy == g.ny - 1))
+            b |= 1u << p;
+    }
+    return b;
+}
+
+__device__ __forceinline__ unsigned dir_z(const Geom &g, int gz)
+{
+    unsigned b = 0;
+#pragma unroll
+    for (int p = 0; p < 3; ++p) {
+        const unsigned m = g.dm[p];
+        if (((m & 16u) && gz == 0) || ((m & 32u) && gz == g.nz - 1)) b |= 1u << p;
+    }
+    return b;
+}
+
+// out: this thread's node column (gx, gy) of component 0; dxy: its x/y Dirichlet
+// bits.  The residual's sum of squares is formed only when a norm is wanted.
 template <int MODE>
-__device__ __forceinline__ void finalize_f(const SweepArgs<float, float> &a, int gx, int gy, int gz, const float *Ku,
-                                           float pss, const float *uv, const float *fv, double &ssq)
+__device__ __forceinline__ void finalize_f(const SweepArgs<float, float> &a, float *outc, unsigned dxy, int gz,
+                                           const float *Ku, float pss, const float *uv, const float *fv, double &ssq)
 {
     const Geom &g = a.g;
-    const long long o = gidx(g, gx, gy, gz);
+    float *o = outc + (long long)g.sy * gz;
+    const unsigned dm = dxy | dir_z(g, gz);
     if (MODE == kJacobi) {
-        const float ip = 1.0f / pss;
+        const float ip = __frcp_rn(pss);
 #pragma unroll
         for (int p = 0; p < 3; ++p) {
             float v = uv[p];
-            if (!is_dir(g, p, gx, gy, gz)) v = madd((fv[p] - Ku[p]) * ip, a.wk[p], v);
-            a.out[p * g.cs + o] = v;
+            if (!((dm >> p) & 1u)) v = madd((fv[p] - Ku[p]) * ip, a.wk[p], v);
+            o[p * g.cs] = v;
         }
     } else if (MODE == kResidual) {
+        float s = 0.f;
 #pragma unroll
         for (int p = 0; p < 3; ++p) {
-            const float r = is_dir(g, p, gx, gy, gz) ? 0.0f : fv[p] - Ku[p];
-            a.out[p * g.cs + o] = r;
-            ssq += double(r) * double(r);
+            const float r = ((dm >> p) & 1u) ? 0.0f : fv[p] - Ku[p];
+            o[p * g.cs] = r;
+            s = fmaf(r, r, s);
         }
+        if (a.part) ssq += double(s);
     } else {
 #pragma unroll
-        for (int p = 0; p < 3; ++p) a.out[p * g.cs + o] = Ku[p];
+        for (int p = 0; p < 3; ++p) o[p * g.cs] = Ku[p];
     }
 }
 
@@ -199,6 +230,8 @@ __global__ void __launch_bounds__(NTP) k_sweep3_f2(const __grid_constant__ CUten
 
     const int gx = x0 + tx, gy = y0 + ty;
     const bool own = gx < g.nx && gy < g.ny && (tx < TXP || gx == g.nx - 1) && (ty < TYP || gy == g.ny - 1);
+    float *const outc = a.out + (own ? gx + (long long)g.sx * gy : 0);
+    const unsigned dxy = own ? dir_xy(g, gx, gy) : 0u;
     const int me = ty * PXF + tx;
     float carry[3][4];
 #pragma unroll
@@ -285,13 +318,13 @@ __global__ void __launch_bounds__(NTP) k_sweep3_f2(const __grid_constant__ CUten
                 const float Ku[3] = {Ku2[0].v.x, Ku2[1].v.x, Ku2[2].v.x};
                 const float uv[3] = {P0[onode], P0[PYF * WX + onode], P0[2 * PYF * WX + onode]};
                 const float fv[3] = {P0[F_OFF + onode], P0[F_OFF + PYF * WX + onode], P0[F_OFF + 2 * PYF * WX + onode]};
-                finalize_f<MODE>(a, gx, gy, k, Ku, pss.v.x, uv, fv, ssq);
+                finalize_f<MODE>(a, outc, dxy, k, Ku, pss.v.x, uv, fv, ssq);
             }
             if (k + 1 >= kz0 && k + 1 <= kend) {
                 const float Ku[3] = {Ku2[0].v.y, Ku2[1].v.y, Ku2[2].v.y};
                 const float uv[3] = {P1[onode], P1[PYF * WX + onode], P1[2 * PYF * WX + onode]};
                 const float fv[3] = {P1[F_OFF + onode], P1[F_OFF + PYF * WX + onode], P1[F_OFF + 2 * PYF * WX + onode]};
-                finalize_f<MODE>(a, gx, gy, k + 1, Ku, pss.v.y, uv, fv, ssq);
+                finalize_f<MODE>(a, outc, dxy, k + 1, Ku, pss.v.y, uv, fv, ssq);
             }
         }
         __syncthreads();
