@@ -231,6 +231,24 @@ sbm_status sbm_amr_set_source(sbm_grid grid, int a, const double *f_nodes);
  * filled, smoothing); u += e on owned dofs.  SBM_MIXED runs the cycle in FP32.
  * opts->inner_cycles is ignored.  Status as for sbm_solve. */
 sbm_status sbm_amr_solve(sbm_grid grid, double *const *u, const sbm_opts *opts, sbm_info *info);
+/* Adjoint of the composite problem of sbm_amr_solve (Sec. 2.2 levels, Sec. 2.4 psi
+ * averaging; the adjoint reading D10 applied to every level).  u: the composite
+ * solution (layouts as sbm_amr_solve).  dJdu[a]: dJ/du on level a, packed like u[a];
+ * only its owned free dofs count.  Out: lambda[a] (packed like u[a]), the solution of
+ * A^T lambda = dJ/du for the composite operator A (0 off the owned free dofs), by the
+ * transposed correction iteration lambda += B^T (dJ/du - A^T lambda), B^T the
+ * transpose of one FP64 correction cycle (damped Jacobi: opts->smoother must be
+ * SBM_JACOBI), to relative residual opts->tol within opts->max_cycles iterations
+ * (the iteration converges at the rate of the forward one); dJdpsi[a] (the
+ * array or all of dJdpsi may be null): dJ/dpsi of level a's cells, packed like the
+ * psi of sbm_set_psi (a = 0) / sbm_amr_set_psi (a >= 1): -lambda_c^T S_c u_c, where a
+ * coarse cell under a patch passes its gradient to its 2^d fine cells and keeps
+ * none (its psi is the fine mean), and 0 where psi sits at psi_min.  All pointers
+ * are device pointers.  info: cycles = Krylov iterations, relres, history.
+ * SBM_ERR_STATE without patch levels (use sbm_adjoint); status otherwise as for
+ * sbm_solve. */
+sbm_status sbm_amr_adjoint(sbm_grid grid, double *const *u, double *const *dJdu, double *const *lambda,
+                           double *const *dJdpsi, const sbm_opts *opts, sbm_info *info);
 /* Composite residual of u (layouts as sbm_amr_solve): r[a] = f_a - K_a u_a on the
  * owned free dofs of level a, 0 on ghost, covered and Dirichlet dofs; *norm (host)
  * = its 2-norm over all levels.  u is not modified.  SBM_ERR_STATE when no patch

@@ -199,6 +199,28 @@ class Grid:
         self._check(st, allow=(SBM_OK,) if raise_on_fail else (SBM_OK, SBM_ERR_NOCONV, SBM_ERR_DIVERGED))
         return self._to_info(info, hist)
 
+    def amr_adjoint(self, us, dJdus, raise_on_fail: bool = True, **opts):
+        """lambda (per level) of A^T lambda = dJ/du for the composite operator and
+        dJ/dpsi (per level cells, packed like the psi arrays)."""
+        o = make_opts(**opts)
+        info, hist = self._info(o.max_cycles)
+        lams = [torch.zeros_like(u) for u in us]
+        grads = []
+        for a in range(len(us)):
+            nc = self.ncells() if a == 0 else self._patch_ncells(a)
+            grads.append(torch.zeros(nc, dtype=torch.float64, device=us[0].device))
+        st = lib().sbm_amr_adjoint(self._h, self._ptr_array(us), self._ptr_array(dJdus), self._ptr_array(lams),
+                                   self._ptr_array(grads), C.byref(o), C.byref(info))
+        self._check(st, allow=(SBM_OK,) if raise_on_fail else (SBM_OK, SBM_ERR_NOCONV, SBM_ERR_DIVERGED))
+        return lams, grads, self._to_info(info, hist)
+
+    def _patch_ncells(self, a):
+        lo, hi = self.boxes[a - 1]
+        n = 1
+        for ax in range(self.dim):
+            n *= hi[ax] - lo[ax] + 2          # padded box nodes - 1
+        return n
+
     def amr_residual(self, us):
         rs = [torch.empty_like(u) for u in us]
         nrm = C.c_double()

@@ -76,6 +76,8 @@ _SIGS = {
     "sbm_amr_set_source": (C.c_int, [_grid, C.c_int, _dptr]),
     "sbm_amr_solve": (C.c_int, [_grid, C.POINTER(C.c_void_p), C.POINTER(sbm_opts), C.POINTER(sbm_info)]),
     "sbm_amr_residual": (C.c_int, [_grid, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.POINTER(C.c_double)]),
+    "sbm_amr_adjoint": (C.c_int, [_grid, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
+                                  C.POINTER(C.c_void_p), C.POINTER(sbm_opts), C.POINTER(sbm_info)]),
     "sbm_residual_noalloc": (C.c_int, [C.c_int, C.POINTER(C.c_int), C.c_double, C.POINTER(C.c_double),
                                        C.POINTER(C.c_uint), _dptr, _dptr, _dptr, _dptr, C.POINTER(C.c_double),
                                        C.c_void_p]),

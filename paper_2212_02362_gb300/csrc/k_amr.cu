@@ -252,6 +252,228 @@ __global__ void k_amr_set_cells(const Geom s, const double *packed, double psi_m
     lev[gidx(s, i, j, k)] = fmax(v, psi_min);
 }
 
+// ------------------------------------------------ adjoint of the composite problem
+
+// Transpose of the ghost fill: parent node G collects w from the child ghosts that
+// interpolate it (child nodes 2G + {-1, 0, 1} per axis that are not in the child's
+// box region, inside the domain), with the interpolation weights (1 on coincident
+// axes, 1/2 on odd ones), and adds the sum to wp.
+// with_solved != 0: also the child's solved free nodes (the correction
+// prolongation adds the interpolated parent value there).
+__global__ void k_amr_ghostT(const Geom sc, const AmrInfo Lc, const Geom sp, const AmrInfo Lp, const double *wc,
+                             double *wp, int with_solved)
+{
+    int i, j, k, G[3];
+    if (!thread_node(sp, Lp, i, j, k, G)) return;
+    const bool d3 = Lp.dim == 3;
+    const long long op = gidx(sp, i, j, k);
+    for (int p = 0; p < Lp.dim; ++p) {
+        double s = 0.0;
+        for (int dk = (d3 ? -1 : 0); dk <= (d3 ? 1 : 0); ++dk)
+            for (int dj = -1; dj <= 1; ++dj)
+                for (int di = -1; di <= 1; ++di) {
+                    const int g[3] = {2 * G[0] + di, 2 * G[1] + dj, d3 ? 2 * G[2] + dk : 0};
+                    const int l[3] = {g[0] - Lc.org[0], g[1] - Lc.org[1], g[2] - Lc.org[2]};
+                    if (l[0] < 0 || l[1] < 0 || l[2] < 0 || l[0] >= sc.nx || l[1] >= sc.ny || l[2] >= sc.nz) continue;
+                    if (!inside_domain(Lc, g)) continue;
+                    if (axes_owned(Lc, g) && (!with_solved || domain_dirichlet(Lc, g, p))) continue;
+                    const double w = (di ? 0.5 : 1.0) * (dj ? 0.5 : 1.0) * (dk ? 0.5 : 1.0);
+                    s += w * wc[p * sc.cs + gidx(sc, l[0], l[1], l[2])];
+                }
+        wp[p * sp.cs + op] += s;
+    }
+}
+
+// Zero everything but the solved free dofs (box region, not on a Dirichlet face):
+// the dofs a patch's smoother updates.
+__global__ void k_amr_mask_solved(const Geom s, const AmrInfo L, double *x)
+{
+    int i, j, k, g[3];
+    if (!thread_node(s, L, i, j, k, g)) return;
+    const bool solved = axes_owned(L, g);
+    const long long o = gidx(s, i, j, k);
+    for (int p = 0; p < L.dim; ++p)
+        if (!solved || domain_dirichlet(L, g, p)) x[p * s.cs + o] = 0.0;
+}
+
+// out = W x on the solved free dofs (W = omega / (kdiag_p * sum of the psi of the
+// node's cells), the damped-Jacobi scaling), 0 elsewhere.
+__global__ void k_amr_scaleW(const Geom s, const AmrInfo L, const double *psi, double omega, double k0, double k1,
+                             double k2, const double *x, double *out)
+{
+    int i, j, k, g[3];
+    if (!thread_node(s, L, i, j, k, g)) return;
+    const long long o = gidx(s, i, j, k);
+    const bool solved = axes_owned(L, g);
+    double ps = 0.0;
+    if (solved) {
+        const bool d3 = L.dim == 3;
+        for (int c = 0; c < (1 << L.dim); ++c) {
+            const int ci = i - (c & 1), cj = j - ((c >> 1) & 1), ck = d3 ? k - ((c >> 2) & 1) : 0;
+            if (ci < 0 || cj < 0 || ck < 0 || ci >= s.nx - 1 || cj >= s.ny - 1 || (d3 && ck >= s.nz - 1)) continue;
+            const int C[3] = {ci + L.org[0], cj + L.org[1], ck + L.org[2]};
+            bool in = true;
+            for (int ax = 0; ax < L.dim; ++ax)
+                if (C[ax] < 0 || C[ax] > L.N[ax] - 2) in = false;
+            if (in) ps += psi[gidx(s, ci, cj, ck)];
+        }
+    }
+    const double kd[3] = {k0, k1, k2};
+    for (int p = 0; p < L.dim; ++p) {
+        const bool free = solved && !domain_dirichlet(L, g, p) && ps > 0.0 && kd[p] != 0.0;
+        out[p * s.cs + o] = free ? omega / (kd[p] * ps) * x[p * s.cs + o] : 0.0;
+    }
+}
+
+// Transpose of the full-weighting restriction onto the covered parent nodes:
+// child node g collects scale * w(g - 2G) * rp(G) from the covered parents G with
+// |g - 2G| <= 1 (parents on a Dirichlet face of the component contribute 0).
+__global__ void k_amr_restrictT(const Geom sc, const AmrInfo Lc, const Geom sp, const AmrInfo Lp, const double *rp,
+                                double *rc)
+{
+    int i, j, k, g[3];
+    if (!thread_node(sc, Lc, i, j, k, g)) return;
+    const bool d3 = Lc.dim == 3;
+    const double scale = d3 ? 0.125 : 0.25;
+    const long long oc = gidx(sc, i, j, k);
+    for (int p = 0; p < Lc.dim; ++p) {
+        double s = 0.0;
+        // parents G with 2G in {g-1, g, g+1} per axis
+        for (int dk = (d3 ? -1 : 0); dk <= (d3 ? 1 : 0); ++dk)
+            for (int dj = -1; dj <= 1; ++dj)
+                for (int di = -1; di <= 1; ++di) {
+                    const int t[3] = {g[0] + di, g[1] + dj, d3 ? g[2] + dk : 0};
+                    if ((t[0] & 1) || (t[1] & 1) || (t[2] & 1)) continue;
+                    const int G[3] = {t[0] / 2, t[1] / 2, t[2] / 2};
+                    if (!covered(Lp, G) || domain_dirichlet(Lp, G, p)) continue;
+                    const int l[3] = {G[0] - Lp.org[0], G[1] - Lp.org[1], G[2] - Lp.org[2]};
+                    if (l[0] < 0 || l[1] < 0 || l[2] < 0 || l[0] >= sp.nx || l[1] >= sp.ny || l[2] >= sp.nz) continue;
+                    const double w = (di ? 0.5 : 1.0) * (dj ? 0.5 : 1.0) * (dk ? 0.5 : 1.0);
+                    s += scale * w * rp[p * sp.cs + gidx(sp, l[0], l[1], l[2])];
+                }
+        rc[p * sc.cs + oc] = s;
+    }
+}
+
+// Transpose of the injection: a child node of the box region with even
+// coordinates receives w of the coincident (covered) parent node.
+__global__ void k_amr_injectT(const Geom sc, const AmrInfo Lc, const Geom sp, const AmrInfo Lp, const double *wp,
+                              double *wc)
+{
+    int i, j, k, g[3];
+    if (!thread_node(sc, Lc, i, j, k, g)) return;
+    for (int ax = 0; ax < Lc.dim; ++ax)
+        if (g[ax] & 1) return;
+    if (!axes_owned(Lc, g)) return;
+    const int lp[3] = {g[0] / 2 - Lp.org[0], g[1] / 2 - Lp.org[1], Lc.dim == 3 ? g[2] / 2 - Lp.org[2] : 0};
+    if (lp[0] < 0 || lp[1] < 0 || lp[2] < 0 || lp[0] >= sp.nx || lp[1] >= sp.ny || lp[2] >= sp.nz) return;
+    const long long oc = gidx(sc, i, j, k), op = gidx(sp, lp[0], lp[1], lp[2]);
+    for (int p = 0; p < Lc.dim; ++p) wc[p * sc.cs + oc] += wp[p * sp.cs + op];
+}
+
+// Per-block sums of x.y over the owned free dofs (fixed order).
+__global__ void k_amr_dot(const Geom s, const AmrInfo L, const double *x, const double *y, double *part)
+{
+    __shared__ double red[256];
+    int i, j, k, g[3];
+    double acc = 0.0;
+    if (thread_node(s, L, i, j, k, g) && owned(L, g)) {
+        const long long o = gidx(s, i, j, k);
+        for (int p = 0; p < L.dim; ++p)
+            if (!domain_dirichlet(L, g, p)) acc += x[p * s.cs + o] * y[p * s.cs + o];
+    }
+    const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    red[tid] = acc;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (tid < w) red[tid] += red[tid + w];
+        __syncthreads();
+    }
+    if (tid == 0) part[blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)] = red[0];
+}
+
+// dJ/dpsi of every storage cell: -lam_c^T S_c u_c (unit-psi cell matrix of the
+// level, via the cell routine), 0 for cells outside the domain.
+__global__ void k_amr_dJdpsi(const Geom s, const AmrInfo L, const Coef<double> c, const double *u, const double *lam,
+                             double *g)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z * blockDim.z + threadIdx.z;
+    const bool d3 = L.dim == 3;
+    if (i >= s.nx - 1 || j >= s.ny - 1 || (d3 ? k >= s.nz - 1 : k > 0)) return;
+    const int C[3] = {i + L.org[0], j + L.org[1], k + L.org[2]};
+    bool in = true;
+    for (int ax = 0; ax < L.dim; ++ax)
+        if (C[ax] < 0 || C[ax] > L.N[ax] - 2) in = false;
+    double acc = 0.0;
+    if (in) {
+        if (d3) {
+            double U[3][8], Lm[3][8];
+            for (int b = 0; b < 8; ++b) {
+                const long long o = gidx(s, i + (b & 1), j + ((b >> 1) & 1), k + ((b >> 2) & 1));
+                for (int p = 0; p < 3; ++p) {
+                    U[p][b] = u[p * s.cs + o];
+                    Lm[p][b] = lam[p * s.cs + o];
+                }
+            }
+            cell_forces3<double>(U, 1.0, c);
+            for (int b = 0; b < 8; ++b)
+                for (int p = 0; p < 3; ++p) acc += Lm[p][b] * U[p][b];
+        } else {
+            double U[2][4], Lm[2][4];
+            for (int b = 0; b < 4; ++b) {
+                const long long o = gidx(s, i + (b & 1), j + ((b >> 1) & 1), 0);
+                for (int p = 0; p < 2; ++p) {
+                    U[p][b] = u[p * s.cs + o];
+                    Lm[p][b] = lam[p * s.cs + o];
+                }
+            }
+            cell_forces2<double>(U, 1.0, c);
+            for (int b = 0; b < 4; ++b)
+                for (int p = 0; p < 2; ++p) acc += Lm[p][b] * U[p][b];
+        }
+    }
+    g[gidx(s, i, j, k)] = -acc;
+}
+
+// Coarse cells under the child box hold the fine mean: their gradient passes to
+// their 2^d fine cells and they keep none.
+__global__ void k_amr_grad_chain(const Geom sc, const AmrInfo Lc, const Geom sp, const AmrInfo Lp, double *gp,
+                                 double *gc)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z * blockDim.z + threadIdx.z;
+    const bool d3 = Lp.dim == 3;
+    if (i >= sp.nx - 1 || j >= sp.ny - 1 || (d3 ? k >= sp.nz - 1 : k > 0)) return;
+    const int C[3] = {i + Lp.org[0], j + Lp.org[1], k + Lp.org[2]};
+    for (int ax = 0; ax < Lp.dim; ++ax)
+        if (2 * C[ax] < Lc.lo[ax] || 2 * C[ax] + 2 > Lc.hi[ax]) return;
+    const long long op = gidx(sp, i, j, k);
+    const int nc = 1 << Lp.dim;
+    const double share = gp[op] / nc;
+    for (int c = 0; c < nc; ++c) {
+        const int li = 2 * C[0] + (c & 1) - Lc.org[0], lj = 2 * C[1] + ((c >> 1) & 1) - Lc.org[1];
+        const int lk = d3 ? 2 * C[2] + ((c >> 2) & 1) - Lc.org[2] : 0;
+        gc[gidx(sc, li, lj, lk)] += share;
+    }
+    gp[op] = 0.0;
+}
+
+// node-indexed cells of a padded box -> packed (i + (nx-1)*(j + (ny-1)*k)); cells
+// whose psi sits at the floor get 0 (psi = max(raw, psi_min) is flat there).
+__global__ void k_amr_get_cells(const Geom s, const double *lev, const double *psi, double psi_min, double *packed)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z * blockDim.z + threadIdx.z;
+    const int ncx = s.nx - 1, ncy = s.ny - 1, ncz = s.dim == 3 ? s.nz - 1 : 1;
+    if (i >= ncx || j >= ncy || k >= ncz) return;
+    const long long o = gidx(s, i, j, k);
+    packed[i + (long long)ncx * (j + (long long)ncy * k)] = psi[o] > psi_min ? lev[o] : 0.0;
+}
+
 const dim3 kAmrBlock(32, 4, 2);
 inline dim3 amr_grid(const Geom &s) { return dim3((s.nx + 31) / 32, (s.ny + 3) / 4, (s.nz + 1) / 2); }
 
@@ -331,6 +553,77 @@ cudaError_t launch_amr_set_cells(const Geom &s, const double *packed, double psi
                                  cudaStream_t st)
 {
     k_amr_set_cells<<<amr_grid(s), kAmrBlock, 0, st>>>(s, packed, psi_min, lev, bad);
+    ++g_launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_amr_ghostT(const Geom &sc, const AmrInfo &Lc, const Geom &sp, const AmrInfo &Lp, const double *wc,
+                              double *wp, int with_solved, cudaStream_t st)
+{
+    k_amr_ghostT<<<amr_grid(sp), kAmrBlock, 0, st>>>(sc, Lc, sp, Lp, wc, wp, with_solved);
+    ++g_launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_amr_mask_solved(const Geom &s, const AmrInfo &L, double *x, cudaStream_t st)
+{
+    k_amr_mask_solved<<<amr_grid(s), kAmrBlock, 0, st>>>(s, L, x);
+    ++g_launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_amr_scaleW(const Geom &s, const AmrInfo &L, const double *psi, double omega, const double kdiag[3],
+                              const double *x, double *out, cudaStream_t st)
+{
+    k_amr_scaleW<<<amr_grid(s), kAmrBlock, 0, st>>>(s, L, psi, omega, kdiag[0], kdiag[1], kdiag[2], x, out);
+    ++g_launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_amr_restrictT(const Geom &sc, const AmrInfo &Lc, const Geom &sp, const AmrInfo &Lp,
+                                 const double *rp, double *rc, cudaStream_t st)
+{
+    k_amr_restrictT<<<amr_grid(sc), kAmrBlock, 0, st>>>(sc, Lc, sp, Lp, rp, rc);
+    ++g_launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_amr_injectT(const Geom &sc, const AmrInfo &Lc, const Geom &sp, const AmrInfo &Lp, const double *wp,
+                               double *wc, cudaStream_t st)
+{
+    k_amr_injectT<<<amr_grid(sc), kAmrBlock, 0, st>>>(sc, Lc, sp, Lp, wp, wc);
+    ++g_launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_amr_dot(const Geom &s, const AmrInfo &L, const double *x, const double *y, double *part,
+                           cudaStream_t st)
+{
+    k_amr_dot<<<amr_grid(s), kAmrBlock, 0, st>>>(s, L, x, y, part);
+    ++g_launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_amr_dJdpsi(const Geom &s, const AmrInfo &L, const Coef<double> &c, const double *u,
+                              const double *lam, double *g, cudaStream_t st)
+{
+    k_amr_dJdpsi<<<amr_grid(s), kAmrBlock, 0, st>>>(s, L, c, u, lam, g);
+    ++g_launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_amr_grad_chain(const Geom &sc, const AmrInfo &Lc, const Geom &sp, const AmrInfo &Lp, double *gp,
+                                  double *gc, cudaStream_t st)
+{
+    k_amr_grad_chain<<<amr_grid(sp), kAmrBlock, 0, st>>>(sc, Lc, sp, Lp, gp, gc);
+    ++g_launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_amr_get_cells(const Geom &s, const double *lev, const double *psi, double psi_min, double *packed,
+                                 cudaStream_t st)
+{
+    k_amr_get_cells<<<amr_grid(s), kAmrBlock, 0, st>>>(s, lev, psi, psi_min, packed);
     ++g_launches;
     return cudaGetLastError();
 }

@@ -293,6 +293,32 @@ __global__ void k_add(long long n, const TE *__restrict__ e, double *__restrict_
     if (t < n) u[t] += double(e[t]);
 }
 
+// out = a x + b y (+ c z): the vector updates of the adjoint Krylov solver.
+__global__ void k_lincomb(long long n, double a, const double *x, double b, const double *y, double c,
+                          const double *z, double *out)
+{
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    double v = a * x[t] + b * y[t];
+    if (z) v += c * z[t];
+    out[t] = v;
+}
+
+// out[0] = sum of part[0..n) in a fixed order (one block).
+__global__ void k_sum_parts(const double *part, int n, double *out)
+{
+    __shared__ double red[kThreads];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s += part[i];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = kThreads / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[0] = red[0];
+}
+
 __global__ void k_round(long long n, const double *__restrict__ src, float *__restrict__ dst)
 {
     const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -671,6 +697,21 @@ cudaError_t launch_gauss_jordan(const Geom &g, int n, double *A, double *tmp, un
     e = cudaLaunchCooperativeKernel((const void *)k_gauss_jordan, dim3(nblocks), dim3(kThreads), args, 0, s);
     ++g_launches;
     return e;
+}
+
+cudaError_t launch_lincomb(long long n, double a, const double *x, double b, const double *y, double c,
+                           const double *z, double *out, cudaStream_t s)
+{
+    k_lincomb<<<nblk(n), kThreads, 0, s>>>(n, a, x, b, y, c, z, out);
+    ++g_launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sum_parts(const double *part, int n, double *out, cudaStream_t s)
+{
+    k_sum_parts<<<1, kThreads, 0, s>>>(part, n, out);
+    ++g_launches;
+    return cudaGetLastError();
 }
 
 cudaError_t launch_round(long long n, const double *src, float *dst, cudaStream_t s)

@@ -108,6 +108,7 @@ struct sbm_grid_s {
     double *amr_part = nullptr;   // partial sums of the composite norm
     long long amr_npart = 0;
     double *amr_u0 = nullptr, *amr_r0 = nullptr;   // composite solution / residual on the base level
+    double *adj[9][9] = {};                            // adjoint Krylov vectors [vector][level]
 };
 
 namespace {
@@ -701,7 +702,7 @@ cudaError_t amr_residual(sbm_grid G, int which)
 // parent nodes), the base multigrid V-cycle, patches bottom-up (prolongate the
 // parent correction, fill ghosts, smooth), then u += e on owned dofs.
 template <typename T>
-cudaError_t amr_cycle(sbm_grid G, const sbm_opts &o)
+cudaError_t amr_cycle(sbm_grid G, const sbm_opts &o, double *const *target = nullptr)
 {
     const int A = G->npatch;
     Level &B = G->L[G->nl - 1];
@@ -734,12 +735,136 @@ cudaError_t amr_cycle(sbm_grid G, const sbm_opts &o)
                                     PP<T>::e(G->P[a - 2], cur[a - 1]), 1, G->st));
         CKE(patch_smooth<T>(G, Pt, cur[a], o, o.nu2, true));
     }
-    CKE(launch_amr_update<T>(B.g, G->base_info, P<T>::u(B, cb), G->amr_u0, G->st));
+    // u += e on owned free dofs (target: the composite solution, or other level arrays)
+    CKE(launch_amr_update<T>(B.g, G->base_info, P<T>::u(B, cb), target ? target[0] : G->amr_u0, G->st));
     for (int a = 1; a <= A; ++a) {
         Patch &Pt = G->P[a - 1];
-        CKE(launch_amr_update<T>(Pt.s, Pt.info, PP<T>::e(Pt, cur[a]), Pt.u64, G->st));
+        CKE(launch_amr_update<T>(Pt.s, Pt.info, PP<T>::e(Pt, cur[a]), target ? target[a] : Pt.u64, G->st));
     }
     return cudaSuccess;
+}
+
+// ------------------------------------------------ adjoint of the composite problem
+//
+// Composite vectors: one FP64 array per level in the level layout, nonzero only on
+// the owned free dofs.  A^T is applied as the transpose of "fill, apply K_a, keep
+// owned rows": K_a on every level, then the ghost values go back to the parent
+// (transposed interpolation, finest first) and the covered values to the finer
+// level (transposed injection, coarsest first), then the owned free rows are kept.
+
+const Geom &amr_geom(sbm_grid G, int a) { return a == 0 ? G->L[G->nl - 1].g : G->P[a - 1].s; }
+const AmrInfo &amr_info(sbm_grid G, int a) { return a == 0 ? G->base_info : G->P[a - 1].info; }
+size_t amr_vec_len(sbm_grid G, int a) { const Geom &g = amr_geom(G, a); return (size_t)g.dim * g.cs; }
+
+cudaError_t cv_zero(sbm_grid G, double *const *x)
+{
+    for (int a = 0; a <= G->npatch; ++a) CKE(cudaMemsetAsync(x[a], 0, sizeof(double) * amr_vec_len(G, a), G->st));
+    return cudaSuccess;
+}
+
+cudaError_t cv_lincomb(sbm_grid G, double al, double *const *x, double be, double *const *y, double ga,
+                       double *const *z, double *const *out)
+{
+    for (int a = 0; a <= G->npatch; ++a)
+        CKE(launch_lincomb((long long)amr_vec_len(G, a), al, x[a], be, y[a], ga, z ? z[a] : nullptr, out[a], G->st));
+    return cudaSuccess;
+}
+
+// <x, y> over the owned free dofs into scal[slot] (device)
+cudaError_t cv_dot(sbm_grid G, double *const *x, double *const *y, int slot)
+{
+    long long off = 0;
+    for (int a = 0; a <= G->npatch; ++a) {
+        CKE(launch_amr_dot(amr_geom(G, a), amr_info(G, a), x[a], y[a], G->amr_part + off, G->st));
+        off += amr_blocks(amr_geom(G, a));
+    }
+    return launch_sum_parts(G->amr_part, (int)off, G->scal + slot, G->st);
+}
+
+cudaError_t amr_apply_T(sbm_grid G, double *const *x, double *const *out)
+{
+    const int A = G->npatch;
+    CKE(cv_zero(G, out));
+    CKE(sweep<double>(G, G->nl - 1, kApply, x[0], nullptr, out[0], nullptr, 0.0));
+    for (int a = 1; a <= A; ++a) CKE(sweep_view<double>(G, G->P[a - 1], kApply, x[a], nullptr, out[a], 0.0));
+    for (int a = A; a >= 1; --a)
+        CKE(launch_amr_ghostT(amr_geom(G, a), amr_info(G, a), amr_geom(G, a - 1), amr_info(G, a - 1), out[a],
+                               out[a - 1], 0, G->st));
+    for (int a = 0; a < A; ++a)
+        CKE(launch_amr_injectT(amr_geom(G, a + 1), amr_info(G, a + 1), amr_geom(G, a), amr_info(G, a), out[a],
+                               out[a + 1], G->st));
+    for (int a = 0; a <= A; ++a) CKE(launch_amr_mask(amr_geom(G, a), amr_info(G, a), out[a], G->st));
+    return cudaSuccess;
+}
+
+// One transposed (damped-Jacobi) sweep on patch a's solved dofs: eb <- eb - K_a W eb
+// and rb += W eb, with W the Jacobi scaling (the transpose of e <- e + W (r - K e)).
+cudaError_t patch_jacobiT(sbm_grid G, int a, const sbm_opts &o, double *eb, double *rb, double *t1, double *t2)
+{
+    Patch &Pt = G->P[a - 1];
+    const size_t n = amr_vec_len(G, a);
+    CKE(launch_amr_scaleW(Pt.s, Pt.info, Pt.psi64, o.omega, Pt.c64.kdiag, eb, t1, G->st));
+    CKE(cudaMemsetAsync(t2, 0, sizeof(double) * n, G->st));
+    CKE(sweep_view<double>(G, Pt, kApply, t1, nullptr, t2, 0.0));
+    CKE(launch_lincomb((long long)n, 1.0, eb, -1.0, t2, 0.0, nullptr, eb, G->st));
+    return launch_lincomb((long long)n, 1.0, rb, 1.0, t1, 0.0, nullptr, rb, G->st);
+}
+
+// z = B^T y: the transpose of one FP64 correction cycle (Jacobi smoother), taken
+// step by step in reverse: the update's mask; per patch, finest first, the
+// post-smoothing sweeps transposed and the correction prolongation transposed
+// (into the parent's adjoint); the base V-cycle (symmetric); per patch, coarsest
+// first, the restriction onto covered parents transposed, the residual
+// transposed and the pre-smoothing sweeps transposed; z = the right-hand sides'
+// adjoints on the owned free dofs.  Scratch: vectors 6, 7, 8 of adj.
+cudaError_t amr_precondT(sbm_grid G, const sbm_opts &o, double *const *y, double *const *z)
+{
+    const int A = G->npatch;
+    Level &B = G->L[G->nl - 1];
+    double *const *EB = G->adj[6];     // adjoints of the corrections e_a
+    double *const *T1 = G->adj[7];
+    double *const *T2 = G->adj[8];
+    // z holds the right-hand sides' adjoints while they accumulate
+    CKE(cv_zero(G, z));
+    CKE(cv_lincomb(G, 1.0, y, 0.0, y, 0.0, nullptr, EB));
+    for (int a = A; a >= 1; --a) {
+        for (int s_ = 0; s_ < o.nu2; ++s_) CKE(patch_jacobiT(G, a, o, EB[a], z[a], T1[a], T2[a]));
+        CKE(launch_amr_ghostT(amr_geom(G, a), amr_info(G, a), amr_geom(G, a - 1), amr_info(G, a - 1), EB[a], EB[a - 1],
+                              1, G->st));
+        CKE(launch_amr_mask_solved(amr_geom(G, a), amr_info(G, a), EB[a], G->st));
+    }
+    // base: rhs adjoint = V_0 (adjoint of its output)
+    CKE(cudaMemcpyAsync(B.df, EB[0], sizeof(double) * amr_vec_len(G, 0), cudaMemcpyDeviceToDevice, G->st));
+    CKE(cudaMemsetAsync(P<double>::u(B, 0), 0, level_bytes(B, sizeof(double)), G->st));
+    int cb = 0;
+    CKE(vcycle<double>(G, G->nl - 1, cb, o, B.df));
+    CKE(launch_lincomb((long long)amr_vec_len(G, 0), 1.0, z[0], 1.0, P<double>::u(B, cb), 0.0, nullptr, z[0], G->st));
+    for (int a = 1; a <= A; ++a) {
+        // restriction onto the covered parent nodes, transposed: residual adjoint
+        CKE(launch_amr_restrictT(amr_geom(G, a), amr_info(G, a), amr_geom(G, a - 1), amr_info(G, a - 1), z[a - 1],
+                                 T1[a], G->st));
+        CKE(launch_amr_mask_solved(amr_geom(G, a), amr_info(G, a), T1[a], G->st));
+        // residual r = rhs - K e (solved dofs): rhs_adj += res_adj, e_adj -= K res_adj
+        const size_t n = amr_vec_len(G, a);
+        CKE(launch_lincomb((long long)n, 1.0, z[a], 1.0, T1[a], 0.0, nullptr, z[a], G->st));
+        CKE(cudaMemsetAsync(T2[a], 0, sizeof(double) * n, G->st));
+        CKE(sweep_view<double>(G, G->P[a - 1], kApply, T1[a], nullptr, T2[a], 0.0));
+        CKE(launch_lincomb((long long)n, 1.0, EB[a], -1.0, T2[a], 0.0, nullptr, EB[a], G->st));
+        for (int s_ = 0; s_ < o.nu1; ++s_) CKE(patch_jacobiT(G, a, o, EB[a], z[a], T1[a], T2[a]));
+    }
+    for (int a = 0; a <= A; ++a) CKE(launch_amr_mask(amr_geom(G, a), amr_info(G, a), z[a], G->st));
+    return cudaSuccess;
+}
+
+sbm_status amr_alloc_adjoint(sbm_grid G)
+{
+    for (auto &vec : G->adj)
+        for (int a = 0; a <= G->npatch; ++a)
+            if (!vec[a]) {
+                CK(cudaMalloc(&vec[a], sizeof(double) * amr_vec_len(G, a)));
+                CK(cudaMemset(vec[a], 0, sizeof(double) * amr_vec_len(G, a)));
+            }
+    return SBM_OK;
 }
 
 sbm_status amr_prepare(sbm_grid G)
@@ -929,6 +1054,9 @@ sbm_status sbm_grid_destroy(sbm_grid G)
             if (p) cudaFree(p);
     }
     for (int a = 0; a < G->npatch; ++a) free_patch(G->P[a]);
+    for (auto &vec : G->adj)
+        for (double *q : vec)
+            if (q) cudaFree(q);
     void *ptrs[] = {G->fsrc, G->fadj, G->psi_raw, G->rho, G->part, G->scal, G->dbad, G->A64, G->A32, G->gjtmp, G->gjbar, G->gather,
                     G->derr, G->amr_part, G->amr_u0, G->amr_r0};
     for (void *p : ptrs)
@@ -1626,6 +1754,106 @@ sbm_status sbm_amr_solve(sbm_grid G, double *const *u, const sbm_opts *opts, sbm
     if (s2 != SBM_OK) return s2;
     CK(cudaStreamSynchronize(G->st));
     return s;
+}
+
+sbm_status sbm_amr_adjoint(sbm_grid G, double *const *u, double *const *dJdu, double *const *lambda,
+                           double *const *dJdpsi, const sbm_opts *opts, sbm_info *info)
+{
+    sbm_status s = check_ready(G);
+    if (s != SBM_OK) return s;
+    if (!u || !dJdu || !lambda) return fail(G, SBM_ERR_ARG, "null argument");
+    if (G->npatch == 0) return fail(G, SBM_ERR_STATE, "no patch levels: use sbm_adjoint");
+    sbm_opts o;
+    sbm_default_opts(&o);
+    if (opts) o = *opts;
+    if ((s = validate_opts(G, o)) != SBM_OK) return s;
+    CK(cudaSetDevice(G->dev));
+    for (int a = 0; a <= G->npatch; ++a) {
+        if (!is_dev_ptr(dJdu[a], G->dev) || !is_dev_ptr(lambda[a], G->dev) || (dJdpsi && !is_dev_ptr(dJdpsi[a], G->dev)))
+            return fail(G, SBM_ERR_ARG, "dJdu[a], lambda[a] and dJdpsi[a] must be device pointers");
+    }
+    if ((s = amr_prepare(G)) != SBM_OK) return s;
+    if ((s = setup_bottom(G)) != SBM_OK) return s;
+    if ((s = amr_alloc_adjoint(G)) != SBM_OK) return s;
+    const int A = G->npatch;
+    if (o.smoother != SBM_JACOBI) return fail(G, SBM_ERR_ARG, "the composite adjoint needs the Jacobi smoother");
+    double *const *X = G->adj[0], *const *Gv = G->adj[1], *const *R = G->adj[2], *const *Zv = G->adj[3];
+    const long long launches0 = g_launches;
+    CK(cudaEventRecord(G->ev0, G->st));
+    // right-hand side g = dJ/du on the owned free dofs
+    for (int a = 0; a <= A; ++a) {
+        CK(launch_pack<double, double>(amr_geom(G, a), amr_geom(G, a).dim, dJdu[a], Gv[a], G->st));
+        CK(launch_amr_mask(amr_geom(G, a), amr_info(G, a), Gv[a], G->st));
+    }
+    CK(cv_zero(G, X));
+    double hs[2];
+    auto norm_of = [&](double *const *v, double *out) -> cudaError_t {
+        cudaError_t e = cv_dot(G, v, v, 8);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(hs, G->scal + 8, sizeof(double), cudaMemcpyDeviceToHost, G->st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(G->st);
+        *out = std::sqrt(hs[0]);
+        return e;
+    };
+    double bnorm = 0.0;
+    CK(norm_of(Gv, &bnorm));
+    if (info) {
+        info->r0 = bnorm;
+        info->levels = G->nl + G->npatch;
+        if (info->history && info->history_capacity > 0) info->history[0] = 1.0;
+    }
+    // lambda <- lambda + B^T (g - A^T lambda): the transposed correction iteration,
+    // which converges at the rate of the forward one
+    double rel = bnorm > 0.0 ? 1.0 : 0.0;
+    int it = 0;
+    sbm_status status = bnorm > 0.0 ? SBM_ERR_NOCONV : SBM_OK;
+    CK(cv_lincomb(G, 1.0, Gv, 0.0, Gv, 0.0, nullptr, R));
+    while (status == SBM_ERR_NOCONV && it < o.max_cycles) {
+        CK(amr_precondT(G, o, R, Zv));
+        CK(cv_lincomb(G, 1.0, X, 1.0, Zv, 0.0, nullptr, X));
+        CK(amr_apply_T(G, X, Zv));
+        CK(cv_lincomb(G, 1.0, Gv, -1.0, Zv, 0.0, nullptr, R));
+        double rn = 0.0;
+        CK(norm_of(R, &rn));
+        ++it;
+        rel = rn / bnorm;
+        if (info && info->history && it < info->history_capacity) info->history[it] = rel;
+        if (!std::isfinite(rel) || rel > 1e10) status = SBM_ERR_DIVERGED;
+        else if (rel <= o.tol) status = SBM_OK;
+    }
+    double *const *T = G->adj[4];
+    for (int a = 0; a <= A; ++a)
+        CK(launch_unpack<double, double>(amr_geom(G, a), amr_geom(G, a).dim, X[a], lambda[a], G->st));
+    if (dJdpsi) {
+        // filled solution, per-level cell gradients, coarse-to-fine chain, floor mask
+        if ((s = amr_pack_u(G, u)) != SBM_OK) return s;
+        CK(amr_fill(G));
+        for (int a = 0; a <= A; ++a) {
+            const Coef<double> &c = a == 0 ? G->L[G->nl - 1].c64 : G->P[a - 1].c64;
+            CK(launch_amr_dJdpsi(amr_geom(G, a), amr_info(G, a), c, a == 0 ? G->amr_u0 : G->P[a - 1].u64, X[a], T[a],
+                                 G->st));
+        }
+        for (int a = 0; a < A; ++a)
+            CK(launch_amr_grad_chain(amr_geom(G, a + 1), amr_info(G, a + 1), amr_geom(G, a), amr_info(G, a), T[a],
+                                     T[a + 1], G->st));
+        for (int a = 0; a <= A; ++a)
+            CK(launch_amr_get_cells(amr_geom(G, a), T[a], a == 0 ? G->L[G->nl - 1].psi64 : G->P[a - 1].psi64,
+                                    G->psi_min, dJdpsi[a], G->st));
+    }
+    CK(cudaEventRecord(G->ev1, G->st));
+    CK(cudaEventSynchronize(G->ev1));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, G->ev0, G->ev1);
+    if (info) {
+        info->status = status;
+        info->cycles = it;
+        info->vcycles = it;
+        info->relres = rel;
+        info->solve_ms = ms;
+        info->launches = g_launches - launches0;
+    }
+    if (status == SBM_ERR_NOCONV) G->err = "max_cycles reached before the tolerance";
+    if (status == SBM_ERR_DIVERGED) G->err = "relative residual not finite or above 1e10";
+    return status;
 }
 
 sbm_status sbm_amr_residual(sbm_grid G, double *const *u, double *const *r, double *norm)

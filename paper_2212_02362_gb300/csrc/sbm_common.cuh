@@ -171,6 +171,27 @@ struct AmrInfo {
     unsigned dm[3];        // Dirichlet faces of the domain, per component
 };
 
+cudaError_t launch_lincomb(long long n, double a, const double *x, double b, const double *y, double c,
+                           const double *z, double *out, cudaStream_t s);
+cudaError_t launch_sum_parts(const double *part, int n, double *out, cudaStream_t s);
+// adjoint of the composite problem
+cudaError_t launch_amr_ghostT(const Geom &sc, const AmrInfo &Lc, const Geom &sp, const AmrInfo &Lp, const double *wc,
+                              double *wp, int with_solved, cudaStream_t st);
+cudaError_t launch_amr_mask_solved(const Geom &s, const AmrInfo &L, double *x, cudaStream_t st);
+cudaError_t launch_amr_scaleW(const Geom &s, const AmrInfo &L, const double *psi, double omega, const double kdiag[3],
+                              const double *x, double *out, cudaStream_t st);
+cudaError_t launch_amr_restrictT(const Geom &sc, const AmrInfo &Lc, const Geom &sp, const AmrInfo &Lp,
+                                 const double *rp, double *rc, cudaStream_t st);
+cudaError_t launch_amr_injectT(const Geom &sc, const AmrInfo &Lc, const Geom &sp, const AmrInfo &Lp, const double *wp,
+                               double *wc, cudaStream_t st);
+cudaError_t launch_amr_dot(const Geom &s, const AmrInfo &L, const double *x, const double *y, double *part,
+                           cudaStream_t st);
+cudaError_t launch_amr_dJdpsi(const Geom &s, const AmrInfo &L, const Coef<double> &c, const double *u,
+                              const double *lam, double *g, cudaStream_t st);
+cudaError_t launch_amr_grad_chain(const Geom &sc, const AmrInfo &Lc, const Geom &sp, const AmrInfo &Lp, double *gp,
+                                  double *gc, cudaStream_t st);
+cudaError_t launch_amr_get_cells(const Geom &s, const double *lev, const double *psi, double psi_min, double *packed,
+                                 cudaStream_t st);
 long long amr_blocks(const Geom &s);
 bool amr_owned_host(const AmrInfo &L, int i, int j, int k);
 cudaError_t launch_amr_mask(const Geom &s, const AmrInfo &L, double *r, cudaStream_t st);

@@ -12,7 +12,7 @@ import pytest
 
 import oracle
 import workloads as W
-from _amr import dense_solve
+from _amr import dense_solve, dense_system
 from _sbm import cuda, host
 
 pytestmark = pytest.mark.gpu
@@ -218,4 +218,99 @@ def test_C5_full_size_sampled_parity(built):
     sol = [host(u) for u in us]
     r = oracle.amr_residual_at(A, psis, fs, sol, lev, nodes, comps)
     assert np.abs(r).max() <= 2e-10 * nrm0, (np.abs(r).max() / nrm0, info.cycles)
+
+
+def _filled_dense_solution(A, psis, fs, us0):
+    unk, M, b = dense_system(A, psis, fs, us0)
+    x = np.linalg.solve(M, b)
+    us = [u.copy() for u in us0]
+    for (a, e), v in zip(unk, x):
+        us[a][e] += v
+    oracle.amr_fill(A, us)
+    return unk, M, us
+
+
+@pytest.mark.parametrize("case", list(SMALL))
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_composite_adjoint_matches_dense_oracle(built, case, precision):
+    """lambda of A^T lambda = g and dJ/dpsi per level against the oracle's dense
+    transpose solve and its composite gradient (floor cells masked); the
+    transposed correction iteration converges like the forward one."""
+    wk = SMALL[case]()
+    A, psis = _oracle(wk)
+    fs = [W.uniform(800 + a, A.level_problem(a).ndofs, -1, 1) for a in range(A.nlev)]
+    us0 = [np.ascontiguousarray(wk.level_u0(a)) for a in range(A.nlev)]
+    unk, M, us = _filled_dense_solution(A, psis, fs, us0)
+    gs = [W.uniform(900 + a, A.level_problem(a).ndofs, -1, 1) for a in range(A.nlev)]
+    gvec = np.array([gs[a][e] for a, e in unk])
+    lam = np.linalg.solve(M.T, gvec)
+    lams = [np.zeros_like(u) for u in us]
+    for (a, e), v in zip(unk, lam):
+        lams[a][e] = v
+    ref = oracle.amr_dJdpsi(A, us, lams)
+    g = _gpu(wk, precision)
+    lg, gg, info = g.amr_adjoint([cuda(u) for u in us], [cuda(x) for x in gs], tol=1e-12, max_cycles=300,
+                                 omega=wk.omega, smoother="jacobi")
+    assert info.converged, info
+    assert info.cycles <= 60, info.cycles
+    num = np.sqrt(sum(((host(lg[a]) - lams[a]) ** 2).sum() for a in range(A.nlev)))
+    assert num <= 1e-9 * np.linalg.norm(lam), num / np.linalg.norm(lam)
+    scale = max(np.abs(r).max() for r in ref)
+    for a in range(A.nlev):
+        mask = np.maximum(wk.level_psi(a), wk.psi_min) > wk.psi_min
+        assert np.abs(host(gg[a]) - np.where(mask, ref[a], 0.0)).max() <= 1e-9 * scale, a
+
+
+def test_C5_full_size_adjoint_directional_derivative(built):
+    """3D refinement at full size: one adjoint solve for J = g.u, then the predicted
+    change of J along a smooth psi perturbation of every level against central
+    differences of two forward solves."""
+    wk = W.voids_amr(3, 129, 2, count=16, rmin=0.04, rmax=0.12)
+    raw = [np.ascontiguousarray(wk.level_psi(a)) for a in range(3)]
+    g = sbm.Grid(3, wk.n, wk.h, precision="mixed")
+    g.set_moduli(sbm.SBM_CUBIC, wk.moduli)
+    for face, comp, _ in wk.bcs:
+        g.set_bc(face, comp, sbm.SBM_DIRICHLET_FROM_U)
+    g.set_psi(cuda(raw[0]), wk.psi_min)
+    for lo, hi in wk.boxes:
+        g.amr_add_level(lo, hi)
+    for a in (1, 2):
+        g.amr_set_psi(a, cuda(raw[a]), wk.psi_min)
+    us0 = [cuda(wk.level_u0(a)) for a in range(3)]
+    # J = g.u over the owned free dofs: the composite residual of a random field is
+    # zero exactly off them
+    rnd = [torch.from_numpy(W.uniform(1100 + a, u.numel(), -1, 1)).cuda() for a, u in enumerate(us0)]
+    rs, _ = g.amr_residual(rnd)
+    gs = [torch.from_numpy(W.uniform(1000 + a, u.numel(), -1, 1)).cuda() * (r != 0) for a, (u, r) in
+          enumerate(zip(us0, rs))]
+    del rnd, rs
+    opts = dict(omega=wk.omega, smoother=wk.smoother, max_cycles=300)
+
+    def J(psi_levels):
+        g.set_psi(cuda(psi_levels[0]), wk.psi_min)
+        for a in (1, 2):
+            g.amr_set_psi(a, cuda(psi_levels[a]), wk.psi_min)
+        us = [u.clone() for u in us0]
+        g.amr_solve(us, tol=1e-12, **opts)
+        tot = 0.0
+        for a in range(3):
+            tot += float((gs[a] * us[a]).sum())
+        return tot, us
+
+    J0, us = J(raw)
+    lams, grads, info = g.amr_adjoint(us, gs, tol=1e-10, **opts)
+    assert info.converged, info
+    rng = np.random.default_rng(5)
+    dpsi = []
+    for a in range(3):
+        X = np.arange(raw[a].size)
+        d = 0.01 * raw[a] * np.sin(0.37 * X + rng.uniform(0, 6))
+        d[np.maximum(raw[a], wk.psi_min) <= 1.5 * wk.psi_min] = 0.0
+        dpsi.append(d)
+    pred = sum(float((host(grads[a]) * dpsi[a]).sum()) for a in range(3))
+    eps = 1e-3
+    Jp, _ = J([r + eps * d for r, d in zip(raw, dpsi)])
+    Jm, _ = J([r - eps * d for r, d in zip(raw, dpsi)])
+    fd = (Jp - Jm) / (2 * eps)
+    assert abs(fd - pred) <= 1e-4 * abs(pred), (fd, pred, info.cycles)
 
