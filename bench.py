@@ -94,7 +94,7 @@ def workload_config(wk, precision, inner=1):
     return {"workload": f"{wk.name} {'x'.join(str(v) for v in wk.n[:wk.dim])} nodes",
             "dofs": wk.ndofs, "moduli_c11_c12_c44": list(wk.moduli), "psi_min": wk.psi_min,
             "precision": precision, "tol": 1e-10, "cycle": "V(2,2) damped Jacobi",
-            "fp32_vcycles_per_fp64_residual": inner if precision == "mixed" else None,
+            "fp32_vcycles_per_fp64_residual": (f"adaptive, at most {inner}" if precision == "mixed" else None),
             "omega": wk.omega, "l2": "flushed (256 MB write) between timed steps"}
 
 
@@ -260,7 +260,8 @@ def run_ours(args, rank, world, local_rank):
     rho_d = t64(wk.rho) if args.adjoint and wk.rho is not None else None
     dJdu = f_d * wk.h ** wk.dim
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    opts = {"omega": wk.omega, "tol": 1e-10, "inner_cycles": args.inner if args.precision == "mixed" else 1}
+    opts = {"omega": wk.omega, "tol": 1e-10, "inner_cycles": args.inner if args.precision == "mixed" else 1,
+            "inner_rtol": args.inner_rtol if args.precision == "mixed" else 0.0}
 
     def timed_solves(g, nsteps, nwarm):
         with torch.cuda.stream(stream):
@@ -572,7 +573,11 @@ def main():
     ap.add_argument("--workload", default="damage_3d_129")
     ap.add_argument("--precision", choices=["mixed", "fp64"], default=None,
                     help="default: the workload's (mixed for the 3D configurations)")
-    ap.add_argument("--inner", type=int, default=8, help="FP32 V-cycles per FP64 defect residual (mixed)")
+    ap.add_argument("--inner", type=int, default=12,
+                    help="FP32 V-cycles per FP64 defect residual (mixed; the maximum when --inner-rtol > 0)")
+    ap.add_argument("--inner-rtol", type=float, default=1e-6,
+                    help="stop an outer iteration's FP32 V-cycles once their residual falls below this "
+                         "fraction of the FP64 residual (or below the tolerance); 0: fixed count")
     ap.add_argument("--roofline-kernel", choices=["residual64", "jacobi"], default="jacobi")
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per launch of the roofline kernel from an ncu capture")

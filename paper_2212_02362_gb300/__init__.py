@@ -55,12 +55,12 @@ class SolveInfo:
 
 
 def make_opts(tol=1e-10, max_cycles=500, nu1=2, nu2=2, omega=2.0 / 3.0, smoother="jacobi",
-              inner_cycles=1, use_graph=True) -> _capi.sbm_opts:
+              inner_cycles=1, use_graph=True, inner_rtol=0.0) -> _capi.sbm_opts:
     o = _capi.sbm_opts()
     lib().sbm_default_opts(C.byref(o))
     o.tol, o.max_cycles, o.nu1, o.nu2, o.omega = tol, max_cycles, nu1, nu2, omega
     o.smoother = SBM_MCGS if smoother in ("gs", "mcgs", "rbgs") else SBM_JACOBI
-    o.inner_cycles, o.use_graph = inner_cycles, int(bool(use_graph))
+    o.inner_cycles, o.use_graph, o.inner_rtol = inner_cycles, int(bool(use_graph)), inner_rtol
     return o
 
 

@@ -28,7 +28,7 @@ class sbm_grid_desc(C.Structure):
 class sbm_opts(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_cycles", C.c_int), ("nu1", C.c_int), ("nu2", C.c_int),
                 ("omega", C.c_double), ("smoother", C.c_int), ("inner_cycles", C.c_int),
-                ("use_graph", C.c_int)]
+                ("use_graph", C.c_int), ("inner_rtol", C.c_double)]
 
 
 class sbm_box(C.Structure):

@@ -62,8 +62,9 @@ __device__ __forceinline__ T fw_row(const T *__restrict__ row, int I, int nx)
 // The 3^d fine rows are read with independent loads (clamped index, zero weight
 // outside the grid) so they are all in flight together.
 template <typename T, int D>
-__global__ void k_restrict(const Geom gf, const Geom gc, const T *__restrict__ rf, T *__restrict__ fc)
+__global__ void k_restrict(const Geom gf, const Geom gc, const T *__restrict__ rf, T *__restrict__ fc, const int *gate)
 {
+    if (gate && *gate) return;
     const int I = blockIdx.x * blockDim.x + threadIdx.x;
     const int J = blockIdx.y * blockDim.y + threadIdx.y;
     const int K = blockIdx.z * blockDim.z + threadIdx.z;
@@ -104,8 +105,10 @@ __global__ void k_restrict(const Geom gf, const Geom gc, const T *__restrict__ r
 // node copies e_c, the others average the 2, 4 or 8 coarse neighbours.  The x
 // pair (2I, 2I+1) is read and written as one aligned vector.
 template <typename T, int D>
-__global__ void k_prolong_add(const Geom gf, const Geom gc, const T *__restrict__ ec, T *__restrict__ uf)
+__global__ void k_prolong_add(const Geom gf, const Geom gc, const T *__restrict__ ec, T *__restrict__ uf,
+                              const int *gate)
 {
+    if (gate && *gate) return;
     using V = typename Vec2<T>::type;
     const int I = blockIdx.x * blockDim.x + threadIdx.x;
     const int J = blockIdx.y * blockDim.y + threadIdx.y;
@@ -346,6 +349,28 @@ __global__ void k_norm_final(const double *__restrict__ part, int n, double *sca
         scal[which] = ss;
         scal[which + 1] = sqrt(ss);
         if (which == 2) scal[4] = (scal[1] > 0.0) ? sqrt(ss) / scal[1] : 0.0;
+        if (which == 0 || which == 2) scal[7] = sqrt(ss);     // latest FP64 residual norm
+    }
+}
+
+__global__ void k_inner_gate(const double *__restrict__ part, int n, const double *scal, double rtol,
+                             double tol_frac, int *gate, int *count)
+{
+    if (*gate) return;
+    __shared__ double red[kThreads];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += kThreads) s += part[i];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = kThreads / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double rn = sqrt(red[0]);
+        const double thr = fmax(rtol * scal[7], tol_frac * scal[1]);
+        *count += 1;
+        if (rn <= thr) *gate = 1;
     }
 }
 
@@ -452,10 +477,15 @@ __device__ __forceinline__ int next_pivot(const Geom &g, long long N, int k, int
     return n;
 }
 
-__global__ void k_gauss_jordan(const Geom g, int n, double *A, double *tmp, unsigned *bar)
+__global__ void k_gauss_jordan(const Geom g, int n, double *A, double *tmp, unsigned *bar, int in_smem)
 {
+    // in_smem: the block's rows (blockIdx.x + m gridDim.x) live in shared memory
+    extern __shared__ double srow[];
     const long long N = (long long)g.nx * g.ny * g.nz;
     const unsigned nb = gridDim.x;
+    if (in_smem)
+        for (int i = blockIdx.x, m = 0; i < n; i += gridDim.x, ++m)
+            for (int j = threadIdx.x; j < n; j += blockDim.x) srow[(long long)m * n + j] = A[(long long)i * n + j];
     // tmp[b * 2n + j]: row of the pivot; tmp[b * 2n + n + i]: its column (both unscaled)
     int k = next_pivot(g, N, 0, n);
     if (k >= n) return;
@@ -471,8 +501,8 @@ __global__ void k_gauss_jordan(const Geom g, int n, double *A, double *tmp, unsi
         double *Rn = tmp + (long long)(1 - cur) * 2 * n, *Cn = Rn + n;
         // the pivot row and column were written by other blocks: read them from L2
         const double ip = 1.0 / __ldcg(R + k);
-        for (int i = blockIdx.x; i < n; i += gridDim.x) {
-            double *row = A + (long long)i * n;
+        for (int i = blockIdx.x, r = 0; i < n; i += gridDim.x, ++r) {
+            double *row = in_smem ? srow + (long long)r * n : A + (long long)i * n;
             const double m = __ldcg(Cc + i);
             for (int j = threadIdx.x; j < n; j += blockDim.x) {
                 const double rkj = (j == k) ? ip : __ldcg(R + j) * ip;
@@ -488,13 +518,17 @@ __global__ void k_gauss_jordan(const Geom g, int n, double *A, double *tmp, unsi
         cur ^= 1;
         k = kn;
     }
+    if (in_smem)
+        for (int i = blockIdx.x, m = 0; i < n; i += gridDim.x, ++m)
+            for (int j = threadIdx.x; j < n; j += blockDim.x) A[(long long)i * n + j] = srow[(long long)m * n + j];
 }
 
 // u[gather[r]] (+)= sum_c Ainv[r][c] b[gather[c]]: one warp per row.
 template <typename T>
 __global__ void k_bottom_apply(int n, const T *__restrict__ Ainv, const int *__restrict__ gather,
-                               const T *__restrict__ b, T *__restrict__ u, int accumulate)
+                               const T *__restrict__ b, T *__restrict__ u, int accumulate, const int *gate)
 {
+    if (gate && *gate) return;
     const int row = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (row >= n) return;
@@ -560,26 +594,29 @@ __global__ void k_dJdpsi(const Geom g, const Coef<double> c, const double *__res
 // ------------------------------------------------------------------ launchers
 
 template <typename T>
-cudaError_t launch_restrict(const Geom &gf, const Geom &gc, const T *rf, T *fc, cudaStream_t s)
+cudaError_t launch_restrict(const Geom &gf, const Geom &gc, const T *rf, T *fc, cudaStream_t s, const int *gate)
 {
-    if (gf.dim == 3) k_restrict<T, 3><<<node_grid(gc), kNodeBlock, 0, s>>>(gf, gc, rf, fc);
-    else k_restrict<T, 2><<<node_grid(gc), kNodeBlock, 0, s>>>(gf, gc, rf, fc);
+    if (gf.dim == 3) k_restrict<T, 3><<<node_grid(gc), kNodeBlock, 0, s>>>(gf, gc, rf, fc, gate);
+    else k_restrict<T, 2><<<node_grid(gc), kNodeBlock, 0, s>>>(gf, gc, rf, fc, gate);
     ++g_launches;
     return cudaGetLastError();
 }
-template cudaError_t launch_restrict<double>(const Geom &, const Geom &, const double *, double *, cudaStream_t);
-template cudaError_t launch_restrict<float>(const Geom &, const Geom &, const float *, float *, cudaStream_t);
+template cudaError_t launch_restrict<double>(const Geom &, const Geom &, const double *, double *, cudaStream_t,
+                                             const int *);
+template cudaError_t launch_restrict<float>(const Geom &, const Geom &, const float *, float *, cudaStream_t, const int *);
 
 template <typename T>
-cudaError_t launch_prolong_add(const Geom &gf, const Geom &gc, const T *ec, T *uf, cudaStream_t s)
+cudaError_t launch_prolong_add(const Geom &gf, const Geom &gc, const T *ec, T *uf, cudaStream_t s, const int *gate)
 {
-    if (gf.dim == 3) k_prolong_add<T, 3><<<node_grid(gc), kNodeBlock, 0, s>>>(gf, gc, ec, uf);
-    else k_prolong_add<T, 2><<<node_grid(gc), kNodeBlock, 0, s>>>(gf, gc, ec, uf);
+    if (gf.dim == 3) k_prolong_add<T, 3><<<node_grid(gc), kNodeBlock, 0, s>>>(gf, gc, ec, uf, gate);
+    else k_prolong_add<T, 2><<<node_grid(gc), kNodeBlock, 0, s>>>(gf, gc, ec, uf, gate);
     ++g_launches;
     return cudaGetLastError();
 }
-template cudaError_t launch_prolong_add<double>(const Geom &, const Geom &, const double *, double *, cudaStream_t);
-template cudaError_t launch_prolong_add<float>(const Geom &, const Geom &, const float *, float *, cudaStream_t);
+template cudaError_t launch_prolong_add<double>(const Geom &, const Geom &, const double *, double *, cudaStream_t,
+                                                const int *);
+template cudaError_t launch_prolong_add<float>(const Geom &, const Geom &, const float *, float *, cudaStream_t,
+                                               const int *);
 
 cudaError_t launch_coarsen_psi(const Geom &gf, const Geom &gc, const double *pf, double *pc, cudaStream_t s)
 {
@@ -663,6 +700,14 @@ cudaError_t launch_norm_final(const double *part, int nparts, double *scal, int 
     return cudaGetLastError();
 }
 
+cudaError_t launch_inner_gate(const double *part, int nparts, const double *scal, double rtol, double tol_frac,
+                              int *gate, int *count, cudaStream_t s)
+{
+    k_inner_gate<<<1, kThreads, 0, s>>>(part, nparts, scal, rtol, tol_frac, gate, count);
+    ++g_launches;
+    return cudaGetLastError();
+}
+
 cudaError_t launch_bottom_assemble(const Geom &g, const double *psi, const Coef<double> &c, double *A, cudaStream_t s)
 {
     const long long n = (long long)g.nx * g.ny * g.nz * g.dim;
@@ -685,16 +730,25 @@ cudaError_t launch_gauss_jordan(const Geom &g, int n, double *A, double *tmp, un
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gauss_jordan, kThreads, 0);
     if (e != cudaSuccess) return e;
-    if (!coop || per_sm < 1) return cudaErrorNotSupported;
     int nblocks = nsm;                      // one block per SM, all co-resident
     if (nblocks > n) nblocks = n;
+    // the rows of each block in shared memory when they fit
+    const size_t rows_bytes = (size_t)((n + nblocks - 1) / nblocks) * n * sizeof(double);
+    int in_smem = rows_bytes <= 160 * 1024 ? 1 : 0;
+    const size_t smem = in_smem ? rows_bytes : 0;
+    if (smem > 48 * 1024) {
+        e = cudaFuncSetAttribute(k_gauss_jordan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gauss_jordan, kThreads, smem);
+    if (e != cudaSuccess) return e;
+    if (!coop || per_sm < 1) return cudaErrorNotSupported;
     e = cudaMemsetAsync(bar, 0, 4 * sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
     Geom gg = g;
-    void *args[] = {&gg, &n, &A, &tmp, &bar};
-    e = cudaLaunchCooperativeKernel((const void *)k_gauss_jordan, dim3(nblocks), dim3(kThreads), args, 0, s);
+    void *args[] = {&gg, &n, &A, &tmp, &bar, &in_smem};
+    e = cudaLaunchCooperativeKernel((const void *)k_gauss_jordan, dim3(nblocks), dim3(kThreads), args, smem, s);
     ++g_launches;
     return e;
 }
@@ -723,16 +777,18 @@ cudaError_t launch_round(long long n, const double *src, float *dst, cudaStream_
 
 template <typename T>
 cudaError_t launch_bottom_apply(int n, const T *Ainv, const int *gather, const T *b, T *u, int accumulate,
-                                cudaStream_t s)
+                                cudaStream_t s, const int *gate)
 {
     const int rows_per_block = 8;
     k_bottom_apply<T><<<(n + rows_per_block - 1) / rows_per_block, 32 * rows_per_block, 0, s>>>(n, Ainv, gather, b, u,
-                                                                                                accumulate);
+                                                                                                accumulate, gate);
     ++g_launches;
     return cudaGetLastError();
 }
-template cudaError_t launch_bottom_apply<double>(int, const double *, const int *, const double *, double *, int, cudaStream_t);
-template cudaError_t launch_bottom_apply<float>(int, const float *, const int *, const float *, float *, int, cudaStream_t);
+template cudaError_t launch_bottom_apply<double>(int, const double *, const int *, const double *, double *, int, cudaStream_t,
+                                                 const int *);
+template cudaError_t launch_bottom_apply<float>(int, const float *, const int *, const float *, float *, int, cudaStream_t,
+                                                const int *);
 
 cudaError_t launch_dJdpsi(const Geom &g, const Coef<double> &c, const double *u, const double *lam, double *g_out,
                           double *grho_out, const double *rho, const double *psi_raw, double psi_min, double q,

@@ -68,6 +68,7 @@ __device__ __forceinline__ void block_partial(double ssq, double *part, double *
 template <typename T, typename TO, int MODE>
 __global__ void __launch_bounds__((TX3 + 1) * (TY3 + 1)) k_sweep3(const SweepArgs<T, TO> a)
 {
+    if (a.gate && *a.gate) return;
     constexpr int BX = TX3 + 1, BY = TY3 + 1, NT = BX * BY;
     constexpr int PX = TX3 + 2, PY = TY3 + 2, PP = PX * PY;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -192,6 +193,7 @@ constexpr int TXD = 32, TYD = 12;
 template <typename TO, int MODE>
 __global__ void __launch_bounds__((TXD + 1) * (TYD + 1)) k_sweep3_dp(const SweepArgs<double, TO> a)
 {
+    if (a.gate && *a.gate) return;
     constexpr int BX = TXD + 1, BY = TYD + 1, NT = BX * BY;
     constexpr int PX = TXD + 2, PY = TYD + 2, PP = PX * PY;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -296,6 +298,7 @@ constexpr size_t smem_dp() { return sizeof(double) * (2 * 3 + 12 + 1) * (TXD + 2
 template <typename T, typename TO, int MODE>
 __global__ void __launch_bounds__((TX2 + 1) * (TY2 + 1)) k_sweep2(const SweepArgs<T, TO> a)
 {
+    if (a.gate && *a.gate) return;
     constexpr int BX = TX2 + 1, BY = TY2 + 1, NT = BX * BY;
     constexpr int PX = TX2 + 2, PY = TY2 + 2, PP = PX * PY;
     __shared__ T up[2 * PP];
@@ -368,8 +371,9 @@ constexpr size_t smem3()
 // Ke is the unit-psi cell matrix for this level, row = corner*d + component.
 template <typename T, int D>
 __global__ void k_gs(const Geom g, const T *__restrict__ psi, const T *__restrict__ Ke,
-                     const T *__restrict__ f, T *__restrict__ u, int colour)
+                     const T *__restrict__ f, T *__restrict__ u, int colour, const int *gate)
 {
+    if (gate && *gate) return;
     constexpr int NC = 1 << D, ND = NC * D;
     const int cxb = colour & 1, cyb = (colour >> 1) & 1, czb = (colour >> 2) & 1;
     const int i = 2 * (blockIdx.x * blockDim.x + threadIdx.x) + cxb;
@@ -464,6 +468,7 @@ long long sweep_blocks(const Geom &g, bool fp64)
 template <int MODE>
 __global__ void __launch_bounds__(128) k_sweep3_node(const SweepArgs<float, float> a)
 {
+    if (a.gate && *a.gate) return;
     const Geom &g = a.g;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
@@ -568,22 +573,25 @@ template cudaError_t launch_sweep<float, float>(int, const SweepArgs<float, floa
 template cudaError_t launch_sweep<double, float>(int, const SweepArgs<double, float> &, cudaStream_t);
 
 template <typename T>
-cudaError_t launch_gs(const Geom &g, const T *psi, const T *Ke, const T *f, T *u, int colour, cudaStream_t s)
+cudaError_t launch_gs(const Geom &g, const T *psi, const T *Ke, const T *f, T *u, int colour, cudaStream_t s,
+                      const int *gate)
 {
     if (g.dim == 3) {
         dim3 b(32, 4, 2);
         dim3 gr(((g.nx + 1) / 2 + b.x - 1) / b.x, ((g.ny + 1) / 2 + b.y - 1) / b.y, ((g.nz + 1) / 2 + b.z - 1) / b.z);
-        k_gs<T, 3><<<gr, b, 0, s>>>(g, psi, Ke, f, u, colour);
+        k_gs<T, 3><<<gr, b, 0, s>>>(g, psi, Ke, f, u, colour, gate);
     } else {
         dim3 b(32, 8, 1);
         dim3 gr(((g.nx + 1) / 2 + b.x - 1) / b.x, ((g.ny + 1) / 2 + b.y - 1) / b.y, 1);
-        k_gs<T, 2><<<gr, b, 0, s>>>(g, psi, Ke, f, u, colour);
+        k_gs<T, 2><<<gr, b, 0, s>>>(g, psi, Ke, f, u, colour, gate);
     }
     ++g_launches;
     return cudaGetLastError();
 }
 
-template cudaError_t launch_gs<double>(const Geom &, const double *, const double *, const double *, double *, int, cudaStream_t);
-template cudaError_t launch_gs<float>(const Geom &, const float *, const float *, const float *, float *, int, cudaStream_t);
+template cudaError_t launch_gs<double>(const Geom &, const double *, const double *, const double *, double *, int, cudaStream_t,
+                                       const int *);
+template cudaError_t launch_gs<float>(const Geom &, const float *, const float *, const float *, float *, int, cudaStream_t,
+                                      const int *);
 
 }  // namespace sbm

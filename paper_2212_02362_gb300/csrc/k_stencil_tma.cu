@@ -177,6 +177,7 @@ __global__ void __launch_bounds__(NTP) k_sweep3_f2(const __grid_constant__ CUten
                                                     const __grid_constant__ CUtensorMap tmap_psi,
                                                     const SweepArgs<float, float> a, int *err)
 {
+    if (a.gate && *a.gate) return;
     extern __shared__ unsigned char smem_raw[];
     unsigned char *base = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
     float *ring = reinterpret_cast<float *>(base);

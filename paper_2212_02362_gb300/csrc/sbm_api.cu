@@ -62,7 +62,7 @@ struct GraphSlot {
     bool valid = false;
     cudaGraphExec_t exec = nullptr;
     int mixed = 0, smoother = 0, nu1 = 0, nu2 = 0, inner = 0;
-    double omega = 0;
+    double omega = 0, inner_rtol = 0;
     const double *rhs = nullptr;
     unsigned version = 0;
     long long body_launches = 0;
@@ -88,6 +88,9 @@ struct sbm_grid_s {
     double *part = nullptr;
     long long npart = 0;
     int *derr = nullptr;        // device error flag of the TMA kernels
+    int *dgate = nullptr;       // adaptive inner cycles: [0] gate flag, [1] FP32 V-cycles run
+    const int *cur_gate = nullptr;   // gate applied to the launches being enqueued (or null)
+    double gate_rtol = 0, gate_tol = 0;
     double *scal = nullptr;     // device scalars, see k_norm_final
     double *hscal = nullptr;    // pinned host copy
     int *dbad = nullptr;
@@ -186,6 +189,7 @@ cudaError_t sweep(sbm_grid G, int l, int mode, const T *u, const T *f, T *out, d
     a.c = P<T>::c(L);
     for (int p = 0; p < 3; ++p) a.wk[p] = (L.c64.kdiag[p] != 0.0) ? T(omega / L.c64.kdiag[p]) : T(0);
     a.kchunk = 0;
+    a.gate = G->cur_gate;
     return launch_sweep<T, T>(mode, a, G->st);
 }
 
@@ -207,6 +211,7 @@ cudaError_t sweep<float>(sbm_grid G, int l, int mode, const float *u, const floa
     a.c = L.c32;
     for (int p = 0; p < 3; ++p) a.wk[p] = (L.c64.kdiag[p] != 0.0) ? float(omega / L.c64.kdiag[p]) : 0.f;
     a.kchunk = 0;
+    a.gate = G->cur_gate;
     if (L.g.dim == 3 && part == nullptr && (long long)L.g.nx * L.g.ny * L.g.nz <= kNodeKernelMaxNodes)
         return launch_sweep_node(mode, a, G->st);
     if (L.has_tm && (u == L.su[0] || u == L.su[1]) && (mode == kApply || f == L.sf))
@@ -272,7 +277,8 @@ cudaError_t smooth(sbm_grid G, int l, int &cur, const sbm_opts &o, int nsweeps, 
     for (int s = 0; s < nsweeps; ++s) {
         if (o.smoother == SBM_MCGS) {
             for (int c = 0; c < ncol; ++c)
-                CKE(launch_gs<T>(L.g, P<T>::psi(L), P<T>::Ke(L), f, P<T>::u(L, cur), descending ? ncol - 1 - c : c, G->st));
+                CKE(launch_gs<T>(L.g, P<T>::psi(L), P<T>::Ke(L), f, P<T>::u(L, cur), descending ? ncol - 1 - c : c, G->st,
+                                 G->cur_gate));
         } else {
             CKE(sweep<T>(G, l, kJacobi, P<T>::u(L, cur), f, P<T>::u(L, 1 - cur), nullptr, o.omega));
             cur ^= 1;
@@ -292,20 +298,29 @@ cudaError_t vcycle(sbm_grid G, int l, int &cur, const sbm_opts &o, const T *f)
     if (l == 0) {
         if (G->nl == 1) {
             CKE(sweep<T>(G, 0, kResidual, P<T>::u(L, cur), f, P<T>::r(L), nullptr, 0.0));
-            CKE(launch_bottom_apply<T>(G->nb, P<T>::A(G), G->gather, P<T>::r(L), P<T>::u(L, cur), 1, G->st));
+            CKE(launch_bottom_apply<T>(G->nb, P<T>::A(G), G->gather, P<T>::r(L), P<T>::u(L, cur), 1, G->st,
+                                       G->cur_gate));
         } else {
-            CKE(launch_bottom_apply<T>(G->nb, P<T>::A(G), G->gather, f, P<T>::u(L, cur), 0, G->st));
+            CKE(launch_bottom_apply<T>(G->nb, P<T>::A(G), G->gather, f, P<T>::u(L, cur), 0, G->st, G->cur_gate));
         }
         return cudaSuccess;
     }
     Level &C = G->L[l - 1];
     CKE(smooth<T>(G, l, cur, o, o.nu1, false, f));
-    CKE(sweep<T>(G, l, kResidual, P<T>::u(L, cur), f, P<T>::r(L), nullptr, 0.0));
-    CKE(launch_restrict<T>(L.g, C.g, P<T>::r(L), P<T>::f(C), G->st));
+    if (G->cur_gate && l == G->nl - 1 && std::is_same<T, float>::value) {
+        // adaptive inner cycles: the norm of this residual decides whether the
+        // FP32 V-cycles of the outer iteration go on
+        CKE(sweep<T>(G, l, kResidual, P<T>::u(L, cur), f, P<T>::r(L), G->part, 0.0));
+        CKE(launch_inner_gate(G->part, (int)sweep_nblocks(G, l, true, P<T>::u(L, cur), f), G->scal, G->gate_rtol,
+                              G->gate_tol, G->dgate, G->dgate + 1, G->st));
+    } else {
+        CKE(sweep<T>(G, l, kResidual, P<T>::u(L, cur), f, P<T>::r(L), nullptr, 0.0));
+    }
+    CKE(launch_restrict<T>(L.g, C.g, P<T>::r(L), P<T>::f(C), G->st, G->cur_gate));
     int cc = 0;
     if (l - 1 > 0) CKE(cudaMemsetAsync(P<T>::u(C, 0), 0, level_bytes(C, sizeof(T)), G->st));
     CKE(vcycle<T>(G, l - 1, cc, o, P<T>::f(C)));
-    CKE(launch_prolong_add<T>(L.g, C.g, P<T>::u(C, cc), P<T>::u(L, cur), G->st));
+    CKE(launch_prolong_add<T>(L.g, C.g, P<T>::u(C, cc), P<T>::u(L, cur), G->st, G->cur_gate));
     CKE(smooth<T>(G, l, cur, o, o.nu2, true, f));
     return cudaSuccess;
 }
@@ -343,7 +358,16 @@ cudaError_t enqueue_body(sbm_grid G, const sbm_opts &o, const double *rhs)
     if (G->desc.precision == SBM_MIXED) {
         CKE(cudaMemsetAsync(L.su[0], 0, level_bytes(L, sizeof(float)), G->st));
         int cur = 0;
-        for (int it = 0; it < o.inner_cycles; ++it) CKE(vcycle<float>(G, fine, cur, o, L.sf));
+        if (o.inner_rtol > 0.0) {
+            CKE(cudaMemsetAsync(G->dgate, 0, sizeof(int), G->st));
+            G->cur_gate = G->dgate;
+            G->gate_rtol = o.inner_rtol;
+            G->gate_tol = 0.1 * o.tol;      // margin: the FP32 residual underestimates the FP64 one
+        }
+        cudaError_t e = cudaSuccess;
+        for (int it = 0; it < o.inner_cycles && e == cudaSuccess; ++it) e = vcycle<float>(G, fine, cur, o, L.sf);
+        G->cur_gate = nullptr;
+        CKE(e);
         CKE(launch_add<float>((long long)L.g.dim * L.g.cs, L.su[cur], L.du[0], G->st));
         return residual64(G, rhs, 1, 2);
     }
@@ -424,7 +448,7 @@ sbm_status validate_opts(sbm_grid G, const sbm_opts &o)
 {
     if (!(o.tol >= 0.0) || o.max_cycles < 1 || o.nu1 < 0 || o.nu2 < 0 || o.nu1 + o.nu2 < 1 ||
         (o.smoother != SBM_JACOBI && o.smoother != SBM_MCGS) || !(o.omega > 0.0 && o.omega < 2.0) ||
-        o.inner_cycles < 1)
+        o.inner_cycles < 1 || !(o.inner_rtol >= 0.0 && std::isfinite(o.inner_rtol)))
         return fail(G, SBM_ERR_ARG, "invalid sbm_opts");
     return SBM_OK;
 }
@@ -462,6 +486,7 @@ sbm_status run_solve(sbm_grid G, const sbm_opts &o, const double *rhs, sbm_info 
     if (o.use_graph) {
         const bool match = gs.valid && gs.mixed == mixed && gs.smoother == o.smoother && gs.nu1 == o.nu1 &&
                            gs.nu2 == o.nu2 && gs.inner == o.inner_cycles && gs.omega == o.omega && gs.rhs == rhs &&
+                           gs.inner_rtol == o.inner_rtol &&
                            gs.version == G->version;
         if (!match) {
             if (gs.valid) cudaGraphExecDestroy(gs.exec);
@@ -488,6 +513,7 @@ sbm_status run_solve(sbm_grid G, const sbm_opts &o, const double *rhs, sbm_info 
             gs.nu2 = o.nu2;
             gs.inner = o.inner_cycles;
             gs.omega = o.omega;
+            gs.inner_rtol = o.inner_rtol;
             gs.rhs = rhs;
             gs.version = G->version;
             gs.body_launches = nbody;
@@ -500,6 +526,8 @@ sbm_status run_solve(sbm_grid G, const sbm_opts &o, const double *rhs, sbm_info 
         status = SBM_OK;
         rel = 0.0;
     }
+    const bool gated = mixed && o.inner_rtol > 0.0;
+    if (gated) CK(cudaMemsetAsync(G->dgate + 1, 0, sizeof(int), G->st));
     while (status == SBM_ERR_NOCONV && cyc < o.max_cycles) {
         if (o.use_graph) {
             CK(cudaGraphLaunch(gs.exec, G->st));
@@ -527,10 +555,12 @@ sbm_status run_solve(sbm_grid G, const sbm_opts &o, const double *rhs, sbm_info 
             return fail(G, SBM_ERR_CUDA, "a TMA pipeline wait timed out in the FP32 sweep kernel");
         }
     }
+    int vrun = cyc * (mixed ? o.inner_cycles : 1);
+    if (gated) CK(cudaMemcpy(&vrun, G->dgate + 1, sizeof(int), cudaMemcpyDeviceToHost));
     if (info) {
         info->status = status;
         info->cycles = cyc;
-        info->vcycles = cyc * (mixed ? o.inner_cycles : 1);
+        info->vcycles = vrun;
         info->relres = rel;
         info->solve_ms = ms;
         info->launches = g_launches - launches0 + replayed;
@@ -1022,6 +1052,7 @@ void sbm_default_opts(sbm_opts *o)
     o->smoother = SBM_JACOBI;
     o->inner_cycles = 1;
     o->use_graph = 1;
+    o->inner_rtol = 0.0;
 }
 
 const char *sbm_status_string(int s)
@@ -1058,7 +1089,7 @@ sbm_status sbm_grid_destroy(sbm_grid G)
         for (double *q : vec)
             if (q) cudaFree(q);
     void *ptrs[] = {G->fsrc, G->fadj, G->psi_raw, G->rho, G->part, G->scal, G->dbad, G->A64, G->A32, G->gjtmp, G->gjbar, G->gather,
-                    G->derr, G->amr_part, G->amr_u0, G->amr_r0};
+                    G->derr, G->dgate, G->amr_part, G->amr_u0, G->amr_r0};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (G->hscal) cudaFreeHost(G->hscal);
@@ -1165,6 +1196,8 @@ sbm_status sbm_grid_create(const sbm_grid_desc *d, sbm_grid *out)
                              sweep_blocks_f2(G->L[l].g)});
     CK(cudaMalloc(&G->part, sizeof(double) * G->npart));
     CK(cudaMalloc(&G->derr, sizeof(int)));
+    CK(cudaMalloc(&G->dgate, 2 * sizeof(int)));
+    CK(cudaMemset(G->dgate, 0, 2 * sizeof(int)));
     CK(cudaMemset(G->derr, 0, sizeof(int)));
     CK(cudaMalloc(&G->scal, sizeof(double) * 16));
     CK(cudaMemset(G->scal, 0, sizeof(double) * 16));

@@ -52,6 +52,7 @@ struct SweepArgs {
     Coef<T> c;
     T wk[3];               // Jacobi: omega / kdiag[p]
     int kchunk;            // node planes per block along z (3D)
+    const int *gate = nullptr;   // device flag: when set, the launch does nothing
 };
 
 // Number of z chunks for a z-streaming stencil launch: minimises
@@ -103,13 +104,15 @@ long long sweep_blocks_f2(const Geom &g);
 
 template <typename T>
 cudaError_t launch_gs(const Geom &g, const T *psi, const T *Ke, const T *f, T *u, int colour,
-                      cudaStream_t s);
+                      cudaStream_t s, const int *gate = nullptr);
 
 template <typename T>
-cudaError_t launch_restrict(const Geom &gf, const Geom &gc, const T *rf, T *fc, cudaStream_t s);
+cudaError_t launch_restrict(const Geom &gf, const Geom &gc, const T *rf, T *fc, cudaStream_t s,
+                            const int *gate = nullptr);
 
 template <typename T>
-cudaError_t launch_prolong_add(const Geom &gf, const Geom &gc, const T *ec, T *uf, cudaStream_t s);
+cudaError_t launch_prolong_add(const Geom &gf, const Geom &gc, const T *ec, T *uf, cudaStream_t s,
+                               const int *gate = nullptr);
 
 cudaError_t launch_coarsen_psi(const Geom &gf, const Geom &gc, const double *pf, double *pc,
                                cudaStream_t s);
@@ -150,7 +153,13 @@ cudaError_t launch_gauss_jordan(const Geom &g, int n, double *A, double *tmp, un
 cudaError_t launch_round(long long n, const double *src, float *dst, cudaStream_t s);
 template <typename T>
 cudaError_t launch_bottom_apply(int n, const T *Ainv, const int *gather, const T *b, T *u,
-                                int accumulate, cudaStream_t s);
+                                int accumulate, cudaStream_t s, const int *gate = nullptr);
+// Adaptive inner cycles: sum the partial sums of the FP32 residual of this V-cycle
+// and set *gate when its norm <= max(rtol * scal[7], tol_frac * scal[1]) (scal[7]:
+// the latest FP64 residual norm, scal[1]: the initial one); counts the V-cycles
+// run in *count.  Skipped itself once the gate is set.
+cudaError_t launch_inner_gate(const double *part, int nparts, const double *scal, double rtol, double tol_frac,
+                              int *gate, int *count, cudaStream_t s);
 // dJ/dpsi_c = -lambda_c^T S_c u_c (packed u, lambda; packed cell output) and the
 // optional chain rule through the SIMP map or the psi_min floor.
 cudaError_t launch_dJdpsi(const Geom &g, const Coef<double> &c, const double *u, const double *lam,

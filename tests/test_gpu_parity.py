@@ -196,6 +196,29 @@ def test_solve_parity(built, case, precision, smoother, bcvals):
     assert oracle.norm_free(P, r) / oracle.norm_free(P, r0) <= 2e-10
 
 
+@pytest.mark.parametrize("case", ["plate65", "damage33", "ragged3d"])
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_adaptive_inner_cycles(built, case, use_graph):
+    """Mixed precision with the device-side stop of the FP32 V-cycles: the same
+    fixed point (the oracle's solution) and about as many V-cycles as with the
+    fixed count, with and without graph replay."""
+    wk = CASES[case]()
+    if case.startswith("ragged"):
+        wk.omega = 0.5
+    uref, _ = _oracle_solution(wk, "jacobi")
+    g = gpu_grid(wk, precision="mixed")
+    u = cuda(wk.u0)
+    fixed = g.solve(u, tol=1e-10, omega=wk.omega, inner_cycles=12, use_graph=use_graph)
+    u = cuda(wk.u0)
+    info = g.solve(u, tol=1e-10, omega=wk.omega, inner_cycles=12, inner_rtol=1e-6, use_graph=use_graph)
+    err = np.linalg.norm(host(u) - uref) / np.linalg.norm(uref)
+    assert info.converged and info.relres <= 1e-10
+    assert err <= 1e-8, (err, info.cycles)
+    # the stop is decided one V-cycle late at most per outer iteration
+    assert info.vcycles <= fixed.vcycles + info.cycles, (info.vcycles, fixed.vcycles)
+    assert info.vcycles < 12 * info.cycles or info.cycles <= fixed.cycles
+
+
 def test_solve_graph_and_eager_agree_bitwise(built):
     wk = W.damage3d(17)
     g = gpu_grid(wk, precision="mixed")
