@@ -3,6 +3,7 @@
 // the coarsest-level dense solve (assembly, Gauss-Jordan inverse, matvec), the
 // FP64 defect update and the dJ/dpsi gradient kernel.
 #include "sbm_common.cuh"
+#include "sbm_bodies.cuh"
 
 namespace sbm {
 
@@ -32,35 +33,6 @@ inline dim3 node_grid(const Geom &g)
     return dim3((g.nx + 31) / 32, (g.ny + 3) / 4, (g.nz + 1) / 2);
 }
 
-template <typename T> struct Vec2;
-template <> struct Vec2<float> { using type = float2; };
-template <> struct Vec2<double> { using type = double2; };
-
-// Fine values x = 2I-1, 2I, 2I+1 of one row, with weights 1/2, 1, 1/2 (missing
-// neighbours beyond the row weigh 0).  2I is even and rows start on 8-element
-// boundaries, so (2I, 2I+1) is one aligned vector load when 2I+1 is in the row.
-template <typename T>
-__device__ __forceinline__ T fw_row(const T *__restrict__ row, int I, int nx)
-{
-    using V = typename Vec2<T>::type;
-    const int i = 2 * I;
-    const T lo = (i > 0) ? row[i - 1] : T(0);
-    T c, hi;
-    if (i + 1 < nx) {
-        const V v = *reinterpret_cast<const V *>(row + i);
-        c = v.x;
-        hi = v.y;
-    } else {
-        c = row[i];
-        hi = T(0);
-    }
-    return c + T(0.5) * (lo + hi);
-}
-
-// r_c = P^T r_f / 2^d on free coarse dofs (Sec. 2.2 level transfers); coarse
-// node (I,J,K) sits on fine node (2I,2J,2K), the linear weights are 1, 1/2.
-// The 3^d fine rows are read with independent loads (clamped index, zero weight
-// outside the grid) so they are all in flight together.
 template <typename T, int D>
 __global__ void k_restrict(const Geom gf, const Geom gc, const T *__restrict__ rf, T *__restrict__ fc, const int *gate)
 {
@@ -69,106 +41,19 @@ __global__ void k_restrict(const Geom gf, const Geom gc, const T *__restrict__ r
     const int J = blockIdx.y * blockDim.y + threadIdx.y;
     const int K = blockIdx.z * blockDim.z + threadIdx.z;
     if (I >= gc.nx || J >= gc.ny || K >= gc.nz) return;
-    constexpr bool d3 = D == 3;
-    const T scale = d3 ? T(0.125) : T(0.25);
-    const long long oc = gidx(gc, I, J, K);
-    constexpr int nz_rows = d3 ? 3 : 1;
-#pragma unroll
-    for (int p = 0; p < D; ++p) {
-        T s = T(0);
-        if (!is_dir(gc, p, I, J, K)) {
-            const T *base = rf + p * gf.cs;
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                if (a >= nz_rows) break;
-                const int k = d3 ? 2 * K + a - 1 : 0;
-                const bool kin = k >= 0 && k < gf.nz;
-                const T wk = !d3 ? T(1) : (kin ? (a == 1 ? T(1) : T(0.5)) : T(0));
-                const int kc = kin ? k : 2 * K;
-#pragma unroll
-                for (int b = 0; b < 3; ++b) {
-                    const int j = 2 * J + b - 1;
-                    const bool jin = j >= 0 && j < gf.ny;
-                    const T w = wk * (jin ? (b == 1 ? T(1) : T(0.5)) : T(0));
-                    const int jc = jin ? j : 2 * J;
-                    s += w * fw_row<T>(base + gidx(gf, 0, jc, kc), I, gf.nx);
-                }
-            }
-            s *= scale;
-        }
-        fc[p * gc.cs + oc] = s;
-    }
+    body::restrict_node<T, D>(gf, gc, rf, fc, I, J, K);
 }
 
-// u_f += P e_c on free fine dofs.  One thread per coarse node (I,J,K) writes the
-// fine nodes (2I+a, 2J+b, 2K+c), a, b, c in {0, 1}, that exist: the coincident
-// node copies e_c, the others average the 2, 4 or 8 coarse neighbours.  The x
-// pair (2I, 2I+1) is read and written as one aligned vector.
 template <typename T, int D>
 __global__ void k_prolong_add(const Geom gf, const Geom gc, const T *__restrict__ ec, T *__restrict__ uf,
                               const int *gate)
 {
     if (gate && *gate) return;
-    using V = typename Vec2<T>::type;
     const int I = blockIdx.x * blockDim.x + threadIdx.x;
     const int J = blockIdx.y * blockDim.y + threadIdx.y;
     const int K = blockIdx.z * blockDim.z + threadIdx.z;
     if (I >= gc.nx || J >= gc.ny || K >= gc.nz) return;
-    constexpr bool d3 = D == 3;
-    const bool hx = I + 1 < gc.nx, hy = J + 1 < gc.ny, hz = d3 && K + 1 < gc.nz;
-    const int I1 = hx ? I + 1 : I, J1 = hy ? J + 1 : J, K1 = hz ? K + 1 : K;
-    const int i0 = 2 * I, j0 = 2 * J, k0 = d3 ? 2 * K : 0;
-#pragma unroll
-    for (int p = 0; p < D; ++p) {
-        const T *e = ec + p * gc.cs;
-        // coarse values of the cell above (I,J,K): [z][y][x]
-        T c[2][2][2];
-        c[0][0][0] = e[gidx(gc, I, J, K)];
-        c[0][0][1] = e[gidx(gc, I1, J, K)];
-        c[0][1][0] = e[gidx(gc, I, J1, K)];
-        c[0][1][1] = e[gidx(gc, I1, J1, K)];
-        c[1][0][0] = e[gidx(gc, I, J, K1)];
-        c[1][0][1] = e[gidx(gc, I1, J, K1)];
-        c[1][1][0] = e[gidx(gc, I, J1, K1)];
-        c[1][1][1] = e[gidx(gc, I1, J1, K1)];
-        T *u = uf + p * gf.cs;
-#pragma unroll
-        for (int zc = 0; zc < 2; ++zc) {
-            if (zc == 1 && !hz) break;
-#pragma unroll
-            for (int yc = 0; yc < 2; ++yc) {
-                if (yc == 1 && !hy) break;
-                // values at x = 2I (even) and 2I+1 (odd) on this fine row
-                T ev, od;
-                if (zc == 0 && yc == 0) {
-                    ev = c[0][0][0];
-                    od = T(0.5) * (c[0][0][0] + c[0][0][1]);
-                } else if (zc == 0) {
-                    ev = T(0.5) * (c[0][0][0] + c[0][1][0]);
-                    od = T(0.25) * ((c[0][0][0] + c[0][0][1]) + (c[0][1][0] + c[0][1][1]));
-                } else if (yc == 0) {
-                    ev = T(0.5) * (c[0][0][0] + c[1][0][0]);
-                    od = T(0.25) * ((c[0][0][0] + c[0][0][1]) + (c[1][0][0] + c[1][0][1]));
-                } else {
-                    ev = T(0.25) * ((c[0][0][0] + c[0][1][0]) + (c[1][0][0] + c[1][1][0]));
-                    od = T(0.125) * (((c[0][0][0] + c[0][0][1]) + (c[0][1][0] + c[0][1][1])) +
-                                     ((c[1][0][0] + c[1][0][1]) + (c[1][1][0] + c[1][1][1])));
-                }
-                const int j = j0 + yc, k = k0 + zc;
-                T *row = u + gidx(gf, 0, j, k);
-                const T me = is_dir(gf, p, i0, j, k) ? T(0) : T(1);
-                if (hx) {
-                    const T mo = is_dir(gf, p, i0 + 1, j, k) ? T(0) : T(1);
-                    V v = *reinterpret_cast<V *>(row + i0);
-                    v.x += me * ev;
-                    v.y += mo * od;
-                    *reinterpret_cast<V *>(row + i0) = v;
-                } else {
-                    row[i0] += me * ev;
-                }
-            }
-        }
-    }
+    body::prolong_node<T, D>(gf, gc, ec, uf, I, J, K);
 }
 
 // Coarse psi = mean of the 2^d fine cells (Sec. 2.4 material averaging).
@@ -435,31 +320,28 @@ __global__ void k_bottom_dirichlet(const Geom g, double *A)
 // One cooperative launch runs every pivot: the grid updates the matrix row by
 // row (block per row, threads over columns), and while doing so copies the next
 // pivot's row and column into the other half of a double buffer, so one grid
-// barrier per pivot suffices.  The barrier is a counter + generation in global
-// memory; every wait is bounded (on timeout bar[2] is set and the kernel ends).
+// barrier per pivot suffices.  Every wait is bounded (on timeout bar[2] is set
+// and the kernel ends).
 constexpr long long kGridSpinLimit = 1LL << 22;
 
-__device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned nblocks)
+// Grid barrier number `phase` (1, 2, ...): every block adds 1 to a counter that is
+// never reset during the launch and waits until it reaches nblocks * phase.  One
+// atomic per block and plain polling; the wait is bounded (bar[2] set on timeout).
+__device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned nblocks, unsigned phase)
 {
     __syncthreads();
     int ok = 1;
     if (threadIdx.x == 0) {
-        volatile unsigned *gen = bar + 1;
-        const unsigned g0 = *gen;
         __threadfence();
-        if (atomicAdd(bar, 1u) == nblocks - 1) {
-            atomicExch(bar, 0u);
-            __threadfence();
-            atomicAdd(bar + 1, 1u);
-        } else {
-            long long it = 0;
-            while (*gen == g0) {
-                if (++it > kGridSpinLimit || *(volatile unsigned *)(bar + 2)) {
-                    atomicExch(bar + 2, 1u);
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(32);
+        atomicAdd(bar, 1u);
+        const unsigned target = nblocks * phase;
+        volatile unsigned *cnt = bar;
+        long long it = 0;
+        while (*cnt < target) {
+            if (++it > kGridSpinLimit || *(volatile unsigned *)(bar + 2)) {
+                atomicExch(bar + 2, 1u);
+                ok = 0;
+                break;
             }
         }
         __threadfence();
@@ -493,7 +375,8 @@ __global__ void k_gauss_jordan(const Geom g, int n, double *A, double *tmp, unsi
         tmp[t] = A[(long long)k * n + t];
         tmp[n + t] = A[(long long)t * n + k];
     }
-    if (!grid_barrier(bar, nb)) return;
+    unsigned phase = 1;
+    if (!grid_barrier(bar, nb, phase++)) return;
     int cur = 0;
     while (k < n) {
         const int kn = next_pivot(g, N, k + 1, n);
@@ -514,7 +397,7 @@ __global__ void k_gauss_jordan(const Geom g, int n, double *A, double *tmp, unsi
                 if (j == kn) Cn[i] = v;
             }
         }
-        if (!grid_barrier(bar, nb)) return;
+        if (!grid_barrier(bar, nb, phase++)) return;
         cur ^= 1;
         k = kn;
     }
@@ -530,15 +413,8 @@ __global__ void k_bottom_apply(int n, const T *__restrict__ Ainv, const int *__r
 {
     if (gate && *gate) return;
     const int row = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
     if (row >= n) return;
-    T s = T(0);
-    for (int c = lane; c < n; c += 32) s += Ainv[(long long)row * n + c] * b[gather[c]];
-    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
-    if (lane == 0) {
-        if (accumulate) u[gather[row]] += s;
-        else u[gather[row]] = s;
-    }
+    body::bottom_row<T>(n, Ainv, gather, b, u, accumulate, row, threadIdx.x & 31);
 }
 
 // ----------------------------------------------------------------- gradient

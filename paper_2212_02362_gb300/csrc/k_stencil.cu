@@ -14,6 +14,7 @@
 //   and one extra layer per z chunk.
 // 2D kernel: the same with a single layer.
 #include "sbm_common.cuh"
+#include "sbm_bodies.cuh"
 
 namespace sbm {
 
@@ -21,30 +22,6 @@ namespace {
 
 constexpr int TX3 = 32, TY3 = 8;     // 3D tile (cells)
 constexpr int TX2 = 32, TY2 = 8;     // 2D tile (cells)
-
-template <typename T, typename TO, int MODE>
-__device__ __forceinline__ void finalize(const SweepArgs<T, TO> &a, int gx, int gy, int gz, const T *Ku,
-                                         T psisum, const T *uval, double &ssq)
-{
-    const Geom &g = a.g;
-    const long long o = gidx(g, gx, gy, gz);
-    if (MODE == kJacobi) {
-        const T ip = T(1) / psisum;
-        for (int p = 0; p < g.dim; ++p) {
-            T v = uval[p];
-            if (!is_dir(g, p, gx, gy, gz)) v += (a.f[p * g.cs + o] - Ku[p]) * ip * a.wk[p];
-            a.out[p * g.cs + o] = TO(v);
-        }
-    } else if (MODE == kResidual) {
-        for (int p = 0; p < g.dim; ++p) {
-            T r = is_dir(g, p, gx, gy, gz) ? T(0) : a.f[p * g.cs + o] - Ku[p];
-            a.out[p * g.cs + o] = TO(r);
-            ssq += double(r) * double(r);
-        }
-    } else {
-        for (int p = 0; p < g.dim; ++p) a.out[p * g.cs + o] = TO(Ku[p]);
-    }
-}
 
 // Deterministic block reduction of ssq into part[block]: every thread stores its
 // value, warp 0 folds the padded array in a fixed order and reduces by shuffles.
@@ -163,7 +140,7 @@ __global__ void __launch_bounds__((TX3 + 1) * (TY3 + 1)) k_sweep3(const SweepArg
                     Ku[p] = carry[p] + sb[p];
                     uv[p] = pl[p * PP + me + PX + 1];
                 }
-                finalize<T, TO, MODE>(a, gx, gy, lz, Ku, carry_ps + pss, uv, ssq);
+                body::finalize<T, TO, MODE>(a, gx, gy, lz, Ku, carry_ps + pss, uv, ssq);
             }
 #pragma unroll
             for (int p = 0; p < 3; ++p) carry[p] = st[p];
@@ -176,7 +153,7 @@ __global__ void __launch_bounds__((TX3 + 1) * (TY3 + 1)) k_sweep3(const SweepArg
         const T *pl = up + (kz1 & 1) * 3 * PP;
 #pragma unroll
         for (int p = 0; p < 3; ++p) uv[p] = pl[p * PP + (ty + 1) * PX + tx + 1];
-        finalize<T, TO, MODE>(a, gx, gy, kz1, carry, carry_ps, uv, ssq);
+        body::finalize<T, TO, MODE>(a, gx, gy, kz1, carry, carry_ps, uv, ssq);
     }
     if (MODE == kResidual && a.part) block_partial<NT>(ssq, a.part, red);
 }
@@ -286,7 +263,7 @@ __global__ void __launch_bounds__((TXD + 1) * (TYD + 1)) k_sweep3_dp(const Sweep
                 uv[p] = pl[p * PP + me + PX + 1];
             }
             const double pss = (ps[me] + ps[me + 1]) + (ps[me + PX] + ps[me + PX + 1]);
-            finalize<double, TO, MODE>(a, gx, gy, lz, Ku, pss, uv, ssq);
+            body::finalize<double, TO, MODE>(a, gx, gy, lz, Ku, pss, uv, ssq);
         }
         __syncthreads();
     }
@@ -352,7 +329,7 @@ __global__ void __launch_bounds__((TX2 + 1) * (TY2 + 1)) k_sweep2(const SweepArg
             uv[p] = up[p * PP + me + PX + 1];
         }
         const T pss = ps[me] + ps[me + 1] + ps[me + PX] + ps[me + PX + 1];
-        finalize<T, TO, MODE>(a, gx, gy, 0, Ku, pss, uv, ssq);
+        body::finalize<T, TO, MODE>(a, gx, gy, 0, Ku, pss, uv, ssq);
     }
     if (MODE == kResidual && a.part) block_partial<NT>(ssq, a.part, red);
 }
@@ -474,38 +451,7 @@ __global__ void __launch_bounds__(128) k_sweep3_node(const SweepArgs<float, floa
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const int k = blockIdx.z * blockDim.z + threadIdx.z;
     if (i >= g.nx || j >= g.ny || k >= g.nz) return;
-    float nb[3][27];
-#pragma unroll
-    for (int q = 0; q < 27; ++q) {
-        const int x = i + q % 3 - 1, y = j + (q / 3) % 3 - 1, z = k + q / 9 - 1;
-        const bool in = x >= 0 && x < g.nx && y >= 0 && y < g.ny && z >= 0 && z < g.nz;
-        const long long o = in ? gidx(g, x, y, z) : 0;
-#pragma unroll
-        for (int p = 0; p < 3; ++p) nb[p][q] = in ? a.u[p * g.cs + o] : 0.f;
-    }
-    float Ku[3] = {0.f, 0.f, 0.f}, psisum = 0.f;
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        // cell with lower corner (i - cx, j - cy, k - cz); this node is its corner (cx, cy, cz)
-        const int cx = c & 1, cy = (c >> 1) & 1, cz = (c >> 2) & 1;
-        const int ci = i - cx, cj = j - cy, ck = k - cz;
-        if (ci < 0 || cj < 0 || ck < 0 || ci >= g.nx - 1 || cj >= g.ny - 1 || ck >= g.nz - 1) continue;
-        const float ps = a.psi[gidx(g, ci, cj, ck)];
-        psisum += ps;
-        float U[3][8];
-#pragma unroll
-        for (int b = 0; b < 8; ++b) {
-            const int q = ((b & 1) - cx + 1) + 3 * (((b >> 1) & 1) - cy + 1) + 9 * (((b >> 2) & 1) - cz + 1);
-#pragma unroll
-            for (int p = 0; p < 3; ++p) U[p][b] = nb[p][q];
-        }
-        cell_forces3<float>(U, ps, a.c);
-#pragma unroll
-        for (int p = 0; p < 3; ++p) Ku[p] += U[p][c];
-    }
-    double ssq = 0.0;
-    const float uv[3] = {nb[0][13], nb[1][13], nb[2][13]};
-    finalize<float, float, MODE>(a, i, j, k, Ku, psisum, uv, ssq);
+    body::node_sweep<MODE>(a, i, j, k);
 }
 
 cudaError_t launch_sweep_node(int mode, const SweepArgs<float, float> &a, cudaStream_t s)
