@@ -33,21 +33,30 @@ inline dim3 node_grid(const Geom &g)
     return dim3((g.nx + 31) / 32, (g.ny + 3) / 4, (g.nz + 1) / 2);
 }
 
+// zero_uc (may be null): the coarse correction, zeroed at each coarse node (the
+// start of the coarse level's cycle).
 template <typename T, int D>
-__global__ void k_restrict(const Geom gf, const Geom gc, const T *__restrict__ rf, T *__restrict__ fc, const int *gate)
+__global__ void k_restrict(const Geom gf, const Geom gc, const T *__restrict__ rf, T *__restrict__ fc, const int *gate,
+                           T *__restrict__ zero_uc)
 {
+    pdl_begin();
     if (gate && *gate) return;
     const int I = blockIdx.x * blockDim.x + threadIdx.x;
     const int J = blockIdx.y * blockDim.y + threadIdx.y;
     const int K = blockIdx.z * blockDim.z + threadIdx.z;
     if (I >= gc.nx || J >= gc.ny || K >= gc.nz) return;
     body::restrict_node<T, D>(gf, gc, rf, fc, I, J, K);
+    if (zero_uc) {
+        const long long o = gidx(gc, I, J, K);
+        for (int p = 0; p < D; ++p) zero_uc[p * gc.cs + o] = T(0);
+    }
 }
 
 template <typename T, int D>
 __global__ void k_prolong_add(const Geom gf, const Geom gc, const T *__restrict__ ec, T *__restrict__ uf,
                               const int *gate)
 {
+    pdl_begin();
     if (gate && *gate) return;
     const int I = blockIdx.x * blockDim.x + threadIdx.x;
     const int J = blockIdx.y * blockDim.y + threadIdx.y;
@@ -177,6 +186,7 @@ __global__ void k_set_face(const Geom g, int face, int comp, double value, doubl
 template <typename TE>
 __global__ void k_add(long long n, const TE *__restrict__ e, double *__restrict__ u)
 {
+    pdl_begin();
     const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (t < n) u[t] += double(e[t]);
 }
@@ -220,6 +230,7 @@ __global__ void k_round(long long n, const double *__restrict__ src, float *__re
 // sqrt(scal[2]) / scal[1] (scal[1] holds ||r0||).
 __global__ void k_norm_final(const double *__restrict__ part, int n, double *scal, int which)
 {
+    pdl_begin();
     __shared__ double red[kThreads];
     double s = 0.0;
     for (int i = threadIdx.x; i < n; i += kThreads) s += part[i];
@@ -241,6 +252,7 @@ __global__ void k_norm_final(const double *__restrict__ part, int n, double *sca
 __global__ void k_inner_gate(const double *__restrict__ part, int n, const double *scal, double rtol,
                              double tol_frac, int *gate, int *count)
 {
+    pdl_begin();
     if (*gate) return;
     __shared__ double red[kThreads];
     double s = 0.0;
@@ -411,6 +423,7 @@ template <typename T>
 __global__ void k_bottom_apply(int n, const T *__restrict__ Ainv, const int *__restrict__ gather,
                                const T *__restrict__ b, T *__restrict__ u, int accumulate, const int *gate)
 {
+    pdl_begin();
     if (gate && *gate) return;
     const int row = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
     if (row >= n) return;
@@ -470,22 +483,26 @@ __global__ void k_dJdpsi(const Geom g, const Coef<double> c, const double *__res
 // ------------------------------------------------------------------ launchers
 
 template <typename T>
-cudaError_t launch_restrict(const Geom &gf, const Geom &gc, const T *rf, T *fc, cudaStream_t s, const int *gate)
+cudaError_t launch_restrict(const Geom &gf, const Geom &gc, const T *rf, T *fc, cudaStream_t s, const int *gate,
+                            T *zero_uc)
 {
-    if (gf.dim == 3) k_restrict<T, 3><<<node_grid(gc), kNodeBlock, 0, s>>>(gf, gc, rf, fc, gate);
-    else k_restrict<T, 2><<<node_grid(gc), kNodeBlock, 0, s>>>(gf, gc, rf, fc, gate);
+    cudaError_t e = gf.dim == 3 ? launch_pdl(k_restrict<T, 3>, node_grid(gc), kNodeBlock, 0, s, gf, gc, rf, fc, gate, zero_uc)
+                                : launch_pdl(k_restrict<T, 2>, node_grid(gc), kNodeBlock, 0, s, gf, gc, rf, fc, gate, zero_uc);
+    if (e != cudaSuccess) return e;
     ++g_launches;
     return cudaGetLastError();
 }
 template cudaError_t launch_restrict<double>(const Geom &, const Geom &, const double *, double *, cudaStream_t,
-                                             const int *);
-template cudaError_t launch_restrict<float>(const Geom &, const Geom &, const float *, float *, cudaStream_t, const int *);
+                                             const int *, double *);
+template cudaError_t launch_restrict<float>(const Geom &, const Geom &, const float *, float *, cudaStream_t, const int *,
+                                            float *);
 
 template <typename T>
 cudaError_t launch_prolong_add(const Geom &gf, const Geom &gc, const T *ec, T *uf, cudaStream_t s, const int *gate)
 {
-    if (gf.dim == 3) k_prolong_add<T, 3><<<node_grid(gc), kNodeBlock, 0, s>>>(gf, gc, ec, uf, gate);
-    else k_prolong_add<T, 2><<<node_grid(gc), kNodeBlock, 0, s>>>(gf, gc, ec, uf, gate);
+    cudaError_t e = gf.dim == 3 ? launch_pdl(k_prolong_add<T, 3>, node_grid(gc), kNodeBlock, 0, s, gf, gc, ec, uf, gate)
+                                : launch_pdl(k_prolong_add<T, 2>, node_grid(gc), kNodeBlock, 0, s, gf, gc, ec, uf, gate);
+    if (e != cudaSuccess) return e;
     ++g_launches;
     return cudaGetLastError();
 }
@@ -562,7 +579,8 @@ cudaError_t launch_set_face(const Geom &g, int face, int comp, double value, dou
 template <typename TE>
 cudaError_t launch_add(long long n, const TE *e, double *u, cudaStream_t s)
 {
-    k_add<TE><<<nblk(n), kThreads, 0, s>>>(n, e, u);
+    cudaError_t err = launch_pdl(k_add<TE>, dim3(nblk(n)), dim3(kThreads), 0, s, n, e, u);
+    if (err != cudaSuccess) return err;
     ++g_launches;
     return cudaGetLastError();
 }
@@ -571,7 +589,8 @@ template cudaError_t launch_add<double>(long long, const double *, double *, cud
 
 cudaError_t launch_norm_final(const double *part, int nparts, double *scal, int which, cudaStream_t s)
 {
-    k_norm_final<<<1, kThreads, 0, s>>>(part, nparts, scal, which);
+    cudaError_t e = launch_pdl(k_norm_final, dim3(1), dim3(kThreads), 0, s, part, nparts, scal, which);
+    if (e != cudaSuccess) return e;
     ++g_launches;
     return cudaGetLastError();
 }
@@ -579,7 +598,8 @@ cudaError_t launch_norm_final(const double *part, int nparts, double *scal, int 
 cudaError_t launch_inner_gate(const double *part, int nparts, const double *scal, double rtol, double tol_frac,
                               int *gate, int *count, cudaStream_t s)
 {
-    k_inner_gate<<<1, kThreads, 0, s>>>(part, nparts, scal, rtol, tol_frac, gate, count);
+    cudaError_t e = launch_pdl(k_inner_gate, dim3(1), dim3(kThreads), 0, s, part, nparts, scal, rtol, tol_frac, gate, count);
+    if (e != cudaSuccess) return e;
     ++g_launches;
     return cudaGetLastError();
 }
@@ -656,8 +676,9 @@ cudaError_t launch_bottom_apply(int n, const T *Ainv, const int *gather, const T
                                 cudaStream_t s, const int *gate)
 {
     const int rows_per_block = 8;
-    k_bottom_apply<T><<<(n + rows_per_block - 1) / rows_per_block, 32 * rows_per_block, 0, s>>>(n, Ainv, gather, b, u,
-                                                                                                accumulate, gate);
+    cudaError_t e = launch_pdl(k_bottom_apply<T>, dim3((n + rows_per_block - 1) / rows_per_block),
+                               dim3(32 * rows_per_block), 0, s, n, Ainv, gather, b, u, accumulate, gate);
+    if (e != cudaSuccess) return e;
     ++g_launches;
     return cudaGetLastError();
 }

@@ -45,6 +45,7 @@ __device__ __forceinline__ void block_partial(double ssq, double *part, double *
 template <typename T, typename TO, int MODE>
 __global__ void __launch_bounds__((TX3 + 1) * (TY3 + 1)) k_sweep3(const SweepArgs<T, TO> a)
 {
+    pdl_begin();
     if (a.gate && *a.gate) return;
     constexpr int BX = TX3 + 1, BY = TY3 + 1, NT = BX * BY;
     constexpr int PX = TX3 + 2, PY = TY3 + 2, PP = PX * PY;
@@ -170,6 +171,7 @@ constexpr int TXD = 32, TYD = 12;
 template <typename TO, int MODE>
 __global__ void __launch_bounds__((TXD + 1) * (TYD + 1)) k_sweep3_dp(const SweepArgs<double, TO> a)
 {
+    pdl_begin();
     if (a.gate && *a.gate) return;
     constexpr int BX = TXD + 1, BY = TYD + 1, NT = BX * BY;
     constexpr int PX = TXD + 2, PY = TYD + 2, PP = PX * PY;
@@ -275,6 +277,7 @@ constexpr size_t smem_dp() { return sizeof(double) * (2 * 3 + 12 + 1) * (TXD + 2
 template <typename T, typename TO, int MODE>
 __global__ void __launch_bounds__((TX2 + 1) * (TY2 + 1)) k_sweep2(const SweepArgs<T, TO> a)
 {
+    pdl_begin();
     if (a.gate && *a.gate) return;
     constexpr int BX = TX2 + 1, BY = TY2 + 1, NT = BX * BY;
     constexpr int PX = TX2 + 2, PY = TY2 + 2, PP = PX * PY;
@@ -350,6 +353,7 @@ template <typename T, int D>
 __global__ void k_gs(const Geom g, const T *__restrict__ psi, const T *__restrict__ Ke,
                      const T *__restrict__ f, T *__restrict__ u, int colour, const int *gate)
 {
+    pdl_begin();
     if (gate && *gate) return;
     constexpr int NC = 1 << D, ND = NC * D;
     const int cxb = colour & 1, cyb = (colour >> 1) & 1, czb = (colour >> 2) & 1;
@@ -445,6 +449,7 @@ long long sweep_blocks(const Geom &g, bool fp64)
 template <int MODE>
 __global__ void __launch_bounds__(128) k_sweep3_node(const SweepArgs<float, float> a)
 {
+    pdl_begin();
     if (a.gate && *a.gate) return;
     const Geom &g = a.g;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -457,12 +462,14 @@ __global__ void __launch_bounds__(128) k_sweep3_node(const SweepArgs<float, floa
 cudaError_t launch_sweep_node(int mode, const SweepArgs<float, float> &a, cudaStream_t s)
 {
     const dim3 b(32, 4, 1), gr((a.g.nx + 31) / 32, (a.g.ny + 3) / 4, a.g.nz);
+    cudaError_t e;
     switch (mode) {
-    case kApply: k_sweep3_node<kApply><<<gr, b, 0, s>>>(a); break;
-    case kResidual: k_sweep3_node<kResidual><<<gr, b, 0, s>>>(a); break;
-    case kJacobi: k_sweep3_node<kJacobi><<<gr, b, 0, s>>>(a); break;
+    case kApply: e = launch_pdl(k_sweep3_node<kApply>, gr, b, 0, s, a); break;
+    case kResidual: e = launch_pdl(k_sweep3_node<kResidual>, gr, b, 0, s, a); break;
+    case kJacobi: e = launch_pdl(k_sweep3_node<kJacobi>, gr, b, 0, s, a); break;
     default: return cudaErrorInvalidValue;
     }
+    if (e != cudaSuccess) return e;
     ++g_launches;
     return cudaGetLastError();
 }
@@ -481,8 +488,9 @@ static cudaError_t launch_mode(const SweepArgs<T, TO> &a0, cudaStream_t s)
             if (e != cudaSuccess) return e;
             attr_dp = true;
         }
-        k_sweep3_dp<TO, MODE><<<dim3(grid[0], grid[1], grid[2]), dim3(TXD + 1, TYD + 1), sm, s>>>(
-            reinterpret_cast<const SweepArgs<double, TO> &>(a));
+        cudaError_t e = launch_pdl(k_sweep3_dp<TO, MODE>, dim3(grid[0], grid[1], grid[2]), dim3(TXD + 1, TYD + 1), sm, s,
+                                   reinterpret_cast<const SweepArgs<double, TO> &>(a));
+        if (e != cudaSuccess) return e;
         ++g_launches;
         return cudaGetLastError();
     }
@@ -495,9 +503,11 @@ static cudaError_t launch_mode(const SweepArgs<T, TO> &a0, cudaStream_t s)
             if (e != cudaSuccess) return e;
             attr_done = true;
         }
-        k_sweep3<T, TO, MODE><<<dim3(grid[0], grid[1], grid[2]), dim3(TX3 + 1, TY3 + 1), sm, s>>>(a);
+        cudaError_t e = launch_pdl(k_sweep3<T, TO, MODE>, dim3(grid[0], grid[1], grid[2]), dim3(TX3 + 1, TY3 + 1), sm, s, a);
+        if (e != cudaSuccess) return e;
     } else {
-        k_sweep2<T, TO, MODE><<<dim3(grid[0], grid[1], 1), dim3(TX2 + 1, TY2 + 1), 0, s>>>(a);
+        cudaError_t e = launch_pdl(k_sweep2<T, TO, MODE>, dim3(grid[0], grid[1], 1), dim3(TX2 + 1, TY2 + 1), 0, s, a);
+        if (e != cudaSuccess) return e;
     }
     ++g_launches;
     return cudaGetLastError();
@@ -525,11 +535,13 @@ cudaError_t launch_gs(const Geom &g, const T *psi, const T *Ke, const T *f, T *u
     if (g.dim == 3) {
         dim3 b(32, 4, 2);
         dim3 gr(((g.nx + 1) / 2 + b.x - 1) / b.x, ((g.ny + 1) / 2 + b.y - 1) / b.y, ((g.nz + 1) / 2 + b.z - 1) / b.z);
-        k_gs<T, 3><<<gr, b, 0, s>>>(g, psi, Ke, f, u, colour, gate);
+        cudaError_t e = launch_pdl(k_gs<T, 3>, gr, b, 0, s, g, psi, Ke, f, u, colour, gate);
+        if (e != cudaSuccess) return e;
     } else {
         dim3 b(32, 8, 1);
         dim3 gr(((g.nx + 1) / 2 + b.x - 1) / b.x, ((g.ny + 1) / 2 + b.y - 1) / b.y, 1);
-        k_gs<T, 2><<<gr, b, 0, s>>>(g, psi, Ke, f, u, colour, gate);
+        cudaError_t e = launch_pdl(k_gs<T, 2>, gr, b, 0, s, g, psi, Ke, f, u, colour, gate);
+        if (e != cudaSuccess) return e;
     }
     ++g_launches;
     return cudaGetLastError();

@@ -177,6 +177,7 @@ __global__ void __launch_bounds__(NTP) k_sweep3_f2(const __grid_constant__ CUten
                                                     const __grid_constant__ CUtensorMap tmap_psi,
                                                     const SweepArgs<float, float> a, int *err)
 {
+    pdl_begin();
     if (a.gate && *a.gate) return;
     extern __shared__ unsigned char smem_raw[];
     unsigned char *base = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
@@ -381,7 +382,9 @@ static cudaError_t launch_f2_mode(const SweepArgs<float, float> &a0, const CUten
         if (e != cudaSuccess) return e;
         attr_done = true;
     }
-    k_sweep3_f2<MODE><<<dim3(grid[0], grid[1], grid[2]), dim3(BXP, BYP), sm, s>>>(tmap[0], tmap[1], tmap[2], a, err);
+    cudaError_t e = launch_pdl(k_sweep3_f2<MODE>, dim3(grid[0], grid[1], grid[2]), dim3(BXP, BYP), sm, s, tmap[0], tmap[1],
+                               tmap[2], a, err);
+    if (e != cudaSuccess) return e;
     ++g_launches;
     return cudaGetLastError();
 }

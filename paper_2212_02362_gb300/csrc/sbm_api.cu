@@ -316,9 +316,10 @@ cudaError_t vcycle(sbm_grid G, int l, int &cur, const sbm_opts &o, const T *f)
     } else {
         CKE(sweep<T>(G, l, kResidual, P<T>::u(L, cur), f, P<T>::r(L), nullptr, 0.0));
     }
-    CKE(launch_restrict<T>(L.g, C.g, P<T>::r(L), P<T>::f(C), G->st, G->cur_gate));
+    // the restriction also zeroes the coarse correction (the coarsest level's is
+    // overwritten by the dense solve), keeping the cycle a chain of kernels
+    CKE(launch_restrict<T>(L.g, C.g, P<T>::r(L), P<T>::f(C), G->st, G->cur_gate, l - 1 > 0 ? P<T>::u(C, 0) : nullptr));
     int cc = 0;
-    if (l - 1 > 0) CKE(cudaMemsetAsync(P<T>::u(C, 0), 0, level_bytes(C, sizeof(T)), G->st));
     CKE(vcycle<T>(G, l - 1, cc, o, P<T>::f(C)));
     CKE(launch_prolong_add<T>(L.g, C.g, P<T>::u(C, cc), P<T>::u(L, cur), G->st, G->cur_gate));
     CKE(smooth<T>(G, l, cur, o, o.nu2, true, f));

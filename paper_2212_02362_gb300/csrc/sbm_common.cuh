@@ -39,6 +39,34 @@ __host__ __device__ __forceinline__ bool is_dir(const Geom &g, int p, int i, int
            ((m & 8u) && j == g.ny - 1) || ((m & 16u) && k == 0) || ((m & 32u) && k == g.nz - 1);
 }
 
+// Programmatic dependent launch: the kernels of the V-cycle path are launched
+// with the programmatic-serialisation attribute, so a launch is processed while
+// its predecessor drains; each of them first waits for its predecessor to
+// complete (griddepcontrol.wait: memory visible) and then lets its own successor
+// be scheduled.  Launched without the attribute, both are no-ops.
+__device__ __forceinline__ void pdl_begin()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 enum SweepMode { kApply = 0, kResidual = 1, kJacobi = 2 };
 
 template <typename T, typename TO>
@@ -108,7 +136,7 @@ cudaError_t launch_gs(const Geom &g, const T *psi, const T *Ke, const T *f, T *u
 
 template <typename T>
 cudaError_t launch_restrict(const Geom &gf, const Geom &gc, const T *rf, T *fc, cudaStream_t s,
-                            const int *gate = nullptr);
+                            const int *gate = nullptr, T *zero_uc = nullptr);
 
 template <typename T>
 cudaError_t launch_prolong_add(const Geom &gf, const Geom &gc, const T *ec, T *uf, cudaStream_t s,
