@@ -359,7 +359,7 @@ def run_ours(args, rank, world, local_rank):
     elif args.workload == "damage_3d_129" and args.roofline_kernel == "jacobi":
         # dram__bytes_read.sum + dram__bytes_write.sum of this launch in the ncu capture
         # summarised in profiles/k_sweep3_f2_jacobi_damage129.md
-        roof["traffic"] = 68.0e6
+        roof["traffic"] = None   # kernel changed since the last ncu capture
 
     # ---- plain FP64 solve of the same problem ----
     fp64 = None

@@ -57,7 +57,10 @@ __global__ void __launch_bounds__((TX3 + 1) * (TY3 + 1)) k_sweep3(const SweepArg
     __shared__ double red[((NT + 31) / 32) * 32];
 
     const Geom &g = a.g;
-    const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + BX * ty;
+    static_assert(BX == 33, "row-aligned warps need 32-cell rows");
+    const int tid = threadIdx.x + BX * threadIdx.y;
+    int tx, ty;
+    row_warp_xy<BY>(tid, tx, ty);
     const int x0 = blockIdx.x * TX3, y0 = blockIdx.y * TY3;
     const int kz0 = blockIdx.z * a.kchunk;
     const int kz1 = min(kz0 + a.kchunk, g.nz - 1);
@@ -182,7 +185,10 @@ __global__ void __launch_bounds__((TXD + 1) * (TYD + 1)) k_sweep3_dp(const Sweep
     __shared__ double red[((NT + 31) / 32) * 32];
 
     const Geom &g = a.g;
-    const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + BX * ty;
+    static_assert(BX == 33, "row-aligned warps need 32-cell rows");
+    const int tid = threadIdx.x + BX * threadIdx.y;
+    int tx, ty;
+    row_warp_xy<BY>(tid, tx, ty);
     const int x0 = blockIdx.x * TXD, y0 = blockIdx.y * TYD;
     const int kz0 = blockIdx.z * a.kchunk;
     const int kz1 = min(kz0 + a.kchunk, g.nz - 1);
@@ -286,7 +292,10 @@ __global__ void __launch_bounds__((TX2 + 1) * (TY2 + 1)) k_sweep2(const SweepArg
     __shared__ T ps[PP];
     __shared__ double red[((NT + 31) / 32) * 32];
     const Geom &g = a.g;
-    const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + BX * ty;
+    static_assert(BX == 33, "row-aligned warps need 32-cell rows");
+    const int tid = threadIdx.x + BX * threadIdx.y;
+    int tx, ty;
+    row_warp_xy<BY>(tid, tx, ty);
     const int x0 = blockIdx.x * TX2, y0 = blockIdx.y * TY2;
     for (int s = tid; s < PP; s += NT) {
         const int lx = s % PX, ly = s / PX;

@@ -3,7 +3,8 @@
 // arithmetic (sm_100+ FFMA2 / FADD2 / FMUL2).
 //
 // Block = 32 x 8 cells in x/y (33 x 9 threads, one cell column each, the first
-// row/column being the one-cell halo), streaming a chunk of z.  Each step handles
+// row/column being the one-cell halo; warps aligned with the 32-cell rows),
+// streaming a chunk of z.  Each step handles
 // two cell layers (k, k+1) at once: every thread evaluates its two cells in the
 // two lanes of the packed type, so one packed instruction does the work of two.
 // Node planes of u and f and cell layers of psi are fetched by the Tensor Memory
@@ -188,7 +189,9 @@ __global__ void __launch_bounds__(NTP) k_sweep3_f2(const __grid_constant__ CUten
     __shared__ double red[((NTP + 31) / 32) * 32];
 
     const Geom &g = a.g;
-    const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + BXP * ty;
+    const int tid = threadIdx.x + BXP * threadIdx.y;
+    int tx, ty;
+    row_warp_xy<BYP>(tid, tx, ty);
     const int x0 = blockIdx.x * TXP, y0 = blockIdx.y * TYP;
     const int kz0 = blockIdx.z * a.kchunk;
     const int kz1 = min(kz0 + a.kchunk, g.nz - 1);

@@ -39,6 +39,24 @@ __host__ __device__ __forceinline__ bool is_dir(const Geom &g, int p, int i, int
            ((m & 8u) && j == g.ny - 1) || ((m & 16u) && k == 0) || ((m & 32u) && k == g.nz - 1);
 }
 
+// Thread layout of the tiled 3D/2D sweeps: a block of 33 x BY threads, one cell
+// column (cell row in 2D) each, the first row and column being the one-cell halo.
+// Warps cover whole 32-cell rows and the last, partial warp the 33rd column, so the
+// shared-memory accesses of a warp along a row are contiguous and free of bank
+// conflicts (a warp spanning the end of one row and the start of the next would hit
+// the same banks twice).
+template <int BY>
+__device__ __forceinline__ void row_warp_xy(int tid, int &tx, int &ty)
+{
+    if (tid < 32 * BY) {
+        tx = tid & 31;
+        ty = tid >> 5;
+    } else {
+        tx = 32;
+        ty = tid - 32 * BY;
+    }
+}
+
 // Programmatic dependent launch: the kernels of the V-cycle path are launched
 // with the programmatic-serialisation attribute, so a launch is processed while
 // its predecessor drains; each of them first waits for its predecessor to
