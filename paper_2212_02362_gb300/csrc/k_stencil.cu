@@ -450,27 +450,52 @@ long long sweep_blocks(const Geom &g, bool fp64)
     return (long long)grid[0] * grid[1] * grid[2];
 }
 
-// Small 3D levels (FP32): one thread per node gathers its 3x3x3 neighbourhood and
-// evaluates the 2^3 cells around it, keeping its own corner's force.  Every cell
-// is evaluated by each of its 8 corner nodes (8x the arithmetic), but the kernel
-// has no shared memory, no barriers and no z streaming: on coarse levels, whose
-// cost is latency, it finishes in a fraction of the time of the tiled kernels.
+// Small 3D levels (FP32): eight consecutive threads per node, thread c evaluating
+// the cell of which the node is corner c; the node's force and psi sum are summed
+// over the eight lanes by shuffles and the first lane finalises.  There is no
+// shared memory, no barrier and no z streaming, and each thread's dependent
+// chain is one cell: on coarse levels, whose cost is latency, a launch takes
+// little more than one cell evaluation.
+constexpr int kNodeThreads = 256;
+
 template <int MODE>
-__global__ void __launch_bounds__(128) k_sweep3_node(const SweepArgs<float, float> a)
+__global__ void __launch_bounds__(kNodeThreads) k_sweep3_node(const SweepArgs<float, float> a)
 {
     pdl_begin();
     if (a.gate && *a.gate) return;
     const Geom &g = a.g;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    const int k = blockIdx.z * blockDim.z + threadIdx.z;
-    if (i >= g.nx || j >= g.ny || k >= g.nz) return;
-    body::node_sweep<MODE>(a, i, j, k);
+    const long long n = (long long)g.nx * g.ny * g.nz;
+    const long long node = (long long)blockIdx.x * (kNodeThreads / 8) + (threadIdx.x >> 3);
+    const int c = threadIdx.x & 7;
+    const bool valid = node < n;
+    int i = 0, j = 0, k = 0;
+    if (valid) {
+        i = (int)(node % g.nx);
+        const long long t = node / g.nx;
+        j = (int)(t % g.ny);
+        k = (int)(t / g.ny);
+    }
+    float F[3] = {0.f, 0.f, 0.f}, ps = 0.f;
+    if (valid) body::node_cell(a, i, j, k, c, F, ps);
+    // every lane takes part in the sums; the xor partners stay in the group of eight
+#pragma unroll
+    for (int off = 4; off > 0; off >>= 1) {
+#pragma unroll
+        for (int p = 0; p < 3; ++p) F[p] += __shfl_xor_sync(0xffffffffu, F[p], off);
+        ps += __shfl_xor_sync(0xffffffffu, ps, off);
+    }
+    if (valid && c == 0) {
+        const long long o = gidx(g, i, j, k);
+        const float uv[3] = {a.u[o], a.u[g.cs + o], a.u[2 * g.cs + o]};
+        double ssq = 0.0;
+        body::finalize<float, float, MODE>(a, i, j, k, F, ps, uv, ssq);
+    }
 }
 
 cudaError_t launch_sweep_node(int mode, const SweepArgs<float, float> &a, cudaStream_t s)
 {
-    const dim3 b(32, 4, 1), gr((a.g.nx + 31) / 32, (a.g.ny + 3) / 4, a.g.nz);
+    const long long n = (long long)a.g.nx * a.g.ny * a.g.nz;
+    const dim3 b(kNodeThreads), gr((unsigned)((n + kNodeThreads / 8 - 1) / (kNodeThreads / 8)));
     cudaError_t e;
     switch (mode) {
     case kApply: e = launch_pdl(k_sweep3_node<kApply>, gr, b, 0, s, a); break;

@@ -1,8 +1,8 @@
-// sbm_bodies.cuh — per-element device bodies shared by the standalone kernels
-// and the single-launch coarse V-cycle: the sweep finalisation (damped Jacobi /
-// residual / apply at one node), the per-node FP32 3D sweep, full-weighting
-// restriction and linear prolongation at one coarse node, and one row of the
-// coarsest-level dense matvec.
+// sbm_bodies.cuh — per-element device bodies of the stencil and transfer kernels:
+// the sweep finalisation (damped Jacobi / residual / apply at one node), one cell
+// of the cell-parallel FP32 3D sweep of small levels, full-weighting restriction
+// and linear prolongation at one coarse node, and one row of the coarsest-level
+// dense matvec.
 #pragma once
 
 #include "sbm_common.cuh"
@@ -34,45 +34,35 @@ __device__ __forceinline__ void finalize(const SweepArgs<T, TO> &a, int gx, int 
     }
 }
 
-// Small 3D levels (FP32): the node gathers its 3x3x3 neighbourhood and evaluates
-// the 2^3 cells around it, keeping its own corner's force (8x the arithmetic of
-// the cell-wise kernels, no shared memory, no barriers).
-template <int MODE>
-__device__ __forceinline__ void node_sweep(const SweepArgs<float, float> &a, int i, int j, int k)
+// Small 3D levels (FP32), one cell of a node's eight: thread c of the node's group
+// of eight evaluates the cell of which node (i, j, k) is corner c (bit m = the
+// node's offset along axis m within the cell) and returns the force on that
+// corner and the cell's psi; cells outside the grid give zeros.
+__device__ __forceinline__ void node_cell(const SweepArgs<float, float> &a, int i, int j, int k, int c,
+                                          float (&F)[3], float &ps)
 {
     const Geom &g = a.g;
-    float nb[3][27];
+    const int cx = c & 1, cy = (c >> 1) & 1, cz = (c >> 2) & 1;
+    const int ci = i - cx, cj = j - cy, ck = k - cz;
+    F[0] = F[1] = F[2] = 0.f;
+    ps = 0.f;
+    if (ci < 0 || cj < 0 || ck < 0 || ci >= g.nx - 1 || cj >= g.ny - 1 || ck >= g.nz - 1) return;
+    ps = a.psi[gidx(g, ci, cj, ck)];
+    float U[3][8];
 #pragma unroll
-    for (int q = 0; q < 27; ++q) {
-        const int x = i + q % 3 - 1, y = j + (q / 3) % 3 - 1, z = k + q / 9 - 1;
-        const bool in = x >= 0 && x < g.nx && y >= 0 && y < g.ny && z >= 0 && z < g.nz;
-        const long long o = in ? gidx(g, x, y, z) : 0;
+    for (int b = 0; b < 8; ++b) {
+        const long long o = gidx(g, ci + (b & 1), cj + ((b >> 1) & 1), ck + (b >> 2));
 #pragma unroll
-        for (int p = 0; p < 3; ++p) nb[p][q] = in ? a.u[p * g.cs + o] : 0.f;
+        for (int p = 0; p < 3; ++p) U[p][b] = a.u[p * g.cs + o];
     }
-    float Ku[3] = {0.f, 0.f, 0.f}, psisum = 0.f;
+    cell_forces3<float>(U, ps, a.c);
 #pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        // cell with lower corner (i - cx, j - cy, k - cz); this node is its corner (cx, cy, cz)
-        const int cx = c & 1, cy = (c >> 1) & 1, cz = (c >> 2) & 1;
-        const int ci = i - cx, cj = j - cy, ck = k - cz;
-        if (ci < 0 || cj < 0 || ck < 0 || ci >= g.nx - 1 || cj >= g.ny - 1 || ck >= g.nz - 1) continue;
-        const float ps = a.psi[gidx(g, ci, cj, ck)];
-        psisum += ps;
-        float U[3][8];
+    for (int p = 0; p < 3; ++p) {
+        float v = U[p][0];
 #pragma unroll
-        for (int b = 0; b < 8; ++b) {
-            const int q = ((b & 1) - cx + 1) + 3 * (((b >> 1) & 1) - cy + 1) + 9 * (((b >> 2) & 1) - cz + 1);
-#pragma unroll
-            for (int p = 0; p < 3; ++p) U[p][b] = nb[p][q];
-        }
-        cell_forces3<float>(U, ps, a.c);
-#pragma unroll
-        for (int p = 0; p < 3; ++p) Ku[p] += U[p][c];
+        for (int b = 1; b < 8; ++b) v = (c == b) ? U[p][b] : v;
+        F[p] = v;
     }
-    double ssq = 0.0;
-    const float uv[3] = {nb[0][13], nb[1][13], nb[2][13]};
-    finalize<float, float, MODE>(a, i, j, k, Ku, psisum, uv, ssq);
 }
 
 template <typename T> struct Vec2;

@@ -188,9 +188,9 @@ cudaError_t launch_norm_final(const double *part, int nparts, double *scal, int 
 cudaError_t launch_bottom_assemble(const Geom &g, const double *psi, const Coef<double> &c,
                                    double *A, cudaStream_t s);
 cudaError_t launch_bottom_dirichlet(const Geom &g, double *A, cudaStream_t s);
-// FP32 3D sweep, one thread per node (small levels; no partial sums).
+// FP32 3D sweep, eight threads (one per cell) per node (small levels; no partial sums).
 cudaError_t launch_sweep_node(int mode, const SweepArgs<float, float> &a, cudaStream_t s);
-// Levels with at most this many nodes use the per-node FP32 kernel.
+// Levels with at most this many nodes use the cell-parallel per-node FP32 kernel.
 constexpr long long kNodeKernelMaxNodes = 80000;
 
 // Inverse of the coarsest-level matrix in place (one cooperative launch);
