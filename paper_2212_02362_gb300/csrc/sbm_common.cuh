@@ -191,7 +191,7 @@ cudaError_t launch_bottom_dirichlet(const Geom &g, double *A, cudaStream_t s);
 // FP32 3D sweep, eight threads (one per cell) per node (small levels; no partial sums).
 cudaError_t launch_sweep_node(int mode, const SweepArgs<float, float> &a, cudaStream_t s);
 // Levels with at most this many nodes use the cell-parallel per-node FP32 kernel.
-constexpr long long kNodeKernelMaxNodes = 80000;
+constexpr long long kNodeKernelMaxNodes = 20000;
 
 // Inverse of the coarsest-level matrix in place (one cooperative launch);
 // bar: 4 device words, bar[2] != 0 afterwards if a grid barrier timed out.
