@@ -459,7 +459,8 @@ def run_amr(args, rank, world, local_rank):
     u0_d = [t.to(dev) for t in u0_h]
     unknowns = amr_unknowns(wk)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    opts = {"omega": wk.omega, "tol": 1e-10, "smoother": wk.smoother, "max_cycles": 500}
+    opts = {"omega": wk.omega, "tol": 1e-10, "smoother": wk.smoother, "max_cycles": 500,
+            "inner_cycles": args.amr_inner if precision == "mixed" else 1}
 
     def make_grid(prec):
         g = sbm.Grid(wk.dim, wk.n, wk.h, precision=prec, device=local_rank, stream=stream.cuda_stream)
@@ -510,12 +511,14 @@ def run_amr(args, rank, world, local_rank):
     fp64 = None
     if precision == "mixed" and not args.skip_fp64:
         g64 = make_grid("fp64")
+        opts["inner_cycles"] = 1
         timed(g64, 0, 1)
         i64, ms64, u64 = timed(g64, 1, 0)
         num = sum(float(((a - b) ** 2).sum()) for a, b in zip(u64, us))
         den = sum(float((b ** 2).sum()) for b in u64)
         fp64 = {"ms_per_step": ms64[0], "value": unknowns / (ms64[0] / 1e3) / 1e6, "cycles": i64[0].cycles,
                 "rel_diff_vs_mixed": (num / den) ** 0.5}
+        opts["inner_cycles"] = args.amr_inner
         del g64
     # end to end: host psi and initial guess in, solution out
     out_h = [torch.empty_like(u).pin_memory() for u in u0_h]
@@ -555,8 +558,10 @@ def run_amr(args, rank, world, local_rank):
                                        f"{len(wk.boxes)} levels", "boxes": [list(map(list, b)) for b in wk.boxes],
                            "composite_unknowns": unknowns, "precision": precision, "tol": 1e-10,
                            "smoother": wk.smoother, "omega": wk.omega,
+                           "fp32_cycles_per_fp64_residual": opts["inner_cycles"] if precision == "mixed" else None,
                            "l2": "flushed (256 MB write) between timed steps"},
-                "cycles_to_tol": cyc, "cycles_per_s": cyc / (ms_per_step / 1e3), "fp64_solve": fp64,
+                "cycles_to_tol": cyc, "correction_cycles_to_tol": infos[-1].vcycles,
+                "cycles_per_s": cyc / (ms_per_step / 1e3), "fp64_solve": fp64,
                 "roofline": None, "cpu_baseline": None,
                 "e2e": {"value": world * unknowns / (statistics.mean(e2e_ms) / 1e3) / 1e6, "unit": UNIT,
                         "h2d_bytes_per_step": sum(t.numel() * 8 for t in psi_h + u0_h),
@@ -579,6 +584,8 @@ def main():
                     help="default: the workload's (mixed for the 3D configurations)")
     ap.add_argument("--inner", type=int, default=12,
                     help="FP32 V-cycles per FP64 defect residual (mixed; the maximum when --inner-rtol > 0)")
+    ap.add_argument("--amr-inner", type=int, default=6,
+                    help="refinement workloads, mixed: FP32 correction cycles per FP64 composite residual")
     ap.add_argument("--inner-rtol", type=float, default=1e-6,
                     help="stop an outer iteration's FP32 V-cycles once their residual falls below this "
                          "fraction of the FP64 residual (or below the tolerance); 0: fixed count")

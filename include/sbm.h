@@ -231,8 +231,12 @@ sbm_status sbm_amr_set_source(sbm_grid grid, int a, const double *f_nodes);
  * cycle: FP64 composite residual; patches top-down (smoothing of the correction,
  * full-weighting of its residual onto the covered parent nodes); the base
  * multigrid V-cycle; patches bottom-up (parent correction prolongated and ghosts
- * filled, smoothing); u += e on owned dofs.  SBM_MIXED runs the cycle in FP32.
- * opts->inner_cycles is ignored.  Status as for sbm_solve. */
+ * filled, smoothing); u += e on owned dofs.  SBM_MIXED runs the cycle in FP32, and
+ * opts->inner_cycles of them per FP64 residual: between two of them the FP32
+ * right-hand side becomes r - A e (the correction injected into covered parents,
+ * every level's residual of it, owned free rows kept); opts->inner_rtol is ignored
+ * (the count is fixed).  info->cycles counts FP64 residuals, info->vcycles
+ * correction cycles.  Status as for sbm_solve. */
 sbm_status sbm_amr_solve(sbm_grid grid, double *const *u, const sbm_opts *opts, sbm_info *info);
 /* Adjoint of the composite problem of sbm_amr_solve (Sec. 2.2 levels, Sec. 2.4 psi
  * averaging; the adjoint reading D10 applied to every level).  u: the composite

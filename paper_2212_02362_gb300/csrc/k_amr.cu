@@ -121,8 +121,8 @@ __global__ void k_amr_mask(const Geom s, const AmrInfo L, double *r)
         if (!own || domain_dirichlet(L, g, p)) r[p * s.cs + o] = 0.0;
 }
 
-__global__ void k_amr_inject(const Geom sc, const AmrInfo Lc, const Geom sp, const AmrInfo Lp, const double *uc,
-                             double *up)
+template <typename T>
+__global__ void k_amr_inject(const Geom sc, const AmrInfo Lc, const Geom sp, const AmrInfo Lp, const T *uc, T *up)
 {
     int i, j, k, g[3];
     if (!thread_node(sc, Lc, i, j, k, g)) return;
@@ -133,6 +133,19 @@ __global__ void k_amr_inject(const Geom sc, const AmrInfo Lc, const Geom sp, con
     if (lp[0] < 0 || lp[1] < 0 || lp[2] < 0 || lp[0] >= sp.nx || lp[1] >= sp.ny || lp[2] >= sp.nz) return;
     const long long oc = gidx(sc, i, j, k), op = gidx(sp, lp[0], lp[1], lp[2]);
     for (int p = 0; p < Lc.dim; ++p) up[p * sp.cs + op] = uc[p * sc.cs + oc];
+}
+
+// out <- r on the owned rows that are not on a Dirichlet face of the domain, 0 on
+// every other storage node (the residual of the correction equation in the
+// layout of the cycle's right-hand side).
+template <typename T>
+__global__ void k_amr_mask_to(const Geom s, const AmrInfo L, const T *r, T *out)
+{
+    int i, j, k, g[3];
+    if (!thread_node(s, L, i, j, k, g)) return;
+    const bool own = owned(L, g);
+    const long long o = gidx(s, i, j, k);
+    for (int p = 0; p < L.dim; ++p) out[p * s.cs + o] = (own && !domain_dirichlet(L, g, p)) ? r[p * s.cs + o] : T(0);
 }
 
 // mode 0: ghosts <- interpolated parent values (owned/active nodes untouched).
@@ -498,13 +511,27 @@ cudaError_t launch_amr_mask(const Geom &s, const AmrInfo &L, double *r, cudaStre
     return cudaGetLastError();
 }
 
-cudaError_t launch_amr_inject(const Geom &sc, const AmrInfo &Lc, const Geom &sp, const AmrInfo &Lp, const double *uc,
-                              double *up, cudaStream_t st)
+template <typename T>
+cudaError_t launch_amr_inject(const Geom &sc, const AmrInfo &Lc, const Geom &sp, const AmrInfo &Lp, const T *uc, T *up,
+                              cudaStream_t st)
 {
-    k_amr_inject<<<amr_grid(sc), kAmrBlock, 0, st>>>(sc, Lc, sp, Lp, uc, up);
+    k_amr_inject<T><<<amr_grid(sc), kAmrBlock, 0, st>>>(sc, Lc, sp, Lp, uc, up);
     ++g_launches;
     return cudaGetLastError();
 }
+template cudaError_t launch_amr_inject<double>(const Geom &, const AmrInfo &, const Geom &, const AmrInfo &,
+                                               const double *, double *, cudaStream_t);
+template cudaError_t launch_amr_inject<float>(const Geom &, const AmrInfo &, const Geom &, const AmrInfo &,
+                                              const float *, float *, cudaStream_t);
+
+template <typename T>
+cudaError_t launch_amr_mask_to(const Geom &s, const AmrInfo &L, const T *r, T *out, cudaStream_t st)
+{
+    k_amr_mask_to<T><<<amr_grid(s), kAmrBlock, 0, st>>>(s, L, r, out);
+    ++g_launches;
+    return cudaGetLastError();
+}
+template cudaError_t launch_amr_mask_to<float>(const Geom &, const AmrInfo &, const float *, float *, cudaStream_t);
 
 template <typename T>
 cudaError_t launch_amr_ghost(const Geom &sc, const AmrInfo &Lc, const Geom &sp, const AmrInfo &Lp, T *uc, const T *up,

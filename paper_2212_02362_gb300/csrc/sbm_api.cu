@@ -732,8 +732,11 @@ cudaError_t amr_residual(sbm_grid G, int which)
 // One correction cycle: patches top-down (smooth, residual, restrict to covered
 // parent nodes), the base multigrid V-cycle, patches bottom-up (prolongate the
 // parent correction, fill ghosts, smooth), then u += e on owned dofs.
+// cur_out / cb_out (optional): which of the two correction buffers of each patch /
+// of the base level holds the final correction.
 template <typename T>
-cudaError_t amr_cycle(sbm_grid G, const sbm_opts &o, double *const *target = nullptr)
+cudaError_t amr_cycle(sbm_grid G, const sbm_opts &o, double *const *target = nullptr, int *cur_out = nullptr,
+                      int *cb_out = nullptr)
 {
     const int A = G->npatch;
     Level &B = G->L[G->nl - 1];
@@ -771,6 +774,39 @@ cudaError_t amr_cycle(sbm_grid G, const sbm_opts &o, double *const *target = nul
     for (int a = 1; a <= A; ++a) {
         Patch &Pt = G->P[a - 1];
         CKE(launch_amr_update<T>(Pt.s, Pt.info, PP<T>::e(Pt, cur[a]), target ? target[a] : Pt.u64, G->st));
+    }
+    if (cur_out)
+        for (int a = 0; a <= A; ++a) cur_out[a] = cur[a];
+    if (cb_out) *cb_out = cb;
+    return cudaSuccess;
+}
+
+// Mixed-precision inner iterations: once an FP32 correction cycle has added its
+// correction e to u, the cycle's FP32 right-hand side becomes the residual of the
+// correction equation, r <- r - A e, on the owned free rows of every level, so the
+// next FP32 cycle needs no FP64 residual.  A e is the composite operator applied
+// to e filled like a solution: e injected into the covered parent nodes (finest
+// first; the cycle left each patch's ghosts interpolated from its parent's final
+// correction, and the ghosts depend on uncovered parent nodes only), then K of
+// every level on its nodes.
+cudaError_t amr_inner_residual(sbm_grid G, const int *cur, int cb)
+{
+    const int A = G->npatch;
+    Level &B = G->L[G->nl - 1];
+    for (int a = A; a >= 1; --a) {
+        Patch &Pt = G->P[a - 1];
+        if (a == 1)
+            CKE(launch_amr_inject<float>(Pt.s, Pt.info, B.g, G->base_info, Pt.se[cur[a]], B.su[cb], G->st));
+        else
+            CKE(launch_amr_inject<float>(Pt.s, Pt.info, G->P[a - 2].s, G->P[a - 2].info, Pt.se[cur[a]],
+                                         G->P[a - 2].se[cur[a - 1]], G->st));
+    }
+    CKE(sweep<float>(G, G->nl - 1, kResidual, B.su[cb], B.sf, B.sr, nullptr, 0.0));
+    CKE(launch_amr_mask_to<float>(B.g, G->base_info, B.sr, B.sf, G->st));
+    for (int a = 1; a <= A; ++a) {
+        Patch &Pt = G->P[a - 1];
+        CKE(sweep_view<float>(G, Pt, kResidual, Pt.se[cur[a]], Pt.srhs, Pt.sres, 0.0));
+        CKE(launch_amr_mask_to<float>(Pt.s, Pt.info, Pt.sres, Pt.srhs, G->st));
     }
     return cudaSuccess;
 }
@@ -970,8 +1006,17 @@ sbm_status amr_run(sbm_grid G, const sbm_opts &o, sbm_info *info)
         status = SBM_OK;
         rel = 0.0;
     }
+    // SBM_MIXED: inner_cycles FP32 correction cycles per FP64 residual
+    const int inner = std::is_same<T, float>::value ? o.inner_cycles : 1;
+    int ncycles = 0;
     while (status == SBM_ERR_NOCONV && cyc < o.max_cycles) {
-        CK(amr_cycle<T>(G, o));
+        for (int it = 0; it < inner; ++it) {
+            int cur[9], cb = 0;
+            CK(amr_cycle<T>(G, o, nullptr, cur, &cb));
+            ++ncycles;
+            if constexpr (std::is_same<T, float>::value)
+                if (it + 1 < inner) CK(amr_inner_residual(G, cur, cb));
+        }
         CK(amr_residual<T>(G, 2));
         CK(cudaMemcpyAsync(G->hscal + 4, G->scal + 4, sizeof(double), cudaMemcpyDeviceToHost, G->st));
         CK(cudaStreamSynchronize(G->st));
@@ -989,7 +1034,7 @@ sbm_status amr_run(sbm_grid G, const sbm_opts &o, sbm_info *info)
     if (info) {
         info->status = status;
         info->cycles = cyc;
-        info->vcycles = cyc;
+        info->vcycles = ncycles;
         info->relres = rel;
         info->solve_ms = ms;
         info->launches = g_launches - launches0;

@@ -250,8 +250,12 @@ cudaError_t launch_amr_get_cells(const Geom &s, const double *lev, const double 
 long long amr_blocks(const Geom &s);
 bool amr_owned_host(const AmrInfo &L, int i, int j, int k);
 cudaError_t launch_amr_mask(const Geom &s, const AmrInfo &L, double *r, cudaStream_t st);
-cudaError_t launch_amr_inject(const Geom &sc, const AmrInfo &Lc, const Geom &sp, const AmrInfo &Lp, const double *uc,
-                              double *up, cudaStream_t st);
+template <typename T>
+cudaError_t launch_amr_inject(const Geom &sc, const AmrInfo &Lc, const Geom &sp, const AmrInfo &Lp, const T *uc, T *up,
+                              cudaStream_t st);
+// out <- r on owned free rows, 0 elsewhere (every storage node of the level).
+template <typename T>
+cudaError_t launch_amr_mask_to(const Geom &s, const AmrInfo &L, const T *r, T *out, cudaStream_t st);
 template <typename T>
 cudaError_t launch_amr_ghost(const Geom &sc, const AmrInfo &Lc, const Geom &sp, const AmrInfo &Lp, T *uc, const T *up,
                              int mode, cudaStream_t st);

@@ -104,6 +104,29 @@ def test_composite_solve_matches_dense_oracle(built, case, precision):
     assert num <= 1e-8 * den, (num / den, info.cycles)
 
 
+@pytest.mark.parametrize("case", list(SMALL))
+@pytest.mark.parametrize("inner", [3, 8])
+def test_composite_mixed_inner_cycles(built, case, inner):
+    """Mixed precision with several FP32 correction cycles per FP64 residual (the
+    FP32 right-hand side becomes r - A e in between): the dense oracle's solution,
+    with fewer FP64 residuals than one cycle each and about as many cycles."""
+    wk = SMALL[case]()
+    A, psis = _oracle(wk)
+    us0 = [np.ascontiguousarray(wk.level_u0(a)) for a in range(A.nlev)]
+    ref = dense_solve(A, psis, _zeros_f(A), us0)
+    g = _gpu(wk, "mixed")
+    one = g.amr_solve([cuda(u) for u in us0], tol=1e-10, omega=wk.omega, smoother=wk.smoother)
+    us = [cuda(u) for u in us0]
+    info = g.amr_solve(us, tol=1e-10, omega=wk.omega, smoother=wk.smoother, inner_cycles=inner)
+    assert info.converged
+    num = np.sqrt(sum(((host(us[a]) - ref[a]) ** 2).sum() for a in range(A.nlev)))
+    den = np.sqrt(sum((ref[a] ** 2).sum() for a in range(A.nlev)))
+    assert num <= 1e-8 * den, (num / den, info.cycles, info.vcycles)
+    assert info.vcycles == info.cycles * inner
+    assert info.cycles < one.cycles, (info.cycles, one.cycles)
+    assert info.vcycles <= one.vcycles + 2 * inner, (info.vcycles, one.vcycles)
+
+
 def test_P10_patch_over_domain_equals_uniform_fine_gpu_solve(built):
     n0 = 17
     wk = _custom(2, n0, [((0, 0, 0), (32, 32, 0))])
@@ -126,8 +149,9 @@ def test_P10_patch_over_domain_equals_uniform_fine_gpu_solve(built):
     assert np.linalg.norm(patch - host(uf)) <= 1e-9 * np.linalg.norm(host(uf))
 
 
-@pytest.mark.parametrize("dim,n0,levels,precision", [(2, 129, 3, "fp64"), (3, 33, 2, "mixed")])
-def test_full_hierarchy_converges_with_oracle_residual(built, dim, n0, levels, precision):
+@pytest.mark.parametrize("dim,n0,levels,precision,inner", [(2, 129, 3, "fp64", 1), (3, 33, 2, "mixed", 1),
+                                                           (3, 33, 2, "mixed", 6)])
+def test_full_hierarchy_converges_with_oracle_residual(built, dim, n0, levels, precision, inner):
     """The refinement recipes of the 2D (GS, FP64) and 3D (mixed) AMR workloads:
     the oracle's composite residual of the GPU solution is at the tolerance."""
     wk = W.voids_amr(dim, n0, levels) if dim == 2 else W.voids_amr(3, n0, levels, count=16, rmin=0.04, rmax=0.12)
@@ -135,7 +159,7 @@ def test_full_hierarchy_converges_with_oracle_residual(built, dim, n0, levels, p
     A, psis = _oracle(wk)
     us0 = [np.ascontiguousarray(wk.level_u0(a)) for a in range(A.nlev)]
     us = [cuda(u) for u in us0]
-    info = g.amr_solve(us, tol=1e-10, omega=wk.omega, smoother=wk.smoother, max_cycles=300)
+    info = g.amr_solve(us, tol=1e-10, omega=wk.omega, smoother=wk.smoother, max_cycles=300, inner_cycles=inner)
     assert info.converged, info
     fs = _zeros_f(A)
     r0 = oracle.amr_residual(A, psis, fs, [u.copy() for u in us0])
