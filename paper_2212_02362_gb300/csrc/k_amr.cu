@@ -148,6 +148,20 @@ __global__ void k_amr_mask_to(const Geom s, const AmrInfo L, const T *r, T *out)
     for (int p = 0; p < L.dim; ++p) out[p * s.cs + o] = (own && !domain_dirichlet(L, g, p)) ? r[p * s.cs + o] : T(0);
 }
 
+// psi of the cells of a patch's view (storage cells 1 .. n-3 per axis, the view
+// starting at storage node 1), 0 on the padding cells and the unused last index:
+// the cell field the TMA sweep of the view stages.
+__global__ void k_amr_view_cells(const Geom s, const float *src, float *dst)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z * blockDim.z + threadIdx.z;
+    if (i >= s.nx || j >= s.ny || k >= s.nz) return;
+    const bool in = i >= 1 && i <= s.nx - 3 && j >= 1 && j <= s.ny - 3 && (s.dim == 2 || (k >= 1 && k <= s.nz - 3));
+    const long long o = gidx(s, i, j, k);
+    dst[o] = in ? src[o] : 0.f;
+}
+
 // mode 0: ghosts <- interpolated parent values (owned/active nodes untouched).
 // mode 1: correction prolongation: nodes solved on this level (inside the box or
 //         on a domain face) += interpolated parent correction; ghosts <- it.
@@ -523,6 +537,13 @@ template cudaError_t launch_amr_inject<double>(const Geom &, const AmrInfo &, co
                                                const double *, double *, cudaStream_t);
 template cudaError_t launch_amr_inject<float>(const Geom &, const AmrInfo &, const Geom &, const AmrInfo &,
                                               const float *, float *, cudaStream_t);
+
+cudaError_t launch_amr_view_cells(const Geom &s, const float *src, float *dst, cudaStream_t st)
+{
+    k_amr_view_cells<<<amr_grid(s), kAmrBlock, 0, st>>>(s, src, dst);
+    ++g_launches;
+    return cudaGetLastError();
+}
 
 template <typename T>
 cudaError_t launch_amr_mask_to(const Geom &s, const AmrInfo &L, const T *r, T *out, cudaStream_t st)

@@ -16,7 +16,9 @@
 // float2 per corner and component; the top-plane forces of layer k+1 stay in
 // registers and join the next step.  Every mbarrier wait is bounded: on timeout
 // the block records an error code, waits (bounded) for its copies in flight and
-// returns.
+// returns.  The grid swept may sit inside a larger storage at an offset (a
+// refinement patch's view inside its padded box); the tensor maps then describe
+// the storage and each block aligns its boxes itself.
 #include <cuda.h>
 
 #include "sbm_common.cuh"
@@ -29,8 +31,7 @@ constexpr int TXP = 32, TYP = 8;                 // cells per block in x, y
 constexpr int BXP = TXP + 1, BYP = TYP + 1;      // threads per block in x, y
 constexpr int NTP = BXP * BYP;
 constexpr int PXF = TXP + 2, PYF = TYP + 2, PPF = PXF * PYF;   // exchange tiles
-constexpr int WX = 40;                           // TMA box width: nodes x0-4 .. x0+35
-constexpr int XOFF = 3;                          // box-local x of node x0-1
+constexpr int WX = 40;                           // TMA box width: 34 nodes x0-1 .. x0+32 plus alignment
 constexpr int PLANE_FLOATS = 3 * PYF * WX;       // one staged plane: 3 comps x 10 rows x 40
 constexpr int PSI_FLOATS = PYF * WX;             // one staged cell layer of psi
 // A ring slot holds node plane p of u, node plane p of f and cell layer p of psi.
@@ -176,7 +177,7 @@ template <int MODE>
 __global__ void __launch_bounds__(NTP) k_sweep3_f2(const __grid_constant__ CUtensorMap tmap,
                                                     const __grid_constant__ CUtensorMap tmap_f,
                                                     const __grid_constant__ CUtensorMap tmap_psi,
-                                                    const SweepArgs<float, float> a, int *err)
+                                                    const SweepArgs<float, float> a, const int3 org, int *err)
 {
     pdl_begin();
     if (a.gate && *a.gate) return;
@@ -193,6 +194,15 @@ __global__ void __launch_bounds__(NTP) k_sweep3_f2(const __grid_constant__ CUten
     int tx, ty;
     row_warp_xy<BYP>(tid, tx, ty);
     const int x0 = blockIdx.x * TXP, y0 = blockIdx.y * TYP;
+    // The tensor maps describe the storage the sweep's grid sits in at offset org
+    // (0 for a whole level, the view origin for a refinement patch).  The boxes
+    // start at the multiple of 4 at or below node x0-1 (a TMA box's x coordinate
+    // must be 16-byte aligned), xoff in 0..3 being node x0-1's box-local x; the
+    // 40-wide box covers the 34 nodes x0-1 .. x0+32 for any xoff.
+    const int xv = x0 - 1 + org.x;
+    const int xs = xv - (((xv % 4) + 4) % 4);
+    const int xoff = xv - xs;
+    const int ybox = y0 - 1 + org.y;
     const int kz0 = blockIdx.z * a.kchunk;
     const int kz1 = min(kz0 + a.kchunk, g.nz - 1);
     const int kend = (kz1 == g.nz - 1) ? g.nz - 1 : kz1 - 1;   // last plane finalised here
@@ -221,9 +231,9 @@ __global__ void __launch_bounds__(NTP) k_sweep3_f2(const __grid_constant__ CUten
         const uint32_t b = smem_addr(&bar[s]);
         mbar_expect_tx(b, TX_BYTES);
         float *slot = ring + s * SLOT_FLOATS;
-        tma_load_4d(smem_addr(slot), &tmap, x0 - 4, y0 - 1, p, 0, b);
-        tma_load_4d(smem_addr(slot + F_OFF), &tmap_f, x0 - 4, y0 - 1, p, 0, b);
-        tma_load_3d(smem_addr(slot + PSI_OFF), &tmap_psi, x0 - 4, y0 - 1, p, b);
+        tma_load_4d(smem_addr(slot), &tmap, xs, ybox, p + org.z, 0, b);
+        tma_load_4d(smem_addr(slot + F_OFF), &tmap_f, xs, ybox, p + org.z, 0, b);
+        tma_load_3d(smem_addr(slot + PSI_OFF), &tmap_psi, xs, ybox, p + org.z, b);
     };
     if (tid == 0)
         for (int j = 0; j < RING; ++j) issue(kfirst + j);
@@ -272,14 +282,14 @@ __global__ void __launch_bounds__(NTP) k_sweep3_f2(const __grid_constant__ CUten
         const float *P2 = ring + slot_of(k + 2) * SLOT_FLOATS;
         // cell (x0+tx-1, y0+ty-1) of layers k, k+1; the tensor map zero-fills cells
         // outside the grid, so no bounds test is needed
-        const float p0 = P0[PSI_OFF + ty * WX + tx + XOFF];
-        const float p1 = P1[PSI_OFF + ty * WX + tx + XOFF];
+        const float p0 = P0[PSI_OFF + ty * WX + tx + xoff];
+        const float p1 = P1[PSI_OFF + ty * WX + tx + xoff];
         F2 U[3][8];
 #pragma unroll
         for (int p = 0; p < 3; ++p)
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                const int off = p * PYF * WX + (ty + (q >> 1)) * WX + tx + (q & 1) + XOFF;
+                const int off = p * PYF * WX + (ty + (q >> 1)) * WX + tx + (q & 1) + xoff;
                 const float v0 = P0[off], v1 = P1[off], v2 = P2[off];
                 U[p][q] = F2(v0, v1);        // lower corners of cells k, k+1
                 U[p][q + 4] = F2(v1, v2);    // upper corners
@@ -318,7 +328,7 @@ __global__ void __launch_bounds__(NTP) k_sweep3_f2(const __grid_constant__ CUten
             q2.v = ps[me + PXF];
             q3.v = ps[me + PXF + 1];
             const F2 pss = (q0 + q1) + (q2 + q3);
-            const int onode = (ty + 1) * WX + tx + 1 + XOFF;
+            const int onode = (ty + 1) * WX + tx + 1 + xoff;
             if (k >= kz0 && k <= kend) {
                 const float Ku[3] = {Ku2[0].v.x, Ku2[1].v.x, Ku2[2].v.x};
                 const float uv[3] = {P0[onode], P0[PYF * WX + onode], P0[2 * PYF * WX + onode]};
@@ -373,7 +383,8 @@ void sweep_grid_f2(const Geom &g, int *grid, int *kchunk)
 }
 
 template <int MODE>
-static cudaError_t launch_f2_mode(const SweepArgs<float, float> &a0, const CUtensorMap *tmap, int *err, cudaStream_t s)
+static cudaError_t launch_f2_mode(const SweepArgs<float, float> &a0, const CUtensorMap *tmap, int *err, cudaStream_t s,
+                                  int3 org)
 {
     SweepArgs<float, float> a = a0;
     int grid[3];
@@ -386,19 +397,21 @@ static cudaError_t launch_f2_mode(const SweepArgs<float, float> &a0, const CUten
         attr_done = true;
     }
     cudaError_t e = launch_pdl(k_sweep3_f2<MODE>, dim3(grid[0], grid[1], grid[2]), dim3(BXP, BYP), sm, s, tmap[0], tmap[1],
-                               tmap[2], a, err);
+                               tmap[2], a, org, err);
     if (e != cudaSuccess) return e;
     ++g_launches;
     return cudaGetLastError();
 }
 
-cudaError_t launch_sweep_f2(int mode, const SweepArgs<float, float> &a, const void *tmap, int *err, cudaStream_t s)
+cudaError_t launch_sweep_f2(int mode, const SweepArgs<float, float> &a, const void *tmap, int *err, cudaStream_t s,
+                            int3 org)
 {
     const CUtensorMap *m = static_cast<const CUtensorMap *>(tmap);
+    if (org.x < 0 || org.y < 0 || org.z < 0) return cudaErrorInvalidValue;
     switch (mode) {
-    case kApply: return launch_f2_mode<kApply>(a, m, err, s);
-    case kResidual: return launch_f2_mode<kResidual>(a, m, err, s);
-    case kJacobi: return launch_f2_mode<kJacobi>(a, m, err, s);
+    case kApply: return launch_f2_mode<kApply>(a, m, err, s, org);
+    case kResidual: return launch_f2_mode<kResidual>(a, m, err, s, org);
+    case kJacobi: return launch_f2_mode<kJacobi>(a, m, err, s, org);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -52,6 +52,9 @@ struct Patch {
     double *u64 = nullptr, *f64 = nullptr, *r64 = nullptr;
     double *de[2] = {nullptr, nullptr}, *drhs = nullptr, *dres = nullptr;
     float *se[2] = {nullptr, nullptr}, *srhs = nullptr, *sres = nullptr;
+    float *psiv32 = nullptr;  // psi32 on the view's cells, 0 on the padding (TMA sweep input)
+    CUtensorMap tm32[2][3];   // 3D: TMA maps of (se[i], srhs, psiv32) over the storage
+    bool has_tm = false;
     Coef<double> c64{};
     Coef<float> c32{};
     double *Ke64 = nullptr;
@@ -657,6 +660,23 @@ template <> struct PP<float> {
 template <typename T>
 cudaError_t sweep_view(sbm_grid G, Patch &Pt, int mode, const T *u, const T *f, T *out, double omega)
 {
+    if constexpr (std::is_same<T, float>::value) {
+        // 3D FP32 views of the patch's own buffers: the TMA sweep over the storage's
+        // tensor maps, the view starting at storage node (1, 1, 1)
+        if (Pt.has_tm && (u == Pt.se[0] || u == Pt.se[1]) && (mode == kApply || f == Pt.srhs)) {
+            SweepArgs<float, float> a;
+            a.g = Pt.v;
+            a.u = u + Pt.voff;
+            a.f = f ? f + Pt.voff : nullptr;
+            a.psi = Pt.psiv32 + Pt.voff;
+            a.out = out + Pt.voff;
+            a.part = nullptr;
+            a.c = Pt.c32;
+            for (int p = 0; p < 3; ++p) a.wk[p] = (Pt.c64.kdiag[p] != 0.0) ? float(omega / Pt.c64.kdiag[p]) : 0.f;
+            a.kchunk = 0;
+            return launch_sweep_f2(mode, a, Pt.tm32[u == Pt.se[0] ? 0 : 1], G->derr, G->st, make_int3(1, 1, 1));
+        }
+    }
     SweepArgs<T, T> a;
     a.g = Pt.v;
     a.u = u + Pt.voff;
@@ -972,8 +992,10 @@ sbm_status amr_prepare(sbm_grid G)
             if (a == 1) CK(launch_amr_coarsen_psi(Pt.s, Pt.info, B.g, G->base_info, Pt.psi64, B.psi64, G->st));
             else CK(launch_amr_coarsen_psi(Pt.s, Pt.info, G->P[a - 2].s, G->P[a - 2].info, Pt.psi64, G->P[a - 2].psi64, G->st));
         }
-        for (int a = 1; a <= G->npatch; ++a)
+        for (int a = 1; a <= G->npatch; ++a) {
             CK(launch_round(G->P[a - 1].s.cs, G->P[a - 1].psi64, G->P[a - 1].psi32, G->st));
+            CK(launch_amr_view_cells(G->P[a - 1].s, G->P[a - 1].psi32, G->P[a - 1].psiv32, G->st));
+        }
         for (int l = G->nl - 1; l > 0; --l)
             CK(launch_coarsen_psi(G->L[l].g, G->L[l - 1].g, G->L[l].psi64, G->L[l - 1].psi64, G->st));
         for (int l = 0; l < G->nl; ++l) CK(launch_round_cells(G->L[l].g, G->L[l].psi64, G->L[l].psi32, G->st));
@@ -1031,6 +1053,14 @@ sbm_status amr_run(sbm_grid G, const sbm_opts &o, sbm_info *info)
     CK(cudaEventSynchronize(G->ev1));
     float ms = 0.f;
     cudaEventElapsedTime(&ms, G->ev0, G->ev1);
+    {
+        int herr = 0;
+        CK(cudaMemcpy(&herr, G->derr, sizeof(int), cudaMemcpyDeviceToHost));
+        if (herr) {
+            cudaMemset(G->derr, 0, sizeof(int));
+            return fail(G, SBM_ERR_CUDA, "a TMA pipeline wait timed out in the FP32 sweep kernel");
+        }
+    }
     if (info) {
         info->status = status;
         info->cycles = cyc;
@@ -1074,7 +1104,7 @@ sbm_status amr_unpack(sbm_grid G, double *base, double *const *pat, bool residua
 void free_patch(Patch &Pt)
 {
     void *ptrs[] = {Pt.psi64, Pt.psi32, Pt.u64, Pt.f64, Pt.r64, Pt.de[0], Pt.de[1], Pt.drhs, Pt.dres,
-                    Pt.se[0], Pt.se[1], Pt.srhs, Pt.sres, Pt.Ke64, Pt.Ke32};
+                    Pt.se[0], Pt.se[1], Pt.srhs, Pt.sres, Pt.psiv32, Pt.Ke64, Pt.Ke32};
     for (void *p : ptrs)
         if (p) cudaFree(p);
 }
@@ -1760,6 +1790,14 @@ sbm_status sbm_amr_add_level(sbm_grid G, const sbm_box *box)
     for (float **q : fp) {
         CK(cudaMalloc(q, sizeof(float) * nd));
         CK(cudaMemset(*q, 0, sizeof(float) * nd));
+    }
+    CK(cudaMalloc(&Pt.psiv32, sizeof(float) * g.cs));
+    CK(cudaMemset(Pt.psiv32, 0, sizeof(float) * g.cs));
+    if (d == 3) {
+        Pt.has_tm = true;
+        for (int i = 0; i < 2; ++i)
+            Pt.has_tm = Pt.has_tm && encode_plane_map(&Pt.tm32[i][0], Pt.se[i], g) &&
+                        encode_plane_map(&Pt.tm32[i][1], Pt.srhs, g) && encode_cell_map(&Pt.tm32[i][2], Pt.psiv32, g);
     }
     const int nk = (1 << d) * d;
     CK(cudaMalloc(&Pt.Ke64, sizeof(double) * nk * nk));

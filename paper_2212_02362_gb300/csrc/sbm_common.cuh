@@ -141,11 +141,14 @@ template <typename T, typename TO>
 cudaError_t launch_sweep(int mode, const SweepArgs<T, TO> &a, cudaStream_t s);
 
 // FP32 3D sweep with TMA plane staging and packed FP32x2 arithmetic
-// (k_stencil_tma.cu).  tmap: three CUtensorMaps — a.u and a.f as 4D (x, y, z,
-// component) with a 40 x 10 x 1 x 3 box, a.psi as 3D cells with a 40 x 10 x 1 box;
+// (k_stencil_tma.cu).  tmap: three CUtensorMaps — u and f as 4D (x, y, z,
+// component) with a 40 x 10 x 1 x 3 box, psi as 3D cells with a 40 x 10 x 1 box —
+// of the storage that a.g's grid sits in at offset org (>= 0; zero for a whole
+// level).  psi must be 0 on the cells of that storage outside a.g's grid (beyond
+// the storage the tensor maps read zeros).  a.out is written at a.g's nodes.
 // err: device flag set when an mbarrier wait times out.
 cudaError_t launch_sweep_f2(int mode, const SweepArgs<float, float> &a, const void *tmap, int *err,
-                            cudaStream_t s);
+                            cudaStream_t s, int3 org = make_int3(0, 0, 0));
 long long sweep_blocks_f2(const Geom &g);
 
 template <typename T>
@@ -253,6 +256,8 @@ cudaError_t launch_amr_mask(const Geom &s, const AmrInfo &L, double *r, cudaStre
 template <typename T>
 cudaError_t launch_amr_inject(const Geom &sc, const AmrInfo &Lc, const Geom &sp, const AmrInfo &Lp, const T *uc, T *up,
                               cudaStream_t st);
+// psi of a patch view's cells, 0 on the storage's padding cells (for the TMA sweep).
+cudaError_t launch_amr_view_cells(const Geom &s, const float *src, float *dst, cudaStream_t st);
 // out <- r on owned free rows, 0 elsewhere (every storage node of the level).
 template <typename T>
 cudaError_t launch_amr_mask_to(const Geom &s, const AmrInfo &L, const T *r, T *out, cudaStream_t st);
