@@ -359,7 +359,7 @@ def run_ours(args, rank, world, local_rank):
     elif args.workload == "damage_3d_129" and args.roofline_kernel == "jacobi":
         # dram__bytes_read.sum + dram__bytes_write.sum of this launch in the ncu capture
         # summarised in profiles/k_sweep3_f2_jacobi_damage129.md
-        roof["traffic"] = 68.8e6
+        roof["traffic"] = 68.3e6
 
     # ---- plain FP64 solve of the same problem ----
     fp64 = None
@@ -592,7 +592,7 @@ def main():
     ap.add_argument("--roofline-kernel", choices=["residual64", "jacobi"], default="jacobi")
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per launch of the roofline kernel from an ncu capture (default: the "
-                         "capture of the finest Jacobi sweep on damage_3d 129^3, 68.8 MB)")
+                         "capture of the finest Jacobi sweep on damage_3d 129^3, 68.3 MB)")
     ap.add_argument("--adjoint", action="store_true",
                     help="each step also runs the adjoint solve and dJ/drho of the compliance (topology optimisation)")
     ap.add_argument("--skip-fp64", action="store_true")
