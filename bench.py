@@ -533,7 +533,8 @@ def run_amr(args, rank, world, local_rank):
             e1.synchronize()
         adjoint = {"ms": e0.elapsed_time(e1), "iterations": ai.cycles, "relres": ai.relres,
                    "objective": "J = sum of u over owned free dofs",
-                   "method": "FP64 transposed correction iteration + dJ/dpsi of every level",
+                   "method": "transposed correction iteration (FP64 A^T and updates; the transposed cycle "
+                             "in FP32 on mixed grids) + dJ/dpsi of every level",
                    "grad_norm": sum(float(t.norm()) ** 2 for t in grads) ** 0.5}
     # end to end: host psi and initial guess in, solution out
     out_h = [torch.empty_like(u).pin_memory() for u in u0_h]

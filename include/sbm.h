@@ -244,8 +244,10 @@ sbm_status sbm_amr_solve(sbm_grid grid, double *const *u, const sbm_opts *opts, 
  * only its owned free dofs count.  Out: lambda[a] (packed like u[a]), the solution of
  * A^T lambda = dJ/du for the composite operator A (0 off the owned free dofs), by the
  * transposed correction iteration lambda += B^T (dJ/du - A^T lambda), B^T the
- * transpose of one FP64 correction cycle (damped Jacobi: opts->smoother must be
- * SBM_JACOBI), to relative residual opts->tol within opts->max_cycles iterations
+ * transpose of one correction cycle (damped Jacobi: opts->smoother must be
+ * SBM_JACOBI; on SBM_MIXED grids its stencil products and base V-cycle run in FP32,
+ * A^T lambda and the vector updates in FP64), to relative residual opts->tol within
+ * opts->max_cycles iterations
  * (the iteration converges at the rate of the forward one); dJdpsi[a] (the
  * array or all of dJdpsi may be null): dJ/dpsi of level a's cells, packed like the
  * psi of sbm_set_psi (a = 0) / sbm_amr_set_psi (a >= 1): -lambda_c^T S_c u_c, where a

@@ -884,6 +884,21 @@ cudaError_t amr_apply_T(sbm_grid G, double *const *x, double *const *out)
     return cudaSuccess;
 }
 
+// y = K x on patch a's view, 0 elsewhere (FP64 vectors).  Inside the transposed
+// correction cycle of a mixed-precision grid the product is taken in FP32 (x
+// rounded into the patch's FP32 correction buffer, the FP32 sweep, the result
+// widened): the cycle only preconditions the adjoint iteration, whose fixed point
+// A^T lambda = g is set by the FP64 A^T alone.
+cudaError_t view_apply(sbm_grid G, Patch &Pt, const double *x, double *y, size_t n)
+{
+    CKE(cudaMemsetAsync(y, 0, sizeof(double) * n, G->st));
+    if (G->desc.precision != SBM_MIXED) return sweep_view<double>(G, Pt, kApply, x, nullptr, y, 0.0);
+    CKE(launch_round((long long)n, x, Pt.se[0], G->st));
+    CKE(cudaMemsetAsync(Pt.sres, 0, sizeof(float) * n, G->st));
+    CKE(sweep_view<float>(G, Pt, kApply, Pt.se[0], nullptr, Pt.sres, 0.0));
+    return launch_add<float>((long long)n, Pt.sres, y, G->st);
+}
+
 // One transposed (damped-Jacobi) sweep on patch a's solved dofs: eb <- eb - K_a W eb
 // and rb += W eb, with W the Jacobi scaling (the transpose of e <- e + W (r - K e)).
 cudaError_t patch_jacobiT(sbm_grid G, int a, const sbm_opts &o, double *eb, double *rb, double *t1, double *t2)
@@ -891,13 +906,13 @@ cudaError_t patch_jacobiT(sbm_grid G, int a, const sbm_opts &o, double *eb, doub
     Patch &Pt = G->P[a - 1];
     const size_t n = amr_vec_len(G, a);
     CKE(launch_amr_scaleW(Pt.s, Pt.info, Pt.psi64, o.omega, Pt.c64.kdiag, eb, t1, G->st));
-    CKE(cudaMemsetAsync(t2, 0, sizeof(double) * n, G->st));
-    CKE(sweep_view<double>(G, Pt, kApply, t1, nullptr, t2, 0.0));
+    CKE(view_apply(G, Pt, t1, t2, n));
     CKE(launch_lincomb((long long)n, 1.0, eb, -1.0, t2, 0.0, nullptr, eb, G->st));
     return launch_lincomb((long long)n, 1.0, rb, 1.0, t1, 0.0, nullptr, rb, G->st);
 }
 
-// z = B^T y: the transpose of one FP64 correction cycle (Jacobi smoother), taken
+// z = B^T y: the transpose of one correction cycle (Jacobi smoother; its stencil
+// products and base V-cycle in FP32 on mixed-precision grids, see view_apply), taken
 // step by step in reverse: the update's mask; per patch, finest first, the
 // post-smoothing sweeps transposed and the correction prolongation transposed
 // (into the parent's adjoint); the base V-cycle (symmetric); per patch, coarsest
@@ -920,12 +935,20 @@ cudaError_t amr_precondT(sbm_grid G, const sbm_opts &o, double *const *y, double
                               1, G->st));
         CKE(launch_amr_mask_solved(amr_geom(G, a), amr_info(G, a), EB[a], G->st));
     }
-    // base: rhs adjoint = V_0 (adjoint of its output)
-    CKE(cudaMemcpyAsync(B.df, EB[0], sizeof(double) * amr_vec_len(G, 0), cudaMemcpyDeviceToDevice, G->st));
-    CKE(cudaMemsetAsync(P<double>::u(B, 0), 0, level_bytes(B, sizeof(double)), G->st));
+    // base: rhs adjoint = V_0 (adjoint of its output); the FP32 V-cycle on mixed grids
+    const size_t n0 = amr_vec_len(G, 0);
     int cb = 0;
-    CKE(vcycle<double>(G, G->nl - 1, cb, o, B.df));
-    CKE(launch_lincomb((long long)amr_vec_len(G, 0), 1.0, z[0], 1.0, P<double>::u(B, cb), 0.0, nullptr, z[0], G->st));
+    if (G->desc.precision == SBM_MIXED) {
+        CKE(launch_round((long long)n0, EB[0], B.sf, G->st));
+        CKE(cudaMemsetAsync(P<float>::u(B, 0), 0, level_bytes(B, sizeof(float)), G->st));
+        CKE(vcycle<float>(G, G->nl - 1, cb, o, B.sf));
+        CKE(launch_add<float>((long long)n0, P<float>::u(B, cb), z[0], G->st));
+    } else {
+        CKE(cudaMemcpyAsync(B.df, EB[0], sizeof(double) * n0, cudaMemcpyDeviceToDevice, G->st));
+        CKE(cudaMemsetAsync(P<double>::u(B, 0), 0, level_bytes(B, sizeof(double)), G->st));
+        CKE(vcycle<double>(G, G->nl - 1, cb, o, B.df));
+        CKE(launch_lincomb((long long)n0, 1.0, z[0], 1.0, P<double>::u(B, cb), 0.0, nullptr, z[0], G->st));
+    }
     for (int a = 1; a <= A; ++a) {
         // restriction onto the covered parent nodes, transposed: residual adjoint
         CKE(launch_amr_restrictT(amr_geom(G, a), amr_info(G, a), amr_geom(G, a - 1), amr_info(G, a - 1), z[a - 1],
@@ -934,8 +957,7 @@ cudaError_t amr_precondT(sbm_grid G, const sbm_opts &o, double *const *y, double
         // residual r = rhs - K e (solved dofs): rhs_adj += res_adj, e_adj -= K res_adj
         const size_t n = amr_vec_len(G, a);
         CKE(launch_lincomb((long long)n, 1.0, z[a], 1.0, T1[a], 0.0, nullptr, z[a], G->st));
-        CKE(cudaMemsetAsync(T2[a], 0, sizeof(double) * n, G->st));
-        CKE(sweep_view<double>(G, G->P[a - 1], kApply, T1[a], nullptr, T2[a], 0.0));
+        CKE(view_apply(G, G->P[a - 1], T1[a], T2[a], n));
         CKE(launch_lincomb((long long)n, 1.0, EB[a], -1.0, T2[a], 0.0, nullptr, EB[a], G->st));
         for (int s_ = 0; s_ < o.nu1; ++s_) CKE(patch_jacobiT(G, a, o, EB[a], z[a], T1[a], T2[a]));
     }
