@@ -10,7 +10,7 @@ import pytest
 
 import oracle
 import workloads as W
-from _amr import cells_inside_domain, dense_solve, dense_system, level_coords
+from _amr import cells_inside_domain, dense_solve, dense_system, dirichlet_dof, level_coords
 
 
 def _amr(dim, n0, boxes, moduli=(1.0, 0.6, 0.5), bits=(0, 0, 0)):
@@ -289,3 +289,45 @@ def test_composite_gradient_matches_central_differences(oracle_lib, dim, n0, box
     assert grads[0][cid] == 0.0
     assert checked >= 2 * A.nlev
 
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_composite_residual_is_affine_in_the_owned_values(oracle_lib, dim):
+    """The two properties a correction cycle of the composite problem rests on:
+    the residual depends on the owned values only (ghosts and covered parents are
+    re-derived by the fill), and it is affine in them, r(u + e) = r(u) + r_0(e) with
+    r_0 the residual for a zero load (e is zero on the Dirichlet dofs here, as a
+    correction is)."""
+    boxes = [((2, 2, 2)[:dim], (10, 12, 10)[:dim]), ((6, 8, 6)[:dim], (16, 18, 16)[:dim])]
+    A = _amr(dim, 9, boxes, bits=(1, 1 | 4, 1))
+    rng = np.random.default_rng(40 + dim)
+    psis = _psi(A, lambda X, Y, Z: 0.2 + 0.8 * np.abs(np.sin(7 * X + 3 * Y + 5 * Z)))
+    fs = [rng.uniform(-1, 1, A.level_problem(a).ndofs) for a in range(A.nlev)]
+    zeros = _zeros(A)
+    us = [rng.uniform(-1, 1, A.level_problem(a).ndofs) for a in range(A.nlev)]
+    e = [rng.uniform(-1, 1, A.level_problem(a).ndofs) for a in range(A.nlev)]
+    nonowned = []
+    for a in range(A.nlev):
+        P = A.level_problem(a)
+        X, Y, Z = level_coords(A, a)
+        for n in range(P.nnodes):
+            g = (int(X[n]), int(Y[n]), int(Z[n]))
+            own = A.owned(a, *g)
+            for p in range(dim):
+                if own and dirichlet_dof(A, a, g, p):
+                    e[a][p * P.nnodes + n] = 0.0
+                if not own:
+                    nonowned.append((a, p * P.nnodes + n))
+    r_u = oracle.amr_residual(A, psis, fs, [u.copy() for u in us])
+    r_ue = oracle.amr_residual(A, psis, fs, [u + d for u, d in zip(us, e)])
+    r0_e = oracle.amr_residual(A, psis, zeros, [d.copy() for d in e])
+    scale = max(np.abs(r).max() for r in r_u)
+    for a in range(A.nlev):
+        assert np.abs(r_ue[a] - (r_u[a] + r0_e[a])).max() <= 1e-12 * scale, a
+    # values off the owned dofs do not enter
+    junk = [u.copy() for u in us]
+    for a, i in nonowned:
+        junk[a][i] += 3.0
+    r_junk = oracle.amr_residual(A, psis, fs, junk)
+    for a in range(A.nlev):
+        assert np.array_equal(r_junk[a], r_u[a]), a
