@@ -196,9 +196,10 @@ cudaError_t sweep(sbm_grid G, int l, int mode, const T *u, const T *f, T *out, d
     return launch_sweep<T, T>(mode, a, G->st);
 }
 
-// FP32 3D sweeps: small levels (no norm wanted) use the per-node kernel; larger
-// ones whose input is one of the level's TMA-described buffers the TMA +
-// packed-FP32x2 block kernel; everything else the generic kernel.
+// FP32 3D sweeps: levels of at most kNodeKernelMaxNodes nodes (no norm wanted) use
+// the cell-parallel per-node kernel; larger ones whose input is one of the level's
+// TMA-described buffers the TMA + packed-FP32x2 block kernel; everything else the
+// generic kernel.
 template <>
 cudaError_t sweep<float>(sbm_grid G, int l, int mode, const float *u, const float *f, float *out, double *part,
                          double omega)
