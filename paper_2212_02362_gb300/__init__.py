@@ -193,6 +193,10 @@ class Grid:
         return arr
 
     def amr_solve(self, us, raise_on_fail: bool = True, **opts) -> SolveInfo:
+        """Composite solve of the patch hierarchy; us[a] = level a's nodes (base
+        packed, patches on their padded boxes), in: initial guess, out: solution.
+        On mixed-precision grids ``inner_cycles`` FP32 correction cycles run per
+        FP64 composite residual."""
         o = make_opts(**opts)
         info, hist = self._info(o.max_cycles)
         st = lib().sbm_amr_solve(self._h, self._ptr_array(us), C.byref(o), C.byref(info))
