@@ -357,8 +357,8 @@ def run_ours(args, rank, world, local_rank):
     if args.traffic is not None:
         roof["traffic"] = args.traffic
     elif args.workload == "damage_3d_129" and args.roofline_kernel == "jacobi":
-        # dram__bytes_read.sum + dram__bytes_write.sum of this launch in the ncu capture
-        # summarised in profiles/k_sweep3_f2_jacobi_damage129.md
+        # dram__bytes_read.sum + dram__bytes_write.sum of this launch in an ncu capture
+        # of the same kernel on the same workload (one launch after an L2 flush)
         roof["traffic"] = 68.3e6
 
     # ---- plain FP64 solve of the same problem ----

@@ -85,6 +85,7 @@ class Grid:
         self._check(lib().sbm_grid_levels(self._h, C.byref(nl)))
         self.nlevels = nl.value
         self.psi_min = None
+        self.psi_version = 0      # bumped whenever the grid's psi changes
 
     # -- bookkeeping
     def _check(self, st, allow=(SBM_OK,)):
@@ -123,10 +124,12 @@ class Grid:
     def set_psi(self, psi: torch.Tensor, psi_min: float):
         self._check(lib().sbm_set_psi(self._h, self.finest, _ptr(psi), psi_min))
         self.psi_min = psi_min
+        self.psi_version += 1
 
     def set_density(self, rho: torch.Tensor, psi_min: float, q: float = 3.0):
         self._check(lib().sbm_set_density(self._h, self.finest, _ptr(rho), psi_min, q))
         self.psi_min = psi_min
+        self.psi_version += 1
 
     def set_moduli(self, kind: int, params):
         arr = (C.c_double * 3)(*[float(v) for v in (list(params) + [0.0, 0.0, 0.0])[:3]])
@@ -181,6 +184,7 @@ class Grid:
 
     def amr_set_psi(self, a: int, psi: torch.Tensor, psi_min: float):
         self._check(lib().sbm_amr_set_psi(self._h, a, _ptr(psi), psi_min))
+        self.psi_version += 1
 
     def amr_set_source(self, a: int, f: torch.Tensor):
         self._check(lib().sbm_amr_set_source(self._h, a, _ptr(f)))
@@ -283,20 +287,28 @@ class SBMSolve(torch.autograd.Function):
     forward(rho, grid, u0, opts): sets the SIMP stiffness psi = psi_min + (1 - psi_min)
     rho^q on the grid (grid.psi_min, grid.q), solves from u0 and returns u.
     backward: the incoming dL/du is the right-hand side of the adjoint multigrid
-    solve; the fused kernel returns dL/drho = -p'(rho) lambda_c^T S_c u_c.
+    solve; the fused kernel returns dL/drho = -p'(rho) lambda_c^T S_c u_c.  The
+    density of the forward pass is saved with the solution: when the grid's psi
+    has changed since (another forward on the same grid), backward sets it again
+    before the adjoint solve.
     """
 
     @staticmethod
     def forward(ctx, rho, grid, u0, opts):
-        grid.set_density(rho.detach().contiguous(), grid.psi_min, getattr(grid, "q", 3.0))
+        rho_c = rho.detach().contiguous()
+        q = getattr(grid, "q", 3.0)
+        grid.set_density(rho_c, grid.psi_min, q)
         u = u0.detach().clone().contiguous()
         grid.solve(u, **(opts or {}))
-        ctx.grid, ctx.opts = grid, opts
-        ctx.save_for_backward(u)
+        ctx.grid, ctx.opts, ctx.q, ctx.psi_min = grid, opts, q, grid.psi_min
+        ctx.version = grid.psi_version
+        ctx.save_for_backward(u, rho_c)
         return u
 
     @staticmethod
     def backward(ctx, grad_u):
-        (u,) = ctx.saved_tensors
+        u, rho = ctx.saved_tensors
+        if ctx.grid.psi_version != ctx.version:
+            ctx.grid.set_density(rho, ctx.psi_min, ctx.q)
         _, _, grho, _ = ctx.grid.adjoint(u, grad_u.contiguous(), want_rho=True, **(ctx.opts or {}))
         return grho, None, None, None

@@ -7,7 +7,7 @@
 
 namespace sbm {
 
-long long g_launches = 0;
+thread_local long long g_launches = 0;
 
 namespace {
 

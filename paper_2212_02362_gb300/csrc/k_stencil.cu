@@ -516,12 +516,9 @@ static cudaError_t launch_mode(const SweepArgs<T, TO> &a0, cudaStream_t s)
     if (a.g.dim == 3 && sizeof(T) == 8) {
         sweep_grid_dp(a.g, grid, &a.kchunk);
         const size_t sm = smem_dp();
-        static bool attr_dp = false;
-        if (!attr_dp) {
-            cudaError_t e = cudaFuncSetAttribute(k_sweep3_dp<TO, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-            if (e != cudaSuccess) return e;
-            attr_dp = true;
-        }
+        static std::atomic<unsigned long long> attr_dp{0};
+        cudaError_t ea = smem_attr_once(reinterpret_cast<const void *>(k_sweep3_dp<TO, MODE>), sm, attr_dp);
+        if (ea != cudaSuccess) return ea;
         cudaError_t e = launch_pdl(k_sweep3_dp<TO, MODE>, dim3(grid[0], grid[1], grid[2]), dim3(TXD + 1, TYD + 1), sm, s,
                                    reinterpret_cast<const SweepArgs<double, TO> &>(a));
         if (e != cudaSuccess) return e;
@@ -531,12 +528,9 @@ static cudaError_t launch_mode(const SweepArgs<T, TO> &a0, cudaStream_t s)
     sweep_grid(a.g, grid, &a.kchunk);
     if (a.g.dim == 3) {
         const size_t sm = smem3<T>();
-        static bool attr_done = false;
-        if (!attr_done) {
-            cudaError_t e = cudaFuncSetAttribute(k_sweep3<T, TO, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-            if (e != cudaSuccess) return e;
-            attr_done = true;
-        }
+        static std::atomic<unsigned long long> attr_done{0};
+        cudaError_t ea = smem_attr_once(reinterpret_cast<const void *>(k_sweep3<T, TO, MODE>), sm, attr_done);
+        if (ea != cudaSuccess) return ea;
         cudaError_t e = launch_pdl(k_sweep3<T, TO, MODE>, dim3(grid[0], grid[1], grid[2]), dim3(TX3 + 1, TY3 + 1), sm, s, a);
         if (e != cudaSuccess) return e;
     } else {

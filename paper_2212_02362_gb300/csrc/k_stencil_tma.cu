@@ -389,13 +389,10 @@ static cudaError_t launch_f2_mode(const SweepArgs<float, float> &a0, const CUten
     SweepArgs<float, float> a = a0;
     int grid[3];
     sweep_grid_f2(a.g, grid, &a.kchunk);
-    static bool attr_done = false;
+    static std::atomic<unsigned long long> attr_done{0};
     const size_t sm = smem_f2();
-    if (!attr_done) {
-        cudaError_t e = cudaFuncSetAttribute(k_sweep3_f2<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        if (e != cudaSuccess) return e;
-        attr_done = true;
-    }
+    cudaError_t ea = smem_attr_once(reinterpret_cast<const void *>(k_sweep3_f2<MODE>), sm, attr_done);
+    if (ea != cudaSuccess) return ea;
     cudaError_t e = launch_pdl(k_sweep3_f2<MODE>, dim3(grid[0], grid[1], grid[2]), dim3(BXP, BYP), sm, s, tmap[0], tmap[1],
                                tmap[2], a, org, err);
     if (e != cudaSuccess) return e;

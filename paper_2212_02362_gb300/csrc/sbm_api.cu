@@ -19,6 +19,17 @@
 
 using namespace sbm;
 
+bool sbm::is_dev_ptr(const void *p, int dev)
+{
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) && a.device == dev;
+}
+
 namespace {
 
 thread_local std::string g_lib_error;
@@ -139,17 +150,6 @@ sbm_status fail(sbm_grid G, sbm_status st, const std::string &msg)
         cudaError_t e_ = (__VA_ARGS__);           \
         if (e_ != cudaSuccess) return e_;         \
     } while (0)
-
-bool is_dev_ptr(const void *p, int dev)
-{
-    if (!p) return false;
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) && a.device == dev;
-}
 
 long long nnodes(const Geom &g) { return (long long)g.nx * g.ny * g.nz; }
 long long ncells_h(const Geom &g) { return (long long)(g.nx - 1) * (g.ny - 1) * (g.dim == 3 ? g.nz - 1 : 1); }
@@ -1426,9 +1426,7 @@ sbm_status sbm_set_moduli(sbm_grid G, int kind, const double p[3])
     } else {
         return fail(G, SBM_ERR_ARG, "unknown moduli kind");
     }
-    if (!std::isfinite(c11) || !std::isfinite(c12) || !std::isfinite(c44) || !(c44 > 0.0) || !(c11 > std::fabs(c12)))
-        return fail(G, SBM_ERR_ARG, "moduli are not positive definite");
-    if (G->desc.dim == 3 && !(c11 + 2.0 * c12 > 0.0)) return fail(G, SBM_ERR_ARG, "moduli are not positive definite");
+    if (!moduli_definite(G->desc.dim, c11, c12, c44)) return fail(G, SBM_ERR_ARG, "moduli are not positive definite");
     CK(cudaSetDevice(G->dev));
     G->mod[0] = c11;
     G->mod[1] = c12;

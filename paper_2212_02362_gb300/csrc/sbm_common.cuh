@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "sbm_cell.cuh"
 
 namespace sbm {
@@ -126,8 +128,37 @@ inline int choose_chunks(long long xy, int nzc, int slots, bool pair)
 
 // ---- launchers (defined in k_stencil.cu / k_misc.cu) ----------------------
 
-// Number of kernels the launchers have enqueued (graph capture included).
-extern long long g_launches;
+// Number of kernels the launchers have enqueued from the calling host thread
+// (graph capture included).  Entry points report the difference over a call, so
+// the counter is per thread: handles used from different threads do not mix.
+extern thread_local long long g_launches;
+
+// Raise a kernel's dynamic shared-memory limit on the current device.  The
+// attribute belongs to the device context, so it is set once per device (bit
+// `dev` of `done`); setting it twice from racing threads is harmless.
+inline cudaError_t smem_attr_once(const void *kernel, size_t bytes, std::atomic<unsigned long long> &done)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = (dev >= 0 && dev < 64) ? (1ull << dev) : 0ull;
+    if (bit && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess && bit) done.fetch_or(bit, std::memory_order_release);
+    return e;
+}
+
+// True when p is device (or managed) memory of device dev (sbm_api.cu).
+bool is_dev_ptr(const void *p, int dev);
+
+// Axis-aligned cubic moduli (C11, C12, C44) give a positive-definite stiffness:
+// finite, C44 > 0, C11 > |C12|, and in 3D C11 + 2 C12 > 0 (the bulk mode).
+inline bool moduli_definite(int dim, double c11, double c12, double c44)
+{
+    const bool fin = c11 - c11 == 0.0 && c12 - c12 == 0.0 && c44 - c44 == 0.0;   // finite (no NaN / Inf)
+    if (!fin || !(c44 > 0.0) || !(c11 > (c12 < 0 ? -c12 : c12))) return false;
+    return dim != 3 || c11 + 2.0 * c12 > 0.0;
+}
 
 // Message returned by sbm_last_error(NULL) (defined in sbm_api.cu).
 void set_library_error(const char *msg);

@@ -58,7 +58,8 @@ extern "C" sbm_status sbm_residual_noalloc(int dim, const int n[3], double h, co
     if (n[0] < 2 || n[1] < 2 || (dim == 3 && n[2] < 2) || (dim == 2 && n[2] != 1))
         return fail(SBM_ERR_ARG, "node counts must be >= 2 (n[2] == 1 in 2D)");
     if (!(h > 0.0) || !std::isfinite(h)) return fail(SBM_ERR_ARG, "h must be positive");
-    if (!(moduli[2] > 0.0) || !(moduli[0] > std::fabs(moduli[1]))) return fail(SBM_ERR_ARG, "moduli are not positive definite");
+    if (!moduli_definite(dim, moduli[0], moduli[1], moduli[2]))
+        return fail(SBM_ERR_ARG, "moduli are not positive definite");
     Geom g{};
     g.dim = dim;
     g.nx = n[0];
@@ -77,6 +78,10 @@ extern "C" sbm_status sbm_residual_noalloc(int dim, const int n[3], double h, co
     }
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return fail(SBM_ERR_CUDA, "cudaGetDevice failed");
+    // every array must be memory of the current device: a host pointer or another
+    // GPU's pointer is refused here instead of reaching the kernel
+    if (!is_dev_ptr(psi, dev) || !is_dev_ptr(f, dev) || !is_dev_ptr(u, dev) || !is_dev_ptr(r, dev))
+        return fail(SBM_ERR_ARG, "psi, f, u and r must be device memory of the current device");
     double *scratch = nullptr;
     cudaError_t e = scratch_address(dev, &scratch);
     if (e != cudaSuccess) return fail(SBM_ERR_CUDA, cudaGetErrorString(e));

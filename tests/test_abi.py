@@ -56,3 +56,32 @@ def test_status_strings_and_null_handles(libpath):
     lib.sbm_default_opts(ctypes.byref(o))
     assert o.tol == 1e-10 and o.max_cycles == 500 and o.nu1 == 2 and o.nu2 == 2
     assert abs(o.omega - 2.0 / 3.0) < 1e-15
+
+
+def test_noalloc_argument_checks_run_on_the_host(libpath):
+    # sbm_residual_noalloc validates sizes and moduli before any CUDA call, with the
+    # same moduli rule as sbm_set_moduli (3D bulk mode: C11 + 2 C12 > 0; finite)
+    import numpy as np
+    from paper_2212_02362_gb300 import _capi
+    lib = _capi.load(libpath)
+    buf = np.zeros(8)
+    p = buf.ctypes.data_as(ctypes.c_void_p)
+    bits = (ctypes.c_uint * 3)(0, 0, 0)
+    nrm = ctypes.c_double()
+
+    def call(dim, n, h, mod):
+        return lib.sbm_residual_noalloc(dim, (ctypes.c_int * 3)(*n), h, (ctypes.c_double * 3)(*mod), bits,
+                                        p, p, p, p, ctypes.byref(nrm), None)
+
+    for mod in [(1.0, -0.6, 0.5), (float("inf"), 0.6, 0.5), (1.0, 0.6, 0.0), (0.5, 0.6, 0.5)]:
+        assert call(3, (9, 9, 9), 0.125, mod) == _capi.SBM_ERR_ARG, mod
+        assert b"positive definite" in lib.sbm_last_error(None)
+    # the same cubic moduli are definite in plane strain (no bulk condition in 2D)
+    assert call(2, (9, 9, 1), 0.125, (1.0, -0.6, 0.5)) != _capi.SBM_ERR_ARG or \
+        b"positive definite" not in lib.sbm_last_error(None)
+    assert call(3, (1, 9, 9), 0.125, (1.0, 0.6, 0.5)) == _capi.SBM_ERR_ARG
+    assert call(3, (9, 9, 9), 0.0, (1.0, 0.6, 0.5)) == _capi.SBM_ERR_ARG
+    assert call(4, (9, 9, 9), 0.125, (1.0, 0.6, 0.5)) == _capi.SBM_ERR_ARG
+    # beyond the fixed scratch: rejected before the device is touched
+    assert call(2, (4097, 4097, 1), 1.0 / 4096, (1.0, 0.6, 0.5)) == _capi.SBM_ERR_ARG
+    assert b"fixed scratch" in lib.sbm_last_error(None)

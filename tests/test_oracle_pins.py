@@ -487,3 +487,25 @@ def test_mg_converges_on_plate_hole(oracle_lib):
     assert res.status == 0
     assert res.cycles < 200
     assert np.all(np.diff(res.history) < 0)
+
+
+@pytest.mark.parametrize("dim,n,bits", [(2, (9, 7, 1), (1 | 8, 4, 0)), (3, (5, 6, 7), (16 | 2, 32, 1 | 4 | 8))])
+def test_norm_free_is_the_2norm_over_free_dofs(oracle_lib, dim, n, bits):
+    """The residual norm of the stopping rule (D6b): the Euclidean norm over the
+    dofs that carry no Dirichlet condition.  The mask is built here from the face
+    numbering (0:-x 1:+x 2:-y 3:+y 4:-z 5:+z) alone, and huge values planted on the
+    Dirichlet dofs must not count."""
+    oracle = oracle_lib
+    P = _prob(oracle, dim, n, bits=bits)
+    r = W.uniform(91, P.ndofs, -1.0, 1.0)
+    k, j, i = np.meshgrid(np.arange(n[2]), np.arange(n[1]), np.arange(n[0]), indexing="ij")
+    on_face = [i == 0, i == n[0] - 1, j == 0, j == n[1] - 1, k == 0, k == n[2] - 1]
+    mask = np.zeros((dim,) + i.shape, dtype=bool)
+    for p in range(dim):
+        for f in range(2 * dim):
+            if bits[p] >> f & 1:
+                mask[p] |= on_face[f]
+    mask = mask.reshape(-1)
+    assert mask.any() and not mask.all()
+    r[mask] = 1e6
+    assert np.isclose(oracle.norm_free(P, r), np.linalg.norm(r[~mask]), rtol=1e-14, atol=0)

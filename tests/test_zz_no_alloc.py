@@ -1,5 +1,6 @@
-"""sbm_residual_noalloc: the allocation-free residual + norm gives what the grid
-entry point sbm_residual gives, on two calls in a row.
+"""sbm_residual_noalloc: the allocation-free residual + norm gives the oracle's
+FP64 residual r = f - K u and norm (and what the grid entry point sbm_residual
+gives), on two calls in a row.
 
 The call exists for callers that cannot allocate device memory (a host program
 whose device memory belongs to its own pool, code that must not trigger the
@@ -63,23 +64,47 @@ def _noalloc(wk, psi_d, f_d, u_d, r_d):
 
 
 @pytest.mark.parametrize("case", list(CASES))
-def test_noalloc_residual_matches_grid_residual(built, case):
+def test_noalloc_residual_matches_oracle_and_grid_residual(built, case):
     wk = CASES[case]()
-    g = gpu_grid(wk)
     P = oracle.Problem(wk.dim, wk.n, wk.h, *wk.moduli, dirichlet=wk.dirichlet_bits())
     mask = oracle.dirichlet_mask(P)
     u = wk.u0 + W.uniform(31, P.ndofs, -1e-3, 1e-3) * ~mask
+    # the plain FP64 definition r = f - K u on free dofs (the oracle) ...
+    r_ora = oracle.residual(P, oracle.floor_psi(wk.psi, wk.psi_min), wk.f, u)
+    n_ora = oracle.norm_free(P, r_ora)
+    # ... and the grid entry point, which runs the same kernel through a handle
+    g = gpu_grid(wk)
     f_d, u_d = cuda(wk.f), cuda(u)
-    r_ref, n_ref = g.residual(g.finest, f_d, u_d)
-    r_ref = host(r_ref)
+    r_grid, n_grid = g.residual(g.finest, f_d, u_d)
+    r_grid = host(r_grid)
     psi_d = cuda(_node_indexed_psi(wk))
     for call in range(2):                              # two calls in a row share the scratch
         r_d = torch.full_like(u_d, float("nan"))
         st, nrm = _noalloc(wk, psi_d, f_d, u_d, r_d)
         assert st == _capi.SBM_OK, sbm.lib().sbm_last_error(None)
         r = host(r_d)
-        assert np.abs(r - r_ref).max() <= 1e-12 * np.abs(r_ref).max(), call
-        assert abs(nrm - n_ref) <= 1e-12 * n_ref, (call, nrm, n_ref)
+        assert np.abs(r - r_ora).max() <= 1e-12 * np.abs(r_ora).max(), call
+        assert abs(nrm - n_ora) <= 1e-12 * n_ora, (call, nrm, n_ora)
+        assert np.abs(r - r_grid).max() <= 1e-12 * np.abs(r_grid).max(), call
+        assert abs(nrm - n_grid) <= 1e-12 * n_grid, (call, nrm, n_grid)
+
+
+def test_noalloc_rejects_host_pointers(built):
+    # a host buffer where device memory is required is refused before any launch
+    wk = W.damage3d(17)
+    P = oracle.Problem(wk.dim, wk.n, wk.h, *wk.moduli, dirichlet=wk.dirichlet_bits())
+    psi_d, f_d, u_d = cuda(_node_indexed_psi(wk)), cuda(wk.f), cuda(wk.u0)
+    r_h = np.zeros(P.ndofs)
+    n = (C.c_int * 3)(*wk.n)
+    mod = (C.c_double * 3)(*wk.moduli)
+    bits = (C.c_uint * 3)(*wk.dirichlet_bits())
+    nrm = C.c_double(-1.0)
+    st = sbm.lib().sbm_residual_noalloc(wk.dim, n, wk.h, mod, bits, psi_d.data_ptr(), f_d.data_ptr(),
+                                         u_d.data_ptr(), r_h.ctypes.data_as(C.c_void_p), C.byref(nrm), None)
+    assert st == _capi.SBM_ERR_ARG
+    assert b"device memory" in sbm.lib().sbm_last_error(None)
+    assert np.all(r_h == 0.0) and nrm.value == -1.0
+    torch.cuda.synchronize()                           # the context is still usable
 
 
 def test_noalloc_rejects_grids_beyond_the_scratch(built):
