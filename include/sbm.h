@@ -193,9 +193,10 @@ enum { SBM_K_RESIDUAL64 = 0, SBM_K_JACOBI = 1, SBM_K_RESIDUAL = 2 };
  * Bytes count one read of u, f and psi and one write of the output per node;
  * flops count the sum-factorised cell arithmetic per cell plus the per-node
  * gather and update.  flush_l2 != 0: before every launch a 256 MB scratch buffer
- * (allocated for the call) is written so that the launch reads its inputs from
- * HBM, and each launch is timed by its own pair of events.  Uses the level's work
- * buffers (overwrites them). */
+ * (allocated for the call) is written and a second 256 MB buffer read, so that the
+ * launch reads its inputs from HBM and finds no dirty lines of other data in L2
+ * (their write-back would be charged to it); each launch is timed by its own pair
+ * of events.  Uses the level's work buffers (overwrites them). */
 sbm_status sbm_time_kernel(sbm_grid grid, int which, int reps, int flush_l2, double *ms_per_launch,
                            double *bytes_per_launch, double *flops_per_launch);
 

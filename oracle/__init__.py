@@ -283,7 +283,14 @@ _AMR_SIGS = {
                             [C.c_long, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
                              C.POINTER(C.c_double)]),
     "orc_amr_dJdpsi": (None, [C.POINTER(_Amr)] + [C.POINTER(C.POINTER(C.c_double))] * 3),
+    "orc_amr_solve": (C.c_int, [C.POINTER(_Amr)] + [C.POINTER(C.POINTER(C.c_double))] * 3 +
+                      [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int)]),
 }
+
+
+class _AmrOpts(C.Structure):
+    _fields_ = [("nu1", C.c_int), ("nu2", C.c_int), ("omega", C.c_double), ("omega_base", C.c_double),
+                ("smoother_base", C.c_int), ("tol", C.c_double), ("max_cycles", C.c_int)]
 
 
 def _La():
@@ -387,3 +394,18 @@ def amr_residual(A: Amr, psis, fs, us):
     rs = [np.zeros_like(u) for u in us]
     _La().orc_amr_residual(C.byref(A.c()), _ptrs(psis), _ptrs(fs), _ptrs(us), _ptrs(rs))
     return rs
+
+
+def amr_solve(A: Amr, psis, fs, us, *, omega=0.5, omega_base=None, smoother_base="jacobi", nu1=2, nu2=2,
+              tol=1e-14, max_cycles=200):
+    """Composite solve by the oracle's correction iteration (orc_amr_solve): us
+    (level arrays, initial guess with the Dirichlet values) are solved in place and
+    filled.  psis must already hold the coarse means under the patches.  Returns a
+    result with status, cycles and the relres history."""
+    o = _AmrOpts(nu1, nu2, omega, omega if omega_base is None else omega_base,
+                 1 if smoother_base in ("gs", "mcgs") else 0, tol, max_cycles)
+    hist = np.zeros(max_cycles + 1)
+    cyc = C.c_int()
+    st = _La().orc_amr_solve(C.byref(A.c()), _ptrs(psis), _ptrs(fs), _ptrs(us), C.cast(C.byref(o), C.c_void_p),
+                             hist.ctypes.data_as(C.POINTER(C.c_double)), C.byref(cyc))
+    return MGResult(us, st, cyc.value, hist[: cyc.value + 1])

@@ -967,3 +967,225 @@ void orc_amr_dJdpsi(const orc_amr *A, double *const *u, double *const *lam, doub
     }
 }
 
+
+/* ------------------------------------------------- composite correction iteration */
+
+/* Level a's storage psi with the padding cells beyond the domain zeroed (they are
+ * not part of the body), as orc_amr_residual uses it. */
+static double *amr_body_psi(const orc_amr *A, int a, const double *psi_a)
+{
+    orc_problem P;
+    orc_amr_level_problem(A, a, &P);
+    const int d = A->base.dim;
+    const long nc = orc_ncells(&P);
+    const int ncx = P.n[0] - 1, ncy = P.n[1] - 1;
+    double *pa = malloc(sizeof(double) * nc);
+    for (long c = 0; c < nc; ++c) {
+        const int C[3] = {(int)(c % ncx), (int)((c / ncx) % ncy), (int)(c / ((long)ncx * ncy))};
+        int in = 1;
+        for (int ax = 0; ax < d; ++ax) {
+            const int gc = a ? C[ax] + A->lo[a][ax] - 1 : C[ax];
+            if (gc < 0 || gc > amr_N(A, a, ax) - 2) in = 0;
+        }
+        pa[c] = in ? psi_a[c] : 0.0;
+    }
+    return pa;
+}
+
+/* Damped Jacobi sweeps on K_a e = rhs over the free dofs of level a's solve region
+ * (owned and covered nodes); every other value of e is held fixed. */
+static void amr_masked_jacobi(const orc_amr *A, int a, const double *pa, const double *rhs, double *e,
+                              double omega, int nsweeps)
+{
+    orc_problem P;
+    orc_amr_level_problem(A, a, &P);
+    const int d = A->base.dim;
+    const long N = orc_nnodes(&P);
+    double *Ke = malloc(sizeof(double) * d * N), *D = malloc(sizeof(double) * d * N);
+    orc_diagonal(&P, pa, D);
+    for (int s = 0; s < nsweeps; ++s) {
+        orc_apply(&P, pa, e, Ke);
+        AMR_FOR_NODES(A, a, P, g, loc) {
+            if (!amr_box_owned(A, a, g)) continue;
+            for (int p = 0; p < d; ++p) {
+                if (amr_dirichlet(A, a, g, p)) continue;
+                const long q = p * N + loc;
+                e[q] += omega * (rhs[q] - Ke[q]) / D[q];
+            }
+        }
+    }
+    free(Ke);
+    free(D);
+}
+
+/* res = rhs - K_a e on the free dofs of level a's solve region, 0 elsewhere. */
+static void amr_region_residual(const orc_amr *A, int a, const double *pa, const double *rhs, const double *e,
+                                double *res)
+{
+    orc_problem P;
+    orc_amr_level_problem(A, a, &P);
+    const int d = A->base.dim;
+    const long N = orc_nnodes(&P);
+    orc_apply(&P, pa, e, res);
+    AMR_FOR_NODES(A, a, P, g, loc) {
+        const int in = amr_box_owned(A, a, g);
+        for (int p = 0; p < d; ++p) {
+            const long q = p * N + loc;
+            res[q] = (in && !amr_dirichlet(A, a, g, p)) ? rhs[q] - res[q] : 0.0;
+        }
+    }
+}
+
+/* rhs_c at the level a-1 nodes covered by level a += R res_a, R = P^T / 2^d (full
+ * weighting about the coincident fine node); Dirichlet dofs are left alone. */
+static void amr_restrict_covered(const orc_amr *A, int a, const double *res, double *rhs_c)
+{
+    orc_problem Pf, Pc;
+    orc_amr_level_problem(A, a, &Pf);
+    orc_amr_level_problem(A, a - 1, &Pc);
+    const int d = A->base.dim;
+    const long Nf = orc_nnodes(&Pf), Nc = orc_nnodes(&Pc);
+    AMR_FOR_NODES(A, a - 1, Pc, gc, locc) {
+        if (!amr_covered(A, a - 1, gc)) continue;
+        for (int p = 0; p < d; ++p) {
+            if (amr_dirichlet(A, a - 1, gc, p)) continue;
+            double s = 0.0;
+            for (int dk = (d == 3 ? -1 : 0); dk <= (d == 3 ? 1 : 0); ++dk)
+                for (int dj = -1; dj <= 1; ++dj)
+                    for (int di = -1; di <= 1; ++di) {
+                        int gf[3] = {2 * gc[0] + di, 2 * gc[1] + dj, d == 3 ? 2 * gc[2] + dk : 0};
+                        const long lf = amr_local(A, a, gf);
+                        if (lf < 0) continue;
+                        s += pw(di) * pw(dj) * (d == 3 ? pw(dk) : 1.0) * res[p * Nf + lf];
+                    }
+            rhs_c[p * Nc + locc] += s / (double)(1 << d);
+        }
+    }
+}
+
+/* e_a += P e_{a-1} at every storage node of level a inside the domain
+ * ((bi/tri)linear interpolation, coincident nodes copy). */
+static void amr_interpolate_add(const orc_amr *A, int a, const double *ec, double *ef)
+{
+    orc_problem Pf, Pc;
+    orc_amr_level_problem(A, a, &Pf);
+    orc_amr_level_problem(A, a - 1, &Pc);
+    const int d = A->base.dim;
+    const long Nf = orc_nnodes(&Pf), Nc = orc_nnodes(&Pc);
+    AMR_FOR_NODES(A, a, Pf, g, loc) {
+        int outside = 0, nodd = 0;
+        for (int ax = 0; ax < d; ++ax) {
+            if (g[ax] < 0 || g[ax] > amr_N(A, a, ax) - 1) outside = 1;
+            nodd += g[ax] & 1;
+        }
+        if (outside) continue;
+        for (int p = 0; p < d; ++p) {
+            double s = 0.0;
+            for (int c = 0; c < (1 << d); ++c) {
+                int gcn[3] = {0, 0, 0}, skip = 0;
+                for (int ax = 0; ax < d; ++ax) {
+                    const int bit = (c >> ax) & 1;
+                    if (!(g[ax] & 1) && bit) skip = 1;
+                    gcn[ax] = (g[ax] >> 1) + ((g[ax] & 1) ? bit : 0);
+                }
+                if (skip) continue;
+                s += ec[p * Nc + amr_local(A, a - 1, gcn)];
+            }
+            ef[p * Nf + loc] += s / (double)(1 << nodd);
+        }
+    }
+}
+
+int orc_amr_solve(const orc_amr *A, double *const *psi, double *const *f, double *const *u,
+                  const orc_amr_opts *o, double *hist, int *cycles)
+{
+    const int L = A->nlev, d = A->base.dim;
+    double *r[8], *e[8], *rhs[8], *res[8], *pa[8];
+    long N[8];
+    for (int a = 0; a < L; ++a) {
+        orc_problem P;
+        orc_amr_level_problem(A, a, &P);
+        N[a] = orc_nnodes(&P);
+        r[a] = calloc(d * N[a], sizeof(double));
+        e[a] = calloc(d * N[a], sizeof(double));
+        rhs[a] = calloc(d * N[a], sizeof(double));
+        res[a] = calloc(d * N[a], sizeof(double));
+        pa[a] = amr_body_psi(A, a, psi[a]);
+    }
+    orc_mg_opts base = {o->nu1, o->nu2, o->omega_base, o->smoother_base, 0.0, 1};
+    double r0 = 0.0, rel = 1.0;
+    int status = 1, ncyc = 0;
+    for (;;) {
+        orc_amr_residual(A, psi, f, u, r);
+        double s = 0.0;
+        for (int a = 0; a < L; ++a)
+            for (long q = 0; q < d * N[a]; ++q) s += r[a][q] * r[a][q];
+        s = sqrt(s);
+        if (ncyc == 0) {
+            r0 = s;
+            if (hist) hist[0] = 1.0;
+            if (r0 == 0.0) {
+                status = 0;
+                break;
+            }
+        } else {
+            rel = s / r0;
+            if (hist) hist[ncyc] = rel;
+            if (!isfinite(rel) || rel > 1e10) {
+                status = 2;
+                break;
+            }
+        }
+        if (rel <= o->tol) {
+            status = 0;
+            break;
+        }
+        if (ncyc >= o->max_cycles) break;
+        /* patches, finest first: smooth the correction, residual of its equation,
+         * full weighting onto the covered parent nodes */
+        for (int a = L - 1; a >= 0; --a) {
+            memcpy(rhs[a], r[a], sizeof(double) * d * N[a]);
+            if (a + 1 < L) amr_restrict_covered(A, a + 1, res[a + 1], rhs[a]);
+            memset(e[a], 0, sizeof(double) * d * N[a]);
+            if (a == 0) break;
+            amr_masked_jacobi(A, a, pa[a], rhs[a], e[a], o->omega, o->nu1);
+            amr_region_residual(A, a, pa[a], rhs[a], e[a], res[a]);
+        }
+        /* the base level: one multigrid V-cycle on its correction equation */
+        {
+            int c1 = 0;
+            const int st = orc_mg_solve(&A->base, pa[0], rhs[0], e[0], &base, NULL, &c1);
+            if (st == 3) {
+                status = 3;
+                break;
+            }
+        }
+        /* patches, coarsest first: the parent's correction interpolated onto every
+         * node of the patch, then smoothing */
+        for (int a = 1; a < L; ++a) {
+            amr_interpolate_add(A, a, e[a - 1], e[a]);
+            amr_masked_jacobi(A, a, pa[a], rhs[a], e[a], o->omega, o->nu2);
+        }
+        /* u += e on the owned free dofs; ghosts and covered nodes follow at the next fill */
+        for (int a = 0; a < L; ++a) {
+            orc_problem P;
+            orc_amr_level_problem(A, a, &P);
+            AMR_FOR_NODES(A, a, P, g, loc) {
+                if (!orc_amr_owned(A, a, g[0], g[1], g[2])) continue;
+                for (int p = 0; p < d; ++p)
+                    if (!amr_dirichlet(A, a, g, p)) u[a][p * N[a] + loc] += e[a][p * N[a] + loc];
+            }
+        }
+        ++ncyc;
+    }
+    orc_amr_fill(A, u);
+    for (int a = 0; a < L; ++a) {
+        free(r[a]);
+        free(e[a]);
+        free(rhs[a]);
+        free(res[a]);
+        free(pa[a]);
+    }
+    if (cycles) *cycles = ncyc;
+    return status;
+}

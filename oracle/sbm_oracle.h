@@ -153,6 +153,34 @@ void orc_amr_dJdpsi(const orc_amr *A, double *const *u, double *const *lam, doub
 void orc_amr_residual_at(const orc_amr *A, double *const *psi, double *const *f, double *const *u, long n,
                          const int *lev, const int *node, const int *comp, double *r);
 
+typedef struct {
+    int nu1, nu2;          /* pre / post smoothing sweeps (every level) */
+    double omega;          /* damped-Jacobi factor on the patch levels */
+    double omega_base;     /* damping of the base-level V-cycle's smoother */
+    int smoother_base;     /* 0 = damped Jacobi, 1 = 2^d-colour Gauss-Seidel on the base level */
+    double tol;            /* stop when ||r|| / ||r0|| <= tol (composite residual, owned free dofs) */
+    int max_cycles;
+} orc_amr_opts;
+
+/* Composite solve by the correction iteration u += B (f - A u), A the composite
+ * operator above, B one correction cycle in the level order of Sec. 2.2:
+ *   - patches from the finest down: the correction e_a of level a starts at 0 and
+ *     gets nu1 damped-Jacobi sweeps on K_a e_a = rhs_a over the free dofs of the
+ *     level's solve region (owned and covered nodes; ghosts held at 0), where rhs_a
+ *     is the composite residual on the owned dofs and, on the covered nodes, the
+ *     full-weighting restriction R = P^T / 2^d of the next finer level's residual
+ *     rhs - K e after its smoothing;
+ *   - the base level: one V-cycle of orc_mg_solve on its correction equation;
+ *   - patches from the coarsest up: e_a += the (bi/tri)linear interpolation of e_{a-1}
+ *     at every patch node, then nu2 sweeps as above;
+ *   - u_a += e_a on the owned free dofs.
+ * psi must hold the coarse means under the patches (orc_amr_coarsen_psi).  The
+ * fixed point is A u = f whatever B is; B only sets the rate.  u is filled on
+ * return.  hist (max_cycles + 1 entries, may be NULL) receives relres per cycle.
+ * Returns 0 converged, 1 not converged in max_cycles, 2 diverged, 3 bottom failed. */
+int orc_amr_solve(const orc_amr *A, double *const *psi, double *const *f, double *const *u,
+                  const orc_amr_opts *o, double *hist, int *cycles);
+
 #ifdef __cplusplus
 }
 #endif

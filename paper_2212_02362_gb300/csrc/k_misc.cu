@@ -657,6 +657,25 @@ cudaError_t launch_lincomb(long long n, double a, const double *x, double b, con
     return cudaGetLastError();
 }
 
+// Measurement helper: read n4 float4 of a buffer larger than L2 (nothing is
+// written unless the impossible sum appears), so that L2 ends up holding clean
+// lines of that buffer.
+__global__ void k_l2_read(const float4 *__restrict__ a, long long n4, float *sink)
+{
+    float acc = 0.f;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n4; i += (long long)gridDim.x * blockDim.x) {
+        const float4 v = a[i];
+        acc += (v.x + v.y) + (v.z + v.w);
+    }
+    if (acc == 1234567.f) sink[0] = acc;
+}
+
+cudaError_t launch_l2_read(const void *buf, size_t bytes, float *sink, cudaStream_t s)
+{
+    k_l2_read<<<152 * 8, 256, 0, s>>>(static_cast<const float4 *>(buf), (long long)(bytes / 16), sink);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_sum_parts(const double *part, int n, double *out, cudaStream_t s)
 {
     k_sum_parts<<<1, kThreads, 0, s>>>(part, n, out);

@@ -1,24 +1,38 @@
 // k_stencil_tma.cu — FP32 3D apply / residual / damped-Jacobi sweep of the
-// cell-flux SBM elasticity operator with TMA plane staging and packed FP32x2
-// arithmetic (sm_100+ FFMA2 / FADD2 / FMUL2).
+// cell-flux SBM elasticity operator: a persistent kernel with TMA plane staging
+// and packed FP32x2 arithmetic (sm_100+ FFMA2 / FADD2 / FMUL2).
 //
-// Block = 32 x 8 cells in x/y (33 x 9 threads, one cell column each, the first
-// row/column being the one-cell halo; warps aligned with the 32-cell rows),
-// streaming a chunk of z.  Each step handles
-// two cell layers (k, k+1) at once: every thread evaluates its two cells in the
-// two lanes of the packed type, so one packed instruction does the work of two.
-// Node planes of u and f and cell layers of psi are fetched by the Tensor Memory
-// Accelerator into a 6-deep shared-memory ring (40 x 10 x 3 boxes of u and f and a
-// 40 x 10 box of psi per slot, out-of-range elements zero filled), two pairs ahead
-// of use, completion signalled by one mbarrier per slot; the compute loop issues
-// no global loads.  Corner
-// forces of both node planes a cell touches in this step are exchanged as one
-// float2 per corner and component; the top-plane forces of layer k+1 stay in
-// registers and join the next step.  Every mbarrier wait is bounded: on timeout
-// the block records an error code, waits (bounded) for its copies in flight and
-// returns.  The grid swept may sit inside a larger storage at an offset (a
-// refinement patch's view inside its padded box); the tensor maps then describe
-// the storage and each block aligns its boxes itself.
+// Work split.  The grid's cells are cut into tiles of 32 x 12 cells in x/y; a
+// tile's node planes (one per z index) are the units of work.  One CTA runs per
+// SM and owns a contiguous range of units in (tile, plane) order, so every CTA
+// finalises the same number of node planes to within one and streams them as a
+// few long z segments (a range crosses at most a couple of tile boundaries).
+// The TMA ring runs across segment boundaries without draining.
+//
+// A CTA has 33 x 13 threads, one per cell column of the tile plus the one-cell
+// halo column and row (warps aligned with the 32-cell rows, the 33rd column in a
+// warp of its own).  Each step handles two cell layers (k, k+1) in the two lanes
+// of the packed type.  The in-plane (x, y) transform of a node plane is computed
+// once and shared by the two layers it bounds (the previous plane's transform is
+// carried in registers), and the forces a layer sends to its top plane are
+// carried in the transformed basis, so a step costs two in-plane transforms and
+// two transposed ones for two cell layers.
+//
+// Ring.  Node plane p of u, the f values of the tile's own nodes on plane p and
+// cell layer p of psi are fetched by the Tensor Memory Accelerator into a 10-slot
+// shared-memory ring (zero fill outside the grid), completion on one mbarrier per
+// slot.  A step reads the raw u of planes k+1 and k+2 and the f and psi of planes
+// k and k+1 before its single block barrier, after which the slots of planes k
+// and k+1 are free and thread 0 refills them with the planes 10 sequence places
+// ahead.  The in-plane corner forces are exchanged through a double-buffered
+// shared tile (one barrier per step suffices: a buffer is written again only two
+// barriers after it was read).  The compute loop issues no global loads.
+//
+// Every mbarrier wait is bounded: on timeout the block records an error code,
+// waits (bounded) for the copies it has in flight and returns.  The grid swept may
+// sit inside a larger storage at an offset (a refinement patch's view inside its
+// padded box); the tensor maps then describe the storage and each tile aligns its
+// boxes itself.
 #include <cuda.h>
 
 #include "sbm_common.cuh"
@@ -27,23 +41,24 @@ namespace sbm {
 
 namespace {
 
-constexpr int TXP = 32, TYP = 8;                 // cells per block in x, y
-constexpr int BXP = TXP + 1, BYP = TYP + 1;      // threads per block in x, y
-constexpr int NTP = BXP * BYP;
-constexpr int PXF = TXP + 2, PYF = TYP + 2, PPF = PXF * PYF;   // exchange tiles
-constexpr int WX = 40;                           // TMA box width: 34 nodes x0-1 .. x0+32 plus alignment
-constexpr int PLANE_FLOATS = 3 * PYF * WX;       // one staged plane: 3 comps x 10 rows x 40
-constexpr int PSI_FLOATS = PYF * WX;             // one staged cell layer of psi
-// A ring slot holds node plane p of u, node plane p of f and cell layer p of psi.
-// Every TMA destination starts on a 128-byte boundary.
-constexpr int PLANE_STRIDE = (PLANE_FLOATS * 4 + 127) / 128 * 128 / 4;   // floats
-constexpr int F_OFF = PLANE_STRIDE, PSI_OFF = 2 * PLANE_STRIDE;
-constexpr int SLOT_FLOATS = ((PSI_OFF + PSI_FLOATS) * 4 + 127) / 128 * 128 / 4;
-constexpr int TX_BYTES = (2 * PLANE_FLOATS + PSI_FLOATS) * 4;           // bytes the three copies deliver
-static_assert((F_OFF * 4) % 128 == 0 && (PSI_OFF * 4) % 128 == 0 && (SLOT_FLOATS * 4) % 128 == 0,
-              "TMA destinations must be 128-byte aligned");
-constexpr int RING = 6;
+constexpr int TXP = 32, TYP = 12;                // cells per tile in x, y
+constexpr int BXP = TXP + 1, BYP = TYP + 1;      // threads per CTA in x, y
+constexpr int NTP = BXP * BYP;                   // 429: 14 warps, so 128 registers a thread
+constexpr int PXF = TXP + 2, PYF = TYP + 2, PPF = PXF * PYF;   // exchange grid (last row/column zero)
+// Boxes (x width a multiple of 4 floats; each starts at a 16-byte aligned x):
+constexpr int UW = 40, UH = TYP + 2;             // u: nodes x0-1 .. x0+32, y0-1 .. y0+TYP
+constexpr int FW = 36, FH = TYP + 1;             // f: nodes x0 .. x0+32, y0 .. y0+TYP
+constexpr int CW = 40, CH = TYP + 2;             // psi: cells x0-1 .. x0+32, y0-1 .. y0+TYP
+constexpr int U_FLOATS = 3 * UH * UW, F_FLOATS = 3 * FH * FW, C_FLOATS = CH * CW;
+constexpr int up32(int n) { return (n + 31) / 32 * 32; }   // 128-byte aligned TMA destinations
+constexpr int F_OFF = up32(U_FLOATS), C_OFF = F_OFF + up32(F_FLOATS), SLOT_FLOATS = up32(C_OFF + C_FLOATS);
+constexpr int TX_BYTES = (U_FLOATS + F_FLOATS + C_FLOATS) * 4;   // bytes one plane's three copies deliver
+constexpr int RING = 10;
+constexpr int NXQ = 9;                           // exchanged corner forces per cell: corners 0..2 x 3 comps
 constexpr long long kSpinLimit = 1LL << 24;      // mbarrier polls before giving up
+constexpr size_t kSmemBytes = 128 + (size_t)RING * SLOT_FLOATS * 4 + (size_t)2 * NXQ * PPF * 8 + RING * 8;
+static_assert(kSmemBytes <= 227 * 1024, "one CTA per SM must fit");
+static_assert((size_t)RING * SLOT_FLOATS * 4 >= 32 * 32 * 8, "the ring doubles as the reduction buffer");
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p)
 {
@@ -99,20 +114,18 @@ __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map
         : "memory");
 }
 
-template <int NT>
-__device__ __forceinline__ void block_partial_f(double ssq, double *part, double *red)
+// 1 / x by the hardware's approximate reciprocal (PTX rcp.approx, within one ulp):
+// the Jacobi scaling 1 / sum(psi) of a smoother needs no correctly rounded quotient.
+__device__ __forceinline__ float rcp_approx(float x)
 {
-    constexpr int NW = (NT + 31) / 32;
-    const int tid = threadIdx.x + blockDim.x * threadIdx.y;
-    red[tid] = ssq;
-    if (tid < NW * 32 - NT) red[NT + tid] = 0.0;
-    __syncthreads();
-    if (tid < 32) {
-        double s = 0.0;
-        for (int w = 0; w < NW; ++w) s += red[w * 32 + tid];
-        for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
-        if (tid == 0) part[blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)] = s;
-    }
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ void prefetch_map(const CUtensorMap *map)
+{
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
 }
 
 // Dirichlet bits (bit p = component p) of node (gx, gy, *) from the x and y faces;
@@ -141,17 +154,81 @@ __device__ __forceinline__ unsigned dir_z(const Geom &g, int gz)
     return b;
 }
 
-// out: this thread's node column (gx, gy) of component 0; dxy: its x/y Dirichlet
-// bits.  The residual's sum of squares is formed only when a norm is wanted.
+// Segments of a CTA's unit range: units are (tile, node plane) in tile-major order
+// with nz planes per tile.  Node planes [p0, p1] of tile t need cell layers
+// p0-1 .. p1 (those inside the grid); they are swept as npairs steps of two
+// layers from kfirst, reading planes kfirst .. kfirst + 2 npairs (planes beyond
+// the grid read zeros).
+struct Seg {
+    int t, p0, p1, kfirst, npairs;
+};
+
+__device__ __forceinline__ Seg make_seg(int u, int ue, int nz)
+{
+    Seg s;
+    s.t = u / nz;
+    const int base = s.t * nz;
+    s.p0 = u - base;
+    s.p1 = min(ue - base, nz) - 1;
+    s.kfirst = s.p0 > 0 ? s.p0 - 1 : 0;
+    // a step from layer k finalises node planes k and k+1, so the last step must
+    // start at p1 - 1 or later; layers beyond the grid (k >= nz - 1) read psi = 0
+    s.npairs = (s.p1 - s.kfirst) / 2 + 1;
+    return s;
+}
+
+// Cursor of the plane producer (thread 0).
+struct Prod {
+    int u;            // first unit of the next segment
+    int seq;          // sequence number of the next plane to issue
+    int t, next, last;   // current segment: tile, next plane to issue, last plane
+};
+
+// Tile origin (cells / nodes) and the 4-aligned box starts of a tile.
+struct TileBox {
+    int x0, y0;       // first owned node (and the cell to its upper right) of the tile
+    int xs, xoff;     // u and psi boxes start at node / cell xs = x0 - 1 + org.x - xoff
+    int xsf, xofff;   // f box starts at node xsf = x0 + org.x - xofff
+};
+
+__device__ __forceinline__ TileBox tile_box(int t, int ntx, int3 org)
+{
+    TileBox b;
+    b.x0 = (t % ntx) * TXP;
+    b.y0 = (t / ntx) * TYP;
+    const int xv = b.x0 - 1 + org.x;
+    b.xoff = ((xv % 4) + 4) % 4;
+    b.xs = xv - b.xoff;
+    const int xf = b.x0 + org.x;
+    b.xofff = xf % 4;
+    b.xsf = xf - b.xofff;
+    return b;
+}
+
+template <int NT>
+__device__ __forceinline__ void block_partial(double ssq, double *part, double *red)
+{
+    constexpr int NW = (NT + 31) / 32;
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+    red[tid] = ssq;
+    if (tid < NW * 32 - NT) red[NT + tid] = 0.0;
+    __syncthreads();
+    if (tid < 32) {
+        double s = 0.0;
+        for (int w = 0; w < NW; ++w) s += red[w * 32 + tid];
+        for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+        if (tid == 0) part[blockIdx.x] = s;
+    }
+}
+
 template <int MODE>
-__device__ __forceinline__ void finalize_f(const SweepArgs<float, float> &a, float *outc, unsigned dxy, int gz,
-                                           const float *Ku, float pss, const float *uv, const float *fv, double &ssq)
+__device__ __forceinline__ void finalize_node(const SweepArgs<float, float> &a, float *outc, unsigned dm, int gz,
+                                              const float (&Ku)[3], float ip, const float (&uv)[3],
+                                              const float (&fv)[3], double &ssq)
 {
     const Geom &g = a.g;
     float *o = outc + (long long)g.sy * gz;
-    const unsigned dm = dxy | dir_z(g, gz);
     if (MODE == kJacobi) {
-        const float ip = __frcp_rn(pss);
 #pragma unroll
         for (int p = 0; p < 3; ++p) {
             float v = uv[p];
@@ -174,226 +251,322 @@ __device__ __forceinline__ void finalize_f(const SweepArgs<float, float> &a, flo
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(NTP) k_sweep3_f2(const __grid_constant__ CUtensorMap tmap,
-                                                    const __grid_constant__ CUtensorMap tmap_f,
-                                                    const __grid_constant__ CUtensorMap tmap_psi,
-                                                    const SweepArgs<float, float> a, const int3 org, int *err)
+__global__ void __launch_bounds__(NTP, 1) k_sweep3_f2(const __grid_constant__ CUtensorMap tmap,
+                                                       const __grid_constant__ CUtensorMap tmap_f,
+                                                       const __grid_constant__ CUtensorMap tmap_psi,
+                                                       const SweepArgs<float, float> a, const int3 org, int *err)
 {
-    pdl_begin();
-    if (a.gate && *a.gate) return;
     extern __shared__ unsigned char smem_raw[];
     unsigned char *base = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
     float *ring = reinterpret_cast<float *>(base);
-    float2 *fx = reinterpret_cast<float2 *>(base + RING * SLOT_FLOATS * 4);   // [3][4][PPF]
-    float2 *ps = fx + 12 * PPF;                                               // [PPF]
-    unsigned long long *bar = reinterpret_cast<unsigned long long *>(ps + PPF);
-    __shared__ double red[((NTP + 31) / 32) * 32];
+    float2 *fx = reinterpret_cast<float2 *>(base + (size_t)RING * SLOT_FLOATS * 4);   // [2][NXQ][PPF]
+    unsigned long long *bar = reinterpret_cast<unsigned long long *>(fx + 2 * NXQ * PPF);
 
     const Geom &g = a.g;
     const int tid = threadIdx.x + BXP * threadIdx.y;
     int tx, ty;
     row_warp_xy<BYP>(tid, tx, ty);
-    const int x0 = blockIdx.x * TXP, y0 = blockIdx.y * TYP;
-    // The tensor maps describe the storage the sweep's grid sits in at offset org
-    // (0 for a whole level, the view origin for a refinement patch).  The boxes
-    // start at the multiple of 4 at or below node x0-1 (a TMA box's x coordinate
-    // must be 16-byte aligned), xoff in 0..3 being node x0-1's box-local x; the
-    // 40-wide box covers the 34 nodes x0-1 .. x0+32 for any xoff.
-    const int xv = x0 - 1 + org.x;
-    const int xs = xv - (((xv % 4) + 4) % 4);
-    const int xoff = xv - xs;
-    const int ybox = y0 - 1 + org.y;
-    const int kz0 = blockIdx.z * a.kchunk;
-    const int kz1 = min(kz0 + a.kchunk, g.nz - 1);
-    const int kend = (kz1 == g.nz - 1) ? g.nz - 1 : kz1 - 1;   // last plane finalised here
-    const int kfirst = kz0 > 0 ? kz0 - 1 : 0;
-    const int npairs = (kend - kfirst) / 2 + 1;
-    const int pmax = kfirst + 2 * (npairs - 1) + 2;            // last plane the block reads
 
+    // set-up that reads nothing a predecessor kernel writes
     if (tid == 0) {
         for (int s = 0; s < RING; ++s) mbar_init(smem_addr(&bar[s]), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        prefetch_map(&tmap);
+        prefetch_map(&tmap_f);
+        prefetch_map(&tmap_psi);
     }
+    // the exchange grid's last row and column (no cell beyond the tile) stay zero
     for (int s = tid; s < PPF; s += NTP) {
         const int lx = s % PXF, ly = s / PXF;
-        if (lx == BXP || ly == BYP) {
-            for (int q = 0; q < 12; ++q) fx[q * PPF + s] = make_float2(0.f, 0.f);
-            ps[s] = make_float2(0.f, 0.f);
-        }
+        if (lx == BXP || ly == BYP)
+            for (int q = 0; q < 2 * NXQ; ++q) fx[q * PPF + s] = make_float2(0.f, 0.f);
     }
+    pdl_begin();
+    if (a.gate && *a.gate) return;
     __syncthreads();
 
-    auto slot_of = [&](int p) { return (p - kfirst) % RING; };
-    auto parity_of = [&](int p) { return (uint32_t)(((p - kfirst) / RING) & 1); };
-    auto issue = [&](int p) {
-        if (p > pmax) return;
-        const int s = slot_of(p);
-        const uint32_t b = smem_addr(&bar[s]);
-        mbar_expect_tx(b, TX_BYTES);
-        float *slot = ring + s * SLOT_FLOATS;
-        tma_load_4d(smem_addr(slot), &tmap, xs, ybox, p + org.z, 0, b);
-        tma_load_4d(smem_addr(slot + F_OFF), &tmap_f, xs, ybox, p + org.z, 0, b);
-        tma_load_3d(smem_addr(slot + PSI_OFF), &tmap_psi, xs, ybox, p + org.z, b);
+    const int ntx = (g.nx - 2) / TXP + 1, nty = (g.ny - 2) / TYP + 1;
+    const long long U = (long long)ntx * nty * g.nz;   // < 2^31 (checked by the launcher)
+    const int ub = (int)(U * blockIdx.x / gridDim.x), ue = (int)(U * (blockIdx.x + 1) / gridDim.x);
+
+    // ---- producer (thread 0): issues the planes of the CTA's segments in order.
+    // Its cursor lives in shared memory, so the other threads hold no registers for it.
+    __shared__ Prod prod;
+    auto issue_upto = [&](int limit) {   // issue every plane with sequence number < limit
+        Prod P = prod;
+        while (P.seq < limit) {
+            if (P.next > P.last) {
+                if (P.u >= ue) break;
+                const Seg s = make_seg(P.u, ue, g.nz);
+                P.u = s.t * g.nz + s.p1 + 1;
+                P.t = s.t;
+                P.next = s.kfirst;
+                P.last = s.kfirst + 2 * s.npairs;
+            }
+            const TileBox b = tile_box(P.t, ntx, org);
+            const int slot = (int)(P.seq % RING);
+            const uint32_t mb = smem_addr(&bar[slot]);
+            float *dst = ring + slot * SLOT_FLOATS;
+            mbar_expect_tx(mb, TX_BYTES);
+            tma_load_4d(smem_addr(dst), &tmap, b.xs, b.y0 - 1 + org.y, P.next + org.z, 0, mb);
+            tma_load_4d(smem_addr(dst + F_OFF), &tmap_f, b.xsf, b.y0 + org.y, P.next + org.z, 0, mb);
+            tma_load_3d(smem_addr(dst + C_OFF), &tmap_psi, b.xs, b.y0 - 1 + org.y, P.next + org.z, mb);
+            ++P.next;
+            ++P.seq;
+        }
+        prod = P;
     };
-    if (tid == 0)
-        for (int j = 0; j < RING; ++j) issue(kfirst + j);
-    int issued_last = kfirst + RING - 1;
+    if (tid == 0) {
+        prod.u = ub;
+        prod.seq = 0;
+        prod.t = 0;
+        prod.next = 0;
+        prod.last = -1;
+        issue_upto(RING);
+    }
 
-    Coef<F2> c2;
-    c2.ad = F2(a.c.ad); c2.a12 = F2(a.c.a12); c2.a44 = F2(a.c.a44); c2.a11 = F2(a.c.a11);
-    c2.b1 = F2(a.c.b1); c2.b12 = F2(a.c.b12); c2.b44 = F2(a.c.b44); c2.c2 = F2(a.c.c2);
-
-    const int gx = x0 + tx, gy = y0 + ty;
-    const bool own = gx < g.nx && gy < g.ny && (tx < TXP || gx == g.nx - 1) && (ty < TYP || gy == g.ny - 1);
-    float *const outc = a.out + (own ? gx + (long long)g.sx * gy : 0);
-    const unsigned dxy = own ? dir_xy(g, gx, gy) : 0u;
     const int me = ty * PXF + tx;
-    float carry[3][4];
-#pragma unroll
-    for (int p = 0; p < 3; ++p)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) carry[p][q] = 0.f;
-    float psi_prev = 0.f;
     double ssq = 0.0;
     bool failed = false;
-
-    // lanes of this thread's warp (the last warp of the block is partial)
-    const int lane = tid & 31, wlanes = min(32, NTP - (tid & ~31));
-    const unsigned wmask = wlanes == 32 ? 0xffffffffu : ((1u << wlanes) - 1u);
-    for (int it = 0; it < npairs; ++it) {
-        const int k = kfirst + 2 * it;
-        // one lane per warp polls the barriers of planes k..k+2 (bounded); the warp
-        // proceeds when its lane 0 has seen them complete
-        int ok = 1;
-        if (lane == 0)
-            ok = mbar_wait(smem_addr(&bar[slot_of(k)]), parity_of(k)) &&
-                 mbar_wait(smem_addr(&bar[slot_of(k + 1)]), parity_of(k + 1)) &&
-                 mbar_wait(smem_addr(&bar[slot_of(k + 2)]), parity_of(k + 2));
-        ok = __shfl_sync(wmask, ok, 0);
-        // every lane then observes the completed phases itself (acquiring the copied
-        // data); a timed-out wait is reported at the exchange barrier below and
-        // this warp's values are then never used
-        if (ok)
-            ok = mbar_try(smem_addr(&bar[slot_of(k)]), parity_of(k)) &&
-                 mbar_try(smem_addr(&bar[slot_of(k + 1)]), parity_of(k + 1)) &&
-                 mbar_try(smem_addr(&bar[slot_of(k + 2)]), parity_of(k + 2));
-        const float *P0 = ring + slot_of(k) * SLOT_FLOATS;
-        const float *P1 = ring + slot_of(k + 1) * SLOT_FLOATS;
-        const float *P2 = ring + slot_of(k + 2) * SLOT_FLOATS;
-        // cell (x0+tx-1, y0+ty-1) of layers k, k+1; the tensor map zero-fills cells
-        // outside the grid, so no bounds test is needed
-        const float p0 = P0[PSI_OFF + ty * WX + tx + xoff];
-        const float p1 = P1[PSI_OFF + ty * WX + tx + xoff];
-        F2 U[3][8];
-#pragma unroll
-        for (int p = 0; p < 3; ++p)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int off = p * PYF * WX + (ty + (q >> 1)) * WX + tx + (q & 1) + xoff;
-                const float v0 = P0[off], v1 = P1[off], v2 = P2[off];
-                U[p][q] = F2(v0, v1);        // lower corners of cells k, k+1
-                U[p][q + 4] = F2(v1, v2);    // upper corners
-            }
-        cell_forces3<F2>(U, F2(p0, p1), c2);
-        // this thread's cell contributions to node plane k (carry + layer k bottom) and
-        // node plane k+1 (layer k top + layer k+1 bottom); layer k+1 top is carried
-#pragma unroll
-        for (int p = 0; p < 3; ++p)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                fx[(p * 4 + q) * PPF + me] = make_float2(carry[p][q] + U[p][q].v.x, U[p][q + 4].v.x + U[p][q].v.y);
-                carry[p][q] = U[p][q + 4].v.y;
-            }
-        ps[me] = make_float2(psi_prev + p0, p0 + p1);
-        psi_prev = p1;
-        if (__syncthreads_or(!ok)) {
-            failed = true;
-            break;
+    // the consumer's position in the plane sequence: slot and phase parity of the
+    // plane a step starts from, and its sequence number
+    int cseq = 0, cslot = 0;
+    uint32_t cpar = 0;
+    int buf = 0;
+    auto nxt = [](int &slot, uint32_t &par) {
+        if (++slot == RING) {
+            slot = 0;
+            par ^= 1u;
         }
-        if (own) {
-            // node = corner 3 of cell (tx,ty), 2 of (tx+1,ty), 1 of (tx,ty+1), 0 of (tx+1,ty+1)
-            F2 Ku2[3];
+    };
+    auto full_wait = [&](int slot, uint32_t par) { return mbar_wait(smem_addr(&bar[slot]), par); };
+
+    for (int u = ub; u < ue && !failed;) {
+        const Seg s = make_seg(u, ue, g.nz);
+        u = s.t * g.nz + s.p1 + 1;
+        const TileBox b = tile_box(s.t, ntx, org);
+        const int gx = b.x0 + tx, gy = b.y0 + ty;
+        const bool own = gx < g.nx && gy < g.ny && (tx < TXP || gx == g.nx - 1) && (ty < TYP || gy == g.ny - 1);
+        float *const outc = a.out + (own ? gx + (long long)g.sx * gy : 0);
+        const unsigned dxy = own ? dir_xy(g, gx, gy) : 0u;
+        const int ou = ty * UW + tx + b.xoff;     // corner 0 of this thread's cell in the u box
+        const int oc = ty * CW + tx + b.xoff;     // this thread's cell in the psi box
+        const int of = ty * FW + tx + b.xofff;    // the owned node in the f box
+
+        // prime: the in-plane transform of plane kfirst
+        float Tc[3][4];
+        {
+            int ok = full_wait(cslot, cpar);
+            if (__syncthreads_or(!ok)) {
+                failed = true;
+                break;
+            }
+            const float *P = ring + cslot * SLOT_FLOATS;
 #pragma unroll
             for (int p = 0; p < 3; ++p) {
-                F2 s0, s1, s2, s3;
-                s0.v = fx[(p * 4 + 3) * PPF + me];
-                s1.v = fx[(p * 4 + 2) * PPF + me + 1];
-                s2.v = fx[(p * 4 + 1) * PPF + me + PXF];
-                s3.v = fx[(p * 4 + 0) * PPF + me + PXF + 1];
-                Ku2[p] = (s0 + s1) + (s2 + s3);
-            }
-            F2 q0, q1, q2, q3;
-            q0.v = ps[me];
-            q1.v = ps[me + 1];
-            q2.v = ps[me + PXF];
-            q3.v = ps[me + PXF + 1];
-            const F2 pss = (q0 + q1) + (q2 + q3);
-            const int onode = (ty + 1) * WX + tx + 1 + xoff;
-            if (k >= kz0 && k <= kend) {
-                const float Ku[3] = {Ku2[0].v.x, Ku2[1].v.x, Ku2[2].v.x};
-                const float uv[3] = {P0[onode], P0[PYF * WX + onode], P0[2 * PYF * WX + onode]};
-                const float fv[3] = {P0[F_OFF + onode], P0[F_OFF + PYF * WX + onode], P0[F_OFF + 2 * PYF * WX + onode]};
-                finalize_f<MODE>(a, outc, dxy, k, Ku, pss.v.x, uv, fv, ssq);
-            }
-            if (k + 1 >= kz0 && k + 1 <= kend) {
-                const float Ku[3] = {Ku2[0].v.y, Ku2[1].v.y, Ku2[2].v.y};
-                const float uv[3] = {P1[onode], P1[PYF * WX + onode], P1[2 * PYF * WX + onode]};
-                const float fv[3] = {P1[F_OFF + onode], P1[F_OFF + PYF * WX + onode], P1[F_OFF + 2 * PYF * WX + onode]};
-                finalize_f<MODE>(a, outc, dxy, k + 1, Ku, pss.v.y, uv, fv, ssq);
+                const float *Q = P + p * UH * UW + ou;
+                Tc[p][0] = Q[0];
+                Tc[p][1] = Q[1];
+                Tc[p][2] = Q[UW];
+                Tc[p][3] = Q[UW + 1];
+                bfly4xy(Tc[p]);
             }
         }
-        __syncthreads();
-        if (tid == 0) {
-            // planes k and k+1 are no longer read: refill their slots
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            issue(k + RING);
-            issue(k + 1 + RING);
-            issued_last = k + 1 + RING;
+        float Fc[3][4];
+#pragma unroll
+        for (int p = 0; p < 3; ++p)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) Fc[p][q] = 0.f;
+        float sprev = 0.f;                       // in-plane psi sum of the layer below (Jacobi)
+
+#pragma unroll 2
+        for (int it = 0; it < s.npairs; ++it) {
+            const int k = s.kfirst + 2 * it;
+            // planes k, k+1, k+2 in slots s0, s1, s2
+            int s1 = cslot, s2;
+            uint32_t r1 = cpar, r2;
+            nxt(s1, r1);
+            s2 = s1;
+            r2 = r1;
+            nxt(s2, r2);
+            const int ok = full_wait(s1, r1) && full_wait(s2, r2);
+            const float *P0 = ring + cslot * SLOT_FLOATS, *P1 = ring + s1 * SLOT_FLOATS, *P2 = ring + s2 * SLOT_FLOATS;
+            const bool fin0 = own && k >= s.p0 && k <= s.p1;
+            const bool fin1 = own && k + 1 >= s.p0 && k + 1 <= s.p1;
+
+            // raw u of planes k+1, k+2 at the cell's four in-plane corners, then the
+            // in-plane transform of both planes in one packed pass
+            F2 Tt[3][4];
+#pragma unroll
+            for (int p = 0; p < 3; ++p) {
+                const int o = p * UH * UW + ou;
+                Tt[p][0] = F2(P1[o], P2[o]);
+                Tt[p][1] = F2(P1[o + 1], P2[o + 1]);
+                Tt[p][2] = F2(P1[o + UW], P2[o + UW]);
+                Tt[p][3] = F2(P1[o + UW + 1], P2[o + UW + 1]);
+                bfly4xy(Tt[p]);
+            }
+            F2 Tb[3][4];
+#pragma unroll
+            for (int p = 0; p < 3; ++p)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    Tb[p][q] = F2(Tc[p][q], Tt[p][q].v.x);
+                    Tc[p][q] = Tt[p][q].v.y;
+                }
+            // psi of the cell in layers k, k+1 times the moduli constants (scalar
+            // products with the constant-bank parameters)
+            F2 kc[7];
+            {
+                const float q0v = P0[C_OFF + oc], q1v = P1[C_OFF + oc];
+                const float cc[7] = {a.c.ad, a.c.a12, a.c.a44, a.c.b1, a.c.b12, a.c.b44, a.c.c2};
+#pragma unroll
+                for (int i = 0; i < 7; ++i) kc[i] = F2(q0v * cc[i], q1v * cc[i]);
+            }
+            F2 Fb[3][4], Ft[3][4];
+            cell_faces3k<F2>(Tb, Tt, kc, Fb, Ft);
+            // node planes k (top of layer k-1 + bottom of layer k) and k+1 (top of k +
+            // bottom of k+1), transformed back to the four in-plane corners
+            F2 N[3][4];
+#pragma unroll
+            for (int p = 0; p < 3; ++p) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    N[p][q] = F2(Fc[p][q] + Fb[p][q].v.x, Ft[p][q].v.x + Fb[p][q].v.y);
+                    Fc[p][q] = Ft[p][q].v.y;
+                }
+                bfly4xyT(N[p]);
+            }
+            float2 *X = fx + buf * NXQ * PPF;
+#pragma unroll
+            for (int p = 0; p < 3; ++p)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) X[(p * 3 + c) * PPF + me] = N[p][c].v;
+
+            // what the finalisation needs from planes k and k+1, read before the
+            // barrier (their slots are refilled right after it): u and f at the owned
+            // node and, for Jacobi, the psi of the eight cells around it
+            float uv0[3] = {0.f, 0.f, 0.f}, uv1[3] = {0.f, 0.f, 0.f};
+            float fv0[3] = {0.f, 0.f, 0.f}, fv1[3] = {0.f, 0.f, 0.f};
+            float sp0 = 0.f, sp1 = 0.f;
+            if (own) {
+#pragma unroll
+                for (int p = 0; p < 3; ++p) {
+                    if (MODE == kJacobi) {
+                        uv0[p] = P0[p * UH * UW + ou + UW + 1];
+                        uv1[p] = P1[p * UH * UW + ou + UW + 1];
+                    }
+                    if (MODE != kApply) {
+                        fv0[p] = P0[F_OFF + p * FH * FW + of];
+                        fv1[p] = P1[F_OFF + p * FH * FW + of];
+                    }
+                }
+                if (MODE == kJacobi) {
+                    const float *C0 = P0 + C_OFF + oc, *C1 = P1 + C_OFF + oc;
+                    sp0 = (C0[0] + C0[1]) + (C0[CW] + C0[CW + 1]);
+                    sp1 = (C1[0] + C1[1]) + (C1[CW] + C1[CW + 1]);
+                }
+            }
+
+            if (__syncthreads_or(!ok)) {
+                failed = true;
+                break;
+            }
+            cseq += 2;
+            cslot = s2;
+            cpar = r2;
+            if (tid == 0) {
+                // planes k and k+1 are no longer read (after the segment's last step
+                // plane k+2 is not either)
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                issue_upto(cseq + (it + 1 == s.npairs ? 1 : 0) + RING);
+            }
+            if (own) {
+                // node = corner 3 of this cell, 2 of (tx+1,ty), 1 of (tx,ty+1), 0 of (tx+1,ty+1)
+                F2 Ku2[3];
+#pragma unroll
+                for (int p = 0; p < 3; ++p) {
+                    F2 a1, a2, a3;
+                    a1.v = X[(p * 3 + 2) * PPF + me + 1];
+                    a2.v = X[(p * 3 + 1) * PPF + me + PXF];
+                    a3.v = X[(p * 3 + 0) * PPF + me + PXF + 1];
+                    Ku2[p] = (N[p][3] + a1) + (a2 + a3);
+                }
+                if (fin0) {
+                    const float Ku[3] = {Ku2[0].v.x, Ku2[1].v.x, Ku2[2].v.x};
+                    const float ip = MODE == kJacobi ? rcp_approx(sprev + sp0) : 0.f;
+                    finalize_node<MODE>(a, outc, dxy | dir_z(g, k), k, Ku, ip, uv0, fv0, ssq);
+                }
+                if (fin1) {
+                    const float Ku[3] = {Ku2[0].v.y, Ku2[1].v.y, Ku2[2].v.y};
+                    const float ip = MODE == kJacobi ? rcp_approx(sp0 + sp1) : 0.f;
+                    finalize_node<MODE>(a, outc, dxy | dir_z(g, k + 1), k + 1, Ku, ip, uv1, fv1, ssq);
+                }
+            }
+            sprev = sp1;
+            buf ^= 1;
+        }
+        if (!failed) {                           // past the segment's last plane
+            ++cseq;
+            nxt(cslot, cpar);
         }
     }
     if (failed) {
         if (tid == 0) {
             atomicExch(err, 1);
-            // wait (bounded) for every copy this block issued that has not been consumed
-            const int last = min(issued_last, pmax);
-            for (int p = max(kfirst, last - RING + 1); p <= last; ++p) mbar_wait(smem_addr(&bar[slot_of(p)]), parity_of(p));
+            // wait (bounded) for the copies still in flight: the last RING issued
+            // (earlier ones have completed or were consumed)
+            for (int q = max(cseq, prod.seq - RING); q < prod.seq; ++q)
+                mbar_wait(smem_addr(&bar[q % RING]), (uint32_t)((q / RING) & 1));
         }
         __syncthreads();
         return;
     }
-    if (MODE == kResidual && a.part) block_partial_f<NTP>(ssq, a.part, red);
+    if (MODE == kResidual && a.part) {
+        __syncthreads();                          // every copy has been consumed: reuse the ring
+        block_partial<NTP>(ssq, a.part, reinterpret_cast<double *>(ring));
+    }
 }
 
-constexpr size_t smem_f2()
+int sm_count()
 {
-    return 128 + (size_t)RING * SLOT_FLOATS * 4 + (size_t)13 * PPF * 8 + RING * 8;
+    static int count[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+    if (count[dev] == 0) {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 152;
+        count[dev] = n;
+    }
+    return count[dev];
+}
+
+// CTAs of one launch: one per SM, fewer when a CTA would get less than two node
+// planes (small levels).
+int ctas_f2(const Geom &g)
+{
+    const long long ntx = (g.nx - 2) / TXP + 1, nty = (g.ny - 2) / TYP + 1;
+    const long long units = ntx * nty * g.nz;
+    return (int)std::max(1LL, std::min((long long)sm_count(), units / 2));
 }
 
 }  // namespace
 
-void sweep_grid_f2(const Geom &g, int *grid, int *kchunk)
+void tma_box_shapes(int u[2], int f[2], int c[2])
 {
-    grid[0] = (g.nx - 1 + TXP - 1) / TXP;
-    grid[1] = (g.ny - 1 + TYP - 1) / TYP;
-    const int nzc = g.nz - 1;
-    const int nc = choose_chunks((long long)grid[0] * grid[1], nzc, 2 * 152, true);   // two blocks per SM
-    const int ch = (nzc + nc - 1) / nc;
-    grid[2] = (nzc + ch - 1) / ch;
-    *kchunk = ch;
+    u[0] = UW; u[1] = UH;
+    f[0] = FW; f[1] = FH;
+    c[0] = CW; c[1] = CH;
 }
 
 template <int MODE>
-static cudaError_t launch_f2_mode(const SweepArgs<float, float> &a0, const CUtensorMap *tmap, int *err, cudaStream_t s,
+static cudaError_t launch_f2_mode(const SweepArgs<float, float> &a, const CUtensorMap *tmap, int *err, cudaStream_t s,
                                   int3 org)
 {
-    SweepArgs<float, float> a = a0;
-    int grid[3];
-    sweep_grid_f2(a.g, grid, &a.kchunk);
     static std::atomic<unsigned long long> attr_done{0};
-    const size_t sm = smem_f2();
-    cudaError_t ea = smem_attr_once(reinterpret_cast<const void *>(k_sweep3_f2<MODE>), sm, attr_done);
+    cudaError_t ea = smem_attr_once(reinterpret_cast<const void *>(k_sweep3_f2<MODE>), kSmemBytes, attr_done);
     if (ea != cudaSuccess) return ea;
-    cudaError_t e = launch_pdl(k_sweep3_f2<MODE>, dim3(grid[0], grid[1], grid[2]), dim3(BXP, BYP), sm, s, tmap[0], tmap[1],
+    cudaError_t e = launch_pdl(k_sweep3_f2<MODE>, dim3(ctas_f2(a.g)), dim3(BXP, BYP), kSmemBytes, s, tmap[0], tmap[1],
                                tmap[2], a, org, err);
     if (e != cudaSuccess) return e;
     ++g_launches;
@@ -404,7 +577,11 @@ cudaError_t launch_sweep_f2(int mode, const SweepArgs<float, float> &a, const vo
                             int3 org)
 {
     const CUtensorMap *m = static_cast<const CUtensorMap *>(tmap);
-    if (org.x < 0 || org.y < 0 || org.z < 0) return cudaErrorInvalidValue;
+    if (org.x < 0 || org.y < 0 || org.z < 0 || a.g.dim != 3 || a.g.nx < 2 || a.g.ny < 2 || a.g.nz < 2)
+        return cudaErrorInvalidValue;
+    // the work split counts (tile, plane) units in 32-bit integers
+    if ((long long)((a.g.nx - 2) / TXP + 1) * ((a.g.ny - 2) / TYP + 1) * a.g.nz >= (1LL << 31))
+        return cudaErrorInvalidValue;
     switch (mode) {
     case kApply: return launch_f2_mode<kApply>(a, m, err, s, org);
     case kResidual: return launch_f2_mode<kResidual>(a, m, err, s, org);
@@ -413,11 +590,6 @@ cudaError_t launch_sweep_f2(int mode, const SweepArgs<float, float> &a, const vo
     }
 }
 
-long long sweep_blocks_f2(const Geom &g)
-{
-    int grid[3], ch;
-    sweep_grid_f2(g, grid, &ch);
-    return (long long)grid[0] * grid[1] * grid[2];
-}
+long long sweep_blocks_f2(const Geom &g) { return ctas_f2(g); }
 
 }  // namespace sbm

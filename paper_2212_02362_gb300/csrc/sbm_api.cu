@@ -245,32 +245,41 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
     return fn;
 }
 
-// 3D map of an FP32 cell array (cells at the node index of their lower corner);
-// box = 40 x 10 x 1 cells, zero fill outside the grid's cells.
-bool encode_cell_map(CUtensorMap *m, float *buf, const Geom &g)
+// 3D map of an FP32 cell array (cells at the node index of their lower corner),
+// box w x h x 1 cells, zero fill outside the grid's cells.
+bool encode_cell_map(CUtensorMap *m, float *buf, const Geom &g, int w, int h)
 {
     PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
     if (!enc) return false;
     cuuint64_t dims[3] = {(cuuint64_t)(g.nx - 1), (cuuint64_t)(g.ny - 1), (cuuint64_t)(g.nz - 1)};
     cuuint64_t strides[2] = {(cuuint64_t)g.sx * 4, (cuuint64_t)g.sy * 4};
-    cuuint32_t box[3] = {40, 10, 1};
+    cuuint32_t box[3] = {(cuuint32_t)w, (cuuint32_t)h, 1};
     cuuint32_t estr[3] = {1, 1, 1};
     return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, buf, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// 4D (x, y, z, component) map of one FP32 level buffer; box = 40 x 10 x 1 x 3 nodes
-// (the staged plane of the TMA sweep), zero fill outside the grid.
-bool encode_plane_map(CUtensorMap *m, float *buf, const Geom &g)
+// 4D (x, y, z, component) map of one FP32 level buffer; box w x h x 1 x 3 nodes,
+// zero fill outside the grid.
+bool encode_plane_map(CUtensorMap *m, float *buf, const Geom &g, int w, int h)
 {
     PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
     if (!enc) return false;
     cuuint64_t dims[4] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz, 3};
     cuuint64_t strides[3] = {(cuuint64_t)g.sx * 4, (cuuint64_t)g.sy * 4, (cuuint64_t)g.cs * 4};
-    cuuint32_t box[4] = {40, 10, 1, 3};
+    cuuint32_t box[4] = {(cuuint32_t)w, (cuuint32_t)h, 1, 3};
     cuuint32_t estr[4] = {1, 1, 1, 1};
     return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, buf, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// The three maps of the TMA sweep for input buffer u, right-hand side f and cells psi.
+bool encode_sweep_maps(CUtensorMap (&m)[3], float *u, float *f, float *psi, const Geom &g)
+{
+    int bu[2], bf[2], bc[2];
+    tma_box_shapes(bu, bf, bc);
+    return encode_plane_map(&m[0], u, g, bu[0], bu[1]) && encode_plane_map(&m[1], f, g, bf[0], bf[1]) &&
+           encode_cell_map(&m[2], psi, g, bc[0], bc[1]);
 }
 
 template <typename T>
@@ -1273,8 +1282,7 @@ sbm_status sbm_grid_create(const sbm_grid_desc *d, sbm_grid *out)
         if (g.dim == 3) {
             L.has_tm = true;
             for (int i = 0; i < 2; ++i)
-                L.has_tm = L.has_tm && encode_plane_map(&L.tm32[i][0], L.su[i], g) &&
-                           encode_plane_map(&L.tm32[i][1], L.sf, g) && encode_cell_map(&L.tm32[i][2], L.psi32, g);
+                L.has_tm = L.has_tm && encode_sweep_maps(L.tm32[i], L.su[i], L.sf, L.psi32, g);
         }
         const int nk = (1 << g.dim) * g.dim;
         CK(cudaMalloc(&L.Ke64, sizeof(double) * nk * nk));
@@ -1718,11 +1726,18 @@ sbm_status sbm_time_kernel(sbm_grid G, int which, int reps, int flush_l2, double
     CK(launch());
     float t = 0.f;
     if (flush_l2) {
+        // flush: write 256 MB, then read a second 256 MB buffer, so that the launch
+        // finds neither its inputs nor dirty lines (whose write-back would be charged
+        // to it) in the 126 MB L2
         const size_t fb = 256ull << 20;
         void *flush = nullptr;
-        CK(cudaMalloc(&flush, fb));
+        CK(cudaMalloc(&flush, 2 * fb + 64));
+        CK(cudaMemsetAsync(flush, 0, 2 * fb + 64, G->st));
+        void *clean = static_cast<char *>(flush) + fb;
+        float *sink = reinterpret_cast<float *>(static_cast<char *>(flush) + 2 * fb);
         for (int r = 0; r < reps; ++r) {
             cudaError_t e = cudaMemsetAsync(flush, r & 0xff, fb, G->st);
+            if (e == cudaSuccess) e = launch_l2_read(clean, fb, sink, G->st);
             if (e == cudaSuccess) e = cudaEventRecord(G->ev0, G->st);
             if (e == cudaSuccess) e = launch();
             if (e == cudaSuccess) e = cudaEventRecord(G->ev1, G->st);
@@ -1817,8 +1832,7 @@ sbm_status sbm_amr_add_level(sbm_grid G, const sbm_box *box)
     if (d == 3) {
         Pt.has_tm = true;
         for (int i = 0; i < 2; ++i)
-            Pt.has_tm = Pt.has_tm && encode_plane_map(&Pt.tm32[i][0], Pt.se[i], g) &&
-                        encode_plane_map(&Pt.tm32[i][1], Pt.srhs, g) && encode_cell_map(&Pt.tm32[i][2], Pt.psiv32, g);
+            Pt.has_tm = Pt.has_tm && encode_sweep_maps(Pt.tm32[i], Pt.se[i], Pt.srhs, Pt.psiv32, g);
     }
     const int nk = (1 << d) * d;
     CK(cudaMalloc(&Pt.Ke64, sizeof(double) * nk * nk));

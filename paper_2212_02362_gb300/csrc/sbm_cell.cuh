@@ -44,6 +44,7 @@ struct F2 {
     __device__ __forceinline__ F2(float lo, float hi) : v(make_float2(lo, hi)) {}
 };
 __device__ __forceinline__ F2 operator+(F2 a, F2 b) { F2 r; r.v = __fadd2_rn(a.v, b.v); return r; }
+// a - b as one FFMA2 (b * -1 + a); there is no packed-subtract intrinsic.
 __device__ __forceinline__ F2 operator-(F2 a, F2 b) { F2 r; r.v = __ffma2_rn(b.v, make_float2(-1.f, -1.f), a.v); return r; }
 __device__ __forceinline__ F2 operator*(F2 a, F2 b) { F2 r; r.v = __fmul2_rn(a.v, b.v); return r; }
 __device__ __forceinline__ F2 madd(F2 a, F2 b, F2 c) { F2 r; r.v = __ffma2_rn(a.v, b.v, c.v); return r; }
@@ -227,11 +228,26 @@ __host__ __device__ __forceinline__ void bfly4xyT(T (&v)[4])
     v[3] = w2 + w3;
 }
 
-// One cell given the in-plane transforms of its bottom (Tb) and top (Tt) faces:
-// returns the transformed face forces Fb (to the bottom plane) and Ft (to the top).
+// The seven moduli constants of a 3D cell scaled by its psi, in the order
+// (ad, a12, a44, b1, b12, b44, c2) of Coef.
 template <typename T>
-__host__ __device__ __forceinline__ void cell_faces3(const T (&Tb)[3][4], const T (&Tt)[3][4], T psi,
-                                                     const Coef<T> &c, T (&Fb)[3][4], T (&Ft)[3][4])
+__host__ __device__ __forceinline__ void scaled_coefs(T psi, const Coef<T> &c, T (&k)[7])
+{
+    k[0] = psi * c.ad;
+    k[1] = psi * c.a12;
+    k[2] = psi * c.a44;
+    k[3] = psi * c.b1;
+    k[4] = psi * c.b12;
+    k[5] = psi * c.b44;
+    k[6] = psi * c.c2;
+}
+
+// One cell given the in-plane transforms of its bottom (Tb) and top (Tt) faces
+// and its psi-scaled constants k (scaled_coefs): returns the transformed face
+// forces Fb (to the bottom plane) and Ft (to the top).
+template <typename T>
+__host__ __device__ __forceinline__ void cell_faces3k(const T (&Tb)[3][4], const T (&Tt)[3][4], const T (&k)[7],
+                                                      T (&Fb)[3][4], T (&Ft)[3][4])
 {
     T U[3][8];
 #pragma unroll
@@ -241,8 +257,7 @@ __host__ __device__ __forceinline__ void cell_faces3(const T (&Tb)[3][4], const 
             U[p][s] = Tb[p][s] + Tt[p][s];
             U[p][s + 4] = Tt[p][s] - Tb[p][s];
         }
-    const T ad = psi * c.ad, a12 = psi * c.a12, a44 = psi * c.a44;
-    const T b1 = psi * c.b1, b12 = psi * c.b12, b44 = psi * c.b44, c2 = psi * c.c2;
+    const T ad = k[0], a12 = k[1], a44 = k[2], b1 = k[3], b12 = k[4], b44 = k[5], c2 = k[6];
     const T ltr = a12 * (U[0][1] + U[1][2] + U[2][4]);
     const T sxx = madd(ad, U[0][1], ltr), syy = madd(ad, U[1][2], ltr), szz = madd(ad, U[2][4], ltr);
     const T sxy = a44 * (U[1][1] + U[0][2]);
@@ -273,6 +288,15 @@ __host__ __device__ __forceinline__ void cell_faces3(const T (&Tb)[3][4], const 
             Ft[p][s] = dU[p][s] + dU[p][s + 4];
         }
     }
+}
+
+template <typename T>
+__host__ __device__ __forceinline__ void cell_faces3(const T (&Tb)[3][4], const T (&Tt)[3][4], T psi,
+                                                     const Coef<T> &c, T (&Fb)[3][4], T (&Ft)[3][4])
+{
+    T k[7];
+    scaled_coefs(psi, c, k);
+    cell_faces3k(Tb, Tt, k, Fb, Ft);
 }
 
 }  // namespace sbm

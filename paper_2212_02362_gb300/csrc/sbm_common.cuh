@@ -171,16 +171,20 @@ long long sweep_blocks(const Geom &g, bool fp64);
 template <typename T, typename TO>
 cudaError_t launch_sweep(int mode, const SweepArgs<T, TO> &a, cudaStream_t s);
 
-// FP32 3D sweep with TMA plane staging and packed FP32x2 arithmetic
-// (k_stencil_tma.cu).  tmap: three CUtensorMaps — u and f as 4D (x, y, z,
-// component) with a 40 x 10 x 1 x 3 box, psi as 3D cells with a 40 x 10 x 1 box —
-// of the storage that a.g's grid sits in at offset org (>= 0; zero for a whole
-// level).  psi must be 0 on the cells of that storage outside a.g's grid (beyond
-// the storage the tensor maps read zeros).  a.out is written at a.g's nodes.
-// err: device flag set when an mbarrier wait times out.
+// FP32 3D sweep with TMA plane staging and packed FP32x2 arithmetic, one
+// persistent CTA per SM (k_stencil_tma.cu).  tmap: three CUtensorMaps of the
+// storage that a.g's grid sits in at offset org (>= 0; zero for a whole level):
+// u and f as 4D (x, y, z, component) maps, psi as a 3D cell map, with the box
+// shapes tma_box_shapes gives ({x, y} extents; z 1, components 3).  psi must be 0
+// on the cells of that storage outside a.g's grid (beyond the storage the tensor
+// maps read zeros).  a.out is written at a.g's nodes.  err: device flag set when
+// an mbarrier wait times out.
 cudaError_t launch_sweep_f2(int mode, const SweepArgs<float, float> &a, const void *tmap, int *err,
                             cudaStream_t s, int3 org = make_int3(0, 0, 0));
+// Partial sums (= CTAs) of one launch of launch_sweep_f2 on the current device.
 long long sweep_blocks_f2(const Geom &g);
+// Box extents {x, y} of the u, f and psi tensor maps of launch_sweep_f2.
+void tma_box_shapes(int u[2], int f[2], int c[2]);
 
 template <typename T>
 cudaError_t launch_gs(const Geom &g, const T *psi, const T *Ke, const T *f, T *u, int colour,
@@ -263,6 +267,8 @@ struct AmrInfo {
 cudaError_t launch_lincomb(long long n, double a, const double *x, double b, const double *y, double c,
                            const double *z, double *out, cudaStream_t s);
 cudaError_t launch_sum_parts(const double *part, int n, double *out, cudaStream_t s);
+// Reads a buffer (measurement: leaves L2 holding clean lines of it).
+cudaError_t launch_l2_read(const void *buf, size_t bytes, float *sink, cudaStream_t s);
 // adjoint of the composite problem
 cudaError_t launch_amr_ghostT(const Geom &sc, const AmrInfo &Lc, const Geom &sp, const AmrInfo &Lp, const double *wc,
                               double *wp, int with_solved, cudaStream_t st);

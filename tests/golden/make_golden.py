@@ -1,11 +1,23 @@
 """Write oracle-only golden records for full-size workloads (tests/golden/*.json).
 
 Every stored value comes from the CPU oracle (oracle/), run here on the seeded
-inputs of workloads/: the multigrid residual history of the FP64 solve, the
-cycles it needs to reach relres 1e-10, and the solution converged to 1e-14 at a
-seeded sample of dofs.  The GPU tests compare the CUDA solve with these samples.
+inputs of workloads/.  A record holds, for each field the oracle computes (the
+displacement u, for topology optimisation also the adjoint lambda and the
+gradients dJ/dpsi, dJ/drho):
+  - its values at a seeded sample of entries;
+  - "sketches": its inner products with seeded random vectors w_j (entries
+    uniform in [-1, 1]).  A difference e between a GPU field and the oracle field
+    shows in every sketch as w_j . e, of size about |e| / sqrt(3), wherever e sits,
+    so the sketches check the whole field and not only the samples;
+  - its 2-norm.
+plus the oracle's multigrid residual history and cycle counts.  The GPU tests
+(tests/test_gpu_full_size.py) compare the CUDA results with these records, and
+bench.py reports the error of its timed solve against the damage_3d records.
 
-    python tests/golden/make_golden.py damage_3d_129      # ~10 min of one CPU core
+    python tests/golden/make_golden.py damage_3d_129      # ~4 min of one CPU core
+    python tests/golden/make_golden.py topopt_3d          # ~20 min
+    python tests/golden/make_golden.py voids_amr_2d       # 129^2 base + 3 levels
+    python tests/golden/make_golden.py voids_amr_3d_65    # 65^3 base + 2 levels, ~1 h
 """
 import json
 import os
@@ -20,22 +32,38 @@ sys.path.insert(0, ROOT)
 import oracle  # noqa: E402
 import workloads as W  # noqa: E402
 
-RECIPES = {
-    "damage_3d_129": lambda: W.damage3d(129),
-    "damage_3d_65": lambda: W.damage3d(65),
-}
+HERE = os.path.dirname(os.path.abspath(__file__))
+NSKETCH = 8
 
 
-def make(name, nsample=4096):
-    wk = RECIPES[name]()
+def sketch_vectors(n, count=NSKETCH, seed=7100):
+    """The seeded random vectors of the sketches (entries uniform in [-1, 1])."""
+    return [W.uniform(seed + j, n, -1.0, 1.0) for j in range(count)]
+
+
+def field_record(x, sample_seed, nsample=4096):
+    idx = np.unique((W.uniform(sample_seed, nsample) * x.size).astype(np.int64))
+    return {"sample_index": idx.tolist(), "sample": x[idx].tolist(),
+            "sketch": [float(w @ x) for w in sketch_vectors(x.size)], "norm": float(np.linalg.norm(x))}
+
+
+def _solve_to_floor(P, psi, f, u0, omega):
+    """FP64 multigrid solve to relres 1e-14, or to the FP64 floor of the field (the
+    rough SIMP fields stagnate near 1e-13): status 1 accepted when the history
+    went below 1e-12."""
+    res = oracle.mg_solve(P, psi, f, u0, omega=omega, tol=1e-14, max_cycles=150)
+    hist = [float(v) for v in res.history]
+    assert res.status == 0 or min(hist) <= 1e-12, (res.status, min(hist))
+    return res, hist
+
+
+def make_damage(name, wk):
     P = oracle.Problem(wk.dim, wk.n, wk.h, *wk.moduli, dirichlet=wk.dirichlet_bits())
     psi = oracle.floor_psi(wk.psi, wk.psi_min)
     t = time.time()
-    res = oracle.mg_solve(P, psi, wk.f, wk.u0, omega=wk.omega, tol=1e-14, max_cycles=500)
+    res, hist = _solve_to_floor(P, psi, wk.f, wk.u0, wk.omega)
     dt = time.time() - t
-    hist = [float(v) for v in res.history]
     cyc10 = next(i for i, v in enumerate(hist) if v <= 1e-10)
-    idx = np.unique((W.uniform(9001, nsample) * P.ndofs).astype(np.int64))
     rec = {
         "workload": name,
         "source": "oracle/sbm_oracle.c orc_mg_solve, FP64, V(2,2) damped Jacobi, "
@@ -43,13 +71,98 @@ def make(name, nsample=4096):
         "n": list(wk.n), "h": wk.h, "moduli": list(wk.moduli), "psi_min": wk.psi_min,
         "status": res.status, "cycles_to_1e-14": res.cycles, "cycles_to_1e-10": cyc10,
         "history": hist, "oracle_seconds": dt, "seconds_per_cycle": dt / max(res.cycles, 1),
-        "sample_index": idx.tolist(), "sample_u": res.u[idx].tolist(),
-        "u_norm": float(np.linalg.norm(res.u)),
+        "u": field_record(res.u, 9001),
     }
-    out = os.path.join(os.path.dirname(os.path.abspath(__file__)), f"{name}_oracle.json")
+    # the sample of the original record format (bench.py reads these two keys)
+    rec["sample_index"] = rec["u"]["sample_index"]
+    rec["sample_u"] = rec["u"]["sample"]
+    rec["u_norm"] = rec["u"]["norm"]
+    return rec
+
+
+def make_topopt(name, wk):
+    """Compliance J = h^3 f . u of the cantilever: the forward solution, the adjoint
+    lambda of K lambda = dJ/du = h^3 f (homogeneous Dirichlet data), and the
+    gradients dJ/dpsi_c = -lambda_c^T S_c u_c and dJ/drho = p'(rho) dJ/dpsi."""
+    P = oracle.Problem(wk.dim, wk.n, wk.h, *wk.moduli, dirichlet=wk.dirichlet_bits())
+    psi, dpsi = oracle.simp(wk.rho, wk.psi_min)
+    t = time.time()
+    res, hist = _solve_to_floor(P, psi, wk.f, wk.u0, wk.omega)
+    mask = oracle.dirichlet_mask(P)
+    dJdu = np.where(mask, 0.0, wk.h ** 3 * wk.f)
+    adj, ahist = _solve_to_floor(P, psi, dJdu, np.zeros(P.ndofs), wk.omega)
+    gpsi = oracle.dJdpsi(P, res.u, adj.u)
+    dt = time.time() - t
+    cyc10 = next(i for i, v in enumerate(hist) if v <= 1e-10)
+    return {
+        "workload": name,
+        "source": "oracle/sbm_oracle.c orc_mg_solve (forward and adjoint, FP64, V(2,2) damped Jacobi, "
+                  f"omega={wk.omega}) and orc_dJdpsi, written by tests/golden/make_golden.py",
+        "n": list(wk.n), "h": wk.h, "moduli": list(wk.moduli), "psi_min": wk.psi_min,
+        "status": res.status, "cycles": res.cycles, "cycles_to_1e-10": cyc10, "history": hist,
+        "adjoint_cycles": adj.cycles, "adjoint_history": ahist, "oracle_seconds": dt,
+        "compliance": float(wk.h ** 3 * wk.f @ res.u),
+        "u": field_record(res.u, 9101), "lambda": field_record(adj.u, 9102),
+        "dJdpsi": field_record(gpsi, 9103), "dJdrho": field_record(gpsi * dpsi, 9103),
+    }
+
+
+def amr_oracle(wk):
+    """The oracle's composite problem for a refinement workload: levels, boxes, psi
+    floored at psi_min with the coarse means under the patches."""
+    P = oracle.Problem(wk.dim, wk.n, wk.h, *wk.moduli, dirichlet=wk.dirichlet_bits())
+    A = oracle.Amr(P, [(lo[:wk.dim], hi[:wk.dim]) for lo, hi in wk.boxes])
+    psis = [np.ascontiguousarray(np.maximum(wk.level_psi(a), wk.psi_min)) for a in range(A.nlev)]
+    oracle.amr_coarsen_psi(A, psis)
+    return A, psis
+
+
+def make_amr(name, wk):
+    """Composite solution of a refinement workload (no load; Dirichlet data from the
+    workload's initial guess) by the oracle's correction iteration to relres 1e-14
+    (or its FP64 floor).  Every level's filled storage array is recorded."""
+    A, psis = amr_oracle(wk)
+    fs = [np.zeros(A.level_problem(a).ndofs) for a in range(A.nlev)]
+    us = [np.ascontiguousarray(wk.level_u0(a)) for a in range(A.nlev)]
+    t = time.time()
+    res = oracle.amr_solve(A, psis, fs, us, omega=0.5, omega_base=wk.omega,
+                           smoother_base="gs" if wk.smoother in ("gs", "mcgs") else "jacobi",
+                           tol=1e-14, max_cycles=400)
+    dt = time.time() - t
+    hist = [float(v) for v in res.history]
+    assert res.status == 0 or min(hist) <= 1e-12, (res.status, min(hist))
+    return {
+        "workload": name,
+        "source": "oracle/sbm_oracle.c orc_amr_solve (composite correction iteration, FP64) of the composite "
+                  "problem of orc_amr_residual, written by tests/golden/make_golden.py",
+        "n": list(wk.n), "h": wk.h, "moduli": list(wk.moduli), "psi_min": wk.psi_min,
+        "boxes": [[list(lo), list(hi)] for lo, hi in wk.boxes],
+        "status": res.status, "cycles": res.cycles, "history": hist, "oracle_seconds": dt,
+        "levels": [field_record(us[a], 9200 + a) for a in range(A.nlev)],
+    }
+
+
+def voids_amr_3d(n0):
+    return W.voids_amr(3, n0, 2, count=16, rmin=0.04, rmax=0.12)
+
+
+RECIPES = {
+    "damage_3d_129": (lambda: W.damage3d(129), make_damage),
+    "damage_3d_65": (lambda: W.damage3d(65), make_damage),
+    "topopt_3d": (lambda: W.topopt3d(), make_topopt),
+    "voids_amr_2d": (lambda: W.voids_amr(2, 129, 3), make_amr),
+    "voids_amr_3d_65": (lambda: voids_amr_3d(65), make_amr),
+    "voids_amr_3d_33": (lambda: voids_amr_3d(33), make_amr),
+}
+
+
+def make(name):
+    build, writer = RECIPES[name]
+    rec = writer(name, build())
+    out = os.path.join(HERE, f"{name}_oracle.json")
     with open(out, "w") as fh:
         json.dump(rec, fh)
-    print(out, res.status, res.cycles, cyc10, f"{dt:.1f}s")
+    print(out, rec.get("status"), f"{rec['oracle_seconds']:.1f}s")
 
 
 if __name__ == "__main__":

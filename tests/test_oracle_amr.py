@@ -331,3 +331,44 @@ def test_composite_residual_is_affine_in_the_owned_values(oracle_lib, dim):
     r_junk = oracle.amr_residual(A, psis, fs, junk)
     for a in range(A.nlev):
         assert np.array_equal(r_junk[a], r_u[a]), a
+
+
+@pytest.mark.parametrize("dim,n0,boxes,bits", [
+    (2, 9, [((4, 4), (12, 10))], (4, 4 | 8, 0)),
+    (2, 9, [((4, 2), (12, 12)), ((10, 6), (20, 18))], (1 | 4, 4, 0)),
+    (2, 9, [((0, 4), (12, 16)), ((0, 10), (14, 30))], (1 | 4, 8, 0)),
+    (3, 5, [((2, 2, 2), (6, 6, 6))], (16, 16 | 32, 16)),
+    (3, 5, [((2, 2, 2), (6, 6, 6)), ((6, 6, 4), (10, 10, 10))], (16 | 32, 16, 1 | 16)),
+])
+def test_composite_iteration_reaches_the_dense_composite_solution(oracle_lib, dim, n0, boxes, bits):
+    """The oracle's correction iteration (orc_amr_solve) converges to the solution
+    of the composite problem: the same values as the dense solve of the probed
+    composite system on every dof of every level, and a composite residual, checked
+    by the oracle's own residual routine, at the requested tolerance.  Cases: one
+    and two nested patches, a patch on the domain boundary, 2D and 3D, random psi
+    down to 1e-3, Dirichlet data on several faces, a random load."""
+    A = _amr(dim, n0, boxes, bits=bits)
+    psis = oracle.amr_coarsen_psi(A, _psi(A, lambda X, Y, Z: np.maximum(
+        1e-3, 0.5 + 0.5 * np.sin(7 * X + 3 * Y - 5 * Z) * np.cos(4 * X - 6 * Y + 2 * Z))))
+    fs = [W.uniform(500 + a, A.level_problem(a).ndofs, -1, 1) for a in range(A.nlev)]
+    us0 = []
+    for a in range(A.nlev):
+        P = A.level_problem(a)
+        X, Y, Z = level_coords(A, a)
+        u = np.zeros(P.ndofs)
+        for p in range(dim):
+            for n in range(P.nnodes):
+                if dirichlet_dof(A, a, (int(X[n]), int(Y[n]), int(Z[n])), p):
+                    u[p * P.nnodes + n] = 0.01 * (p + 1) + 0.002 * X[n] * P.h
+        us0.append(u)
+    ref = dense_solve(A, psis, fs, [u.copy() for u in us0])
+    us = [u.copy() for u in us0]
+    res = oracle.amr_solve(A, psis, fs, us, omega=0.5, tol=1e-13, max_cycles=300)
+    assert res.status == 0, (res.status, res.history[-3:])
+    scale = max(np.abs(r).max() for r in ref)
+    for a in range(A.nlev):
+        assert np.abs(us[a] - ref[a]).max() <= 1e-10 * scale, a
+    r = oracle.amr_residual(A, psis, fs, [u.copy() for u in us])
+    r0 = oracle.amr_residual(A, psis, fs, [u.copy() for u in us0])
+    nrm = lambda rs: np.sqrt(sum(float(x @ x) for x in rs))
+    assert nrm(r) <= 1e-13 * nrm(r0) * (1 + 1e-9)
