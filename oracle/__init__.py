@@ -76,6 +76,9 @@ def _L():
             "orc_direct_solve": (C.c_int, [P, _dp, _dp, _dp]),
             "orc_mg_solve": (C.c_int, [P, _dp, _dp, _dp, C.POINTER(_Opts), _dp, C.POINTER(C.c_int)]),
             "orc_dJdpsi": (None, [P, _dp, _dp, _dp]),
+            "orc_apply_product": (None, [P, C.c_int, _dp, _dp, _dp]),
+            "orc_diagonal_product": (None, [P, C.c_int, _dp, _dp]),
+            "orc_jacobi_product": (None, [P, C.c_int, _dp, _dp, _dp, C.c_double]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -143,6 +146,29 @@ def element_matrix(P: Problem) -> np.ndarray:
 def apply(P: Problem, psi, u) -> np.ndarray:
     out = np.zeros(P.ndofs)
     _L().orc_apply(C.byref(P.c()), _f64(psi), _f64(u), out)
+    return out
+
+
+NODE_PSI, CELL_PSI = 1, 2
+
+
+def apply_product(P: Problem, variant: int, psi, u) -> np.ndarray:
+    """K u of the product-rule strong form (Sec. 2.3) at interior nodes, 0 on the
+    faces; psi at nodes (NODE_PSI) or in cells averaged to the nodes (CELL_PSI)."""
+    out = np.zeros(P.ndofs)
+    _L().orc_apply_product(C.byref(P.c()), variant, _f64(psi), _f64(u), out)
+    return out
+
+
+def diagonal_product(P: Problem, variant: int, psi) -> np.ndarray:
+    out = np.zeros(P.ndofs)
+    _L().orc_diagonal_product(C.byref(P.c()), variant, _f64(psi), out)
+    return out
+
+
+def jacobi_product(P: Problem, variant: int, psi, f, u, omega: float) -> np.ndarray:
+    out = _f64(u).copy()
+    _L().orc_jacobi_product(C.byref(P.c()), variant, _f64(psi), _f64(f), out, omega)
     return out
 
 

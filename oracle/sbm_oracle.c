@@ -1189,3 +1189,133 @@ int orc_amr_solve(const orc_amr *A, double *const *psi, double *const *f, double
     if (cycles) *cycles = ncyc;
     return status;
 }
+
+/* ---------------------------------------- product-rule strong form (Sec. 2.3) */
+
+/* Nodal value of psi and its gradient g at interior node (i,j,k).
+ * variant ORC_NODE_PSI: psi is nodal, g_a = (psi(n + e_a) - psi(n - e_a)) / (2h);
+ * variant ORC_CELL_PSI: psi is in cells, psi_n = mean of the 2^d cells around n and
+ *   g_a = mean over the 2^(d-1) cell pairs facing each other across n along a of
+ *   (psi_+ - psi_-) / h  (in 1D: the cell-placed update of Sec. 2.3). */
+static void product_psi(const orc_problem *P, int variant, const double *psi, int i, int j, int k, double *pn,
+                        double g[3])
+{
+    const int d = P->dim, nc = 1 << d;
+    const int n3[3] = {i, j, k};
+    g[0] = g[1] = g[2] = 0.0;
+    if (variant == ORC_NODE_PSI) {
+        *pn = psi[nid(P, i, j, k)];
+        for (int a = 0; a < d; ++a) {
+            int up[3] = {i, j, k}, dn[3] = {i, j, k};
+            up[a] += 1;
+            dn[a] -= 1;
+            g[a] = (psi[nid(P, up[0], up[1], up[2])] - psi[nid(P, dn[0], dn[1], dn[2])]) / (2.0 * P->h);
+        }
+        return;
+    }
+    double s = 0.0;
+    for (int c = 0; c < nc; ++c) {           /* cell with lower corner n - 1 + bits of c */
+        int cc[3] = {0, 0, 0};
+        for (int a = 0; a < d; ++a) cc[a] = n3[a] - 1 + ((c >> a) & 1);
+        const double v = psi[cid(P, cc[0], cc[1], cc[2])];
+        s += v;
+        for (int a = 0; a < d; ++a) g[a] += (((c >> a) & 1) ? v : -v);
+    }
+    *pn = s / nc;
+    for (int a = 0; a < d; ++a) g[a] /= (double)(nc / 2) * P->h;
+}
+
+void orc_apply_product(const orc_problem *P, int variant, const double *psi, const double *u, double *Ku)
+{
+    const int d = P->dim;
+    const long N = orc_nnodes(P);
+    const double h = P->h;
+    memset(Ku, 0, sizeof(double) * d * N);
+    for (int k = (d == 3 ? 1 : 0); k < (d == 3 ? P->n[2] - 1 : 1); ++k)
+        for (int j = 1; j < P->n[1] - 1; ++j)
+            for (int i = 1; i < P->n[0] - 1; ++i) {
+                const int n3[3] = {i, j, k};
+                double pn, g[3];
+                product_psi(P, variant, psi, i, j, k, &pn, g);
+                /* centred first differences D[l][q] = d_l u_q and second differences
+                 * H[a][b][q] = d_a d_b u_q of u at the node */
+                double D[3][3] = {{0}}, H[3][3][3] = {{{0}}};
+                for (int q = 0; q < d; ++q) {
+                    const double *uq = u + q * N;
+                    const double c = uq[nid(P, i, j, k)];
+                    for (int a = 0; a < d; ++a) {
+                        int up[3] = {i, j, k}, dn[3] = {i, j, k};
+                        up[a] += 1;
+                        dn[a] -= 1;
+                        const double vu = uq[nid(P, up[0], up[1], up[2])], vd = uq[nid(P, dn[0], dn[1], dn[2])];
+                        D[a][q] = (vu - vd) / (2.0 * h);
+                        H[a][a][q] = (vu - 2.0 * c + vd) / (h * h);
+                        for (int b = a + 1; b < d; ++b) {
+                            int pp[3] = {n3[0], n3[1], n3[2]}, pm[3] = {n3[0], n3[1], n3[2]};
+                            int mp[3] = {n3[0], n3[1], n3[2]}, mm[3] = {n3[0], n3[1], n3[2]};
+                            pp[a] += 1; pp[b] += 1;
+                            pm[a] += 1; pm[b] -= 1;
+                            mp[a] -= 1; mp[b] += 1;
+                            mm[a] -= 1; mm[b] -= 1;
+                            const double x = (uq[nid(P, pp[0], pp[1], pp[2])] - uq[nid(P, pm[0], pm[1], pm[2])] -
+                                              uq[nid(P, mp[0], mp[1], mp[2])] + uq[nid(P, mm[0], mm[1], mm[2])]) /
+                                             (4.0 * h * h);
+                            H[a][b][q] = x;
+                            H[b][a][q] = x;
+                        }
+                    }
+                }
+                /* (A u)_p = sum_{a,q,b} C_{p a q b} (psi_n d_a d_b u_q + g_a d_b u_q);  K = -A */
+                for (int p = 0; p < d; ++p) {
+                    double s = 0.0;
+                    for (int a = 0; a < d; ++a)
+                        for (int q = 0; q < d; ++q)
+                            for (int b = 0; b < d; ++b) {
+                                const double C = cubic_C(P, p, a, q, b);
+                                if (C == 0.0) continue;
+                                s += C * (pn * H[a][b][q] + g[a] * D[b][q]);
+                            }
+                    Ku[p * N + nid(P, i, j, k)] = -s;
+                }
+            }
+}
+
+void orc_diagonal_product(const orc_problem *P, int variant, const double *psi, double *D)
+{
+    const int d = P->dim;
+    const long N = orc_nnodes(P);
+    memset(D, 0, sizeof(double) * d * N);
+    for (int k = (d == 3 ? 1 : 0); k < (d == 3 ? P->n[2] - 1 : 1); ++k)
+        for (int j = 1; j < P->n[1] - 1; ++j)
+            for (int i = 1; i < P->n[0] - 1; ++i) {
+                double pn, g[3];
+                product_psi(P, variant, psi, i, j, k, &pn, g);
+                /* only the second differences d_a d_a u_p touch u_p at the node itself
+                 * (coefficient -2/h^2); K = -A */
+                for (int p = 0; p < d; ++p) {
+                    double s = 0.0;
+                    for (int a = 0; a < d; ++a) s += cubic_C(P, p, a, p, a) * 2.0 / (P->h * P->h);
+                    D[p * N + nid(P, i, j, k)] = pn * s;
+                }
+            }
+}
+
+void orc_jacobi_product(const orc_problem *P, int variant, const double *psi, const double *f, double *u,
+                        double omega)
+{
+    const int d = P->dim;
+    const long N = orc_nnodes(P);
+    double *Ku = malloc(sizeof(double) * d * N), *D = malloc(sizeof(double) * d * N);
+    orc_apply_product(P, variant, psi, u, Ku);
+    orc_diagonal_product(P, variant, psi, D);
+    for (int p = 0; p < d; ++p)
+        for (int k = (d == 3 ? 1 : 0); k < (d == 3 ? P->n[2] - 1 : 1); ++k)
+            for (int j = 1; j < P->n[1] - 1; ++j)
+                for (int i = 1; i < P->n[0] - 1; ++i) {
+                    if (orc_is_dirichlet(P, i, j, k, p)) continue;
+                    const long e = p * N + nid(P, i, j, k);
+                    u[e] += omega * (f[e] - Ku[e]) / D[e];
+                }
+    free(Ku);
+    free(D);
+}

@@ -93,6 +93,23 @@ int  orc_direct_solve(const orc_problem *P, const double *psi, const double *f, 
 int  orc_mg_solve(const orc_problem *P, const double *psi, const double *f, double *u,
                   const orc_mg_opts *o, double *hist, int *cycles);
 
+/* Product-rule strong form (Sec. 2.3): the literal discretisation of
+ *     div(psi C grad u) = psi C : grad grad u + grad psi . C grad u
+ * at interior nodes by centred differences (3-point second differences, 4-point
+ * mixed differences), with psi either at nodes (ORC_NODE_PSI, psi packed over nodes;
+ * grad psi by centred differences: the node-placed operator of Sec. 2.3) or in
+ * cells averaged to the node (ORC_CELL_PSI, psi packed over cells; psi_n = mean of
+ * the 2^d cells, grad psi from the cells facing each other across the node: the
+ * cell-placed update of Sec. 2.3, which in 1D is the flux form).  K u = -A u at the
+ * interior nodes, 0 on the box faces (the form is defined at interior nodes only). */
+enum { ORC_NODE_PSI = 1, ORC_CELL_PSI = 2 };
+void orc_apply_product(const orc_problem *P, int variant, const double *psi, const double *u, double *Ku);
+/* Diagonal of K for the product-rule form: psi_n * sum_a 2 C_papa / h^2 (interior). */
+void orc_diagonal_product(const orc_problem *P, int variant, const double *psi, double *D);
+/* One damped Jacobi sweep u += omega (f - K u) / D on the interior free dofs. */
+void orc_jacobi_product(const orc_problem *P, int variant, const double *psi, const double *f, double *u,
+                        double omega);
+
 /* g_c = -lambda_c^T S_c u_c for every cell (S_c = unit-psi element matrix). */
 void orc_dJdpsi(const orc_problem *P, const double *u, const double *lam, double *g);
 
