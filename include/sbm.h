@@ -181,6 +181,30 @@ sbm_status sbm_bottom_correct(sbm_grid grid, int fp32, const double *f, double *
 /* dJdpsi_c = -lambda_c^T S_c u_c for every cell of the finest level. */
 sbm_status sbm_dJdpsi(sbm_grid grid, const double *u, const double *lambda, double *dJdpsi);
 
+/* ---- the operator variants of Sec. 2.3 (for comparison with the cell-flux form) ----
+ * The literal product-rule discretisation of the strong form
+ *     div(psi C grad u) = psi C : grad grad u + grad psi . C grad u
+ * at interior nodes by centred differences (3-point second differences, 4-point
+ * mixed differences; Sec. 2.3 prints its 1D form), K u = -(that), with psi either
+ *   SBM_OP_PRODUCT_NODE: at nodes (psi packed over the nodes of the finest level;
+ *     grad psi by centred differences) -- the node-placed operator whose Jacobi
+ *     update Sec. 2.3 shows to diverge next to a region where psi vanishes, or
+ *   SBM_OP_PRODUCT_CELL: in cells (packed over the cells) and averaged to the node
+ *     (psi_n = mean of the 2^d cells, grad psi from the cells facing each other
+ *     across the node) -- the cell-placed update of Sec. 2.3 (in 1D the flux form).
+ * Both are defined at interior nodes only: K u is 0 on the box faces.  psi is used
+ * as given (no floor), so a psi of 0 is allowed.  Finest-level grid, the grid's
+ * moduli; FP64.  Not part of the solve: the solver's operator is the cell-flux form. */
+enum { SBM_OP_PRODUCT_NODE = 1, SBM_OP_PRODUCT_CELL = 2 };
+/* Ku = K u for the chosen variant (device, packed). */
+sbm_status sbm_apply_product(sbm_grid grid, int variant, const double *psi, const double *u, double *Ku);
+/* `sweeps` damped Jacobi sweeps u += omega (f - K u) / diag(K) on the interior dofs
+ * that carry no Dirichlet condition (diag(K) = psi_n sum_a 2 C_papa / h^2); u (device,
+ * packed) in place; f device, packed.  A vanishing diagonal gives Inf/NaN entries,
+ * not an error (that is the divergence the comparison exhibits). */
+sbm_status sbm_jacobi_product(sbm_grid grid, int variant, const double *psi, const double *f, double *u,
+                              double omega, int sweeps);
+
 /* ---- measurement ---- */
 enum { SBM_K_RESIDUAL64 = 0, SBM_K_JACOBI = 1, SBM_K_RESIDUAL = 2 };
 /* Launch one hot-path kernel of the finest level `reps` times back to back on

@@ -275,6 +275,18 @@ class Grid:
         self._check(lib().sbm_bottom_correct(self._h, int(fp32), _ptr(f), _ptr(out)))
         return out
 
+    # -- the operator variants of Sec. 2.3 (product-rule strong form)
+    def apply_product(self, variant: int, psi: torch.Tensor, u: torch.Tensor) -> torch.Tensor:
+        out = torch.empty_like(u)
+        self._check(lib().sbm_apply_product(self._h, variant, _ptr(psi), _ptr(u), _ptr(out)))
+        return out
+
+    def jacobi_product(self, variant: int, psi: torch.Tensor, f: torch.Tensor, u: torch.Tensor, omega=2.0 / 3.0,
+                       sweeps=1) -> torch.Tensor:
+        out = u.clone()
+        self._check(lib().sbm_jacobi_product(self._h, variant, _ptr(psi), _ptr(f), _ptr(out), omega, sweeps))
+        return out
+
     def dJdpsi(self, u: torch.Tensor, lam: torch.Tensor) -> torch.Tensor:
         out = torch.empty(self.ncells(), dtype=torch.float64, device=u.device)
         self._check(lib().sbm_dJdpsi(self._h, _ptr(u), _ptr(lam), _ptr(out)))

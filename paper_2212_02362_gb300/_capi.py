@@ -69,6 +69,8 @@ _SIGS = {
     "sbm_get_psi": (C.c_int, [_grid, C.c_int, _dptr]),
     "sbm_bottom_correct": (C.c_int, [_grid, C.c_int, _dptr, _dptr]),
     "sbm_dJdpsi": (C.c_int, [_grid, _dptr, _dptr, _dptr]),
+    "sbm_apply_product": (C.c_int, [_grid, C.c_int, _dptr, _dptr, _dptr]),
+    "sbm_jacobi_product": (C.c_int, [_grid, C.c_int, _dptr, _dptr, _dptr, C.c_double, C.c_int]),
     "sbm_time_kernel": (C.c_int, [_grid, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                   C.POINTER(C.c_double)]),
     "sbm_amr_add_level": (C.c_int, [_grid, C.POINTER(sbm_box)]),
@@ -84,6 +86,8 @@ _SIGS = {
 }
 
 EXPORTED = tuple(_SIGS)
+
+SBM_OP_PRODUCT_NODE, SBM_OP_PRODUCT_CELL = 1, 2
 
 _lib = None
 

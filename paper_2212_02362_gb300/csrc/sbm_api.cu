@@ -1698,6 +1698,48 @@ sbm_status sbm_dJdpsi(sbm_grid G, const double *u, const double *lam, double *g)
     return SBM_OK;
 }
 
+sbm_status sbm_apply_product(sbm_grid G, int variant, const double *psi, const double *u, double *Ku)
+{
+    if (!G) return fail(G, SBM_ERR_ARG, "null grid");
+    if (variant != SBM_OP_PRODUCT_NODE && variant != SBM_OP_PRODUCT_CELL) return fail(G, SBM_ERR_ARG, "unknown variant");
+    if (!G->has_moduli) return fail(G, SBM_ERR_STATE, "moduli not set (sbm_set_moduli)");
+    if (!is_dev_ptr(psi, G->dev) || !is_dev_ptr(u, G->dev) || !is_dev_ptr(Ku, G->dev))
+        return fail(G, SBM_ERR_ARG, "psi, u and Ku must be device pointers");
+    CK(cudaSetDevice(G->dev));
+    const Level &L = G->L[G->nl - 1];
+    const int n[3] = {L.g.nx, L.g.ny, L.g.nz};
+    CK(launch_product(0, L.g.dim, n, L.h, G->mod, L.g.dm, variant, 0.0, psi, u, nullptr, Ku, G->st));
+    CK(cudaStreamSynchronize(G->st));
+    return SBM_OK;
+}
+
+sbm_status sbm_jacobi_product(sbm_grid G, int variant, const double *psi, const double *f, double *u, double omega,
+                              int sweeps)
+{
+    if (!G) return fail(G, SBM_ERR_ARG, "null grid");
+    if (variant != SBM_OP_PRODUCT_NODE && variant != SBM_OP_PRODUCT_CELL) return fail(G, SBM_ERR_ARG, "unknown variant");
+    if (sweeps < 0 || !(omega > 0.0 && omega < 2.0)) return fail(G, SBM_ERR_ARG, "sweeps >= 0 and 0 < omega < 2");
+    if (!G->has_moduli) return fail(G, SBM_ERR_STATE, "moduli not set (sbm_set_moduli)");
+    if (!is_dev_ptr(psi, G->dev) || !is_dev_ptr(u, G->dev) || !is_dev_ptr(f, G->dev))
+        return fail(G, SBM_ERR_ARG, "psi, f and u must be device pointers");
+    CK(cudaSetDevice(G->dev));
+    set_dirichlet_bits(G);
+    Level &L = G->L[G->nl - 1];
+    const int n[3] = {L.g.nx, L.g.ny, L.g.nz};
+    const size_t bytes = sizeof(double) * L.g.dim * (size_t)nnodes(L.g);
+    // ping-pong through the finest level's two work buffers (each holds dim * cs >= dim * N)
+    double *buf[2] = {L.du[0], L.du[1]};
+    CK(cudaMemcpyAsync(buf[0], u, bytes, cudaMemcpyDeviceToDevice, G->st));
+    int cur = 0;
+    for (int s = 0; s < sweeps; ++s) {
+        CK(launch_product(1, L.g.dim, n, L.h, G->mod, L.g.dm, variant, omega, psi, buf[cur], f, buf[1 - cur], G->st));
+        cur ^= 1;
+    }
+    CK(cudaMemcpyAsync(u, buf[cur], bytes, cudaMemcpyDeviceToDevice, G->st));
+    CK(cudaStreamSynchronize(G->st));
+    return SBM_OK;
+}
+
 sbm_status sbm_time_kernel(sbm_grid G, int which, int reps, int flush_l2, double *ms, double *bytes, double *flops)
 {
     sbm_status s = check_ready(G);

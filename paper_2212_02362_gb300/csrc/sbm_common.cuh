@@ -267,6 +267,12 @@ struct AmrInfo {
 cudaError_t launch_lincomb(long long n, double a, const double *x, double b, const double *y, double c,
                            const double *z, double *out, cudaStream_t s);
 cudaError_t launch_sum_parts(const double *part, int n, double *out, cudaStream_t s);
+// Product-rule strong form of Sec. 2.3 (k_variant.cu), FP64 packed arrays: mode 0
+// out = K u; mode 1 one damped Jacobi sweep from u into out.  variant 1: psi at
+// nodes, 2: psi in cells.
+cudaError_t launch_product(int mode, int dim, const int n[3], double h, const double mod[3], const unsigned dm[3],
+                           int variant, double omega, const double *psi, const double *u, const double *f, double *out,
+                           cudaStream_t s);
 // Reads a buffer (measurement: leaves L2 holding clean lines of it).
 cudaError_t launch_l2_read(const void *buf, size_t bytes, float *sink, cudaStream_t s);
 // adjoint of the composite problem
