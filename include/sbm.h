@@ -205,6 +205,20 @@ sbm_status sbm_apply_product(sbm_grid grid, int variant, const double *psi, cons
 sbm_status sbm_jacobi_product(sbm_grid grid, int variant, const double *psi, const double *f, double *u,
                               double omega, int sweeps);
 
+/* ---- failure-path hooks (not part of the paper's method) ----
+ * For tests of the error paths without a GPU fault or real memory pressure.
+ * sbm_set_alloc_limit: from now on, a grid creation (or patch addition) whose
+ * device allocations would exceed `bytes` in total fails with SBM_ERR_OOM, as if
+ * cudaMalloc had run out of memory; a failed creation frees what it allocated and
+ * reports through sbm_last_error(NULL).  0 removes the cap.  Process-wide.
+ * sbm_set_wait_limit: polls each block makes at one grid barrier of the
+ * bottom-level inversion (one cooperative launch, run by the first solve after
+ * psi or the moduli change) before it gives up; on a timeout every block leaves
+ * the launch and the solve returns SBM_ERR_CUDA with the GPU context intact.  0
+ * restores the default bound.  Forces the next solve to invert again. */
+void sbm_set_alloc_limit(size_t bytes);
+sbm_status sbm_set_wait_limit(sbm_grid grid, long long spins);
+
 /* ---- measurement ---- */
 enum { SBM_K_RESIDUAL64 = 0, SBM_K_JACOBI = 1, SBM_K_RESIDUAL = 2 };
 /* Launch one hot-path kernel of the finest level `reps` times back to back on

@@ -339,7 +339,7 @@ constexpr long long kGridSpinLimit = 1LL << 22;
 // Grid barrier number `phase` (1, 2, ...): every block adds 1 to a counter that is
 // never reset during the launch and waits until it reaches nblocks * phase.  One
 // atomic per block and plain polling; the wait is bounded (bar[2] set on timeout).
-__device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned nblocks, unsigned phase)
+__device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned nblocks, unsigned phase, long long limit)
 {
     __syncthreads();
     int ok = 1;
@@ -350,7 +350,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned nblocks, un
         volatile unsigned *cnt = bar;
         long long it = 0;
         while (*cnt < target) {
-            if (++it > kGridSpinLimit || *(volatile unsigned *)(bar + 2)) {
+            if (++it > limit || *(volatile unsigned *)(bar + 2)) {
                 atomicExch(bar + 2, 1u);
                 ok = 0;
                 break;
@@ -371,7 +371,8 @@ __device__ __forceinline__ int next_pivot(const Geom &g, long long N, int k, int
     return n;
 }
 
-__global__ void k_gauss_jordan(const Geom g, int n, double *A, double *tmp, unsigned *bar, int in_smem)
+__global__ void k_gauss_jordan(const Geom g, int n, double *A, double *tmp, unsigned *bar, int in_smem,
+                               long long limit)
 {
     // in_smem: the block's rows (blockIdx.x + m gridDim.x) live in shared memory
     extern __shared__ double srow[];
@@ -388,7 +389,7 @@ __global__ void k_gauss_jordan(const Geom g, int n, double *A, double *tmp, unsi
         tmp[n + t] = A[(long long)t * n + k];
     }
     unsigned phase = 1;
-    if (!grid_barrier(bar, nb, phase++)) return;
+    if (!grid_barrier(bar, nb, phase++, limit)) return;
     int cur = 0;
     while (k < n) {
         const int kn = next_pivot(g, N, k + 1, n);
@@ -409,7 +410,7 @@ __global__ void k_gauss_jordan(const Geom g, int n, double *A, double *tmp, unsi
                 if (j == kn) Cn[i] = v;
             }
         }
-        if (!grid_barrier(bar, nb, phase++)) return;
+        if (!grid_barrier(bar, nb, phase++, limit)) return;
         cur ^= 1;
         k = kn;
     }
@@ -620,7 +621,8 @@ cudaError_t launch_bottom_dirichlet(const Geom &g, double *A, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_gauss_jordan(const Geom &g, int n, double *A, double *tmp, unsigned *bar, cudaStream_t s)
+cudaError_t launch_gauss_jordan(const Geom &g, int n, double *A, double *tmp, unsigned *bar, long long spins,
+                                cudaStream_t s)
 {
     int dev = 0, nsm = 0, per_sm = 0, coop = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -643,7 +645,8 @@ cudaError_t launch_gauss_jordan(const Geom &g, int n, double *A, double *tmp, un
     e = cudaMemsetAsync(bar, 0, 4 * sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
     Geom gg = g;
-    void *args[] = {&gg, &n, &A, &tmp, &bar, &in_smem};
+    long long limit = spins > 0 ? spins : kGridSpinLimit;
+    void *args[] = {&gg, &n, &A, &tmp, &bar, &in_smem, &limit};
     e = cudaLaunchCooperativeKernel((const void *)k_gauss_jordan, dim3(nblocks), dim3(kThreads), args, smem, s);
     ++g_launches;
     return e;

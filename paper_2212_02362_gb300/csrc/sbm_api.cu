@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cstring>
 #include <algorithm>
+#include <atomic>
 #include <type_traits>
 #include <string>
 #include <vector>
@@ -33,6 +34,9 @@ bool sbm::is_dev_ptr(const void *p, int dev)
 namespace {
 
 thread_local std::string g_lib_error;
+// Cap on the device bytes one grid may allocate (0: none), for tests of the
+// out-of-memory path without real memory pressure.
+std::atomic<unsigned long long> g_alloc_cap{0};
 
 struct Level {
     Geom g{};
@@ -111,6 +115,8 @@ struct sbm_grid_s {
     int nb = 0;                 // bottom dofs
     double *A64 = nullptr, *gjtmp = nullptr;
     unsigned *gjbar = nullptr;  // grid-barrier words of the bottom-level inversion
+    long long gj_spins = 0;     // polls per grid barrier before it gives up (0: the default)
+    size_t allocated = 0;       // device bytes allocated for the grid (checked against the cap)
     float *A32 = nullptr;
     int *gather = nullptr;
     bool bottom_ready = false;
@@ -129,6 +135,17 @@ struct sbm_grid_s {
 };
 
 namespace {
+
+// cudaMalloc of grid storage, refused (as cudaErrorMemoryAllocation) when the
+// grid's total would exceed the cap set by sbm_set_alloc_limit.
+cudaError_t gmalloc(sbm_grid G, void **p, size_t bytes)
+{
+    const unsigned long long cap = g_alloc_cap.load();
+    if (cap && G->allocated + bytes > cap) return cudaErrorMemoryAllocation;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaSuccess) G->allocated += bytes;
+    return e;
+}
 
 sbm_status fail(sbm_grid G, sbm_status st, const std::string &msg)
 {
@@ -399,7 +416,7 @@ sbm_status setup_bottom(sbm_grid G)
     CK(cudaMemsetAsync(G->A64, 0, sizeof(double) * n * n, G->st));
     CK(launch_bottom_assemble(B.g, B.psi64, B.c64, G->A64, G->st));
     CK(launch_bottom_dirichlet(B.g, G->A64, G->st));
-    CK(launch_gauss_jordan(B.g, (int)n, G->A64, G->gjtmp, G->gjbar, G->st));
+    CK(launch_gauss_jordan(B.g, (int)n, G->A64, G->gjtmp, G->gjbar, G->gj_spins, G->st));
     {
         unsigned hbar[4] = {0, 0, 0, 0};
         CK(cudaMemcpyAsync(hbar, G->gjbar, sizeof(hbar), cudaMemcpyDeviceToHost, G->st));
@@ -980,7 +997,7 @@ sbm_status amr_alloc_adjoint(sbm_grid G)
     for (auto &vec : G->adj)
         for (int a = 0; a <= G->npatch; ++a)
             if (!vec[a]) {
-                CK(cudaMalloc(&vec[a], sizeof(double) * amr_vec_len(G, a)));
+                CK(gmalloc(G, (void **)&vec[a], sizeof(double) * amr_vec_len(G, a)));
                 CK(cudaMemset(vec[a], 0, sizeof(double) * amr_vec_len(G, a)));
             }
     return SBM_OK;
@@ -1208,26 +1225,10 @@ sbm_status sbm_grid_destroy(sbm_grid G)
     return SBM_OK;
 }
 
-sbm_status sbm_grid_create(const sbm_grid_desc *d, sbm_grid *out)
+// Everything of sbm_grid_create after the descriptor checks: the stream, the level
+// hierarchy and its storage.  On failure the caller destroys the partial grid.
+static sbm_status grid_create_impl(const sbm_grid_desc *d, sbm_grid G)
 {
-    sbm_grid G = nullptr;
-    if (!d || !out) return fail(nullptr, SBM_ERR_ARG, "null descriptor or output");
-    *out = nullptr;
-    if (d->dim != 2 && d->dim != 3) return fail(nullptr, SBM_ERR_ARG, "dim must be 2 or 3");
-    if (d->n[0] < 2 || d->n[1] < 2 || (d->dim == 3 && d->n[2] < 2) || (d->dim == 2 && d->n[2] != 1))
-        return fail(nullptr, SBM_ERR_ARG, "node counts must be >= 2 (n[2] == 1 in 2D)");
-    if (!(d->h > 0.0) || !std::isfinite(d->h)) return fail(nullptr, SBM_ERR_ARG, "h must be positive");
-    if (d->precision != SBM_FP64 && d->precision != SBM_MIXED) return fail(nullptr, SBM_ERR_ARG, "bad precision");
-    const double nodes = (double)d->n[0] * d->n[1] * d->n[2];
-    if (nodes > 2.0e9) return fail(nullptr, SBM_ERR_ARG, "grid too large");
-    int ndev = 0;
-    if (cudaGetDeviceCount(&ndev) != cudaSuccess || d->device < 0 || d->device >= ndev) {
-        cudaGetLastError();
-        return fail(nullptr, SBM_ERR_CUDA, "no CUDA device with the requested ordinal");
-    }
-    G = new sbm_grid_s();
-    G->desc = *d;
-    G->dev = d->device;
     CK(cudaSetDevice(G->dev));
     if (d->stream) {
         G->st = (cudaStream_t)d->stream;
@@ -1252,6 +1253,12 @@ sbm_status sbm_grid_create(const sbm_grid_desc *d, sbm_grid *out)
         shapes.push_back({{n[0], n[1], n[2]}, h});
     }
     G->nl = (int)shapes.size();
+    {
+        // the coarsest level is solved densely: refuse before allocating anything
+        const auto &c = shapes.back().first;
+        const long long nb = (long long)c[0] * c[1] * c[2] * d->dim;
+        if (nb * nb > (1LL << 28)) return fail(G, SBM_ERR_ARG, "coarsest level too large for the dense bottom solve");
+    }
     for (int l = 0; l < G->nl; ++l) {
         const auto &sh = shapes[G->nl - 1 - l];   // level 0 = coarsest
         Level &L = G->L[l];
@@ -1265,18 +1272,18 @@ sbm_status sbm_grid_create(const sbm_grid_desc *d, sbm_grid *out)
         g.sy = (long long)g.sx * g.ny;
         g.cs = (g.sy * g.nz + 63) / 64 * 64;
         const size_t nd = (size_t)g.dim * g.cs;
-        CK(cudaMalloc(&L.psi64, sizeof(double) * g.cs));
-        CK(cudaMalloc(&L.psi32, sizeof(float) * g.cs));
+        CK(gmalloc(G, (void **)&L.psi64, sizeof(double) * g.cs));
+        CK(gmalloc(G, (void **)&L.psi32, sizeof(float) * g.cs));
         CK(cudaMemset(L.psi64, 0, sizeof(double) * g.cs));
         CK(cudaMemset(L.psi32, 0, sizeof(float) * g.cs));
         double **dptrs[] = {&L.du[0], &L.du[1], &L.df, &L.dr};
         for (double **p : dptrs) {
-            CK(cudaMalloc(p, sizeof(double) * nd));
+            CK(gmalloc(G, (void **)p, sizeof(double) * nd));
             CK(cudaMemset(*p, 0, sizeof(double) * nd));
         }
         float **sptrs[] = {&L.su[0], &L.su[1], &L.sf, &L.sr};
         for (float **p : sptrs) {
-            CK(cudaMalloc(p, sizeof(float) * nd));
+            CK(gmalloc(G, (void **)p, sizeof(float) * nd));
             CK(cudaMemset(*p, 0, sizeof(float) * nd));
         }
         if (g.dim == 3) {
@@ -1285,43 +1292,39 @@ sbm_status sbm_grid_create(const sbm_grid_desc *d, sbm_grid *out)
                 L.has_tm = L.has_tm && encode_sweep_maps(L.tm32[i], L.su[i], L.sf, L.psi32, g);
         }
         const int nk = (1 << g.dim) * g.dim;
-        CK(cudaMalloc(&L.Ke64, sizeof(double) * nk * nk));
-        CK(cudaMalloc(&L.Ke32, sizeof(float) * nk * nk));
+        CK(gmalloc(G, (void **)&L.Ke64, sizeof(double) * nk * nk));
+        CK(gmalloc(G, (void **)&L.Ke32, sizeof(float) * nk * nk));
     }
     Level &F = G->L[G->nl - 1];
     const size_t nfd = (size_t)F.g.dim * F.g.cs;
-    CK(cudaMalloc(&G->fsrc, sizeof(double) * nfd));
+    CK(gmalloc(G, (void **)&G->fsrc, sizeof(double) * nfd));
     CK(cudaMemset(G->fsrc, 0, sizeof(double) * nfd));
-    CK(cudaMalloc(&G->fadj, sizeof(double) * nfd));
+    CK(gmalloc(G, (void **)&G->fadj, sizeof(double) * nfd));
     CK(cudaMemset(G->fadj, 0, sizeof(double) * nfd));
     const long long nc = ncells_h(F.g);
-    CK(cudaMalloc(&G->psi_raw, sizeof(double) * nc));
-    CK(cudaMalloc(&G->rho, sizeof(double) * nc));
+    CK(gmalloc(G, (void **)&G->psi_raw, sizeof(double) * nc));
+    CK(gmalloc(G, (void **)&G->rho, sizeof(double) * nc));
     G->npart = 1;
     for (int l = 0; l < G->nl; ++l)
         G->npart = std::max({G->npart, sweep_blocks(G->L[l].g, false), sweep_blocks(G->L[l].g, true),
                              sweep_blocks_f2(G->L[l].g)});
-    CK(cudaMalloc(&G->part, sizeof(double) * G->npart));
-    CK(cudaMalloc(&G->derr, sizeof(int)));
-    CK(cudaMalloc(&G->dgate, 2 * sizeof(int)));
+    CK(gmalloc(G, (void **)&G->part, sizeof(double) * G->npart));
+    CK(gmalloc(G, (void **)&G->derr, sizeof(int)));
+    CK(gmalloc(G, (void **)&G->dgate, 2 * sizeof(int)));
     CK(cudaMemset(G->dgate, 0, 2 * sizeof(int)));
     CK(cudaMemset(G->derr, 0, sizeof(int)));
-    CK(cudaMalloc(&G->scal, sizeof(double) * 16));
+    CK(gmalloc(G, (void **)&G->scal, sizeof(double) * 16));
     CK(cudaMemset(G->scal, 0, sizeof(double) * 16));
     CK(cudaMallocHost(&G->hscal, sizeof(double) * 16));
-    CK(cudaMalloc(&G->dbad, sizeof(int)));
+    CK(gmalloc(G, (void **)&G->dbad, sizeof(int)));
     // bottom
     Level &B = G->L[0];
     G->nb = (int)(nnodes(B.g) * B.g.dim);
-    if ((long long)G->nb * G->nb > (1LL << 28)) {
-        sbm_grid_destroy(G);
-        return fail(nullptr, SBM_ERR_ARG, "coarsest level too large for the dense bottom solve");
-    }
-    CK(cudaMalloc(&G->A64, sizeof(double) * G->nb * G->nb));
-    CK(cudaMalloc(&G->A32, sizeof(float) * G->nb * G->nb));
-    CK(cudaMalloc(&G->gjtmp, sizeof(double) * 4 * G->nb));
-    CK(cudaMalloc(&G->gjbar, sizeof(unsigned) * 4));
-    CK(cudaMalloc(&G->gather, sizeof(int) * G->nb));
+    CK(gmalloc(G, (void **)&G->A64, sizeof(double) * G->nb * G->nb));
+    CK(gmalloc(G, (void **)&G->A32, sizeof(float) * G->nb * G->nb));
+    CK(gmalloc(G, (void **)&G->gjtmp, sizeof(double) * 4 * G->nb));
+    CK(gmalloc(G, (void **)&G->gjbar, sizeof(unsigned) * 4));
+    CK(gmalloc(G, (void **)&G->gather, sizeof(int) * G->nb));
     {
         std::vector<int> gi(G->nb);
         const long long N = nnodes(B.g);
@@ -1337,7 +1340,49 @@ sbm_status sbm_grid_create(const sbm_grid_desc *d, sbm_grid *out)
     for (int f = 0; f < 6; ++f)
         for (int p = 0; p < 3; ++p) G->bct[f][p] = SBM_FREE;
     set_dirichlet_bits(G);
+    return SBM_OK;
+}
+
+sbm_status sbm_grid_create(const sbm_grid_desc *d, sbm_grid *out)
+{
+    sbm_grid G = nullptr;
+    if (!d || !out) return fail(nullptr, SBM_ERR_ARG, "null descriptor or output");
+    *out = nullptr;
+    if (d->dim != 2 && d->dim != 3) return fail(nullptr, SBM_ERR_ARG, "dim must be 2 or 3");
+    if (d->n[0] < 2 || d->n[1] < 2 || (d->dim == 3 && d->n[2] < 2) || (d->dim == 2 && d->n[2] != 1))
+        return fail(nullptr, SBM_ERR_ARG, "node counts must be >= 2 (n[2] == 1 in 2D)");
+    if (!(d->h > 0.0) || !std::isfinite(d->h)) return fail(nullptr, SBM_ERR_ARG, "h must be positive");
+    if (d->precision != SBM_FP64 && d->precision != SBM_MIXED) return fail(nullptr, SBM_ERR_ARG, "bad precision");
+    const double nodes = (double)d->n[0] * d->n[1] * d->n[2];
+    if (nodes > 2.0e9) return fail(nullptr, SBM_ERR_ARG, "grid too large");
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || d->device < 0 || d->device >= ndev) {
+        cudaGetLastError();
+        return fail(nullptr, SBM_ERR_CUDA, "no CUDA device with the requested ordinal");
+    }
+    G = new sbm_grid_s();
+    G->desc = *d;
+    G->dev = d->device;
+    const sbm_status st = grid_create_impl(d, G);
+    if (st != SBM_OK) {
+        // nothing of a failed creation is kept: free what was allocated and report
+        // the failure through the library's message (there is no handle)
+        const std::string msg = G->err;
+        sbm_grid_destroy(G);
+        return fail(nullptr, st, msg);
+    }
     *out = G;
+    return SBM_OK;
+}
+
+void sbm_set_alloc_limit(size_t bytes) { g_alloc_cap.store((unsigned long long)bytes); }
+
+sbm_status sbm_set_wait_limit(sbm_grid G, long long spins)
+{
+    if (!G) return fail(G, SBM_ERR_ARG, "null grid");
+    if (spins < 0) return fail(G, SBM_ERR_ARG, "spins must be >= 0");
+    G->gj_spins = spins;
+    G->bottom_ready = false;        // the next solve inverts the bottom matrix again
     return SBM_OK;
 }
 
@@ -1812,6 +1857,57 @@ sbm_status sbm_time_kernel(sbm_grid G, int which, int reps, int flush_l2, double
 
 // ------------------------------------------------------------------- BSAMR
 
+// Storage of patch level a (box already checked and recorded in Pt) and the
+// composite-solve buffers it needs; on failure the caller frees the patch.
+static sbm_status patch_alloc(sbm_grid G, int a, Patch &Pt)
+{
+    const int d = G->desc.dim;
+    const Geom &g = Pt.s;
+    const size_t nd = (size_t)d * g.cs;
+    CK(gmalloc(G, (void **)&Pt.psi64, sizeof(double) * g.cs));
+    CK(cudaMemset(Pt.psi64, 0, sizeof(double) * g.cs));
+    CK(gmalloc(G, (void **)&Pt.psi32, sizeof(float) * g.cs));
+    CK(cudaMemset(Pt.psi32, 0, sizeof(float) * g.cs));
+    double **dp[] = {&Pt.u64, &Pt.f64, &Pt.r64, &Pt.de[0], &Pt.de[1], &Pt.drhs, &Pt.dres};
+    for (double **q : dp) {
+        CK(gmalloc(G, (void **)q, sizeof(double) * nd));
+        CK(cudaMemset(*q, 0, sizeof(double) * nd));
+    }
+    float **fp[] = {&Pt.se[0], &Pt.se[1], &Pt.srhs, &Pt.sres};
+    for (float **q : fp) {
+        CK(gmalloc(G, (void **)q, sizeof(float) * nd));
+        CK(cudaMemset(*q, 0, sizeof(float) * nd));
+    }
+    CK(gmalloc(G, (void **)&Pt.psiv32, sizeof(float) * g.cs));
+    CK(cudaMemset(Pt.psiv32, 0, sizeof(float) * g.cs));
+    if (d == 3) {
+        Pt.has_tm = true;
+        for (int i = 0; i < 2; ++i)
+            Pt.has_tm = Pt.has_tm && encode_sweep_maps(Pt.tm32[i], Pt.se[i], Pt.srhs, Pt.psiv32, g);
+    }
+    const int nk = (1 << d) * d;
+    CK(gmalloc(G, (void **)&Pt.Ke64, sizeof(double) * nk * nk));
+    CK(gmalloc(G, (void **)&Pt.Ke32, sizeof(float) * nk * nk));
+    Level &F = G->L[G->nl - 1];
+    if (!G->amr_u0) {
+        const size_t nb = (size_t)F.g.dim * F.g.cs;
+        CK(gmalloc(G, (void **)&G->amr_u0, sizeof(double) * nb));
+        CK(cudaMemset(G->amr_u0, 0, sizeof(double) * nb));
+        CK(gmalloc(G, (void **)&G->amr_r0, sizeof(double) * nb));
+        CK(cudaMemset(G->amr_r0, 0, sizeof(double) * nb));
+    }
+    long long need = amr_blocks(F.g);
+    for (int b = 1; b <= a; ++b) need += amr_blocks(G->P[b - 1].s);
+    if (need > G->amr_npart) {
+        if (G->amr_part) cudaFree(G->amr_part);
+        G->amr_part = nullptr;
+        G->amr_npart = 0;
+        CK(gmalloc(G, (void **)&G->amr_part, sizeof(double) * need));
+        G->amr_npart = need;
+    }
+    return SBM_OK;
+}
+
 sbm_status sbm_amr_add_level(sbm_grid G, const sbm_box *box)
 {
     if (!G || !box) return fail(G, SBM_ERR_ARG, "null argument");
@@ -1854,47 +1950,14 @@ sbm_status sbm_amr_add_level(sbm_grid G, const sbm_box *box)
     Pt.v.ny = g.ny - 2;
     Pt.v.nz = d == 3 ? g.nz - 2 : 1;
     Pt.voff = 1 + g.sx + (d == 3 ? g.sy : 0);
-    const size_t nd = (size_t)d * g.cs;
-    CK(cudaMalloc(&Pt.psi64, sizeof(double) * g.cs));
-    CK(cudaMemset(Pt.psi64, 0, sizeof(double) * g.cs));
-    CK(cudaMalloc(&Pt.psi32, sizeof(float) * g.cs));
-    CK(cudaMemset(Pt.psi32, 0, sizeof(float) * g.cs));
-    double **dp[] = {&Pt.u64, &Pt.f64, &Pt.r64, &Pt.de[0], &Pt.de[1], &Pt.drhs, &Pt.dres};
-    for (double **q : dp) {
-        CK(cudaMalloc(q, sizeof(double) * nd));
-        CK(cudaMemset(*q, 0, sizeof(double) * nd));
+    const sbm_status st = patch_alloc(G, a, Pt);
+    if (st != SBM_OK) {
+        // the patch is not added: free its storage and leave the grid as it was
+        free_patch(Pt);
+        Pt = Patch();
+        return st;
     }
-    float **fp[] = {&Pt.se[0], &Pt.se[1], &Pt.srhs, &Pt.sres};
-    for (float **q : fp) {
-        CK(cudaMalloc(q, sizeof(float) * nd));
-        CK(cudaMemset(*q, 0, sizeof(float) * nd));
-    }
-    CK(cudaMalloc(&Pt.psiv32, sizeof(float) * g.cs));
-    CK(cudaMemset(Pt.psiv32, 0, sizeof(float) * g.cs));
-    if (d == 3) {
-        Pt.has_tm = true;
-        for (int i = 0; i < 2; ++i)
-            Pt.has_tm = Pt.has_tm && encode_sweep_maps(Pt.tm32[i], Pt.se[i], Pt.srhs, Pt.psiv32, g);
-    }
-    const int nk = (1 << d) * d;
-    CK(cudaMalloc(&Pt.Ke64, sizeof(double) * nk * nk));
-    CK(cudaMalloc(&Pt.Ke32, sizeof(float) * nk * nk));
     G->npatch = a;
-    Level &F = G->L[G->nl - 1];
-    if (!G->amr_u0) {
-        const size_t nb = (size_t)F.g.dim * F.g.cs;
-        CK(cudaMalloc(&G->amr_u0, sizeof(double) * nb));
-        CK(cudaMemset(G->amr_u0, 0, sizeof(double) * nb));
-        CK(cudaMalloc(&G->amr_r0, sizeof(double) * nb));
-        CK(cudaMemset(G->amr_r0, 0, sizeof(double) * nb));
-    }
-    long long need = amr_blocks(F.g);
-    for (int b = 1; b <= G->npatch; ++b) need += amr_blocks(G->P[b - 1].s);
-    if (need > G->amr_npart) {
-        if (G->amr_part) cudaFree(G->amr_part);
-        CK(cudaMalloc(&G->amr_part, sizeof(double) * need));
-        G->amr_npart = need;
-    }
     amr_refresh_infos(G);
     return SBM_OK;
 }

@@ -233,7 +233,9 @@ constexpr long long kNodeKernelMaxNodes = 20000;
 
 // Inverse of the coarsest-level matrix in place (one cooperative launch);
 // bar: 4 device words, bar[2] != 0 afterwards if a grid barrier timed out.
-cudaError_t launch_gauss_jordan(const Geom &g, int n, double *A, double *tmp, unsigned *bar, cudaStream_t s);
+// spins: polls a block makes at one grid barrier before giving up (<= 0: default).
+cudaError_t launch_gauss_jordan(const Geom &g, int n, double *A, double *tmp, unsigned *bar, long long spins,
+                                cudaStream_t s);
 cudaError_t launch_round(long long n, const double *src, float *dst, cudaStream_t s);
 template <typename T>
 cudaError_t launch_bottom_apply(int n, const T *Ainv, const int *gather, const T *b, T *u,
