@@ -75,7 +75,11 @@ typedef struct {
     int nu1, nu2;          /* pre / post smoothing sweeps */
     double omega;          /* Jacobi damping (ignored by SBM_MCGS) */
     int smoother;          /* SBM_JACOBI or SBM_MCGS */
-    int inner_cycles;      /* SBM_MIXED: FP32 V-cycles per FP64 defect (>= 1) */
+    int inner_cycles;      /* SBM_MIXED: FP32 V-cycles per FP64 defect (>= 1).  SBM_FP64: V-cycles
+                              enqueued per host read of the residual (>= 1): each V-cycle is
+                              followed by its FP64 residual and a device-side check that records
+                              relres and stops the rest of the batch once the tolerance is met
+                              or the iteration diverges (same iterates and counts as 1) */
     int use_graph;         /* 1: replay the cycle as a CUDA graph; 0: launch eagerly */
     double inner_rtol;     /* SBM_MIXED, > 0: inner_cycles is a maximum; the FP32 V-cycles of an outer
                               iteration stop (on the device) once the FP32 residual after a V-cycle's

@@ -2,6 +2,8 @@
 // psi coarsening), packed <-> level copies, the deterministic norm reduction,
 // the coarsest-level dense solve (assembly, Gauss-Jordan inverse, matvec), the
 // FP64 defect update and the dJ/dpsi gradient kernel.
+#include <algorithm>
+
 #include "sbm_common.cuh"
 #include "sbm_bodies.cuh"
 
@@ -228,9 +230,10 @@ __global__ void k_round(long long n, const double *__restrict__ src, float *__re
 // scal[which] = sum of part[0..n) in a fixed order (one block, 256 threads);
 // scal[which+1] = sqrt(scal[which]); when which == 2 also scal[4] = relres =
 // sqrt(scal[2]) / scal[1] (scal[1] holds ||r0||).
-__global__ void k_norm_final(const double *__restrict__ part, int n, double *scal, int which)
+__global__ void k_norm_final(const double *__restrict__ part, int n, double *scal, int which, const int *gate)
 {
     pdl_begin();
+    if (gate && *gate) return;
     __shared__ double red[kThreads];
     double s = 0.0;
     for (int i = threadIdx.x; i < n; i += kThreads) s += part[i];
@@ -269,6 +272,31 @@ __global__ void k_inner_gate(const double *__restrict__ part, int n, const doubl
         *count += 1;
         if (rn <= thr) *gate = 1;
     }
+}
+
+// Batched FP64 V-cycles: after each V-cycle's residual norm (scal[4] = relres),
+// record it in hist[count], count the cycle and set the done flag once relres <=
+// tol, relres is not finite or above 1e10, or max_cycles cycles have run; every
+// later kernel of the batch sees the flag and returns at once.  state = {done, count}.
+__global__ void k_outer_gate(const double *scal, double tol, int max_cycles, double *hist, int *state)
+{
+    pdl_begin();
+    if (state[0]) return;
+    const double rel = scal[4];
+    const int c = state[1] + 1;
+    state[1] = c;
+    hist[c] = rel;
+    if (!(rel == rel) || rel > 1e10 || rel <= tol || c >= max_cycles) state[0] = 1;
+}
+
+// dst <- src (n elements) unless the gate is set.
+template <typename T>
+__global__ void k_copy_gated(long long n, const T *__restrict__ src, T *__restrict__ dst, const int *gate)
+{
+    pdl_begin();
+    if (gate && *gate) return;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        dst[i] = src[i];
 }
 
 // -------------------------------------------------------------- bottom solve
@@ -588,9 +616,27 @@ cudaError_t launch_add(long long n, const TE *e, double *u, cudaStream_t s)
 template cudaError_t launch_add<float>(long long, const float *, double *, cudaStream_t);
 template cudaError_t launch_add<double>(long long, const double *, double *, cudaStream_t);
 
-cudaError_t launch_norm_final(const double *part, int nparts, double *scal, int which, cudaStream_t s)
+cudaError_t launch_norm_final(const double *part, int nparts, double *scal, int which, cudaStream_t s,
+                              const int *gate)
 {
-    cudaError_t e = launch_pdl(k_norm_final, dim3(1), dim3(kThreads), 0, s, part, nparts, scal, which);
+    cudaError_t e = launch_pdl(k_norm_final, dim3(1), dim3(kThreads), 0, s, part, nparts, scal, which, gate);
+    if (e != cudaSuccess) return e;
+    ++g_launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_outer_gate(const double *scal, double tol, int max_cycles, double *hist, int *state, cudaStream_t s)
+{
+    cudaError_t e = launch_pdl(k_outer_gate, dim3(1), dim3(1), 0, s, scal, tol, max_cycles, hist, state);
+    if (e != cudaSuccess) return e;
+    ++g_launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_copy_gated(long long n, const double *src, double *dst, const int *gate, cudaStream_t s)
+{
+    cudaError_t e = launch_pdl(k_copy_gated<double>, dim3((unsigned)std::min<long long>(nblk(n), 152 * 8)), dim3(kThreads),
+                               0, s, n, src, dst, gate);
     if (e != cudaSuccess) return e;
     ++g_launches;
     return cudaGetLastError();

@@ -79,8 +79,9 @@ struct Patch {
 struct GraphSlot {
     bool valid = false;
     cudaGraphExec_t exec = nullptr;
-    int mixed = 0, smoother = 0, nu1 = 0, nu2 = 0, inner = 0;
-    double omega = 0, inner_rtol = 0;
+    int mixed = 0, smoother = 0, nu1 = 0, nu2 = 0, inner = 0, max_cycles = 0;
+    double omega = 0, inner_rtol = 0, tol = 0;
+    const double *hist = nullptr;
     const double *rhs = nullptr;
     unsigned version = 0;
     long long body_launches = 0;
@@ -116,6 +117,8 @@ struct sbm_grid_s {
     double *A64 = nullptr, *gjtmp = nullptr;
     unsigned *gjbar = nullptr;  // grid-barrier words of the bottom-level inversion
     long long gj_spins = 0;     // polls per grid barrier before it gives up (0: the default)
+    double *dhist = nullptr;    // batched FP64 V-cycles: relres per cycle (device)
+    int dhist_cap = 0;
     size_t allocated = 0;       // device bytes allocated for the grid (checked against the cap)
     float *A32 = nullptr;
     int *gather = nullptr;
@@ -378,7 +381,7 @@ cudaError_t residual64(sbm_grid G, const double *rhs, int mixed, int which)
         e = sweep<double>(G, G->nl - 1, kResidual, L.du[0], rhs, L.dr, G->part, 0.0);
     }
     if (e != cudaSuccess) return e;
-    return launch_norm_final(G->part, (int)sweep_blocks(L.g, true), G->scal, which, G->st);
+    return launch_norm_final(G->part, (int)sweep_blocks(L.g, true), G->scal, which, G->st, G->cur_gate);
 }
 
 // One outer iteration: V-cycle(s) and the FP64 residual + norm of the result.
@@ -406,6 +409,28 @@ cudaError_t enqueue_body(sbm_grid G, const sbm_opts &o, const double *rhs)
     CKE(vcycle<double>(G, fine, cur, o, rhs));
     if (cur != 0) CKE(cudaMemcpyAsync(L.du[0], L.du[1], level_bytes(L, sizeof(double)), cudaMemcpyDeviceToDevice, G->st));
     return residual64(G, rhs, 0, 2);
+}
+
+// FP64 mode with inner_cycles = batch > 1: `batch` V-cycles, each followed by its
+// FP64 residual, norm and the device gate that records relres, counts the cycle
+// and stops the rest of the batch (every later kernel sees the flag dgate[0] and
+// returns) once the tolerance is met or the iteration diverges.
+cudaError_t enqueue_fp64_batch(sbm_grid G, const sbm_opts &o, const double *rhs, int batch)
+{
+    const int fine = G->nl - 1;
+    Level &L = G->L[fine];
+    G->cur_gate = G->dgate;
+    cudaError_t e = cudaSuccess;
+    for (int b = 0; b < batch && e == cudaSuccess; ++b) {
+        int cur = 0;
+        e = vcycle<double>(G, fine, cur, o, rhs);
+        if (e == cudaSuccess && cur != 0)
+            e = launch_copy_gated((long long)L.g.dim * L.g.cs, L.du[1], L.du[0], G->dgate, G->st);
+        if (e == cudaSuccess) e = residual64(G, rhs, 0, 2);
+        if (e == cudaSuccess) e = launch_outer_gate(G->scal, o.tol, o.max_cycles, G->dhist, G->dgate, G->st);
+    }
+    G->cur_gate = nullptr;
+    return e;
 }
 
 sbm_status setup_bottom(sbm_grid G)
@@ -514,18 +539,27 @@ sbm_status run_solve(sbm_grid G, const sbm_opts &o, const double *rhs, sbm_info 
         if (info->history && info->history_capacity > 0) info->history[0] = 1.0;
     }
     GraphSlot &gs = G->slots[slot];
+    const int batch = mixed ? 1 : o.inner_cycles;
+    if (batch > 1 && G->dhist_cap < o.max_cycles + 1) {
+        if (G->dhist) cudaFree(G->dhist);
+        G->dhist = nullptr;
+        G->dhist_cap = 0;
+        CK(gmalloc(G, (void **)&G->dhist, sizeof(double) * (o.max_cycles + 1)));
+        G->dhist_cap = o.max_cycles + 1;
+    }
+    auto body = [&]() { return batch > 1 ? enqueue_fp64_batch(G, o, rhs, batch) : enqueue_body(G, o, rhs); };
     if (o.use_graph) {
         const bool match = gs.valid && gs.mixed == mixed && gs.smoother == o.smoother && gs.nu1 == o.nu1 &&
                            gs.nu2 == o.nu2 && gs.inner == o.inner_cycles && gs.omega == o.omega && gs.rhs == rhs &&
-                           gs.inner_rtol == o.inner_rtol &&
-                           gs.version == G->version;
+                           gs.inner_rtol == o.inner_rtol && gs.version == G->version &&
+                           (batch == 1 || (gs.tol == o.tol && gs.max_cycles == o.max_cycles && gs.hist == G->dhist));
         if (!match) {
             if (gs.valid) cudaGraphExecDestroy(gs.exec);
             gs.valid = false;
             cudaGraph_t graph;
             CK(cudaStreamBeginCapture(G->st, cudaStreamCaptureModeThreadLocal));
             const long long c0 = g_launches;
-            cudaError_t e = enqueue_body(G, o, rhs);
+            cudaError_t e = body();
             const long long nbody = g_launches - c0;
             g_launches = c0;
             cudaError_t e2 = cudaStreamEndCapture(G->st, &graph);
@@ -547,6 +581,9 @@ sbm_status run_solve(sbm_grid G, const sbm_opts &o, const double *rhs, sbm_info 
             gs.inner_rtol = o.inner_rtol;
             gs.rhs = rhs;
             gs.version = G->version;
+            gs.tol = o.tol;
+            gs.max_cycles = o.max_cycles;
+            gs.hist = G->dhist;
             gs.body_launches = nbody;
         }
     }
@@ -559,12 +596,35 @@ sbm_status run_solve(sbm_grid G, const sbm_opts &o, const double *rhs, sbm_info 
     }
     const bool gated = mixed && o.inner_rtol > 0.0;
     if (gated) CK(cudaMemsetAsync(G->dgate + 1, 0, sizeof(int), G->st));
-    while (status == SBM_ERR_NOCONV && cyc < o.max_cycles) {
+    if (batch > 1 && status == SBM_ERR_NOCONV) {
+        // batched FP64 V-cycles: one host read of {done, count} per batch
+        CK(cudaMemsetAsync(G->dgate, 0, 2 * sizeof(int), G->st));
+        int state[2] = {0, 0};
+        while (!state[0]) {
+            if (o.use_graph) {
+                CK(cudaGraphLaunch(gs.exec, G->st));
+                replayed += gs.body_launches;
+            } else {
+                CK(body());
+            }
+            CK(cudaMemcpyAsync(state, G->dgate, sizeof(state), cudaMemcpyDeviceToHost, G->st));
+            CK(cudaStreamSynchronize(G->st));
+        }
+        cyc = state[1];
+        std::vector<double> hist(cyc + 1, 1.0);
+        if (cyc > 0) CK(cudaMemcpy(hist.data() + 1, G->dhist + 1, sizeof(double) * cyc, cudaMemcpyDeviceToHost));
+        if (info && info->history)
+            for (int c = 1; c <= cyc && c < info->history_capacity; ++c) info->history[c] = hist[c];
+        rel = cyc > 0 ? hist[cyc] : 1.0;
+        if (!std::isfinite(rel) || rel > 1e10) status = SBM_ERR_DIVERGED;
+        else if (rel <= o.tol) status = SBM_OK;
+    }
+    while (status == SBM_ERR_NOCONV && cyc < o.max_cycles && batch == 1) {
         if (o.use_graph) {
             CK(cudaGraphLaunch(gs.exec, G->st));
             replayed += gs.body_launches;
         } else {
-            CK(enqueue_body(G, o, rhs));
+            CK(body());
         }
         CK(cudaMemcpyAsync(G->hscal + 4, G->scal + 4, sizeof(double), cudaMemcpyDeviceToHost, G->st));
         CK(cudaStreamSynchronize(G->st));
@@ -1214,7 +1274,7 @@ sbm_status sbm_grid_destroy(sbm_grid G)
         for (double *q : vec)
             if (q) cudaFree(q);
     void *ptrs[] = {G->fsrc, G->fadj, G->psi_raw, G->rho, G->part, G->scal, G->dbad, G->A64, G->A32, G->gjtmp, G->gjbar, G->gather,
-                    G->derr, G->dgate, G->amr_part, G->amr_u0, G->amr_r0};
+                    G->derr, G->dgate, G->amr_part, G->amr_u0, G->amr_r0, G->dhist};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (G->hscal) cudaFreeHost(G->hscal);

@@ -221,7 +221,11 @@ template <typename TE>
 cudaError_t launch_add(long long n, const TE *e, double *u, cudaStream_t s);
 // deterministic final reduction of block partials: out[0] = sum, optional relres
 cudaError_t launch_norm_final(const double *part, int nparts, double *scal, int which,
-                              cudaStream_t s);
+                              cudaStream_t s, const int *gate = nullptr);
+// Batched FP64 V-cycles (see k_misc.cu): state = {done, count}, hist[count] = relres.
+cudaError_t launch_outer_gate(const double *scal, double tol, int max_cycles, double *hist, int *state, cudaStream_t s);
+// dst <- src unless *gate (gate may be null).
+cudaError_t launch_copy_gated(long long n, const double *src, double *dst, const int *gate, cudaStream_t s);
 // bottom: dense assembly, Dirichlet rows/cols, Gauss-Jordan inverse, matvec
 cudaError_t launch_bottom_assemble(const Geom &g, const double *psi, const Coef<double> &c,
                                    double *A, cudaStream_t s);

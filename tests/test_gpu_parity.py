@@ -219,6 +219,30 @@ def test_adaptive_inner_cycles(built, case, use_graph):
     assert info.vcycles < 12 * info.cycles or info.cycles <= fixed.cycles
 
 
+@pytest.mark.parametrize("case,smoother", [("plate65", "jacobi"), ("plate65", "gs"), ("damage33", "jacobi")])
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_fp64_batched_vcycles_match_one_per_host_read(built, case, smoother, use_graph):
+    """FP64 mode with several V-cycles per host read (inner_cycles > 1): the device
+    stops the batch at the tolerance, so the iterates, the cycle count and the relres
+    history are those of one V-cycle per read, bit for bit; max_cycles falling inside
+    a batch stops there."""
+    wk = CASES[case]()
+    g = gpu_grid(wk)
+    u1 = cuda(wk.u0)
+    i1 = g.solve(u1, smoother=smoother, omega=wk.omega, use_graph=use_graph)
+    for batch in (4, 8):
+        ub = cuda(wk.u0)
+        ib = g.solve(ub, smoother=smoother, omega=wk.omega, inner_cycles=batch, use_graph=use_graph)
+        assert ib.converged and ib.cycles == i1.cycles and ib.vcycles == i1.cycles
+        assert torch.equal(ub, u1)
+        assert ib.history == i1.history
+    u = cuda(wk.u0)
+    info = g.solve(u, smoother=smoother, omega=wk.omega, inner_cycles=4, max_cycles=5, raise_on_fail=False,
+                   use_graph=use_graph)
+    assert info.status == sbm._capi.SBM_ERR_NOCONV and info.cycles == 5 and len(info.history) == 6
+    assert info.history == i1.history[:6]
+
+
 def test_solve_graph_and_eager_agree_bitwise(built):
     wk = W.damage3d(17)
     g = gpu_grid(wk, precision="mixed")
