@@ -76,6 +76,8 @@ def _L():
             "orc_direct_solve": (C.c_int, [P, _dp, _dp, _dp]),
             "orc_mg_solve": (C.c_int, [P, _dp, _dp, _dp, C.POINTER(_Opts), _dp, C.POINTER(C.c_int)]),
             "orc_dJdpsi": (None, [P, _dp, _dp, _dp]),
+            "orc_source_terms": (None, [P, _dp, C.c_void_p, C.c_void_p, C.c_void_p, _dp]),
+            "orc_node_psi": (None, [P, _dp, _dp, _dp, _dp]),
             "orc_apply_product": (None, [P, C.c_int, _dp, _dp, _dp]),
             "orc_diagonal_product": (None, [P, C.c_int, _dp, _dp]),
             "orc_jacobi_product": (None, [P, C.c_int, _dp, _dp, _dp, C.c_double]),
@@ -147,6 +149,23 @@ def apply(P: Problem, psi, u) -> np.ndarray:
     out = np.zeros(P.ndofs)
     _L().orc_apply(C.byref(P.c()), _f64(psi), _f64(u), out)
     return out
+
+
+def source_terms(P: Problem, psi, eps0=None, b=None, t=None) -> np.ndarray:
+    """f of K u = f for eq. SBMLinearElasticity (see sbm_oracle.h): eigenstrain per
+    cell in Voigt components, body force and diffuse traction per node; None = 0."""
+    out = np.zeros(P.ndofs)
+    keep = [None if a is None else _f64(a) for a in (eps0, b, t)]
+    ptr = lambda a: None if a is None else a.ctypes.data_as(C.c_void_p)
+    _L().orc_source_terms(C.byref(P.c()), _f64(psi), ptr(keep[0]), ptr(keep[1]), ptr(keep[2]), out)
+    return out
+
+
+def node_psi(P: Problem, psi):
+    """(psi_n, |grad psi|_n, w_n) of source_terms at every node."""
+    pn, gn, w = np.zeros(P.nnodes), np.zeros(P.nnodes), np.zeros(P.nnodes)
+    _L().orc_node_psi(C.byref(P.c()), _f64(psi), pn, gn, w)
+    return pn, gn, w
 
 
 NODE_PSI, CELL_PSI = 1, 2

@@ -1319,3 +1319,121 @@ void orc_jacobi_product(const orc_problem *P, int variant, const double *psi, co
     free(Ku);
     free(D);
 }
+
+/* ------------------------------------- source terms of eq. SBMLinearElasticity */
+
+/* Voigt index of the symmetric pair (i, j): 2D (xx, yy, xy), 3D (xx, yy, zz, yz, xz, xy). */
+static int voigt(int d, int i, int j)
+{
+    if (i == j) return i;
+    if (d == 2) return 2;
+    const int s = i + j;                      /* (1,2) -> 3, (0,2) -> 4, (0,1) -> 5 */
+    return s == 3 ? 3 : (s == 2 ? 4 : 5);
+}
+
+/* psi, grad psi and the lumping weight at node (i,j,k) from the cells around it:
+ * cells beyond a face of the box take the value of their mirror image inside (no
+ * gradient of psi normal to the box), psi_n is the mean of the 2^d cells, the
+ * gradient along a is the mean over the 2^(d-1) cell pairs facing each other
+ * across the node of (psi_+ - psi_-) / h, and w_n = (cells of the grid around n) / 2^d. */
+static void node_psi(const orc_problem *P, const double *psi, int i, int j, int k, double *pn, double g[3], double *w)
+{
+    const int d = P->dim, nc = 1 << d;
+    const int n3[3] = {i, j, k};
+    double s = 0.0;
+    int inside = 0;
+    g[0] = g[1] = g[2] = 0.0;
+    for (int c = 0; c < nc; ++c) {
+        int cc[3] = {0, 0, 0}, in = 1;
+        for (int a = 0; a < d; ++a) {
+            int v = n3[a] - 1 + ((c >> a) & 1);
+            const int m = ncell_axis(P, a);
+            if (v < 0) { v = 0; in = 0; }
+            if (v > m - 1) { v = m - 1; in = 0; }
+            cc[a] = v;
+        }
+        inside += in;
+        const double v = psi[cid(P, cc[0], cc[1], cc[2])];
+        s += v;
+        for (int a = 0; a < d; ++a) g[a] += ((c >> a) & 1) ? v : -v;
+    }
+    *pn = s / nc;
+    for (int a = 0; a < d; ++a) g[a] /= (double)(nc / 2) * P->h;
+    *w = (double)inside / nc;
+}
+
+void orc_source_terms(const orc_problem *P, const double *psi, const double *eps0, const double *b, const double *t,
+                      double *f)
+{
+    const int d = P->dim, nc = 1 << d, nv = d == 3 ? 6 : 3;
+    const long N = orc_nnodes(P), NC = orc_ncells(P);
+    const double h = P->h;
+    memset(f, 0, sizeof(double) * d * N);
+    if (eps0) {
+        /* K u = f_eps is the weak form of div(psi C (grad u - eps0)) = 0:
+         * f_eps(n) = h^-d sum_c psi_c int_c B_n^T C eps0_c, by 2-point Gauss quadrature */
+        const double gp[2] = {0.5 - 0.5 / sqrt(3.0), 0.5 + 0.5 / sqrt(3.0)};
+        const double wq = pow(h, d) / nc;
+        for (int ck = 0; ck < ncell_axis(P, 2); ++ck)
+            for (int cj = 0; cj < ncell_axis(P, 1); ++cj)
+                for (int ci = 0; ci < ncell_axis(P, 0); ++ci) {
+                    const long c = cid(P, ci, cj, ck);
+                    double sig[3][3];
+                    for (int p = 0; p < d; ++p)
+                        for (int q = 0; q < d; ++q) {
+                            double s = 0.0;
+                            for (int r = 0; r < d; ++r)
+                                for (int l = 0; l < d; ++l) s += cubic_C(P, p, q, r, l) * eps0[voigt(d, r, l) * NC + c];
+                            sig[p][q] = psi[c] * s;
+                        }
+                    for (int gq = 0; gq < nc; ++gq) {
+                        double xi[3];
+                        for (int a = 0; a < d; ++a) xi[a] = gp[(gq >> a) & 1];
+                        for (int a = 0; a < nc; ++a) {
+                            double dN[3];
+                            for (int ax = 0; ax < d; ++ax) {
+                                double v = dshape1((a >> ax) & 1) / h;
+                                for (int bx = 0; bx < d; ++bx)
+                                    if (bx != ax) v *= shape1((a >> bx) & 1, xi[bx]);
+                                dN[ax] = v;
+                            }
+                            int i, j, k;
+                            cell_corner(P, ci, cj, ck, a, &i, &j, &k);
+                            for (int p = 0; p < d; ++p) {
+                                double s = 0.0;
+                                for (int q = 0; q < d; ++q) s += sig[p][q] * dN[q];
+                                f[p * N + nid(P, i, j, k)] += wq * s * pow(h, -d);
+                            }
+                        }
+                    }
+                }
+    }
+    (void)nv;
+    /* body force and diffuse traction:  -w_n (psi_n b_n + t_n |grad psi|_n) */
+    for (int k = 0; k < P->n[2]; ++k)
+        for (int j = 0; j < P->n[1]; ++j)
+            for (int i = 0; i < P->n[0]; ++i) {
+                double pn, g[3], w;
+                node_psi(P, psi, i, j, k, &pn, g, &w);
+                const double gn = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+                const long n = nid(P, i, j, k);
+                for (int p = 0; p < d; ++p) {
+                    double s = 0.0;
+                    if (b) s += pn * b[p * N + n];
+                    if (t) s += t[p * N + n] * gn;
+                    f[p * N + n] -= w * s;
+                }
+            }
+}
+
+void orc_node_psi(const orc_problem *P, const double *psi, double *pn, double *gn, double *w)
+{
+    for (int k = 0; k < P->n[2]; ++k)
+        for (int j = 0; j < P->n[1]; ++j)
+            for (int i = 0; i < P->n[0]; ++i) {
+                double g[3];
+                const long n = nid(P, i, j, k);
+                node_psi(P, psi, i, j, k, &pn[n], g, &w[n]);
+                gn[n] = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+            }
+}

@@ -20,6 +20,8 @@
  *   - Full-weighting restriction R = P^T / 2^d, (bi/tri)linear prolongation P,
  *     V(nu1,nu2) cycle, dense Cholesky bottom solve            [Sec. 2.2 level sequence]
  *   - Dense direct solve, adjoint solve and dJ/dpsi_c = -lambda_c^T S_c u_c.
+ *   - Source terms of eq. SBMLinearElasticity: eigenstrain load, body force psi b
+ *     and the diffuse traction t |grad psi| (Theorem 1)      [Sec. 2.1]
  *
  * Layout (the same packed layout as the C ABI of the CUDA library):
  *   node (i,j,k)  -> i + nx*(j + ny*k);     component p at offset p*nnodes
@@ -109,6 +111,22 @@ void orc_diagonal_product(const orc_problem *P, int variant, const double *psi, 
 /* One damped Jacobi sweep u += omega (f - K u) / D on the interior free dofs. */
 void orc_jacobi_product(const orc_problem *P, int variant, const double *psi, const double *f, double *u,
                         double omega);
+
+/* Right-hand side of eq. SBMLinearElasticity (Sec. 2.1),
+ *     div(psi C (grad u - eps0)) - psi b = t |grad psi|,
+ * in the form K u = f of orc_apply:
+ *     f = h^-d sum_c psi_c int_c B^T C eps0_c  -  w_n (psi_n b_n + t_n |grad psi|_n).
+ * eps0: per cell, Voigt components (2D xx, yy, xy; 3D xx, yy, zz, yz, xz, xy; tensor,
+ * not engineering, shear), component-major over the packed cells; b, t: per node,
+ * component-major; any of the three may be NULL.  psi_n, |grad psi|_n from the cells
+ * around the node (cells beyond the box mirrored inside: no normal gradient at the
+ * box faces), w_n = (cells of the grid around n) / 2^d (the node's share of the
+ * volume).  The diffuse traction t is the value at the node (Sec. 2.1: the traction
+ * of the closest point of the boundary). */
+void orc_source_terms(const orc_problem *P, const double *psi, const double *eps0, const double *b, const double *t,
+                      double *f);
+/* psi_n, |grad psi|_n and w_n of orc_source_terms at every node. */
+void orc_node_psi(const orc_problem *P, const double *psi, double *pn, double *gn, double *w);
 
 /* g_c = -lambda_c^T S_c u_c for every cell (S_c = unit-psi element matrix). */
 void orc_dJdpsi(const orc_problem *P, const double *u, const double *lam, double *g);
