@@ -140,6 +140,26 @@ sbm_status sbm_set_bc(sbm_grid grid, int face, int comp, int type, double value)
 /* Right-hand side f (device, FP64, packed node layout, finest level), K u = f. */
 sbm_status sbm_set_source(sbm_grid grid, int level, const double *f_nodes);
 
+/* Load f of K u = f from the source terms of eq. SBMLinearElasticity (Sec. 2.1),
+ *     div(psi C (grad u - eps0)) - psi b = t |grad psi|
+ * with the cell-flux discretisation of the operator:
+ *     f_n = h^-d sum_{cells c of n} psi_c int_c B_n^T C eps0_c - w_n (psi_n b_n + t_n |grad psi|_n).
+ * psi: device, packed cells of `level` (used as given, no floor).  eps0 (may be NULL):
+ * device, per-cell eigenstrain, Voigt slots 2D (xx, yy, xy), 3D (xx, yy, zz, yz, xz, xy)
+ * holding tensor (not engineering) shear, slot-major over the packed cells.  b, t (each
+ * may be NULL): device, packed nodes; b the body force, t the diffuse traction
+ * (Sec. 2.1: the traction of the closest point of the boundary).  psi_n is the mean of
+ * the 2^d cells around node n, grad psi_n the mean difference of the cells facing each
+ * other across it, cells beyond a face of the box mirrored inside; w_n is the node's
+ * share of the volume ((cells of the grid around n) / 2^d).  By Theorem 1 the traction
+ * term integrates to the boundary load as the interface width goes to 0.  f: device,
+ * packed nodes of `level`, overwritten (Dirichlet dofs included; the solve replaces
+ * their rows).  Uses the grid's moduli; FP64; synchronises the grid stream.  Pass f on
+ * to sbm_set_source.  SBM_ERR_ARG for a level out of range or host pointers,
+ * SBM_ERR_STATE before sbm_set_moduli. */
+sbm_status sbm_source_terms(sbm_grid grid, int level, const double *psi, const double *eps0, const double *b,
+                            const double *t, double *f);
+
 /* Solve K u = f.  u (device, FP64, packed) holds the initial guess on entry and
  * the solution on return; Dirichlet dofs are set from the face conditions and
  * never changed by the iteration.  opts may be NULL (defaults); info may be NULL.

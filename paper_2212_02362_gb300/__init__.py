@@ -275,6 +275,16 @@ class Grid:
         self._check(lib().sbm_bottom_correct(self._h, int(fp32), _ptr(f), _ptr(out)))
         return out
 
+    def source_terms(self, psi: torch.Tensor, eps0=None, b=None, t=None, level=None) -> torch.Tensor:
+        """Load f of K u = f from eq. SBMLinearElasticity: per-cell eigenstrain eps0
+        (Voigt slots), nodal body force b and nodal diffuse traction t (each optional);
+        psi in cells of `level` (default: the finest), used as given."""
+        level = self.finest if level is None else level
+        out = torch.empty(self.dim * self.nnodes(level), dtype=torch.float64, device=psi.device)
+        opt = lambda x: None if x is None else _ptr(x)
+        self._check(lib().sbm_source_terms(self._h, level, _ptr(psi), opt(eps0), opt(b), opt(t), _ptr(out)))
+        return out
+
     # -- the operator variants of Sec. 2.3 (product-rule strong form)
     def apply_product(self, variant: int, psi: torch.Tensor, u: torch.Tensor) -> torch.Tensor:
         out = torch.empty_like(u)

@@ -71,6 +71,7 @@ _SIGS = {
     "sbm_dJdpsi": (C.c_int, [_grid, _dptr, _dptr, _dptr]),
     "sbm_set_alloc_limit": (None, [C.c_size_t]),
     "sbm_set_wait_limit": (C.c_int, [_grid, C.c_longlong]),
+    "sbm_source_terms": (C.c_int, [_grid, C.c_int, _dptr, _dptr, _dptr, _dptr, _dptr]),
     "sbm_apply_product": (C.c_int, [_grid, C.c_int, _dptr, _dptr, _dptr]),
     "sbm_jacobi_product": (C.c_int, [_grid, C.c_int, _dptr, _dptr, _dptr, C.c_double, C.c_int]),
     "sbm_time_kernel": (C.c_int, [_grid, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),

@@ -1818,6 +1818,24 @@ sbm_status sbm_apply_product(sbm_grid G, int variant, const double *psi, const d
     return SBM_OK;
 }
 
+sbm_status sbm_source_terms(sbm_grid G, int level, const double *psi, const double *eps0, const double *b,
+                            const double *t, double *f)
+{
+    if (!G) return fail(G, SBM_ERR_ARG, "null grid");
+    if (!G->has_moduli) return fail(G, SBM_ERR_STATE, "moduli not set (sbm_set_moduli)");
+    if (level < 0 || level >= G->nl) return fail(G, SBM_ERR_ARG, "level out of range");
+    if (!is_dev_ptr(psi, G->dev) || !is_dev_ptr(f, G->dev))
+        return fail(G, SBM_ERR_ARG, "psi and f must be device pointers");
+    if ((eps0 && !is_dev_ptr(eps0, G->dev)) || (b && !is_dev_ptr(b, G->dev)) || (t && !is_dev_ptr(t, G->dev)))
+        return fail(G, SBM_ERR_ARG, "eps0, b and t must be device pointers or NULL");
+    CK(cudaSetDevice(G->dev));
+    const Level &L = G->L[level];
+    const int n[3] = {L.g.nx, L.g.ny, L.g.nz};
+    CK(launch_source_terms(L.g.dim, n, L.h, G->mod, psi, eps0, b, t, f, G->st));
+    CK(cudaStreamSynchronize(G->st));
+    return SBM_OK;
+}
+
 sbm_status sbm_jacobi_product(sbm_grid G, int variant, const double *psi, const double *f, double *u, double omega,
                               int sweeps)
 {

@@ -279,6 +279,11 @@ cudaError_t launch_sum_parts(const double *part, int n, double *out, cudaStream_
 cudaError_t launch_product(int mode, int dim, const int n[3], double h, const double mod[3], const unsigned dm[3],
                            int variant, double omega, const double *psi, const double *u, const double *f, double *out,
                            cudaStream_t s);
+// Source terms of eq. SBMLinearElasticity (k_source.cu), FP64 packed arrays: the
+// load f of K u = f from a per-cell eigenstrain (Voigt, may be null), a nodal body
+// force b and a nodal diffuse traction t (either may be null).
+cudaError_t launch_source_terms(int dim, const int n[3], double h, const double mod[3], const double *psi,
+                                const double *eps0, const double *b, const double *t, double *f, cudaStream_t s);
 // Reads a buffer (measurement: leaves L2 holding clean lines of it).
 cudaError_t launch_l2_read(const void *buf, size_t bytes, float *sink, cudaStream_t s);
 // adjoint of the composite problem
