@@ -41,6 +41,27 @@ class _Problem(C.Structure):
                 ("dirichlet", C.c_uint * 3)]
 
 
+class _Topopt(C.Structure):
+    _fields_ = [(k, C.c_double) for k in ("alpha", "beta", "zeta", "lambda_", "lambda_rate", "V0", "mobility",
+                                          "dt")]
+
+
+@dataclass
+class TopoptParams:
+    """Parameters of the phase-field topology optimisation step (Sec. 3.3)."""
+    alpha: float = 200.0
+    beta: float = 0.01
+    zeta: float = 0.01
+    lam: float = 400.0
+    lam_rate: float = 0.0
+    V0: float = 0.25
+    mobility: float = 1.0
+    dt: float = 1e-4
+
+    def c(self):
+        return _Topopt(self.alpha, self.beta, self.zeta, self.lam, self.lam_rate, self.V0, self.mobility, self.dt)
+
+
 class _Opts(C.Structure):
     _fields_ = [("nu1", C.c_int), ("nu2", C.c_int), ("omega", C.c_double),
                 ("smoother", C.c_int), ("tol", C.c_double), ("max_cycles", C.c_int)]
@@ -78,6 +99,8 @@ def _L():
             "orc_dJdpsi": (None, [P, _dp, _dp, _dp]),
             "orc_source_terms": (None, [P, _dp, C.c_void_p, C.c_void_p, C.c_void_p, _dp]),
             "orc_node_psi": (None, [P, _dp, _dp, _dp, _dp]),
+            "orc_topopt_step": (None, [P, C.POINTER(_Topopt), C.c_int, _dp, _dp, _dp]),
+            "orc_topopt_energy": (None, [P, C.POINTER(_Topopt), C.c_int, _dp, _dp]),
             "orc_apply_product": (None, [P, C.c_int, _dp, _dp, _dp]),
             "orc_diagonal_product": (None, [P, C.c_int, _dp, _dp]),
             "orc_jacobi_product": (None, [P, C.c_int, _dp, _dp, _dp, C.c_double]),
@@ -166,6 +189,25 @@ def node_psi(P: Problem, psi):
     pn, gn, w = np.zeros(P.nnodes), np.zeros(P.nnodes), np.zeros(P.nnodes)
     _L().orc_node_psi(C.byref(P.c()), _f64(psi), pn, gn, w)
     return pn, gn, w
+
+
+def topopt_step(P: Problem, T: TopoptParams, eta, u, step: int = 0) -> np.ndarray:
+    """eta after one explicit step of eq. topop_evolution (see sbm_oracle.h)."""
+    out = np.zeros(P.ncells)
+    _L().orc_topopt_step(C.byref(P.c()), C.byref(T.c()), step, _f64(eta), _f64(u), out)
+    return out
+
+
+def topopt_energy(P: Problem, T: TopoptParams, eta, step: int = 0) -> np.ndarray:
+    """(double-well, gradient, volume-penalty) parts of the discrete energy."""
+    out = np.zeros(3)
+    _L().orc_topopt_energy(C.byref(P.c()), C.byref(T.c()), step, _f64(eta), out)
+    return out
+
+
+def psi_of_eta(T: TopoptParams, eta) -> np.ndarray:
+    """The stiffness of eq. topop_objective, psi = (eta + zeta)^2."""
+    return (np.asarray(eta, dtype=np.float64) + T.zeta) ** 2
 
 
 NODE_PSI, CELL_PSI = 1, 2

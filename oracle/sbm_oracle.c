@@ -1437,3 +1437,77 @@ void orc_node_psi(const orc_problem *P, const double *psi, double *pn, double *g
                 gn[n] = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
             }
 }
+
+/* ------------------------------------- phase-field topology optimisation (Sec. 3.3) */
+
+/* eta of the cell (ci,cj,ck) with the cell's own value beyond a face of the box
+ * (the order parameter's Neumann condition). */
+static double eta_at(const orc_problem *P, const double *eta, int ci, int cj, int ck, int axis, int side,
+                     double self)
+{
+    int c[3] = {ci, cj, ck};
+    c[axis] += side;
+    if (c[axis] < 0 || c[axis] >= ncell_axis(P, axis)) return self;
+    return eta[cid(P, c[0], c[1], c[2])];
+}
+
+void orc_topopt_step(const orc_problem *P, const orc_topopt_params *T, int step, const double *eta, const double *u,
+                     double *eta_out)
+{
+    const int d = P->dim;
+    const long NC = orc_ncells(P);
+    const double hd = pow(P->h, d);
+    /* the volume int eta dx of eq. topop_volume_constraint, cell-centred rule */
+    double V = 0.0;
+    for (long c = 0; c < NC; ++c) V += hd * eta[c];
+    /* lambda(t): grows linearly from lambda at t = 0 at the rate lambda_rate */
+    const double lam = T->lambda + T->lambda_rate * step * T->dt;
+    /* unit-psi cell strain energy e_c = u_c^T S_c u_c = -dJ/dpsi_c of the compliance (lambda = u) */
+    double *e = malloc(sizeof(double) * NC);
+    orc_dJdpsi(P, u, u, e);
+    for (long c = 0; c < NC; ++c) e[c] = -e[c];
+    for (int ck = 0; ck < ncell_axis(P, 2); ++ck)
+        for (int cj = 0; cj < ncell_axis(P, 1); ++cj)
+            for (int ci = 0; ci < ncell_axis(P, 0); ++ci) {
+                const long c = cid(P, ci, cj, ck);
+                const double n = eta[c];
+                /* variational derivative of eq. topop_objective:
+                 *   d/deta [alpha eta^2 (1-eta)^2]      = 2 alpha eta (1-eta)(1-2 eta)
+                 *   d/deta [beta/2 |grad eta|^2]        = -beta Laplacian(eta)
+                 *   d/deta [compliance / 2], psi = (eta+zeta)^2 = -(eta+zeta) e_c      */
+                double lap = 0.0;
+                for (int a = 0; a < d; ++a)
+                    lap += (eta_at(P, eta, ci, cj, ck, a, +1, n) - 2.0 * n + eta_at(P, eta, ci, cj, ck, a, -1, n)) /
+                           (P->h * P->h);
+                const double dW = 2.0 * T->alpha * n * (1.0 - n) * (1.0 - 2.0 * n) - T->beta * lap -
+                                  (n + T->zeta) * e[c];
+                /* eq. topop_evolution, one explicit Euler step */
+                eta_out[c] = n - T->dt * T->mobility * (dW + lam * (V - T->V0));
+            }
+    free(e);
+}
+
+void orc_topopt_energy(const orc_problem *P, const orc_topopt_params *T, int step, const double *eta, double out[3])
+{
+    const int d = P->dim;
+    const double hd = pow(P->h, d);
+    double well = 0.0, grad = 0.0, V = 0.0;
+    for (int ck = 0; ck < ncell_axis(P, 2); ++ck)
+        for (int cj = 0; cj < ncell_axis(P, 1); ++cj)
+            for (int ci = 0; ci < ncell_axis(P, 0); ++ci) {
+                const double n = eta[cid(P, ci, cj, ck)];
+                well += hd * T->alpha * n * n * (1.0 - n) * (1.0 - n);
+                V += hd * n;
+                /* |grad eta|^2 from the differences across the interior faces (each once) */
+                for (int a = 0; a < d; ++a) {
+                    const int cc[3] = {ci, cj, ck};
+                    if (cc[a] + 1 >= ncell_axis(P, a)) continue;
+                    const double m = eta_at(P, eta, ci, cj, ck, a, +1, n);
+                    grad += hd * 0.5 * T->beta * (m - n) * (m - n) / (P->h * P->h);
+                }
+            }
+    const double lam = T->lambda + T->lambda_rate * step * T->dt;
+    out[0] = well;
+    out[1] = grad;
+    out[2] = 0.5 * lam * (V - T->V0) * (V - T->V0);
+}

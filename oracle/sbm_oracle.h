@@ -22,6 +22,8 @@
  *   - Dense direct solve, adjoint solve and dJ/dpsi_c = -lambda_c^T S_c u_c.
  *   - Source terms of eq. SBMLinearElasticity: eigenstrain load, body force psi b
  *     and the diffuse traction t |grad psi| (Theorem 1)      [Sec. 2.1]
+ *   - Phase-field topology optimisation: one explicit Allen-Cahn step with the
+ *     volume constraint, psi = (eta + zeta)^2                 [Sec. 3.3]
  *
  * Layout (the same packed layout as the C ABI of the CUDA library):
  *   node (i,j,k)  -> i + nx*(j + ny*k);     component p at offset p*nnodes
@@ -127,6 +129,30 @@ void orc_source_terms(const orc_problem *P, const double *psi, const double *eps
                       double *f);
 /* psi_n, |grad psi|_n and w_n of orc_source_terms at every node. */
 void orc_node_psi(const orc_problem *P, const double *psi, double *pn, double *gn, double *w);
+
+/* Phase-field topology optimisation (Sec. 3.3, eqs. topop_objective,
+ * topop_volume_constraint, topop_evolution).  eta in cells, stiffness psi = (eta+zeta)^2. */
+typedef struct {
+    double alpha, beta;    /* double-well height and gradient-energy coefficient */
+    double zeta;           /* stiffness regularisation: psi = (eta + zeta)^2 */
+    double lambda;         /* Lagrange multiplier of the volume constraint at t = 0 ... */
+    double lambda_rate;    /* ... growing linearly: lambda(t) = lambda + lambda_rate t, t = step dt */
+    double V0;             /* target volume */
+    double mobility, dt;   /* L of eq. topop_evolution and the explicit time step */
+} orc_topopt_params;
+/* One explicit Euler step of eq. topop_evolution:
+ *   eta_out = eta - dt L [2 alpha eta (1-eta)(1-2eta) - beta Lap(eta) - (eta+zeta) e_c
+ *                         + lambda(t) (V(eta) - V0)],
+ * e_c = u_c^T S_c u_c the unit-psi strain energy of cell c at the equilibrium u of psi,
+ * Lap the (2d+1)-point cell Laplacian with eta's Neumann condition (a missing
+ * neighbour takes the cell's own value), V(eta) = h^d sum_c eta_c. */
+void orc_topopt_step(const orc_problem *P, const orc_topopt_params *T, int step, const double *eta, const double *u,
+                     double *eta_out);
+/* The non-elastic parts of the discrete energy whose eta-gradient the step follows:
+ * out[0] = h^d sum alpha eta^2 (1-eta)^2, out[1] = h^d sum over interior faces
+ * beta/2 (difference / h)^2, out[2] = lambda(t)/2 (V - V0)^2.  (The elastic part is
+ * half the compliance h^d f.u of the equilibrium solve.) */
+void orc_topopt_energy(const orc_problem *P, const orc_topopt_params *T, int step, const double *eta, double out[3]);
 
 /* g_c = -lambda_c^T S_c u_c for every cell (S_c = unit-psi element matrix). */
 void orc_dJdpsi(const orc_problem *P, const double *u, const double *lam, double *g);
