@@ -205,6 +205,55 @@ sbm_status sbm_bottom_correct(sbm_grid grid, int fp32, const double *f, double *
 /* dJdpsi_c = -lambda_c^T S_c u_c for every cell of the finest level. */
 sbm_status sbm_dJdpsi(sbm_grid grid, const double *u, const double *lambda, double *dJdpsi);
 
+/* ---- phase-field topology optimisation (Sec. 3.3): an outer staggered loop ----
+ * The order parameter eta lives in the cells of the finest level and sets the
+ * stiffness psi = (eta + zeta)^2 (eq. topop_objective).  One explicit Euler step of
+ * eq. topop_evolution is
+ *   eta' = eta - dt L [2 alpha eta (1-eta)(1-2eta) - beta Lap(eta) - (eta+zeta) e_c
+ *                      + lambda(t) (V(eta) - V0)],
+ * with e_c = u_c^T S_c u_c the unit-psi strain energy of cell c at the equilibrium u of
+ * psi (the eta-derivative of half the compliance is -(eta+zeta) e_c), Lap the (2d+1)-
+ * point cell Laplacian with eta's Neumann condition (a missing neighbour takes the
+ * cell's own value), V(eta) = h^d sum_c eta_c (eq. topop_volume_constraint) and
+ * lambda(t) = lambda + lambda_rate t, t = step dt.  The step is explicit: it is stable
+ * for dt L (2 alpha + 4 d beta / h^2 + lambda |Omega| + max_c e_c) below about 1.  eta is
+ * not clipped; psi is floored at psi_min for the solve. */
+typedef struct {
+    double alpha, beta;    /* double-well height and gradient-energy coefficient */
+    double zeta;           /* stiffness regularisation: psi = (eta + zeta)^2 */
+    double lambda;         /* volume-constraint multiplier at t = 0 ... */
+    double lambda_rate;    /* ... and its linear growth rate */
+    double V0;             /* target volume int eta dx */
+    double mobility, dt;   /* L of eq. topop_evolution and the time step */
+    double psi_min;        /* floor of psi for the solve (as sbm_set_psi) */
+} sbm_topopt_params;
+typedef struct {
+    int steps;             /* steps completed */
+    int capacity;          /* entries available in each history array below */
+    double *compliance;    /* host, optional: h^d u^T K(psi) u of step s's solve (= h^d f.u for
+                            * homogeneous Dirichlet data) */
+    double *volume;        /* host, optional: V(eta) after step s */
+    int *cycles;           /* host, optional: outer iterations of step s's solve */
+    double ms;             /* wall time of the loop */
+} sbm_topopt_info;
+/* One step: eta_out (device, packed cells of the finest level) from eta (device,
+ * packed cells; not modified) at the displacement u (device, packed nodes; the caller's
+ * equilibrium for psi(eta)); `step` sets lambda(t).  volume (host, may be NULL)
+ * receives V(eta_out); compliance (host, may be NULL) h^d sum_c psi_c e_c with the psi the
+ * grid holds (0 before any psi is set).  Finest level of a single-level grid; needs the
+ * moduli.  Synchronises the grid stream. */
+sbm_status sbm_topopt_step(sbm_grid grid, const sbm_topopt_params *p, int step, const double *eta, const double *u,
+                           double *eta_out, double *volume, double *compliance);
+/* The staggered loop: `steps` times { psi <- max((eta+zeta)^2, psi_min) (as sbm_set_psi);
+ * solve K(psi) u = f from the current u (warm start; f of sbm_set_source, opts as
+ * sbm_solve); eta <- one step }.  eta and u (device, packed) are updated in place.  The
+ * grid keeps the psi of the last solve.  Single-level grids only (SBM_ERR_STATE with
+ * refinement patches).  A solve that ends in SBM_ERR_NOCONV / SBM_ERR_DIVERGED stops the
+ * loop with that status (info->steps counts the completed steps).  opts->tol is
+ * relative to each solve's initial residual, that of its warm start. */
+sbm_status sbm_topopt_run(sbm_grid grid, const sbm_topopt_params *p, int steps, double *eta, double *u,
+                          const sbm_opts *opts, sbm_topopt_info *info);
+
 /* ---- the operator variants of Sec. 2.3 (for comparison with the cell-flux form) ----
  * The literal product-rule discretisation of the strong form
  *     div(psi C grad u) = psi C : grad grad u + grad psi . C grad u

@@ -285,6 +285,38 @@ class Grid:
         self._check(lib().sbm_source_terms(self._h, level, _ptr(psi), opt(eps0), opt(b), opt(t), _ptr(out)))
         return out
 
+    # -- phase-field topology optimisation (Sec. 3.3)
+    @staticmethod
+    def _topopt_params(alpha, beta, zeta, lam, lam_rate, V0, mobility, dt, psi_min):
+        return _capi.sbm_topopt_params(alpha, beta, zeta, lam, lam_rate, V0, mobility, dt, psi_min)
+
+    def topopt_step(self, eta: torch.Tensor, u: torch.Tensor, *, alpha=200.0, beta=0.01, zeta=0.01, lam=400.0,
+                    lam_rate=0.0, V0=0.25, mobility=1.0, dt=1e-4, psi_min=1e-6, step=0):
+        """(eta', V(eta'), compliance): one explicit step of eq. topop_evolution at u."""
+        prm = self._topopt_params(alpha, beta, zeta, lam, lam_rate, V0, mobility, dt, psi_min)
+        out = torch.empty_like(eta)
+        vol, comp = C.c_double(), C.c_double()
+        self._check(lib().sbm_topopt_step(self._h, C.byref(prm), step, _ptr(eta), _ptr(u), _ptr(out),
+                                          C.byref(vol), C.byref(comp)))
+        return out, vol.value, comp.value
+
+    def topopt_run(self, eta: torch.Tensor, u: torch.Tensor, steps: int, *, alpha=200.0, beta=0.01, zeta=0.01,
+                   lam=400.0, lam_rate=0.0, V0=0.25, mobility=1.0, dt=1e-4, psi_min=1e-6, raise_on_fail=True,
+                   **opts):
+        """The staggered loop (eta and u updated in place); returns per-step
+        compliance, volume and solve cycles, and the loop's wall time in ms."""
+        prm = self._topopt_params(alpha, beta, zeta, lam, lam_rate, V0, mobility, dt, psi_min)
+        o = make_opts(**opts)
+        cap = max(steps, 1)
+        comp, vol, cyc = (C.c_double * cap)(), (C.c_double * cap)(), (C.c_int * cap)()
+        info = _capi.sbm_topopt_info(0, cap, C.cast(comp, C.POINTER(C.c_double)), C.cast(vol, C.POINTER(C.c_double)),
+                                     C.cast(cyc, C.POINTER(C.c_int)), 0.0)
+        st = lib().sbm_topopt_run(self._h, C.byref(prm), steps, _ptr(eta), _ptr(u), C.byref(o), C.byref(info))
+        self._check(st, allow=(SBM_OK,) if raise_on_fail else (SBM_OK, SBM_ERR_NOCONV, SBM_ERR_DIVERGED))
+        n = info.steps
+        return {"steps": n, "compliance": list(comp[:n]), "volume": list(vol[:n]), "cycles": list(cyc[:n]),
+                "ms": info.ms, "status": st}
+
     # -- the operator variants of Sec. 2.3 (product-rule strong form)
     def apply_product(self, variant: int, psi: torch.Tensor, u: torch.Tensor) -> torch.Tensor:
         out = torch.empty_like(u)

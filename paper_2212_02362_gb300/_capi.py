@@ -42,6 +42,16 @@ class sbm_info(C.Structure):
                 ("launches", C.c_longlong)]
 
 
+class sbm_topopt_params(C.Structure):
+    _fields_ = [(k, C.c_double) for k in ("alpha", "beta", "zeta", "lambda_", "lambda_rate", "V0", "mobility", "dt",
+                                          "psi_min")]
+
+
+class sbm_topopt_info(C.Structure):
+    _fields_ = [("steps", C.c_int), ("capacity", C.c_int), ("compliance", C.POINTER(C.c_double)),
+                ("volume", C.POINTER(C.c_double)), ("cycles", C.POINTER(C.c_int)), ("ms", C.c_double)]
+
+
 _grid = C.c_void_p
 _dptr = C.c_void_p          # device pointers are passed as plain addresses
 
@@ -72,6 +82,10 @@ _SIGS = {
     "sbm_set_alloc_limit": (None, [C.c_size_t]),
     "sbm_set_wait_limit": (C.c_int, [_grid, C.c_longlong]),
     "sbm_source_terms": (C.c_int, [_grid, C.c_int, _dptr, _dptr, _dptr, _dptr, _dptr]),
+    "sbm_topopt_step": (C.c_int, [_grid, C.POINTER(sbm_topopt_params), C.c_int, _dptr, _dptr, _dptr,
+                                  C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "sbm_topopt_run": (C.c_int, [_grid, C.POINTER(sbm_topopt_params), C.c_int, _dptr, _dptr, C.POINTER(sbm_opts),
+                                 C.POINTER(sbm_topopt_info)]),
     "sbm_apply_product": (C.c_int, [_grid, C.c_int, _dptr, _dptr, _dptr]),
     "sbm_jacobi_product": (C.c_int, [_grid, C.c_int, _dptr, _dptr, _dptr, C.c_double, C.c_int]),
     "sbm_time_kernel": (C.c_int, [_grid, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),

@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cstring>
 #include <algorithm>
+#include <chrono>
 #include <atomic>
 #include <type_traits>
 #include <string>
@@ -135,6 +136,7 @@ struct sbm_grid_s {
     long long amr_npart = 0;
     double *amr_u0 = nullptr, *amr_r0 = nullptr;   // composite solution / residual on the base level
     double *adj[9][9] = {};                            // adjoint Krylov vectors [vector][level]
+    double *top = nullptr;      // topology optimisation: psi, eta scratch, partial sums, scalars
 };
 
 namespace {
@@ -1274,7 +1276,7 @@ sbm_status sbm_grid_destroy(sbm_grid G)
         for (double *q : vec)
             if (q) cudaFree(q);
     void *ptrs[] = {G->fsrc, G->fadj, G->psi_raw, G->rho, G->part, G->scal, G->dbad, G->A64, G->A32, G->gjtmp, G->gjbar, G->gather,
-                    G->derr, G->dgate, G->amr_part, G->amr_u0, G->amr_r0, G->dhist};
+                    G->derr, G->dgate, G->amr_part, G->amr_u0, G->amr_r0, G->dhist, G->top};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (G->hscal) cudaFreeHost(G->hscal);
@@ -1483,13 +1485,9 @@ static sbm_status finish_psi(sbm_grid G)
     return SBM_OK;
 }
 
-sbm_status sbm_set_psi(sbm_grid G, int level, const double *psi, double psi_min)
+// psi of the finest level from a device array: raw copy, floor, coarsening.
+static sbm_status set_psi_dev(sbm_grid G, const double *psi, double psi_min)
 {
-    if (!G) return fail(nullptr, SBM_ERR_ARG, "null grid");
-    if (level != G->nl - 1) return fail(G, SBM_ERR_ARG, "psi must be given on the finest level");
-    if (!is_dev_ptr(psi, G->dev)) return fail(G, SBM_ERR_ARG, "psi is not a device pointer of the grid's device");
-    if (!(psi_min > 0.0) || !std::isfinite(psi_min)) return fail(G, SBM_ERR_ARG, "psi_min must be positive");
-    CK(cudaSetDevice(G->dev));
     Level &F = G->L[G->nl - 1];
     CK(cudaMemsetAsync(G->dbad, 0, sizeof(int), G->st));
     CK(cudaMemcpyAsync(G->psi_raw, psi, sizeof(double) * ncells_h(F.g), cudaMemcpyDeviceToDevice, G->st));
@@ -1498,6 +1496,16 @@ sbm_status sbm_set_psi(sbm_grid G, int level, const double *psi, double psi_min)
     G->psi_min = psi_min;
     if (G->npatch > 0) G->amr_psi_dirty = true;   // covered cells are re-averaged at the next solve
     return finish_psi(G);
+}
+
+sbm_status sbm_set_psi(sbm_grid G, int level, const double *psi, double psi_min)
+{
+    if (!G) return fail(nullptr, SBM_ERR_ARG, "null grid");
+    if (level != G->nl - 1) return fail(G, SBM_ERR_ARG, "psi must be given on the finest level");
+    if (!is_dev_ptr(psi, G->dev)) return fail(G, SBM_ERR_ARG, "psi is not a device pointer of the grid's device");
+    if (!(psi_min > 0.0) || !std::isfinite(psi_min)) return fail(G, SBM_ERR_ARG, "psi_min must be positive");
+    CK(cudaSetDevice(G->dev));
+    return set_psi_dev(G, psi, psi_min);
 }
 
 sbm_status sbm_set_density(sbm_grid G, int level, const double *rho, double psi_min, double q)
@@ -1833,6 +1841,138 @@ sbm_status sbm_source_terms(sbm_grid G, int level, const double *psi, const doub
     const int n[3] = {L.g.nx, L.g.ny, L.g.nz};
     CK(launch_source_terms(L.g.dim, n, L.h, G->mod, psi, eps0, b, t, f, G->st));
     CK(cudaStreamSynchronize(G->st));
+    return SBM_OK;
+}
+
+// ------------------------------------------------- topology optimisation (Sec. 3.3)
+
+static sbm_status topopt_check(sbm_grid G, const sbm_topopt_params *p)
+{
+    if (!G) return fail(nullptr, SBM_ERR_ARG, "null grid");
+    if (!p) return fail(G, SBM_ERR_ARG, "null parameters");
+    const double v[] = {p->alpha, p->beta, p->zeta, p->lambda, p->lambda_rate, p->V0, p->mobility, p->dt, p->psi_min};
+    for (double x : v)
+        if (!std::isfinite(x)) return fail(G, SBM_ERR_ARG, "non-finite topology-optimisation parameter");
+    if (p->alpha < 0 || p->beta < 0 || p->lambda < 0 || p->lambda_rate < 0 || !(p->mobility > 0) || !(p->dt > 0) ||
+        !(p->psi_min > 0) || p->zeta < 0)
+        return fail(G, SBM_ERR_ARG, "need alpha, beta, zeta, lambda, lambda_rate >= 0 and mobility, dt, psi_min > 0");
+    if (!G->has_moduli) return fail(G, SBM_ERR_STATE, "moduli not set (sbm_set_moduli)");
+    if (G->npatch > 0) return fail(G, SBM_ERR_STATE, "topology optimisation runs on single-level grids");
+    if (!G->top) {
+        const long long NC = ncells_h(G->L[G->nl - 1].g);
+        const long long B = topopt_blocks(NC);
+        CK(gmalloc(G, (void **)&G->top, sizeof(double) * (2 * NC + 2 * B + 8)));
+    }
+    return SBM_OK;
+}
+
+static TopoptArgs topopt_args(sbm_grid G, const sbm_topopt_params *p, int step)
+{
+    const Level &F = G->L[G->nl - 1];
+    TopoptArgs A;
+    A.nx = F.g.nx;
+    A.ny = F.g.ny;
+    A.nz = F.g.nz;
+    A.alpha = p->alpha;
+    A.beta = p->beta;
+    A.zeta = p->zeta;
+    A.lam = p->lambda + p->lambda_rate * step * p->dt;
+    A.V0 = p->V0;
+    A.dtL = p->dt * p->mobility;
+    A.hd = std::pow(F.h, F.g.dim);
+    A.ih2 = 1.0 / (F.h * F.h);
+    A.psx = F.g.sx;
+    A.psy = F.g.sy;
+    return A;
+}
+
+sbm_status sbm_topopt_step(sbm_grid G, const sbm_topopt_params *p, int step, const double *eta, const double *u,
+                           double *eta_out, double *volume, double *compliance)
+{
+    sbm_status st = topopt_check(G, p);
+    if (st != SBM_OK) return st;
+    if (step < 0) return fail(G, SBM_ERR_ARG, "step must be >= 0");
+    if (!is_dev_ptr(eta, G->dev) || !is_dev_ptr(u, G->dev) || !is_dev_ptr(eta_out, G->dev))
+        return fail(G, SBM_ERR_ARG, "eta, u and eta_out must be device pointers of the grid's device");
+    if (eta == eta_out) return fail(G, SBM_ERR_ARG, "eta_out must not alias eta");
+    CK(cudaSetDevice(G->dev));
+    const Level &F = G->L[G->nl - 1];
+    const long long NC = ncells_h(F.g);
+    const int B = topopt_blocks(NC);
+    double *part = G->top + 2 * NC, *scal = part + 2 * B;
+    const TopoptArgs A = topopt_args(G, p, step);
+    CK(launch_cell_sum(NC, eta, 0.0, nullptr, part, G->st));
+    CK(launch_sum_parts(part, B, scal, G->st));
+    CK(launch_topopt_step(F.g.dim, A, F.c64, eta, u, G->has_psi ? F.psi64 : nullptr, scal, eta_out, nullptr, part,
+                          G->st));
+    CK(launch_sum_parts(part, B, scal + 1, G->st));
+    CK(launch_sum_parts(part + B, B, scal + 2, G->st));
+    double h[3];
+    CK(cudaMemcpyAsync(h, scal, sizeof(h), cudaMemcpyDeviceToHost, G->st));
+    CK(cudaStreamSynchronize(G->st));
+    if (volume) *volume = A.hd * h[1];
+    if (compliance) *compliance = A.hd * h[2];
+    return SBM_OK;
+}
+
+sbm_status sbm_topopt_run(sbm_grid G, const sbm_topopt_params *p, int steps, double *eta, double *u,
+                          const sbm_opts *opts, sbm_topopt_info *info)
+{
+    sbm_status st = topopt_check(G, p);
+    if (st != SBM_OK) return st;
+    if (steps < 0) return fail(G, SBM_ERR_ARG, "steps must be >= 0");
+    if (!is_dev_ptr(eta, G->dev) || !is_dev_ptr(u, G->dev))
+        return fail(G, SBM_ERR_ARG, "eta and u must be device pointers of the grid's device");
+    sbm_opts o;
+    sbm_default_opts(&o);
+    if (opts) o = *opts;
+    if ((st = validate_opts(G, o)) != SBM_OK) return st;
+    CK(cudaSetDevice(G->dev));
+    if (info) info->steps = 0;
+    Level &F = G->L[G->nl - 1];
+    const long long NC = ncells_h(F.g);
+    const int B = topopt_blocks(NC);
+    double *psi = G->top, *scratch = G->top + NC, *part = G->top + 2 * NC, *scal = part + 2 * B;
+    double *cur = eta, *nxt = scratch;
+    const auto t0 = std::chrono::steady_clock::now();
+    // psi of the first solve and the volume of the initial eta
+    CK(launch_cell_sum(NC, eta, p->zeta, psi, part, G->st));
+    CK(launch_sum_parts(part, B, scal, G->st));
+    for (int s = 0; s < steps; ++s) {
+        if ((st = set_psi_dev(G, psi, p->psi_min)) != SBM_OK) return st;
+        CK(launch_pack<double, double>(F.g, F.g.dim, u, F.du[0], G->st));
+        for (int f = 0; f < 2 * F.g.dim; ++f)
+            for (int q = 0; q < F.g.dim; ++q)
+                if (G->bct[f][q] == SBM_DIRICHLET) CK(launch_set_face(F.g, f, q, G->bcv[f][q], F.du[0], G->st));
+        sbm_info si{};
+        st = run_solve(G, o, G->fsrc, &si, 0);
+        if (st != SBM_OK && st != SBM_ERR_NOCONV && st != SBM_ERR_DIVERGED) return st;
+        CK(launch_unpack<double, double>(F.g, F.g.dim, F.du[0], u, G->st));
+        if (st != SBM_OK) {
+            if (cur != eta) CK(cudaMemcpyAsync(eta, cur, sizeof(double) * NC, cudaMemcpyDeviceToDevice, G->st));
+            CK(cudaStreamSynchronize(G->st));
+            return st;
+        }
+        const TopoptArgs A = topopt_args(G, p, s);
+        CK(launch_topopt_step(F.g.dim, A, F.c64, cur, u, F.psi64, scal, nxt, psi, part, G->st));
+        CK(launch_sum_parts(part, B, scal, G->st));
+        CK(launch_sum_parts(part + B, B, scal + 1, G->st));
+        double h[2];
+        CK(cudaMemcpyAsync(h, scal, sizeof(h), cudaMemcpyDeviceToHost, G->st));
+        CK(cudaStreamSynchronize(G->st));
+        if (info) {
+            if (s < info->capacity) {
+                if (info->compliance) info->compliance[s] = A.hd * h[1];
+                if (info->volume) info->volume[s] = A.hd * h[0];
+                if (info->cycles) info->cycles[s] = si.cycles;
+            }
+            info->steps = s + 1;
+        }
+        std::swap(cur, nxt);
+    }
+    if (cur != eta) CK(cudaMemcpyAsync(eta, cur, sizeof(double) * NC, cudaMemcpyDeviceToDevice, G->st));
+    CK(cudaStreamSynchronize(G->st));
+    if (info) info->ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     return SBM_OK;
 }
 

@@ -284,6 +284,26 @@ cudaError_t launch_product(int mode, int dim, const int n[3], double h, const do
 // force b and a nodal diffuse traction t (either may be null).
 cudaError_t launch_source_terms(int dim, const int n[3], double h, const double mod[3], const double *psi,
                                 const double *eps0, const double *b, const double *t, double *f, cudaStream_t s);
+// Phase-field topology optimisation step (k_topopt.cu): node counts, the
+// coefficients of eq. topop_evolution and the grid factors.
+struct TopoptArgs {
+    int nx, ny, nz;
+    double alpha, beta, zeta;
+    double lam, V0;        // lambda(t) of this step and the target volume
+    double dtL;            // dt * mobility
+    double hd, ih2;        // h^d and 1 / h^2
+    long long psx, psy;    // strides of psi_solve (the level layout: cell (i,j,k) at i + psx j + psy k)
+};
+int topopt_blocks(long long ncells);
+// eta_out = one explicit step from eta (cells, packed) at the equilibrium u (nodes,
+// packed); psi_next (may be null) = (eta_out + zeta)^2; part[0..B) = per-block sums of
+// eta_out, part[B..2B) of psi_solve_c e_c (B = topopt_blocks(cells); psi_solve may be
+// null); eta_sum: device scalar, the sum of eta over the cells.
+cudaError_t launch_topopt_step(int dim, const TopoptArgs &A, const Coef<double> &c, const double *eta,
+                               const double *u, const double *psi_solve, const double *eta_sum, double *eta_out,
+                               double *psi_next, double *part, cudaStream_t s);
+// part[0..B) = per-block sums of x[0..n); psi (may be null) = (x + zeta)^2.
+cudaError_t launch_cell_sum(long long n, const double *x, double zeta, double *psi, double *part, cudaStream_t s);
 // Reads a buffer (measurement: leaves L2 holding clean lines of it).
 cudaError_t launch_l2_read(const void *buf, size_t bytes, float *sink, cudaStream_t s);
 // adjoint of the composite problem
