@@ -293,7 +293,7 @@ void sbm_set_alloc_limit(size_t bytes);
 sbm_status sbm_set_wait_limit(sbm_grid grid, long long spins);
 
 /* ---- measurement ---- */
-enum { SBM_K_RESIDUAL64 = 0, SBM_K_JACOBI = 1, SBM_K_RESIDUAL = 2 };
+enum { SBM_K_RESIDUAL64 = 0, SBM_K_JACOBI = 1, SBM_K_RESIDUAL = 2, SBM_K_SOURCE = 3, SBM_K_TOPOPT = 4 };
 /* Launch one hot-path kernel of the finest level `reps` times back to back on
  * the grid stream between two CUDA events (after one untimed launch) and report
  * the mean duration per launch (host, ms), together with the algorithmic DRAM
@@ -301,13 +301,19 @@ enum { SBM_K_RESIDUAL64 = 0, SBM_K_JACOBI = 1, SBM_K_RESIDUAL = 2 };
  *   SBM_K_RESIDUAL64  the FP64 defect residual (FP32 output on SBM_MIXED grids)
  *   SBM_K_JACOBI      one damped-Jacobi sweep in the V-cycle precision
  *   SBM_K_RESIDUAL    the V-cycle residual in the V-cycle precision
+ *   SBM_K_SOURCE      sbm_source_terms with eigenstrain, body force and traction
+ *                     (FP64; bytes: psi, the d(d+1)/2 eigenstrain slots per cell and b,
+ *                     t, f per node, each once)
+ *   SBM_K_TOPOPT      the step of sbm_topopt_step (FP64; bytes: eta, psi, eta' and the
+ *                     next psi per cell and u per node, each once)
  * Bytes count one read of u, f and psi and one write of the output per node;
  * flops count the sum-factorised cell arithmetic per cell plus the per-node
  * gather and update.  flush_l2 != 0: before every launch a 256 MB scratch buffer
  * (allocated for the call) is written and a second 256 MB buffer read, so that the
  * launch reads its inputs from HBM and finds no dirty lines of other data in L2
  * (their write-back would be charged to it); each launch is timed by its own pair
- * of events.  Uses the level's work buffers (overwrites them). */
+ * of events.  Uses the level's work buffers (overwrites them); SBM_K_SOURCE and
+ * SBM_K_TOPOPT run on scratch arrays allocated for the call. */
 sbm_status sbm_time_kernel(sbm_grid grid, int which, int reps, int flush_l2, double *ms_per_launch,
                            double *bytes_per_launch, double *flops_per_launch);
 

@@ -23,7 +23,7 @@ constexpr int kThr = 256;
 
 struct SourceArgs {
     int nx, ny, nz;
-    double h;
+    double inv;            // 1 / (2^(d-1) h)
     double c11, c12, c44;
 };
 
@@ -41,12 +41,13 @@ __global__ void __launch_bounds__(kThr) k_source_terms(const SourceArgs A, const
                                                        const double *__restrict__ eps0, const double *__restrict__ b,
                                                        const double *__restrict__ t, double *__restrict__ f)
 {
-    const long long N = (long long)A.nx * A.ny * A.nz;
-    const long long n = (long long)blockIdx.x * kThr + threadIdx.x;
+    const int N = A.nx * A.ny * A.nz;          // < 2^31 (checked by the launcher)
+    const int n = blockIdx.x * kThr + threadIdx.x;
     if (n >= N) return;
-    const int nd[3] = {(int)(n % A.nx), (int)((n / A.nx) % A.ny), (int)(n / ((long long)A.nx * A.ny))};
+    const int nxy = A.nx * A.ny;
+    const int nd[3] = {n % A.nx, (n % nxy) / A.nx, n / nxy};
     const int mc[3] = {A.nx - 1, A.ny - 1, D == 3 ? A.nz - 1 : 1};
-    const long long NC = (long long)mc[0] * mc[1] * mc[2];
+    const int NC = mc[0] * mc[1] * mc[2];
     double acc[3] = {0.0, 0.0, 0.0};
     double ps = 0.0, g[3] = {0.0, 0.0, 0.0};
     int inside = 0;
@@ -60,7 +61,7 @@ __global__ void __launch_bounds__(kThr) k_source_terms(const SourceArgs A, const
             if (v < 0 || v >= mc[a]) in = false;
             cc[a] = min(max(v, 0), mc[a] - 1);
         }
-        const long long cid = cc[0] + (long long)mc[0] * (cc[1] + (long long)mc[1] * cc[2]);
+        const int cid = cc[0] + mc[0] * (cc[1] + mc[1] * cc[2]);
         const double pc = psi[cid];
         ps += pc;
 #pragma unroll
@@ -89,13 +90,13 @@ __global__ void __launch_bounds__(kThr) k_source_terms(const SourceArgs A, const
             }
         }
     }
-    const double inv = 1.0 / ((double)(1 << (D - 1)) * A.h);
-    const double pn = ps / (1 << D);
+    const double inv = A.inv;
+    const double pn = ps * (1.0 / (1 << D));
     double gg = 0.0;
 #pragma unroll
     for (int a = 0; a < D; ++a) gg += (g[a] * inv) * (g[a] * inv);
     const double gn = sqrt(gg);
-    const double w = (double)inside / (1 << D);
+    const double w = (double)inside * (1.0 / (1 << D));
 #pragma unroll
     for (int p = 0; p < D; ++p) {
         double s = 0.0;
@@ -114,11 +115,12 @@ cudaError_t launch_source_terms(int dim, const int n[3], double h, const double 
     A.nx = n[0];
     A.ny = n[1];
     A.nz = dim == 3 ? n[2] : 1;
-    A.h = h;
+    A.inv = 1.0 / ((dim == 3 ? 4.0 : 2.0) * h);
     A.c11 = mod[0];
     A.c12 = mod[1];
     A.c44 = mod[2];
     const long long N = (long long)A.nx * A.ny * A.nz;
+    if (N * (dim == 3 ? 6 : 3) >= (1ll << 31)) return cudaErrorInvalidValue;   // 32-bit indexing
     const dim3 grid((unsigned)((N + kThr - 1) / kThr));
     if (dim == 3) k_source_terms<3><<<grid, kThr, 0, s>>>(A, psi, eps0, b, t, f);
     else k_source_terms<2><<<grid, kThr, 0, s>>>(A, psi, eps0, b, t, f);

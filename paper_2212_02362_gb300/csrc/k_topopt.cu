@@ -33,32 +33,31 @@ __global__ void __launch_bounds__(kThr) k_topopt_step(const TopoptArgs A, const 
 {
     __shared__ double red[2][kThr];
     const int mx = A.nx - 1, my = A.ny - 1, mz = D == 3 ? A.nz - 1 : 1;
-    const long long NC = (long long)mx * my * mz;
-    const long long t = (long long)blockIdx.x * kThr + threadIdx.x;
+    const int NC = mx * my * mz;               // node and cell indices < 2^31 (checked by the launcher)
+    const int t = blockIdx.x * kThr + threadIdx.x;
     double s_eta = 0.0, s_J = 0.0;
     if (t < NC) {
-        const int ci = (int)(t % mx);
-        const int cj = (int)((t / mx) % my);
-        const int ck = (int)(t / ((long long)mx * my));
+        const int mxy = mx * my;
+        const int ci = t % mx;
+        const int cj = (t % mxy) / mx;
+        const int ck = t / mxy;
         const double n = eta[t];
         // Neumann Laplacian: a missing neighbour contributes nothing
         double lap = 0.0;
         lap += (ci + 1 < mx ? eta[t + 1] - n : 0.0) + (ci > 0 ? eta[t - 1] - n : 0.0);
         lap += (cj + 1 < my ? eta[t + mx] - n : 0.0) + (cj > 0 ? eta[t - mx] - n : 0.0);
         if (D == 3) {
-            const long long pz = (long long)mx * my;
-            lap += (ck + 1 < mz ? eta[t + pz] - n : 0.0) + (ck > 0 ? eta[t - pz] - n : 0.0);
+            lap += (ck + 1 < mz ? eta[t + mxy] - n : 0.0) + (ck > 0 ? eta[t - mxy] - n : 0.0);
         }
         lap *= A.ih2;
         // unit-psi strain energy of the cell
-        const long long N = (long long)A.nx * A.ny * (D == 3 ? A.nz : 1);
+        const int N = A.nx * A.ny * (D == 3 ? A.nz : 1);
         double e = 0.0;
         if (D == 3) {
             double U[3][8], U0[3][8];
 #pragma unroll
             for (int a = 0; a < 8; ++a) {
-                const long long o = (ci + (a & 1)) + (long long)A.nx * ((cj + ((a >> 1) & 1)) +
-                                                                        (long long)A.ny * (ck + ((a >> 2) & 1)));
+                const int o = (ci + (a & 1)) + A.nx * ((cj + ((a >> 1) & 1)) + A.ny * (ck + ((a >> 2) & 1)));
 #pragma unroll
                 for (int p = 0; p < 3; ++p) U0[p][a] = U[p][a] = u[p * N + o];
             }
@@ -71,7 +70,7 @@ __global__ void __launch_bounds__(kThr) k_topopt_step(const TopoptArgs A, const 
             double U[2][4], U0[2][4];
 #pragma unroll
             for (int a = 0; a < 4; ++a) {
-                const long long o = (ci + (a & 1)) + (long long)A.nx * (cj + ((a >> 1) & 1));
+                const int o = (ci + (a & 1)) + A.nx * (cj + ((a >> 1) & 1));
 #pragma unroll
                 for (int p = 0; p < 2; ++p) U0[p][a] = U[p][a] = u[p * N + o];
             }
@@ -87,7 +86,7 @@ __global__ void __launch_bounds__(kThr) k_topopt_step(const TopoptArgs A, const 
         eta_out[t] = out;
         if (psi_next) psi_next[t] = (out + A.zeta) * (out + A.zeta);
         s_eta = out;
-        s_J = psi_solve ? psi_solve[ci + A.psx * cj + A.psy * ck] * e : 0.0;
+        s_J = psi_solve ? psi_solve[(long long)ci + A.psx * cj + A.psy * ck] * e : 0.0;
     }
     red[0][threadIdx.x] = s_eta;
     red[1][threadIdx.x] = s_J;
@@ -135,6 +134,8 @@ cudaError_t launch_topopt_step(int dim, const TopoptArgs &A, const Coef<double> 
                                double *psi_next, double *part, cudaStream_t s)
 {
     const long long NC = (long long)(A.nx - 1) * (A.ny - 1) * (dim == 3 ? A.nz - 1 : 1);
+    const long long NN = (long long)A.nx * A.ny * (dim == 3 ? A.nz : 1);
+    if (NN * dim >= (1ll << 31)) return cudaErrorInvalidValue;               // 32-bit indexing
     const dim3 grid((unsigned)topopt_blocks(NC));
     if (dim == 3)
         k_topopt_step<3><<<grid, kThr, 0, s>>>(A, c, eta, u, psi_solve, eta_sum, eta_out, psi_next, part);

@@ -2007,7 +2007,7 @@ sbm_status sbm_time_kernel(sbm_grid G, int which, int reps, int flush_l2, double
 {
     sbm_status s = check_ready(G);
     if (s != SBM_OK) return s;
-    if (which < SBM_K_RESIDUAL64 || which > SBM_K_RESIDUAL || reps < 1) return fail(G, SBM_ERR_ARG, "bad kernel id or reps");
+    if (which < SBM_K_RESIDUAL64 || which > SBM_K_TOPOPT || reps < 1) return fail(G, SBM_ERR_ARG, "bad kernel id or reps");
     CK(cudaSetDevice(G->dev));
     const int fine = G->nl - 1;
     Level &L = G->L[fine];
@@ -2015,8 +2015,34 @@ sbm_status sbm_time_kernel(sbm_grid G, int which, int reps, int flush_l2, double
     const int d = L.g.dim;
     const double nn = (double)nnodes(L.g), nc = (double)ncells_h(L.g);
     const double cellf = d == 3 ? 195.0 : 38.0, nodef = d == 3 ? 41.0 : 26.0;
+    // scratch inputs of the source-term and topology-step kernels (packed arrays)
+    const int nv = d == 3 ? 6 : 3;
+    const long long NC = ncells_h(L.g), NN = nnodes(L.g);
+    const int TB = topopt_blocks(NC);
+    double *scr = nullptr;
+    struct FreeOnExit {
+        double *&p;
+        ~FreeOnExit()
+        {
+            if (p) cudaFree(p);
+        }
+    } free_scr{scr};
+    if (which >= SBM_K_SOURCE) {
+        const size_t n = (size_t)NC * (nv + 4) + (size_t)NN * d * 3 + 2 * TB + 8;
+        CK(cudaMalloc(&scr, sizeof(double) * n));
+        CK(cudaMemsetAsync(scr, 0, sizeof(double) * n, G->st));
+    }
+    double *s_eps = scr, *s_eta = scr + NC * nv, *s_eta2 = s_eta + NC, *s_psi = s_eta2 + NC, *s_psi2 = s_psi + NC,
+           *s_b = s_psi2 + NC, *s_t = s_b + NN * d, *s_f = s_t + NN * d, *s_part = s_f + NN * d,
+           *s_scal = s_part + 2 * TB;
+    sbm_topopt_params tp{200.0, 0.01, 0.01, 400.0, 0.0, 0.25, 1.0, 1e-4, 1e-6};
+    const TopoptArgs TA = topopt_args(G, &tp, 0);
+    const int nsz[3] = {L.g.nx, L.g.ny, L.g.nz};
     auto launch = [&]() -> cudaError_t {
         if (which == SBM_K_RESIDUAL64) return residual64(G, G->fsrc, mixed, 5);
+        if (which == SBM_K_SOURCE) return launch_source_terms(d, nsz, L.h, G->mod, G->psi_raw, s_eps, s_b, s_t, s_f, G->st);
+        if (which == SBM_K_TOPOPT)
+            return launch_topopt_step(d, TA, L.c64, s_eta, s_b, L.psi64, s_scal, s_eta2, s_psi2, s_part, G->st);
         int cur = 0;
         sbm_opts o;
         sbm_default_opts(&o);
@@ -2028,7 +2054,10 @@ sbm_status sbm_time_kernel(sbm_grid G, int which, int reps, int flush_l2, double
         if (mixed) return sweep<float>(G, fine, kResidual, L.su[0], L.sf, L.sr, nullptr, 0.0);
         return sweep<double>(G, fine, kResidual, L.du[0], L.df, L.dr, nullptr, 0.0);
     };
-    CK(launch());
+    {
+        cudaError_t e = launch();
+        if (e != cudaSuccess) return fail(G, SBM_ERR_CUDA, std::string("sbm_time_kernel: ") + cudaGetErrorString(e));
+    }
     float t = 0.f;
     if (flush_l2) {
         // flush: write 256 MB, then read a second 256 MB buffer, so that the launch
@@ -2064,6 +2093,16 @@ sbm_status sbm_time_kernel(sbm_grid G, int which, int reps, int flush_l2, double
         CK(cudaEventElapsedTime(&t, G->ev0, G->ev1));
     }
     if (ms) *ms = t / reps;
+    if (which == SBM_K_SOURCE) {
+        if (bytes) *bytes = 8.0 * (NC * (1.0 + nv) + NN * 3.0 * d);
+        if (flops) *flops = (double)NC * (d == 3 ? 60.0 : 24.0) + (double)NN * (d == 3 ? 60.0 : 40.0);
+        return SBM_OK;
+    }
+    if (which == SBM_K_TOPOPT) {
+        if (bytes) *bytes = 8.0 * (NC * 4.0 + NN * d);
+        if (flops) *flops = (double)NC * (cellf + 50.0);
+        return SBM_OK;
+    }
     // per node: read u and f (d values each), psi (one cell per node), write d outputs
     double per_node;
     if (which == SBM_K_RESIDUAL64) per_node = mixed ? (8.0 * d + 8.0 * d + 8.0 + 4.0 * d) : (8.0 * (3 * d + 1));
