@@ -293,7 +293,8 @@ void sbm_set_alloc_limit(size_t bytes);
 sbm_status sbm_set_wait_limit(sbm_grid grid, long long spins);
 
 /* ---- measurement ---- */
-enum { SBM_K_RESIDUAL64 = 0, SBM_K_JACOBI = 1, SBM_K_RESIDUAL = 2, SBM_K_SOURCE = 3, SBM_K_TOPOPT = 4 };
+enum { SBM_K_RESIDUAL64 = 0, SBM_K_JACOBI = 1, SBM_K_RESIDUAL = 2, SBM_K_SOURCE = 3, SBM_K_TOPOPT = 4,
+       SBM_K_FMA64 = 5, SBM_K_FMA32 = 6 };
 /* Launch one hot-path kernel of the finest level `reps` times back to back on
  * the grid stream between two CUDA events (after one untimed launch) and report
  * the mean duration per launch (host, ms), together with the algorithmic DRAM
@@ -306,6 +307,9 @@ enum { SBM_K_RESIDUAL64 = 0, SBM_K_JACOBI = 1, SBM_K_RESIDUAL = 2, SBM_K_SOURCE 
  *                     t, f per node, each once)
  *   SBM_K_TOPOPT      the step of sbm_topopt_step (FP64; bytes: eta, psi, eta' and the
  *                     next psi per cell and u per node, each once)
+ *   SBM_K_FMA64/32    a register-only multiply-add probe on every SM (8 independent
+ *                     chains per thread, 8 blocks of 256 threads per SM): the measured
+ *                     FP64 / FP32 rate that ALU-bound kernels are compared with (bytes 0)
  * Bytes count one read of u, f and psi and one write of the output per node;
  * flops count the sum-factorised cell arithmetic per cell plus the per-node
  * gather and update.  flush_l2 != 0: before every launch a 256 MB scratch buffer

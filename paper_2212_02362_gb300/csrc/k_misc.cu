@@ -719,6 +719,31 @@ __global__ void k_l2_read(const float4 *__restrict__ a, long long n4, float *sin
     if (acc == 1234567.f) sink[0] = acc;
 }
 
+// FMA throughput probe: every thread runs 8 independent multiply-add chains of
+// `iters` steps (2 flops each); the result is stored only under a condition the
+// values never meet, so nothing is optimised away.
+template <typename T>
+__global__ void k_fma_rate(int iters, T a, T b, T *sink)
+{
+    T x[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) x[j] = T(threadIdx.x + j) * T(1e-3);
+    for (int i = 0; i < iters; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) x[j] = x[j] * a + b;
+    T s = 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) s += x[j];
+    if (s == T(-1234567)) sink[0] = s;
+}
+
+cudaError_t launch_fma_rate(int fp64, int blocks, int threads, int iters, void *sink, cudaStream_t s)
+{
+    if (fp64) k_fma_rate<double><<<blocks, threads, 0, s>>>(iters, 0.999999, 1e-7, static_cast<double *>(sink));
+    else k_fma_rate<float><<<blocks, threads, 0, s>>>(iters, 0.9999f, 1e-4f, static_cast<float *>(sink));
+    return cudaGetLastError();
+}
+
 cudaError_t launch_l2_read(const void *buf, size_t bytes, float *sink, cudaStream_t s)
 {
     k_l2_read<<<152 * 8, 256, 0, s>>>(static_cast<const float4 *>(buf), (long long)(bytes / 16), sink);

@@ -2007,7 +2007,7 @@ sbm_status sbm_time_kernel(sbm_grid G, int which, int reps, int flush_l2, double
 {
     sbm_status s = check_ready(G);
     if (s != SBM_OK) return s;
-    if (which < SBM_K_RESIDUAL64 || which > SBM_K_TOPOPT || reps < 1) return fail(G, SBM_ERR_ARG, "bad kernel id or reps");
+    if (which < SBM_K_RESIDUAL64 || which > SBM_K_FMA32 || reps < 1) return fail(G, SBM_ERR_ARG, "bad kernel id or reps");
     CK(cudaSetDevice(G->dev));
     const int fine = G->nl - 1;
     Level &L = G->L[fine];
@@ -2027,7 +2027,12 @@ sbm_status sbm_time_kernel(sbm_grid G, int which, int reps, int flush_l2, double
             if (p) cudaFree(p);
         }
     } free_scr{scr};
-    if (which >= SBM_K_SOURCE) {
+    int nsm = 0;
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, G->dev));
+    const int fma_blocks = 8 * nsm, fma_threads = 256, fma_iters = which == SBM_K_FMA64 ? 1 << 11 : 1 << 14;
+    if (which == SBM_K_FMA64 || which == SBM_K_FMA32) {
+        CK(cudaMalloc(&scr, 64));
+    } else if (which >= SBM_K_SOURCE) {
         const size_t n = (size_t)NC * (nv + 4) + (size_t)NN * d * 3 + 2 * TB + 8;
         CK(cudaMalloc(&scr, sizeof(double) * n));
         CK(cudaMemsetAsync(scr, 0, sizeof(double) * n, G->st));
@@ -2043,6 +2048,8 @@ sbm_status sbm_time_kernel(sbm_grid G, int which, int reps, int flush_l2, double
         if (which == SBM_K_SOURCE) return launch_source_terms(d, nsz, L.h, G->mod, G->psi_raw, s_eps, s_b, s_t, s_f, G->st);
         if (which == SBM_K_TOPOPT)
             return launch_topopt_step(d, TA, L.c64, s_eta, s_b, L.psi64, s_scal, s_eta2, s_psi2, s_part, G->st);
+        if (which == SBM_K_FMA64 || which == SBM_K_FMA32)
+            return launch_fma_rate(which == SBM_K_FMA64, fma_blocks, fma_threads, fma_iters, scr, G->st);
         int cur = 0;
         sbm_opts o;
         sbm_default_opts(&o);
@@ -2101,6 +2108,11 @@ sbm_status sbm_time_kernel(sbm_grid G, int which, int reps, int flush_l2, double
     if (which == SBM_K_TOPOPT) {
         if (bytes) *bytes = 8.0 * (NC * 4.0 + NN * d);
         if (flops) *flops = (double)NC * (cellf + 50.0);
+        return SBM_OK;
+    }
+    if (which == SBM_K_FMA64 || which == SBM_K_FMA32) {
+        if (bytes) *bytes = 0.0;
+        if (flops) *flops = 16.0 * fma_iters * (double)fma_blocks * fma_threads;
         return SBM_OK;
     }
     // per node: read u and f (d values each), psi (one cell per node), write d outputs

@@ -304,6 +304,9 @@ cudaError_t launch_topopt_step(int dim, const TopoptArgs &A, const Coef<double> 
                                double *psi_next, double *part, cudaStream_t s);
 // part[0..B) = per-block sums of x[0..n); psi (may be null) = (x + zeta)^2.
 cudaError_t launch_cell_sum(long long n, const double *x, double zeta, double *psi, double *part, cudaStream_t s);
+// FMA throughput probe (measurement): blocks x threads threads, 8 chains of `iters`
+// multiply-adds each (16 iters flops per thread), FP64 or FP32.
+cudaError_t launch_fma_rate(int fp64, int blocks, int threads, int iters, void *sink, cudaStream_t s);
 // Reads a buffer (measurement: leaves L2 holding clean lines of it).
 cudaError_t launch_l2_read(const void *buf, size_t bytes, float *sink, cudaStream_t s);
 // adjoint of the composite problem
