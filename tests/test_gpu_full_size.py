@@ -173,14 +173,15 @@ def test_C2_voids_amr_2d_full_size_matches_oracle_record(built):
     assert err <= 1e-8 and sk <= 2e-8, (err, sk, info.cycles)
 
 
-def test_C5_voids_amr_3d_65_matches_oracle_record(built):
-    """The 3D refinement workload at a 65^3 base + 2 levels (the largest the
-    single-thread oracle solves offline), mixed precision with 6 FP32 correction
-    cycles per FP64 composite residual, as the bench runs the 129^3 base.  As for
-    C2, relres 1e-10 does not bound the error by 1e-8 on this ill-conditioned
+@pytest.mark.parametrize("base", [33, 65])
+def test_C5_voids_amr_3d_matches_oracle_record(built, base):
+    """The 3D refinement workload at a 33^3 and a 65^3 base + 2 levels (65^3 is the
+    largest the single-thread oracle solves offline), mixed precision with 6 FP32
+    correction cycles per FP64 composite residual, as the bench runs the 129^3 base.
+    As for C2, relres 1e-10 does not bound the error by 1e-8 on this ill-conditioned
     composite problem (two GPU solutions at 1e-10 differ by ~1e-7), so the GPU solves
     to relres 1e-12."""
-    rec = _record("voids_amr_3d_65")
-    wk = W.voids_amr(3, 65, 2, count=16, rmin=0.04, rmax=0.12)
+    rec = _record(f"voids_amr_3d_{base}")
+    wk = W.voids_amr(3, base, 2, count=16, rmin=0.04, rmax=0.12)
     err, sk, info = _amr_parity(rec, wk, "mixed", 1e-12, inner_cycles=6, max_cycles=500)
     assert err <= 1e-8 and sk <= 2e-8, (err, sk, info.cycles)
