@@ -357,7 +357,8 @@ def simp(rho, psi_min: float, q: float = 3.0):
 # ------------------------------------------------------------------ BSAMR
 
 class _Amr(C.Structure):
-    _fields_ = [("base", _Problem), ("nlev", C.c_int), ("lo", (C.c_int * 3) * 8), ("hi", (C.c_int * 3) * 8)]
+    _fields_ = [("base", _Problem), ("nlev", C.c_int), ("lo", (C.c_int * 3) * 16), ("hi", (C.c_int * 3) * 16),
+                ("level", C.c_int * 16), ("parent", C.c_int * 16)]
 
 
 _AMR_SIGS = {
@@ -393,9 +394,11 @@ def _La():
 
 @dataclass
 class Amr:
-    """Level 0 = ``base`` (whole box); level a >= 1 refines level a-1 by 2 on the node
-    box ``boxes[a-1] = (lo, hi)`` given in level-a node indices.  Level a >= 1 arrays
-    live on the box grown by one padding node per side (see sbm_oracle.h)."""
+    """Patch 0 = ``base`` (whole box); patch a >= 1 refines its parent by 2 on the node
+    box ``boxes[a-1] = (lo, hi)`` or ``(lo, hi, parent)`` given in the node indices of
+    its level (default parent a-1: one patch per level).  Parents come before their
+    children.  Patch a >= 1 arrays live on the box grown by one padding node per side
+    (see sbm_oracle.h)."""
     base: Problem
     boxes: list
 
@@ -403,16 +406,30 @@ class Amr:
     def nlev(self):
         return 1 + len(self.boxes)
 
+    def parent(self, a):
+        if a == 0:
+            return -1
+        b = self.boxes[a - 1]
+        return b[2] if len(b) > 2 else a - 1
+
+    def level(self, a):
+        return 0 if a == 0 else self.level(self.parent(a)) + 1
+
     def c(self) -> _Amr:
         s = _Amr()
         s.base = self.base.c()
         s.nlev = self.nlev
-        for a, (lo, hi) in enumerate(self.boxes, start=1):
+        s.level[0], s.parent[0] = 0, -1
+        for a, b in enumerate(self.boxes, start=1):
+            lo, hi = b[0], b[1]
             lo3 = list(lo) + [0] * (3 - len(lo))
             hi3 = list(hi) + [0] * (3 - len(hi))
             for ax in range(3):
                 s.lo[a][ax] = lo3[ax]
                 s.hi[a][ax] = hi3[ax]
+            s.parent[a] = self.parent(a)
+            s.level[a] = self.level(a)
+            assert 0 <= s.parent[a] < a
         return s
 
     def level_problem(self, a) -> Problem:
@@ -421,14 +438,15 @@ class Amr:
         return Problem(out.dim, tuple(out.n), out.h, out.c11, out.c12, out.c44, tuple(out.dirichlet))
 
     def origin(self, a):
-        """global level-a index of local node 0 of level a's storage"""
+        """global index (in patch a's level) of local node 0 of patch a's storage"""
         if a == 0:
             return (0, 0, 0)
         lo = list(self.boxes[a - 1][0]) + [0] * 3
         return tuple(lo[ax] - 1 if ax < self.base.dim else 0 for ax in range(3))
 
     def global_n(self, a):
-        return tuple((self.base.n[ax] - 1) * 2 ** a + 1 if ax < self.base.dim else 1 for ax in range(3))
+        return tuple((self.base.n[ax] - 1) * 2 ** self.level(a) + 1 if ax < self.base.dim else 1
+                     for ax in range(3))
 
     def owned(self, a, i, j, k=0) -> bool:
         return bool(_La().orc_amr_owned(C.byref(self.c()), a, i, j, k))

@@ -627,7 +627,7 @@ void orc_dJdpsi(const orc_problem *P, const double *u, const double *lam, double
 static int amr_N(const orc_amr *A, int a, int axis)
 {
     if (axis >= A->base.dim) return 1;
-    return (A->base.n[axis] - 1) * (1 << a) + 1;
+    return (A->base.n[axis] - 1) * (1 << A->level[a]) + 1;
 }
 
 void orc_amr_level_problem(const orc_amr *A, int a, orc_problem *P)
@@ -636,7 +636,7 @@ void orc_amr_level_problem(const orc_amr *A, int a, orc_problem *P)
     if (a == 0) return;
     for (int ax = 0; ax < 3; ++ax)
         P->n[ax] = (ax < A->base.dim) ? A->hi[a][ax] - A->lo[a][ax] + 3 : 1;
-    P->h = A->base.h / (double)(1 << a);
+    P->h = A->base.h / (double)(1 << A->level[a]);
     P->dirichlet[0] = P->dirichlet[1] = P->dirichlet[2] = 0u;
 }
 
@@ -671,15 +671,19 @@ static int amr_box_owned(const orc_amr *A, int a, const int g[3])
     return 1;
 }
 
-/* Covered: the node coincides with a node of the next finer level's solve region.
- * That node is either owned by the finer level or itself covered, so by induction
- * the finest level whose region contains the point owns it. */
-static int amr_covered(const orc_amr *A, int a, const int g[3])
+/* The child of patch a whose solve region contains the node coincident with g,
+ * or -1.  That node is either owned by the child or itself covered, so by
+ * induction the finest patch whose region contains the point owns it. */
+static int amr_cover_child(const orc_amr *A, int a, const int g[3])
 {
-    if (a + 1 >= A->nlev) return 0;
     const int g2[3] = {2 * g[0], 2 * g[1], A->base.dim == 3 ? 2 * g[2] : 0};
-    return amr_box_owned(A, a + 1, g2);
+    for (int c = a + 1; c < A->nlev; ++c)
+        if (A->parent[c] == a && amr_box_owned(A, c, g2)) return c;
+    return -1;
 }
+
+/* Covered: the node coincides with a node of a child's solve region. */
+static int amr_covered(const orc_amr *A, int a, const int g[3]) { return amr_cover_child(A, a, g) >= 0; }
 
 int orc_amr_owned(const orc_amr *A, int a, int i, int j, int k)
 {
@@ -713,18 +717,19 @@ void orc_amr_coarsen_psi(const orc_amr *A, double *const *psi)
 {
     const int d = A->base.dim, nc = 1 << d;
     for (int a = A->nlev - 1; a >= 1; --a) {
+        const int pa = A->parent[a];
         orc_problem Pf, Pc;
         orc_amr_level_problem(A, a, &Pf);
-        orc_amr_level_problem(A, a - 1, &Pc);
-        /* coarse cell C (level a-1) covers fine cells 2C .. 2C+1; it is inside box a
-         * when 2C >= lo and 2C + 2 <= hi on every axis */
+        orc_amr_level_problem(A, pa, &Pc);
+        /* parent cell C covers fine cells 2C .. 2C+1; it is inside box a when
+         * 2C >= lo and 2C + 2 <= hi on every axis */
         const int ncx = Pc.n[0] - 1, ncy = Pc.n[1] - 1, ncz = (d == 3) ? Pc.n[2] - 1 : 1;
         for (int lk = 0; lk < ncz; ++lk)
             for (int lj = 0; lj < ncy; ++lj)
                 for (int li = 0; li < ncx; ++li) {
                     int C[3] = {li, lj, lk};
-                    if (a - 1 > 0)
-                        for (int ax = 0; ax < d; ++ax) C[ax] += A->lo[a - 1][ax] - 1;
+                    if (pa > 0)
+                        for (int ax = 0; ax < d; ++ax) C[ax] += A->lo[pa][ax] - 1;
                     int in = 1;
                     for (int ax = 0; ax < d; ++ax)
                         if (2 * C[ax] < A->lo[a][ax] || 2 * C[ax] + 2 > A->hi[a][ax]) in = 0;
@@ -735,7 +740,7 @@ void orc_amr_coarsen_psi(const orc_amr *A, double *const *psi)
                         for (int ax = 0; ax < d; ++ax) fl[ax] = 2 * C[ax] + ((c >> ax) & 1) - A->lo[a][ax] + 1;
                         s += psi[a][fl[0] + (long)(Pf.n[0] - 1) * (fl[1] + (long)(Pf.n[1] - 1) * fl[2])];
                     }
-                    psi[a - 1][li + (long)ncx * (lj + (long)ncy * lk)] = s / nc;
+                    psi[pa][li + (long)ncx * (lj + (long)ncy * lk)] = s / nc;
                 }
     }
 }
@@ -743,26 +748,28 @@ void orc_amr_coarsen_psi(const orc_amr *A, double *const *psi)
 void orc_amr_fill(const orc_amr *A, double *const *u)
 {
     const int d = A->base.dim;
-    /* injection, finest first */
+    /* injection, finest first (children have larger indices than their parents) */
     for (int a = A->nlev - 1; a >= 1; --a) {
+        const int pa = A->parent[a];
         orc_problem Pf, Pc;
         orc_amr_level_problem(A, a, &Pf);
-        orc_amr_level_problem(A, a - 1, &Pc);
+        orc_amr_level_problem(A, pa, &Pc);
         const long Nf = orc_nnodes(&Pf), Nc = orc_nnodes(&Pc);
         AMR_FOR_NODES(A, a, Pf, g, loc) {
             int even = 1;
             for (int ax = 0; ax < d; ++ax) even &= (g[ax] % 2 == 0);
             if (!even || !amr_box_owned(A, a, g)) continue;
             int gc[3] = {g[0] / 2, g[1] / 2, d == 3 ? g[2] / 2 : 0};
-            const long lc = amr_local(A, a - 1, gc);
-            for (int p = 0; p < d; ++p) u[a - 1][p * Nc + lc] = u[a][p * Nf + loc];
+            const long lc = amr_local(A, pa, gc);
+            for (int p = 0; p < d; ++p) u[pa][p * Nc + lc] = u[a][p * Nf + loc];
         }
     }
-    /* ghosts, coarsest first: (bi/tri)linear interpolation of level a-1 */
+    /* ghosts, coarsest first: (bi/tri)linear interpolation of the parent */
     for (int a = 1; a < A->nlev; ++a) {
+        const int pa = A->parent[a];
         orc_problem Pf, Pc;
         orc_amr_level_problem(A, a, &Pf);
-        orc_amr_level_problem(A, a - 1, &Pc);
+        orc_amr_level_problem(A, pa, &Pc);
         const long Nf = orc_nnodes(&Pf), Nc = orc_nnodes(&Pc);
         AMR_FOR_NODES(A, a, Pf, g, loc) {
             if (amr_box_owned(A, a, g)) continue;      /* owned, or covered (injected) */
@@ -783,7 +790,7 @@ void orc_amr_fill(const orc_amr *A, double *const *u)
                             gc[ax] = (g[ax] >> 1) + ((g[ax] & 1) ? bit : 0);
                         }
                         if (skip) continue;
-                        s += u[a - 1][p * Nc + amr_local(A, a - 1, gc)];
+                        s += u[pa][p * Nc + amr_local(A, pa, gc)];
                     }
                     s /= (double)(1 << nodd);
                 }
@@ -841,9 +848,10 @@ static double amr_value(const orc_amr *A, double *const *u, int a, const int g[3
     for (int ax = 0; ax < d; ++ax)
         if (g[ax] < 0 || g[ax] > amr_N(A, a, ax) - 1) return 0.0;
     if (amr_box_owned(A, a, g)) {
-        if (amr_covered(A, a, g)) {
+        const int c = amr_cover_child(A, a, g);
+        if (c >= 0) {
             const int g2[3] = {2 * g[0], 2 * g[1], d == 3 ? 2 * g[2] : 0};
-            return amr_value(A, u, a + 1, g2, p);
+            return amr_value(A, u, c, g2, p);
         }
         orc_problem P;
         orc_amr_level_problem(A, a, &P);
@@ -860,7 +868,7 @@ static double amr_value(const orc_amr *A, double *const *u, int a, const int g[3
             gc[ax] = (g[ax] >> 1) + ((g[ax] & 1) ? bit : 0);
         }
         if (skip) continue;
-        s += amr_value(A, u, a - 1, gc, p);
+        s += amr_value(A, u, A->parent[a], gc, p);
     }
     return s / (double)(1 << nodd);
 }
@@ -939,11 +947,13 @@ void orc_amr_dJdpsi(const orc_amr *A, double *const *u, double *const *lam, doub
                 }
     }
     /* coarse cells under a patch hold the mean of their fine cells: their gradient
-     * passes to those cells (coarse to fine) and they keep none of their own */
-    for (int a = 0; a + 1 < A->nlev; ++a) {
+     * passes to those cells (coarse to fine: a parent before its children) and they
+     * keep none of their own */
+    for (int b = 1; b < A->nlev; ++b) {
+        const int a = A->parent[b];
         orc_problem Pc, Pf;
         orc_amr_level_problem(A, a, &Pc);
-        orc_amr_level_problem(A, a + 1, &Pf);
+        orc_amr_level_problem(A, b, &Pf);
         const int ncx = Pc.n[0] - 1, ncy = Pc.n[1] - 1, ncz = d == 3 ? Pc.n[2] - 1 : 1;
         for (int ck = 0; ck < ncz; ++ck)
             for (int cj = 0; cj < ncy; ++cj)
@@ -953,14 +963,14 @@ void orc_amr_dJdpsi(const orc_amr *A, double *const *u, double *const *lam, doub
                         for (int ax = 0; ax < d; ++ax) C[ax] += A->lo[a][ax] - 1;
                     int in = 1;
                     for (int ax = 0; ax < d; ++ax)
-                        if (2 * C[ax] < A->lo[a + 1][ax] || 2 * C[ax] + 2 > A->hi[a + 1][ax]) in = 0;
+                        if (2 * C[ax] < A->lo[b][ax] || 2 * C[ax] + 2 > A->hi[b][ax]) in = 0;
                     if (!in) continue;
                     const long cidx = ci + (long)ncx * (cj + (long)ncy * ck);
                     const double share = g[a][cidx] / nc;
                     for (int c = 0; c < nc; ++c) {
                         int fl[3] = {0, 0, 0};
-                        for (int ax = 0; ax < d; ++ax) fl[ax] = 2 * C[ax] + ((c >> ax) & 1) - A->lo[a + 1][ax] + 1;
-                        g[a + 1][fl[0] + (long)(Pf.n[0] - 1) * (fl[1] + (long)(Pf.n[1] - 1) * fl[2])] += share;
+                        for (int ax = 0; ax < d; ++ax) fl[ax] = 2 * C[ax] + ((c >> ax) & 1) - A->lo[b][ax] + 1;
+                        g[b][fl[0] + (long)(Pf.n[0] - 1) * (fl[1] + (long)(Pf.n[1] - 1) * fl[2])] += share;
                     }
                     g[a][cidx] = 0.0;
                 }
@@ -1036,19 +1046,20 @@ static void amr_region_residual(const orc_amr *A, int a, const double *pa, const
     }
 }
 
-/* rhs_c at the level a-1 nodes covered by level a += R res_a, R = P^T / 2^d (full
+/* rhs_c at the parent nodes covered by patch a += R res_a, R = P^T / 2^d (full
  * weighting about the coincident fine node); Dirichlet dofs are left alone. */
 static void amr_restrict_covered(const orc_amr *A, int a, const double *res, double *rhs_c)
 {
+    const int pa = A->parent[a];
     orc_problem Pf, Pc;
     orc_amr_level_problem(A, a, &Pf);
-    orc_amr_level_problem(A, a - 1, &Pc);
+    orc_amr_level_problem(A, pa, &Pc);
     const int d = A->base.dim;
     const long Nf = orc_nnodes(&Pf), Nc = orc_nnodes(&Pc);
-    AMR_FOR_NODES(A, a - 1, Pc, gc, locc) {
-        if (!amr_covered(A, a - 1, gc)) continue;
+    AMR_FOR_NODES(A, pa, Pc, gc, locc) {
+        if (amr_cover_child(A, pa, gc) != a) continue;
         for (int p = 0; p < d; ++p) {
-            if (amr_dirichlet(A, a - 1, gc, p)) continue;
+            if (amr_dirichlet(A, pa, gc, p)) continue;
             double s = 0.0;
             for (int dk = (d == 3 ? -1 : 0); dk <= (d == 3 ? 1 : 0); ++dk)
                 for (int dj = -1; dj <= 1; ++dj)
@@ -1067,9 +1078,10 @@ static void amr_restrict_covered(const orc_amr *A, int a, const double *res, dou
  * ((bi/tri)linear interpolation, coincident nodes copy). */
 static void amr_interpolate_add(const orc_amr *A, int a, const double *ec, double *ef)
 {
+    const int pa = A->parent[a];
     orc_problem Pf, Pc;
     orc_amr_level_problem(A, a, &Pf);
-    orc_amr_level_problem(A, a - 1, &Pc);
+    orc_amr_level_problem(A, pa, &Pc);
     const int d = A->base.dim;
     const long Nf = orc_nnodes(&Pf), Nc = orc_nnodes(&Pc);
     AMR_FOR_NODES(A, a, Pf, g, loc) {
@@ -1089,7 +1101,7 @@ static void amr_interpolate_add(const orc_amr *A, int a, const double *ec, doubl
                     gcn[ax] = (g[ax] >> 1) + ((g[ax] & 1) ? bit : 0);
                 }
                 if (skip) continue;
-                s += ec[p * Nc + amr_local(A, a - 1, gcn)];
+                s += ec[p * Nc + amr_local(A, pa, gcn)];
             }
             ef[p * Nf + loc] += s / (double)(1 << nodd);
         }
@@ -1100,8 +1112,8 @@ int orc_amr_solve(const orc_amr *A, double *const *psi, double *const *f, double
                   const orc_amr_opts *o, double *hist, int *cycles)
 {
     const int L = A->nlev, d = A->base.dim;
-    double *r[8], *e[8], *rhs[8], *res[8], *pa[8];
-    long N[8];
+    double *r[16], *e[16], *rhs[16], *res[16], *pa[16];
+    long N[16];
     for (int a = 0; a < L; ++a) {
         orc_problem P;
         orc_amr_level_problem(A, a, &P);
@@ -1145,7 +1157,8 @@ int orc_amr_solve(const orc_amr *A, double *const *psi, double *const *f, double
          * full weighting onto the covered parent nodes */
         for (int a = L - 1; a >= 0; --a) {
             memcpy(rhs[a], r[a], sizeof(double) * d * N[a]);
-            if (a + 1 < L) amr_restrict_covered(A, a + 1, res[a + 1], rhs[a]);
+            for (int c = a + 1; c < L; ++c)
+                if (A->parent[c] == a) amr_restrict_covered(A, c, res[c], rhs[a]);
             memset(e[a], 0, sizeof(double) * d * N[a]);
             if (a == 0) break;
             amr_masked_jacobi(A, a, pa[a], rhs[a], e[a], o->omega, o->nu1);
@@ -1163,7 +1176,7 @@ int orc_amr_solve(const orc_amr *A, double *const *psi, double *const *f, double
         /* patches, coarsest first: the parent's correction interpolated onto every
          * node of the patch, then smoothing */
         for (int a = 1; a < L; ++a) {
-            amr_interpolate_add(A, a, e[a - 1], e[a]);
+            amr_interpolate_add(A, a, e[A->parent[a]], e[a]);
             amr_masked_jacobi(A, a, pa[a], rhs[a], e[a], o->omega, o->nu2);
         }
         /* u += e on the owned free dofs; ghosts and covered nodes follow at the next fill */

@@ -158,33 +158,40 @@ void orc_topopt_energy(const orc_problem *P, const orc_topopt_params *T, int ste
 void orc_dJdpsi(const orc_problem *P, const double *u, const double *lam, double *g);
 
 /* ------------------------------------------------------------ BSAMR composite
- * Block-structured refinement (Sec. 2.2): level 0 is the whole box; patch level
- * a >= 1 refines level a-1 by 2 on one node box [lo, hi] given in level-a node
- * indices (even corners, properly nested).  Level a is stored on the box grown by
- * one padding node on every side: nodes [lo-1, hi+1], cells [lo-1, hi]; arrays are
- * packed over that padded box (x fastest, component-major).  Level 0 arrays are
- * the ordinary full-grid arrays.
+ * Block-structured refinement (Sec. 2.2): patch 0 is the whole box (the base
+ * level); patch a >= 1 refines its parent patch (parent[a] < a) by 2 on one node
+ * box [lo, hi] given in the node indices of its level (level[a] = level of the
+ * parent + 1; even corners, nested one parent cell inside the parent's box unless
+ * on the domain boundary).  A level may hold several patches; patches of one
+ * level are disjoint with their padded boxes apart (at least two coarse cells
+ * between them), so no node of one is a ghost or padding node of another.  Patch a
+ * is stored on its box grown by one padding node on every side: nodes [lo-1, hi+1],
+ * cells [lo-1, hi]; arrays are packed over that padded box (x fastest,
+ * component-major).  Patch 0 arrays are the ordinary full-grid arrays.
  *
  * Composite problem (reflux-free reading of Sec. 2.2):
- *  - a patch node is OWNED by its level when on every axis it is inside the box or
+ *  - a patch node is OWNED by its patch when on every axis it is inside the box or
  *    on a box face that lies on the domain boundary; owned nodes obey the fine
  *    equation (K_a u_a)_n = f_a(n);
  *  - the other box nodes (interface) and the padding nodes are GHOSTS, filled from
- *    level a-1 by (bi/tri)linear interpolation (coincident nodes copy);
- *  - a level a-1 node coinciding with a level-a node of the box region (owned or
- *    itself covered by level a+1) is COVERED: its value is the injected value of
- *    the finest level whose region contains the point, and it carries no
- *    equation; so every point is owned by exactly one level.  The other level a-1
- *    nodes obey the coarse equation with covered neighbours injected;
- *  - coarse cells inside the box hold the mean of their 2^d fine cells; padding
- *    cells beyond a domain face are not part of the body (their psi is ignored).
+ *    the parent by (bi/tri)linear interpolation (coincident nodes copy);
+ *  - a parent node coinciding with a node of a child's box region (owned there or
+ *    itself covered by a grandchild) is COVERED: its value is the injected value of
+ *    the finest patch whose region contains the point, and it carries no equation;
+ *    so every point is owned by exactly one patch.  The other parent nodes obey the
+ *    coarse equation with covered neighbours injected;
+ *  - coarse cells inside a child's box hold the mean of their 2^d fine cells;
+ *    padding cells beyond a domain face are not part of the body (psi ignored).
  * The padding layer gives every interface node a complete fine stencil, which
  * the multigrid restriction uses so that it is the same full weighting everywhere.
+ * Functions taking "level a" below take a patch index.
  */
 typedef struct {
     orc_problem base;
-    int nlev;                   /* 1 + number of patch levels (<= 8) */
-    int lo[8][3], hi[8][3];     /* [a] for a >= 1 */
+    int nlev;                   /* number of patches including the base (<= 16) */
+    int lo[16][3], hi[16][3];   /* [a] for a >= 1, in level[a] node indices */
+    int level[16];              /* refinement level of patch a (0 for a = 0) */
+    int parent[16];             /* parent patch of a >= 1 (< a); -1 for a = 0 */
 } orc_amr;
 
 /* Problem (grid, h, moduli, Dirichlet faces) of the padded patch grid of level a. */
