@@ -45,12 +45,15 @@ AMR_WORKLOADS = {
     "voids_amr_2d": lambda: W.voids_amr(2, 129, 3),
     # 3D refinement: 129^3 base + 2 levels around 16 spherical voids, triaxial loading
     "voids_amr_3d": lambda: W.voids_amr(3, 129, 2, count=16, rmin=0.04, rmax=0.12),
+    # several patches per level from tagging and clustering on the host
+    "voids_amr_2d_clustered": lambda: W.voids_amr(2, 129, 3, clustered=True),
+    "voids_amr_3d_clustered": lambda: W.voids_amr(3, 129, 2, count=8, rmin=0.04, rmax=0.08, clustered=True),
 }
 
 
 def amr_unknowns(wk):
-    """Composite unknowns: nodes owned by each level (in its box region and not
-    covered by the next level) times the dimension."""
+    """Composite unknowns: nodes owned by each patch (in its box region and not
+    covered by one of its children) times the dimension."""
     def region(a, ax, lo, hi, N, even=False):
         if a == 0:
             return (N + 1) // 2 if even else N
@@ -58,20 +61,23 @@ def amr_unknowns(wk):
         inner = len(range(lo + step, hi, step))
         return inner + (lo == 0) + (hi == N - 1)
     total = 0
-    nl = len(wk.boxes) + 1
-    for a in range(nl):
+    npatch = len(wk.boxes)
+    for a in range(npatch + 1):
         N = wk.level_N(a)
         own = 1
         for ax in range(wk.dim):
             lo, hi = (wk.boxes[a - 1][0][ax], wk.boxes[a - 1][1][ax]) if a else (0, N[ax] - 1)
             own *= region(a, ax, lo, hi, N[ax])
         cov = 0
-        if a + 1 < nl:
-            Nc = wk.level_N(a + 1)
-            cov = 1
+        for c in range(1, npatch + 1):
+            if wk.parent(c) != a:
+                continue
+            Nc = wk.level_N(c)
+            cc = 1
             for ax in range(wk.dim):
-                lo, hi = wk.boxes[a][0][ax], wk.boxes[a][1][ax]
-                cov *= region(a + 1, ax, lo, hi, Nc[ax], even=True)
+                lo, hi = wk.boxes[c - 1][0][ax], wk.boxes[c - 1][1][ax]
+                cc *= region(c, ax, lo, hi, Nc[ax], even=True)
+            cov += cc
         total += (own - cov) * wk.dim
     return total
 
@@ -661,7 +667,9 @@ def run_amr(args, rank, world, local_rank):
                 "vs_baseline": None, "dtype": "f32+f64" if precision == "mixed" else "f64",
                 "data": "synthetic (seeded voids)",
                 "config": {"workload": f"{wk.name} base {'x'.join(str(v) for v in wk.n[:wk.dim])} + "
-                                       f"{len(wk.boxes)} levels", "boxes": [list(map(list, b)) for b in wk.boxes],
+                                       f"{max(wk.level(a) for a in range(1, len(wk.boxes) + 1))} levels, "
+                                       f"{len(wk.boxes)} patches",
+                           "boxes": [[list(b[0]), list(b[1])] + ([b[2]] if len(b) > 2 else []) for b in wk.boxes],
                            "composite_unknowns": unknowns, "precision": precision, "tol": 1e-10,
                            "smoother": wk.smoother, "omega": wk.omega,
                            "fp32_cycles_per_fp64_residual": opts["inner_cycles"] if precision == "mixed" else None,

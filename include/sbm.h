@@ -322,38 +322,51 @@ sbm_status sbm_time_kernel(sbm_grid grid, int which, int reps, int flush_l2, dou
                            double *bytes_per_launch, double *flops_per_launch);
 
 /* ---- block-structured refinement (Sec. 2.2) ----
- * A grid may carry up to 8 refinement patches, level a refining level a-1 by 2
- * on one node box.  The composite problem: a patch node inside the box (or on a
- * box face lying on the domain boundary) obeys the fine equation; the parent node
- * under it is covered (it takes the injected fine value); the patch's other nodes
- * (its faces inside the domain, and one layer of padding nodes around the box) are
- * ghosts interpolated from the parent; parent cells under the patch hold the mean
- * of their fine cells (Sec. 2.4).  Every fine stencil of an owned node and every
- * full-weighting stencil of a covered node is complete, so no coarse/fine flux
- * correction ("reflux") is applied.  Patch arrays cover the box grown by one
- * padding node per side: nodes [lo-1, hi+1], cells [lo-1, hi], packed x fastest,
- * component-major; values at padding nodes are outputs only. */
+ * A grid may carry up to 64 refinement patches.  A patch of level L refines one
+ * patch of level L-1 (its parent; the base grid for L = 1) by 2 on one node box; a
+ * level may hold several patches (at most 8 children per parent), whose boxes are
+ * at least two parent cells apart.  Patches are numbered 1, 2, ... in the order they
+ * are added, every parent before its children.  The composite problem: a patch node
+ * inside the box (or on a box face lying on the domain boundary) obeys the fine
+ * equation; the parent node under it is covered (it takes the injected fine value);
+ * the patch's other nodes (its faces inside the domain, and one layer of padding
+ * nodes around the box) are ghosts interpolated from the parent; parent cells under
+ * the patch hold the mean of their fine cells (Sec. 2.4).  Every fine stencil of an
+ * owned node and every full-weighting stencil of a covered node is complete, so no
+ * coarse/fine flux correction ("reflux") is applied.  Patch arrays cover the box
+ * grown by one padding node per side: nodes [lo-1, hi+1], cells [lo-1, hi], packed x
+ * fastest, component-major; values at padding nodes are outputs only.  Below, a
+ * "patch a" argument is that numbering (a = 0: the base grid). */
 typedef struct {
     int lo[3], hi[3];      /* node box in the new level's indices; even corners; 2D: lo[2] = hi[2] = 0 */
 } sbm_box;
 
-/* Append patch level a = (patches so far) + 1.  The box must lie inside the parent
- * patch with at least one parent cell to spare on every side that is not on the
- * domain boundary.  Allocates the patch storage; SBM_ERR_ARG on a bad box. */
+/* Add a patch of refinement level `level` (1 .. deepest existing level + 1) on `box`
+ * (node indices of that level).  Its parent is the one patch of level-1 (the base
+ * grid for level 1) that contains the box with at least one parent cell to spare on
+ * every side not on the domain boundary; the box must be at least two parent cells
+ * (four nodes) apart from every other patch of its level.  *index (may be NULL)
+ * receives the new patch number.  Allocates the patch storage.  SBM_ERR_ARG on a bad
+ * box (odd corners, outside the level, thinner than 2, no unique parent, too close to
+ * a sibling, a ninth child, a 65th patch), SBM_ERR_OOM when the storage cannot
+ * be allocated (nothing is kept). */
+sbm_status sbm_amr_add_box(sbm_grid grid, int level, const sbm_box *box, int *index);
+/* sbm_amr_add_box at one level deeper than the deepest patch so far (level 1 on a
+ * grid without patches): the one-patch-per-level hierarchy, patch a at level a. */
 sbm_status sbm_amr_add_level(sbm_grid grid, const sbm_box *box);
-/* psi of patch level a (device, FP64) on the cells of the padded box, floored at
- * psi_min.  Covered parent cells are replaced by fine means at the next solve. */
+/* psi of patch a (device, FP64) on the cells of the padded box, floored at psi_min.
+ * Covered parent cells are replaced by fine means at the next solve. */
 sbm_status sbm_amr_set_psi(sbm_grid grid, int a, const double *psi_cells, double psi_min);
-/* Right-hand side of patch level a (device, FP64, padded-box nodes). */
+/* Right-hand side of patch a (device, FP64, padded-box nodes). */
 sbm_status sbm_amr_set_source(sbm_grid grid, int a, const double *f_nodes);
-/* Composite solve.  u[0]: base level nodes (packed, device); u[a], a >= 1: padded
+/* Composite solve.  u[0]: base grid nodes (packed, device); u[a], a >= 1: padded
  * box nodes of patch a (device).  In: initial guess with the Dirichlet values (the
  * face values of sbm_set_bc are written on the base level; patch Dirichlet values
  * are taken from u[a]).  Out: the composite solution with ghosts filled.  Each
- * cycle: FP64 composite residual; patches top-down (smoothing of the correction,
- * full-weighting of its residual onto the covered parent nodes); the base
- * multigrid V-cycle; patches bottom-up (parent correction prolongated and ghosts
- * filled, smoothing); u += e on owned dofs.  SBM_MIXED runs the cycle in FP32, and
+ * cycle: FP64 composite residual; patches finest first (smoothing of the
+ * correction, full-weighting of its residual onto the parent nodes it covers); the
+ * base multigrid V-cycle; patches coarsest first (parent correction prolongated and
+ * ghosts filled, smoothing); u += e on owned dofs.  SBM_MIXED runs the cycle in FP32, and
  * opts->inner_cycles of them per FP64 residual: between two of them the FP32
  * right-hand side becomes r - A e (the correction injected into covered parents,
  * every level's residual of it, owned free rows kept); opts->inner_rtol is ignored

@@ -357,8 +357,8 @@ def simp(rho, psi_min: float, q: float = 3.0):
 # ------------------------------------------------------------------ BSAMR
 
 class _Amr(C.Structure):
-    _fields_ = [("base", _Problem), ("nlev", C.c_int), ("lo", (C.c_int * 3) * 16), ("hi", (C.c_int * 3) * 16),
-                ("level", C.c_int * 16), ("parent", C.c_int * 16)]
+    _fields_ = [("base", _Problem), ("nlev", C.c_int), ("lo", (C.c_int * 3) * 65), ("hi", (C.c_int * 3) * 65),
+                ("level", C.c_int * 65), ("parent", C.c_int * 65)]
 
 
 _AMR_SIGS = {

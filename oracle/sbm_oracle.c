@@ -1112,8 +1112,8 @@ int orc_amr_solve(const orc_amr *A, double *const *psi, double *const *f, double
                   const orc_amr_opts *o, double *hist, int *cycles)
 {
     const int L = A->nlev, d = A->base.dim;
-    double *r[16], *e[16], *rhs[16], *res[16], *pa[16];
-    long N[16];
+    double *r[65], *e[65], *rhs[65], *res[65], *pa[65];
+    long N[65];
     for (int a = 0; a < L; ++a) {
         orc_problem P;
         orc_amr_level_problem(A, a, &P);

@@ -188,10 +188,10 @@ void orc_dJdpsi(const orc_problem *P, const double *u, const double *lam, double
  */
 typedef struct {
     orc_problem base;
-    int nlev;                   /* number of patches including the base (<= 16) */
-    int lo[16][3], hi[16][3];   /* [a] for a >= 1, in level[a] node indices */
-    int level[16];              /* refinement level of patch a (0 for a = 0) */
-    int parent[16];             /* parent patch of a >= 1 (< a); -1 for a = 0 */
+    int nlev;                   /* number of patches including the base (<= 65) */
+    int lo[65][3], hi[65][3];   /* [a] for a >= 1, in level[a] node indices */
+    int level[65];              /* refinement level of patch a (0 for a = 0) */
+    int parent[65];             /* parent patch of a >= 1 (< a); -1 for a = 0 */
 } orc_amr;
 
 /* Problem (grid, h, moduli, Dirichlet faces) of the padded patch grid of level a. */

@@ -176,11 +176,21 @@ class Grid:
 
     # -- block-structured refinement
     def amr_add_level(self, lo, hi):
+        """A patch one level deeper than the deepest so far; returns its number."""
+        deepest = max([lv for _, _, lv, _ in getattr(self, "patches", [])], default=0)
+        return self.amr_add_box(deepest + 1, lo, hi)
+
+    def amr_add_box(self, level, lo, hi):
+        """A patch of refinement level ``level`` on the node box [lo, hi]; returns its
+        number (the parent is found by the library)."""
         b = _capi.sbm_box()
         b.lo[:] = (list(lo) + [0, 0, 0])[:3]
         b.hi[:] = (list(hi) + [0, 0, 0])[:3]
-        self._check(lib().sbm_amr_add_level(self._h, C.byref(b)))
+        idx = C.c_int(0)
+        self._check(lib().sbm_amr_add_box(self._h, level, C.byref(b), C.byref(idx)))
         self.boxes = getattr(self, "boxes", []) + [(tuple(b.lo), tuple(b.hi))]
+        self.patches = getattr(self, "patches", []) + [(tuple(b.lo), tuple(b.hi), level, idx.value)]
+        return idx.value
 
     def amr_set_psi(self, a: int, psi: torch.Tensor, psi_min: float):
         self._check(lib().sbm_amr_set_psi(self._h, a, _ptr(psi), psi_min))

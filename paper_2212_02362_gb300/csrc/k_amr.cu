@@ -5,15 +5,19 @@
 // residual onto the covered parent nodes, prolongation of a parent correction
 // into a patch, the owned-dof update and the composite norm.
 //
-// A patch of level a refines level a-1 by 2 on one node box [lo, hi] (level-a
-// indices).  Its storage is the box grown by one padding node per side; `AmrInfo`
-// carries the global extents, the box, the storage origin, the child box and the
-// domain Dirichlet faces, from which every node's role follows:
+// A patch refines its parent (the base level or a patch one level coarser) by 2 on
+// one node box [lo, hi] (indices of its level); a level may hold several patches,
+// disjoint and apart.  A patch's storage is the box grown by one padding node per
+// side; `AmrInfo` carries the global extents, the box, the storage origin, the
+// boxes of the patch's children and the domain Dirichlet faces, from which every
+// node's role follows:
 //   owned   - inside the box on every axis, or on a box face lying on the domain
-//             boundary, and not covered by an owned node of the child patch;
-//   covered - coincident with an owned node of the child: carries the injected
+//             boundary, and not covered by a child;
+//   covered - coincident with a node of a child's box region: carries the injected
 //             fine value and no equation of its own;
-//   ghost   - the other storage nodes: interpolated from the parent level.
+//   ghost   - the other storage nodes: interpolated from the parent.
+// Kernels that move data between one child and its parent take both infos and
+// test membership in that child's own box.
 #include "sbm_common.cuh"
 
 namespace sbm {
@@ -34,13 +38,13 @@ __host__ __device__ __forceinline__ bool axes_owned(const AmrInfo &L, const int 
     return true;
 }
 
-// child-level coordinates g2 owned by the child's axes rule
-__host__ __device__ __forceinline__ bool child_axes_owned(const AmrInfo &L, const int g2[3])
+// child-level coordinates g2 in the box region of child c (the child's axes rule)
+__host__ __device__ __forceinline__ bool child_axes_owned(const AmrInfo &L, int c, const int g2[3])
 {
     for (int ax = 0; ax < L.dim; ++ax) {
         const int Nc = 2 * (L.N[ax] - 1) + 1;
-        const bool in = (g2[ax] > L.clo[ax] && g2[ax] < L.chi[ax]) || (g2[ax] == L.clo[ax] && L.clo[ax] == 0) ||
-                        (g2[ax] == L.chi[ax] && L.chi[ax] == Nc - 1);
+        const int lo = L.clo[c][ax], hi = L.chi[c][ax];
+        const bool in = (g2[ax] > lo && g2[ax] < hi) || (g2[ax] == lo && lo == 0) || (g2[ax] == hi && hi == Nc - 1);
         if (!in) return false;
     }
     return true;
@@ -48,9 +52,17 @@ __host__ __device__ __forceinline__ bool child_axes_owned(const AmrInfo &L, cons
 
 __host__ __device__ __forceinline__ bool covered(const AmrInfo &L, const int g[3])
 {
-    if (!L.has_child) return false;
     const int g2[3] = {2 * g[0], 2 * g[1], L.dim == 3 ? 2 * g[2] : 0};
-    return child_axes_owned(L, g2);
+    for (int c = 0; c < L.nchild; ++c)
+        if (child_axes_owned(L, c, g2)) return true;
+    return false;
+}
+
+// parent node G coincides with a node of the box region of the child described by Lc
+__host__ __device__ __forceinline__ bool covered_by(const AmrInfo &Lc, const int G[3])
+{
+    const int g2[3] = {2 * G[0], 2 * G[1], Lc.dim == 3 ? 2 * G[2] : 0};
+    return axes_owned(Lc, g2);
 }
 
 __host__ __device__ __forceinline__ bool owned(const AmrInfo &L, const int g[3])
@@ -181,14 +193,14 @@ __global__ void k_amr_ghost(const Geom sc, const AmrInfo Lc, const Geom sp, cons
     }
 }
 
-// rhs_parent at covered parent nodes <- full weighting of the child residual
-// (the child nodes of the stencil are all inside the child box).
+// rhs_parent at the parent nodes covered by this child <- full weighting of the
+// child residual (the child nodes of the stencil are all inside the child box).
 template <typename T>
 __global__ void k_amr_restrict(const Geom sc, const AmrInfo Lc, const Geom sp, const AmrInfo Lp, const T *rc, T *rhsp)
 {
     int i, j, k, g[3];
     if (!thread_node(sp, Lp, i, j, k, g)) return;
-    if (!covered(Lp, g)) return;
+    if (!covered_by(Lc, g)) return;
     const bool d3 = Lp.dim == 3;
     const T w[3] = {T(0.5), T(1), T(0.5)};
     const T scale = d3 ? T(0.125) : T(0.25);
@@ -353,7 +365,8 @@ __global__ void k_amr_scaleW(const Geom s, const AmrInfo L, const double *psi, d
 }
 
 // Transpose of the full-weighting restriction onto the covered parent nodes:
-// child node g collects scale * w(g - 2G) * rp(G) from the covered parents G with
+// child node g collects scale * w(g - 2G) * rp(G) from the parents G covered by
+// this child with
 // |g - 2G| <= 1 (parents on a Dirichlet face of the component contribute 0).
 __global__ void k_amr_restrictT(const Geom sc, const AmrInfo Lc, const Geom sp, const AmrInfo Lp, const double *rp,
                                 double *rc)
@@ -372,7 +385,7 @@ __global__ void k_amr_restrictT(const Geom sc, const AmrInfo Lc, const Geom sp, 
                     const int t[3] = {g[0] + di, g[1] + dj, d3 ? g[2] + dk : 0};
                     if ((t[0] & 1) || (t[1] & 1) || (t[2] & 1)) continue;
                     const int G[3] = {t[0] / 2, t[1] / 2, t[2] / 2};
-                    if (!covered(Lp, G) || domain_dirichlet(Lp, G, p)) continue;
+                    if (!covered_by(Lc, G) || domain_dirichlet(Lp, G, p)) continue;
                     const int l[3] = {G[0] - Lp.org[0], G[1] - Lp.org[1], G[2] - Lp.org[2]};
                     if (l[0] < 0 || l[1] < 0 || l[2] < 0 || l[0] >= sp.nx || l[1] >= sp.ny || l[2] >= sp.nz) continue;
                     const double w = (di ? 0.5 : 1.0) * (dj ? 0.5 : 1.0) * (dk ? 0.5 : 1.0);

@@ -58,6 +58,8 @@ struct Level {
 // level-a indices, stored with one padding node per side.
 struct Patch {
     int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+    int level = 0;            // refinement level (1 = children of the base)
+    int parent = 0;           // parent patch index (0 = the base level, else 1 .. npatch)
     Geom s{};                 // padded storage (no Dirichlet faces)
     Geom v{};                 // view of the box: interface faces fixed, domain faces as the domain
     long long voff = 0;       // element offset of the view origin in the storage
@@ -129,13 +131,13 @@ struct sbm_grid_s {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     std::string err;
     int npatch = 0;
-    Patch P[8];
+    Patch P[kMaxPatch];
     AmrInfo base_info{};
     bool amr_psi_dirty = false;
     double *amr_part = nullptr;   // partial sums of the composite norm
     long long amr_npart = 0;
     double *amr_u0 = nullptr, *amr_r0 = nullptr;   // composite solution / residual on the base level
-    double *adj[9][9] = {};                            // adjoint Krylov vectors [vector][level]
+    double *adj[9][kMaxPatch + 1] = {};                // adjoint iteration vectors [vector][patch]
     double *top = nullptr;      // topology optimisation: psi, eta scratch, partial sums, scalars
 };
 
@@ -700,7 +702,7 @@ void amr_refresh_infos(sbm_grid G)
         L = AmrInfo{};
         L.dim = d;
         for (int ax = 0; ax < 3; ++ax) {
-            L.N[ax] = level_N(G, a, ax);
+            L.N[ax] = level_N(G, Pt.level, ax);
             L.lo[ax] = Pt.lo[ax];
             L.hi[ax] = Pt.hi[ax];
             L.org[ax] = ax < d ? Pt.lo[ax] - 1 : 0;
@@ -717,16 +719,23 @@ void amr_refresh_infos(sbm_grid G)
             }
         for (int p = 0; p < 3; ++p) Pt.v.dm[p] = vdm[p];
     }
-    for (int a = 0; a < G->npatch; ++a) {
-        AmrInfo &L = a == 0 ? G->base_info : G->P[a - 1].info;
-        const Patch &C = G->P[a];
-        L.has_child = 1;
+    for (int c = 1; c <= G->npatch; ++c) {
+        const Patch &C = G->P[c - 1];
+        AmrInfo &L = C.parent == 0 ? G->base_info : G->P[C.parent - 1].info;
         for (int ax = 0; ax < 3; ++ax) {
-            L.clo[ax] = C.lo[ax];
-            L.chi[ax] = C.hi[ax];
+            L.clo[L.nchild][ax] = C.lo[ax];
+            L.chi[L.nchild][ax] = C.hi[ax];
         }
+        ++L.nchild;
     }
 }
+
+// Patch a's geometry and role info (a = 0: the base level), its parent, its FP64
+// solution array and, inside a correction cycle, its correction and right-hand side.
+const Geom &amr_geom(sbm_grid G, int a) { return a == 0 ? G->L[G->nl - 1].g : G->P[a - 1].s; }
+const AmrInfo &amr_info(sbm_grid G, int a) { return a == 0 ? G->base_info : G->P[a - 1].info; }
+int amr_parent(sbm_grid G, int a) { return G->P[a - 1].parent; }
+double *amr_u64(sbm_grid G, int a) { return a == 0 ? G->amr_u0 : G->P[a - 1].u64; }
 
 template <typename T> struct PP;
 template <> struct PP<double> {
@@ -745,6 +754,20 @@ template <> struct PP<float> {
     static const Coef<float> &c(Patch &P) { return P.c32; }
     static const float *Ke(Patch &P) { return P.Ke32; }
 };
+
+template <typename T>
+T *amr_rhs(sbm_grid G, int a)
+{
+    Level &B = G->L[G->nl - 1];
+    if (a > 0) return PP<T>::rhs(G->P[a - 1]);
+    return std::is_same<T, double>::value ? (T *)B.df : (T *)B.sf;
+}
+
+template <typename T>
+T *amr_e(sbm_grid G, int a, const int *cur, int cb)
+{
+    return a == 0 ? P<T>::u(G->L[G->nl - 1], cb) : PP<T>::e(G->P[a - 1], cur[a]);
+}
 
 template <typename T>
 cudaError_t sweep_view(sbm_grid G, Patch &Pt, int mode, const T *u, const T *f, T *out, double omega)
@@ -801,16 +824,16 @@ size_t patch_bytes(const Patch &Pt, size_t elem) { return (size_t)Pt.s.dim * Pt.
 // Injection into covered parents (finest first), then ghost fill (coarsest first).
 cudaError_t amr_fill(sbm_grid G)
 {
-    Level &B = G->L[G->nl - 1];
+    // patches are numbered parents first, so descending order is finest first
     for (int a = G->npatch; a >= 1; --a) {
         Patch &Pt = G->P[a - 1];
-        if (a == 1) CKE(launch_amr_inject(Pt.s, Pt.info, B.g, G->base_info, Pt.u64, G->amr_u0, G->st));
-        else CKE(launch_amr_inject(Pt.s, Pt.info, G->P[a - 2].s, G->P[a - 2].info, Pt.u64, G->P[a - 2].u64, G->st));
+        const int pa = Pt.parent;
+        CKE(launch_amr_inject(Pt.s, Pt.info, amr_geom(G, pa), amr_info(G, pa), Pt.u64, amr_u64(G, pa), G->st));
     }
     for (int a = 1; a <= G->npatch; ++a) {
         Patch &Pt = G->P[a - 1];
-        if (a == 1) CKE(launch_amr_ghost<double>(Pt.s, Pt.info, B.g, G->base_info, Pt.u64, G->amr_u0, 0, G->st));
-        else CKE(launch_amr_ghost<double>(Pt.s, Pt.info, G->P[a - 2].s, G->P[a - 2].info, Pt.u64, G->P[a - 2].u64, 0, G->st));
+        const int pa = Pt.parent;
+        CKE(launch_amr_ghost<double>(Pt.s, Pt.info, amr_geom(G, pa), amr_info(G, pa), Pt.u64, amr_u64(G, pa), 0, G->st));
     }
     return cudaSuccess;
 }
@@ -849,7 +872,8 @@ cudaError_t amr_cycle(sbm_grid G, const sbm_opts &o, double *const *target = nul
 {
     const int A = G->npatch;
     Level &B = G->L[G->nl - 1];
-    int cur[9] = {0};
+    int cur[kMaxPatch + 1] = {0};
+    // finest first (every child before its parent)
     for (int a = A; a >= 1; --a) {
         Patch &Pt = G->P[a - 1];
         CKE(cudaMemsetAsync(PP<T>::e(Pt, 0), 0, patch_bytes(Pt, sizeof(T)), G->st));
@@ -857,25 +881,20 @@ cudaError_t amr_cycle(sbm_grid G, const sbm_opts &o, double *const *target = nul
         cur[a] = 0;
         CKE(patch_smooth<T>(G, Pt, cur[a], o, o.nu1, false));
         CKE(sweep_view<T>(G, Pt, kResidual, PP<T>::e(Pt, cur[a]), PP<T>::rhs(Pt), PP<T>::res(Pt), 0.0));
-        if (a == 1) {
-            T *base_rhs = std::is_same<T, double>::value ? (T *)B.df : (T *)B.sf;
-            CKE(launch_amr_restrict<T>(Pt.s, Pt.info, B.g, G->base_info, PP<T>::res(Pt), base_rhs, G->st));
-        } else {
-            Patch &Pp = G->P[a - 2];
-            CKE(launch_amr_restrict<T>(Pt.s, Pt.info, Pp.s, Pp.info, PP<T>::res(Pt), PP<T>::rhs(Pp), G->st));
-        }
+        const int pa = Pt.parent;
+        CKE(launch_amr_restrict<T>(Pt.s, Pt.info, amr_geom(G, pa), amr_info(G, pa), PP<T>::res(Pt), amr_rhs<T>(G, pa),
+                                   G->st));
     }
     T *base_rhs = std::is_same<T, double>::value ? (T *)B.df : (T *)B.sf;
     CKE(cudaMemsetAsync(P<T>::u(B, 0), 0, level_bytes(B, sizeof(T)), G->st));
     int cb = 0;
     CKE(vcycle<T>(G, G->nl - 1, cb, o, base_rhs));
+    // coarsest first (every parent's final correction before its children)
     for (int a = 1; a <= A; ++a) {
         Patch &Pt = G->P[a - 1];
-        if (a == 1)
-            CKE(launch_amr_ghost<T>(Pt.s, Pt.info, B.g, G->base_info, PP<T>::e(Pt, cur[a]), P<T>::u(B, cb), 1, G->st));
-        else
-            CKE(launch_amr_ghost<T>(Pt.s, Pt.info, G->P[a - 2].s, G->P[a - 2].info, PP<T>::e(Pt, cur[a]),
-                                    PP<T>::e(G->P[a - 2], cur[a - 1]), 1, G->st));
+        const int pa = Pt.parent;
+        CKE(launch_amr_ghost<T>(Pt.s, Pt.info, amr_geom(G, pa), amr_info(G, pa), PP<T>::e(Pt, cur[a]),
+                                amr_e<T>(G, pa, cur, cb), 1, G->st));
         CKE(patch_smooth<T>(G, Pt, cur[a], o, o.nu2, true));
     }
     // u += e on owned free dofs (target: the composite solution, or other level arrays)
@@ -904,11 +923,9 @@ cudaError_t amr_inner_residual(sbm_grid G, const int *cur, int cb)
     Level &B = G->L[G->nl - 1];
     for (int a = A; a >= 1; --a) {
         Patch &Pt = G->P[a - 1];
-        if (a == 1)
-            CKE(launch_amr_inject<float>(Pt.s, Pt.info, B.g, G->base_info, Pt.se[cur[a]], B.su[cb], G->st));
-        else
-            CKE(launch_amr_inject<float>(Pt.s, Pt.info, G->P[a - 2].s, G->P[a - 2].info, Pt.se[cur[a]],
-                                         G->P[a - 2].se[cur[a - 1]], G->st));
+        const int pa = Pt.parent;
+        CKE(launch_amr_inject<float>(Pt.s, Pt.info, amr_geom(G, pa), amr_info(G, pa), Pt.se[cur[a]],
+                                     amr_e<float>(G, pa, cur, cb), G->st));
     }
     CKE(sweep<float>(G, G->nl - 1, kResidual, B.su[cb], B.sf, B.sr, nullptr, 0.0));
     CKE(launch_amr_mask_to<float>(B.g, G->base_info, B.sr, B.sf, G->st));
@@ -928,8 +945,6 @@ cudaError_t amr_inner_residual(sbm_grid G, const int *cur, int cb)
 // (transposed interpolation, finest first) and the covered values to the finer
 // level (transposed injection, coarsest first), then the owned free rows are kept.
 
-const Geom &amr_geom(sbm_grid G, int a) { return a == 0 ? G->L[G->nl - 1].g : G->P[a - 1].s; }
-const AmrInfo &amr_info(sbm_grid G, int a) { return a == 0 ? G->base_info : G->P[a - 1].info; }
 size_t amr_vec_len(sbm_grid G, int a) { const Geom &g = amr_geom(G, a); return (size_t)g.dim * g.cs; }
 
 cudaError_t cv_zero(sbm_grid G, double *const *x)
@@ -963,12 +978,16 @@ cudaError_t amr_apply_T(sbm_grid G, double *const *x, double *const *out)
     CKE(cv_zero(G, out));
     CKE(sweep<double>(G, G->nl - 1, kApply, x[0], nullptr, out[0], nullptr, 0.0));
     for (int a = 1; a <= A; ++a) CKE(sweep_view<double>(G, G->P[a - 1], kApply, x[a], nullptr, out[a], 0.0));
-    for (int a = A; a >= 1; --a)
-        CKE(launch_amr_ghostT(amr_geom(G, a), amr_info(G, a), amr_geom(G, a - 1), amr_info(G, a - 1), out[a],
-                               out[a - 1], 0, G->st));
-    for (int a = 0; a < A; ++a)
-        CKE(launch_amr_injectT(amr_geom(G, a + 1), amr_info(G, a + 1), amr_geom(G, a), amr_info(G, a), out[a],
-                               out[a + 1], G->st));
+    for (int a = A; a >= 1; --a) {
+        const int pa = amr_parent(G, a);
+        CKE(launch_amr_ghostT(amr_geom(G, a), amr_info(G, a), amr_geom(G, pa), amr_info(G, pa), out[a], out[pa], 0,
+                              G->st));
+    }
+    for (int c = 1; c <= A; ++c) {
+        const int pa = amr_parent(G, c);
+        CKE(launch_amr_injectT(amr_geom(G, c), amr_info(G, c), amr_geom(G, pa), amr_info(G, pa), out[pa], out[c],
+                               G->st));
+    }
     for (int a = 0; a <= A; ++a) CKE(launch_amr_mask(amr_geom(G, a), amr_info(G, a), out[a], G->st));
     return cudaSuccess;
 }
@@ -1020,8 +1039,9 @@ cudaError_t amr_precondT(sbm_grid G, const sbm_opts &o, double *const *y, double
     CKE(cv_lincomb(G, 1.0, y, 0.0, y, 0.0, nullptr, EB));
     for (int a = A; a >= 1; --a) {
         for (int s_ = 0; s_ < o.nu2; ++s_) CKE(patch_jacobiT(G, a, o, EB[a], z[a], T1[a], T2[a]));
-        CKE(launch_amr_ghostT(amr_geom(G, a), amr_info(G, a), amr_geom(G, a - 1), amr_info(G, a - 1), EB[a], EB[a - 1],
-                              1, G->st));
+        const int pa = amr_parent(G, a);
+        CKE(launch_amr_ghostT(amr_geom(G, a), amr_info(G, a), amr_geom(G, pa), amr_info(G, pa), EB[a], EB[pa], 1,
+                              G->st));
         CKE(launch_amr_mask_solved(amr_geom(G, a), amr_info(G, a), EB[a], G->st));
     }
     // base: rhs adjoint = V_0 (adjoint of its output); the FP32 V-cycle on mixed grids
@@ -1040,8 +1060,9 @@ cudaError_t amr_precondT(sbm_grid G, const sbm_opts &o, double *const *y, double
     }
     for (int a = 1; a <= A; ++a) {
         // restriction onto the covered parent nodes, transposed: residual adjoint
-        CKE(launch_amr_restrictT(amr_geom(G, a), amr_info(G, a), amr_geom(G, a - 1), amr_info(G, a - 1), z[a - 1],
-                                 T1[a], G->st));
+        const int pa = amr_parent(G, a);
+        CKE(launch_amr_restrictT(amr_geom(G, a), amr_info(G, a), amr_geom(G, pa), amr_info(G, pa), z[pa], T1[a],
+                                 G->st));
         CKE(launch_amr_mask_solved(amr_geom(G, a), amr_info(G, a), T1[a], G->st));
         // residual r = rhs - K e (solved dofs): rhs_adj += res_adj, e_adj -= K res_adj
         const size_t n = amr_vec_len(G, a);
@@ -1100,8 +1121,9 @@ sbm_status amr_prepare(sbm_grid G)
         Level &B = G->L[G->nl - 1];
         for (int a = G->npatch; a >= 1; --a) {
             Patch &Pt = G->P[a - 1];
-            if (a == 1) CK(launch_amr_coarsen_psi(Pt.s, Pt.info, B.g, G->base_info, Pt.psi64, B.psi64, G->st));
-            else CK(launch_amr_coarsen_psi(Pt.s, Pt.info, G->P[a - 2].s, G->P[a - 2].info, Pt.psi64, G->P[a - 2].psi64, G->st));
+            const int pa = Pt.parent;
+            double *psip = pa == 0 ? B.psi64 : G->P[pa - 1].psi64;
+            CK(launch_amr_coarsen_psi(Pt.s, Pt.info, amr_geom(G, pa), amr_info(G, pa), Pt.psi64, psip, G->st));
         }
         for (int a = 1; a <= G->npatch; ++a) {
             CK(launch_round(G->P[a - 1].s.cs, G->P[a - 1].psi64, G->P[a - 1].psi32, G->st));
@@ -1144,7 +1166,7 @@ sbm_status amr_run(sbm_grid G, const sbm_opts &o, sbm_info *info)
     int ncycles = 0;
     while (status == SBM_ERR_NOCONV && cyc < o.max_cycles) {
         for (int it = 0; it < inner; ++it) {
-            int cur[9], cb = 0;
+            int cur[kMaxPatch + 1], cb = 0;
             CK(amr_cycle<T>(G, o, nullptr, cur, &cb));
             ++ncycles;
             if constexpr (std::is_same<T, float>::value)
@@ -2177,34 +2199,77 @@ static sbm_status patch_alloc(sbm_grid G, int a, Patch &Pt)
     return SBM_OK;
 }
 
-sbm_status sbm_amr_add_level(sbm_grid G, const sbm_box *box)
+// Checks of a new box at `level` (>= 1): even corners inside the level, at least two
+// nodes thick, nested one parent cell inside exactly one patch of level-1 (the base
+// for level 1) unless on the domain boundary, and apart from every patch of the same
+// level (at least two parent cells between the boxes on some axis).  Returns the
+// parent's patch index, or -1 with the grid's error set.
+static int amr_check_box(sbm_grid G, int level, const sbm_box *box)
 {
-    if (!G || !box) return fail(G, SBM_ERR_ARG, "null argument");
-    if (G->npatch >= 8) return fail(G, SBM_ERR_ARG, "at most 8 patch levels");
-    CK(cudaSetDevice(G->dev));
-    const int a = G->npatch + 1, d = G->desc.dim;
-    Patch &Pt = G->P[a - 1];
+    const int d = G->desc.dim;
     for (int ax = 0; ax < 3; ++ax) {
-        const int lo = box->lo[ax], hi = box->hi[ax], N = level_N(G, a, ax);
+        const int lo = box->lo[ax], hi = box->hi[ax], N = level_N(G, level, ax);
         if (ax >= d) {
-            if (lo != 0 || hi != 0) return fail(G, SBM_ERR_ARG, "2D boxes have lo[2] = hi[2] = 0");
+            if (lo != 0 || hi != 0) return fail(G, SBM_ERR_ARG, "2D boxes have lo[2] = hi[2] = 0"), -1;
             continue;
         }
         if ((lo & 1) || (hi & 1) || lo < 0 || hi > N - 1 || hi - lo < 2)
-            return fail(G, SBM_ERR_ARG, "box corners must be even, inside the level and at least 2 apart");
-        if (a > 1) {
-            const Patch &Pp = G->P[a - 2];
-            const int Np = level_N(G, a - 1, ax);
-            const bool lo_ok = (lo == 0 && Pp.lo[ax] == 0) || lo >= 2 * Pp.lo[ax] + 2;
-            const bool hi_ok = (hi == N - 1 && Pp.hi[ax] == Np - 1) || hi <= 2 * Pp.hi[ax] - 2;
-            if (!lo_ok || !hi_ok) return fail(G, SBM_ERR_ARG, "box must lie inside the parent patch by one parent cell");
-        }
+            return fail(G, SBM_ERR_ARG, "box corners must be even, inside the level and at least 2 apart"), -1;
     }
+    int parent = level == 1 ? 0 : -1;
+    if (level > 1) {
+        int found = 0;
+        for (int q = 1; q <= G->npatch; ++q) {
+            const Patch &Pp = G->P[q - 1];
+            if (Pp.level != level - 1) continue;
+            bool inside = true;
+            for (int ax = 0; ax < d; ++ax) {
+                const int lo = box->lo[ax], hi = box->hi[ax], N = level_N(G, level, ax), Np = level_N(G, level - 1, ax);
+                const bool lo_ok = (lo == 0 && Pp.lo[ax] == 0) || lo >= 2 * Pp.lo[ax] + 2;
+                const bool hi_ok = (hi == N - 1 && Pp.hi[ax] == Np - 1) || hi <= 2 * Pp.hi[ax] - 2;
+                inside = inside && lo_ok && hi_ok;
+            }
+            if (inside) {
+                parent = q;
+                ++found;
+            }
+        }
+        if (found != 1) return fail(G, SBM_ERR_ARG, "box must lie inside one patch of the next coarser level by one parent cell"), -1;
+    }
+    for (int q = 1; q <= G->npatch; ++q) {
+        const Patch &Ps = G->P[q - 1];
+        if (Ps.level != level) continue;
+        bool apart = false;
+        for (int ax = 0; ax < d; ++ax)
+            apart = apart || box->lo[ax] >= Ps.hi[ax] + 4 || Ps.lo[ax] >= box->hi[ax] + 4;
+        if (!apart) return fail(G, SBM_ERR_ARG, "boxes of one level must be at least two parent cells apart"), -1;
+    }
+    const AmrInfo &Lp = parent == 0 ? G->base_info : G->P[parent - 1].info;
+    if (Lp.nchild >= kMaxChild) return fail(G, SBM_ERR_ARG, "at most 8 child patches per patch"), -1;
+    return parent;
+}
+
+sbm_status sbm_amr_add_box(sbm_grid G, int level, const sbm_box *box, int *index)
+{
+    if (!G || !box) return fail(G, SBM_ERR_ARG, "null argument");
+    if (G->npatch >= kMaxPatch) return fail(G, SBM_ERR_ARG, "at most 64 patches");
+    int deepest = 0;
+    for (int q = 1; q <= G->npatch; ++q) deepest = std::max(deepest, G->P[q - 1].level);
+    if (level < 1 || level > deepest + 1) return fail(G, SBM_ERR_ARG, "level must be 1 .. (deepest level + 1)");
+    CK(cudaSetDevice(G->dev));
+    amr_refresh_infos(G);
+    const int parent = amr_check_box(G, level, box);
+    if (parent < 0) return SBM_ERR_ARG;
+    const int a = G->npatch + 1, d = G->desc.dim;
+    Patch &Pt = G->P[a - 1];
+    Pt = Patch();
     for (int ax = 0; ax < 3; ++ax) {
         Pt.lo[ax] = box->lo[ax];
         Pt.hi[ax] = box->hi[ax];
     }
-    Pt.h = G->desc.h / (double)(1 << a);
+    Pt.level = level;
+    Pt.parent = parent;
+    Pt.h = G->desc.h / (double)(1 << level);
     Geom &g = Pt.s;
     g.dim = d;
     g.nx = Pt.hi[0] - Pt.lo[0] + 3;
@@ -2228,13 +2293,23 @@ sbm_status sbm_amr_add_level(sbm_grid G, const sbm_box *box)
     }
     G->npatch = a;
     amr_refresh_infos(G);
+    G->amr_psi_dirty = true;
+    if (index) *index = a;
     return SBM_OK;
+}
+
+sbm_status sbm_amr_add_level(sbm_grid G, const sbm_box *box)
+{
+    if (!G) return fail(nullptr, SBM_ERR_ARG, "null grid");
+    int deepest = 0;
+    for (int q = 1; q <= G->npatch; ++q) deepest = std::max(deepest, G->P[q - 1].level);
+    return sbm_amr_add_box(G, deepest + 1, box, nullptr);
 }
 
 sbm_status sbm_amr_set_psi(sbm_grid G, int a, const double *psi, double psi_min)
 {
     if (!G) return fail(nullptr, SBM_ERR_ARG, "null grid");
-    if (a < 1 || a > G->npatch) return fail(G, SBM_ERR_ARG, "patch level out of range");
+    if (a < 1 || a > G->npatch) return fail(G, SBM_ERR_ARG, "patch index out of range");
     if (!is_dev_ptr(psi, G->dev)) return fail(G, SBM_ERR_ARG, "psi is not a device pointer of the grid's device");
     if (!(psi_min > 0.0)) return fail(G, SBM_ERR_ARG, "psi_min must be positive");
     CK(cudaSetDevice(G->dev));
@@ -2252,7 +2327,7 @@ sbm_status sbm_amr_set_psi(sbm_grid G, int a, const double *psi, double psi_min)
 sbm_status sbm_amr_set_source(sbm_grid G, int a, const double *f)
 {
     if (!G) return fail(nullptr, SBM_ERR_ARG, "null grid");
-    if (a < 1 || a > G->npatch) return fail(G, SBM_ERR_ARG, "patch level out of range");
+    if (a < 1 || a > G->npatch) return fail(G, SBM_ERR_ARG, "patch index out of range");
     if (!is_dev_ptr(f, G->dev)) return fail(G, SBM_ERR_ARG, "f is not a device pointer of the grid's device");
     CK(cudaSetDevice(G->dev));
     Patch &Pt = G->P[a - 1];
@@ -2358,9 +2433,11 @@ sbm_status sbm_amr_adjoint(sbm_grid G, double *const *u, double *const *dJdu, do
             CK(launch_amr_dJdpsi(amr_geom(G, a), amr_info(G, a), c, a == 0 ? G->amr_u0 : G->P[a - 1].u64, X[a], T[a],
                                  G->st));
         }
-        for (int a = 0; a < A; ++a)
-            CK(launch_amr_grad_chain(amr_geom(G, a + 1), amr_info(G, a + 1), amr_geom(G, a), amr_info(G, a), T[a],
-                                     T[a + 1], G->st));
+        for (int c = 1; c <= A; ++c) {    // coarse to fine: a parent before its children
+            const int pa = amr_parent(G, c);
+            CK(launch_amr_grad_chain(amr_geom(G, c), amr_info(G, c), amr_geom(G, pa), amr_info(G, pa), T[pa], T[c],
+                                     G->st));
+        }
         for (int a = 0; a <= A; ++a)
             CK(launch_amr_get_cells(amr_geom(G, a), T[a], a == 0 ? G->L[G->nl - 1].psi64 : G->P[a - 1].psi64,
                                     G->psi_min, dJdpsi[a], G->st));

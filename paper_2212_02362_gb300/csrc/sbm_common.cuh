@@ -259,14 +259,16 @@ cudaError_t launch_dJdpsi(const Geom &g, const Coef<double> &c, const double *u,
 // ---- block-structured refinement (k_amr.cu) ---------------------------------
 
 // Roles of the nodes of one refinement level (see k_amr.cu).
+constexpr int kMaxChild = 8;                      // child patches of one patch (or of the base)
+constexpr int kMaxPatch = 64;                     // refinement patches of a grid
 struct AmrInfo {
     int dim;
     int N[3];              // global nodes per axis at this level
     int lo[3], hi[3];      // the patch box (level indices); unused on the base level
     int org[3];            // global index of storage node (0, 0, 0)
     int is_base;
-    int has_child;
-    int clo[3], chi[3];    // child patch box (child-level indices)
+    int nchild;            // child patches (boxes disjoint and apart)
+    int clo[kMaxChild][3], chi[kMaxChild][3];   // their boxes (child-level indices)
     unsigned dm[3];        // Dirichlet faces of the domain, per component
 };
 

@@ -111,7 +111,7 @@ def amr_oracle(wk):
     """The oracle's composite problem for a refinement workload: levels, boxes, psi
     floored at psi_min with the coarse means under the patches."""
     P = oracle.Problem(wk.dim, wk.n, wk.h, *wk.moduli, dirichlet=wk.dirichlet_bits())
-    A = oracle.Amr(P, [(lo[:wk.dim], hi[:wk.dim]) for lo, hi in wk.boxes])
+    A = oracle.Amr(P, [(b[0][:wk.dim], b[1][:wk.dim], wk.parent(a)) for a, b in enumerate(wk.boxes, start=1)])
     psis = [np.ascontiguousarray(np.maximum(wk.level_psi(a), wk.psi_min)) for a in range(A.nlev)]
     oracle.amr_coarsen_psi(A, psis)
     return A, psis
@@ -136,7 +136,7 @@ def make_amr(name, wk):
         "source": "oracle/sbm_oracle.c orc_amr_solve (composite correction iteration, FP64) of the composite "
                   "problem of orc_amr_residual, written by tests/golden/make_golden.py",
         "n": list(wk.n), "h": wk.h, "moduli": list(wk.moduli), "psi_min": wk.psi_min,
-        "boxes": [[list(lo), list(hi)] for lo, hi in wk.boxes],
+        "boxes": [[list(b[0]), list(b[1])] + ([b[2]] if len(b) > 2 else []) for b in wk.boxes],
         "status": res.status, "cycles": res.cycles, "history": hist, "oracle_seconds": dt,
         "levels": [field_record(us[a], 9200 + a) for a in range(A.nlev)],
     }
@@ -146,6 +146,10 @@ def voids_amr_3d(n0):
     return W.voids_amr(3, n0, 2, count=16, rmin=0.04, rmax=0.12)
 
 
+def voids_amr_3d_clustered(n0):
+    return W.voids_amr(3, n0, 2, count=8, rmin=0.04, rmax=0.08, clustered=True)
+
+
 RECIPES = {
     "damage_3d_129": (lambda: W.damage3d(129), make_damage),
     "damage_3d_65": (lambda: W.damage3d(65), make_damage),
@@ -153,6 +157,9 @@ RECIPES = {
     "voids_amr_2d": (lambda: W.voids_amr(2, 129, 3), make_amr),
     "voids_amr_3d_65": (lambda: voids_amr_3d(65), make_amr),
     "voids_amr_3d_33": (lambda: voids_amr_3d(33), make_amr),
+    "voids_amr_2d_clustered": (lambda: W.voids_amr(2, 129, 3, clustered=True), make_amr),
+    "voids_amr_3d_clustered_65": (lambda: voids_amr_3d_clustered(65), make_amr),
+    "voids_amr_3d_clustered_129": (lambda: voids_amr_3d_clustered(129), make_amr),
 }
 
 

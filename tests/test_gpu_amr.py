@@ -46,8 +46,8 @@ def _gpu(wk, precision=None):
     for face, comp, _ in wk.bcs:
         g.set_bc(face, comp, sbm.SBM_DIRICHLET_FROM_U)
     g.set_psi(cuda(wk.level_psi(0)), wk.psi_min)
-    for lo, hi in wk.boxes:
-        g.amr_add_level(lo, hi)
+    for a, b in enumerate(wk.boxes, start=1):
+        assert g.amr_add_box(wk.level(a), b[0], b[1]) == a
     for a in range(1, len(wk.boxes) + 1):
         g.amr_set_psi(a, cuda(wk.level_psi(a)), wk.psi_min)
     return g
@@ -55,7 +55,7 @@ def _gpu(wk, precision=None):
 
 def _oracle(wk):
     P = oracle.Problem(wk.dim, wk.n, wk.h, *wk.moduli, dirichlet=wk.dirichlet_bits())
-    A = oracle.Amr(P, [(lo[:wk.dim], hi[:wk.dim]) for lo, hi in wk.boxes])
+    A = oracle.Amr(P, [(b[0][:wk.dim], b[1][:wk.dim], wk.parent(a)) for a, b in enumerate(wk.boxes, start=1)])
     psis = [np.ascontiguousarray(np.maximum(wk.level_psi(a), wk.psi_min)) for a in range(A.nlev)]
     oracle.amr_coarsen_psi(A, psis)
     return A, psis
@@ -69,6 +69,10 @@ SMALL = {
     "2d_two_patches": lambda: _custom(2, 9, [((4, 4, 0), (12, 12, 0)), ((10, 10, 0), (22, 22, 0))]),
     "2d_touching_boundary": lambda: _custom(2, 9, [((0, 4, 0), (12, 16, 0))]),
     "3d_one_patch": lambda: _custom(3, 5, [((2, 2, 2), (6, 6, 6))]),
+    # several patches per level: (lo, hi, parent), siblings apart, children nested
+    "2d_multibox": lambda: _custom(2, 9, [((2, 2, 0), (6, 6, 0), 0), ((10, 8, 0), (16, 16, 0), 0),
+                                          ((6, 6, 0), (10, 10, 0), 1), ((22, 18, 0), (32, 32, 0), 2)]),
+    "3d_two_slabs": lambda: _custom(3, 5, [((0, 0, 0), (2, 8, 8), 0), ((6, 2, 0), (8, 8, 6), 0)]),
 }
 
 
@@ -179,7 +183,7 @@ def _samples(wk, A, count, seed):
         o = wk.origin(a)
         pts = rng.integers(0, n, size=(count, 3))
         if a > 0:                        # rows on and next to the interface
-            lo, hi = wk.boxes[a - 1]
+            lo, hi = wk.boxes[a - 1][:2]
             face = pts.copy()
             ax = rng.integers(0, wk.dim, size=count)
             side = rng.integers(0, 2, size=count)
@@ -217,12 +221,12 @@ def test_C5_full_size_sampled_parity(built):
     for face, comp, _ in wk.bcs:
         g.set_bc(face, comp, sbm.SBM_DIRICHLET_FROM_U)
     g.set_psi(cuda(raw[0]), wk.psi_min)
-    for lo, hi in wk.boxes:
+    for lo, hi, *_ in wk.boxes:
         g.amr_add_level(lo, hi)
     for a in (1, 2):
         g.amr_set_psi(a, cuda(raw[a]), wk.psi_min)
     P = oracle.Problem(3, wk.n, wk.h, *wk.moduli, dirichlet=wk.dirichlet_bits())
-    A = oracle.Amr(P, [(lo, hi) for lo, hi in wk.boxes])
+    A = oracle.Amr(P, [tuple(b[:2]) for b in wk.boxes])
     psis = [np.ascontiguousarray(np.maximum(r, wk.psi_min)) for r in raw]
     del raw
     oracle.amr_coarsen_psi(A, psis)
@@ -296,7 +300,7 @@ def test_C5_full_size_adjoint_directional_derivative(built):
     for face, comp, _ in wk.bcs:
         g.set_bc(face, comp, sbm.SBM_DIRICHLET_FROM_U)
     g.set_psi(cuda(raw[0]), wk.psi_min)
-    for lo, hi in wk.boxes:
+    for lo, hi, *_ in wk.boxes:
         g.amr_add_level(lo, hi)
     for a in (1, 2):
         g.amr_set_psi(a, cuda(raw[a]), wk.psi_min)

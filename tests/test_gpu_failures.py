@@ -64,7 +64,7 @@ def test_allocation_cap_refuses_a_patch_and_keeps_the_grid(built):
     for face, comp, _ in wk.bcs:
         g.set_bc(face, comp, sbm.SBM_DIRICHLET_FROM_U)
     g.set_psi(cuda(wk.level_psi(0)), wk.psi_min)
-    lo, hi = wk.boxes[0]
+    lo, hi = wk.boxes[0][:2]
     sbm.lib().sbm_set_alloc_limit(1 << 10)
     try:
         with pytest.raises(sbm.SBMError) as e:

@@ -133,8 +133,8 @@ def _amr_gpu(wk, precision):
     for face, comp, _ in wk.bcs:
         g.set_bc(face, comp, sbm.SBM_DIRICHLET_FROM_U)
     g.set_psi(cuda(wk.level_psi(0)), wk.psi_min)
-    for lo, hi in wk.boxes:
-        g.amr_add_level(lo, hi)
+    for a, b in enumerate(wk.boxes, start=1):
+        assert g.amr_add_box(wk.level(a), b[0], b[1]) == a
     for a in range(1, len(wk.boxes) + 1):
         g.amr_set_psi(a, cuda(wk.level_psi(a)), wk.psi_min)
     return g
@@ -143,7 +143,7 @@ def _amr_gpu(wk, precision):
 def _amr_parity(rec, wk, precision, tol, **opts):
     """Composite solve to relres tol; returns the relative error over all levels'
     samples, the largest sketch deviation in units of |u_a| and the solve info."""
-    assert [[list(lo), list(hi)] for lo, hi in wk.boxes] == rec["boxes"]
+    assert [[list(b[0]), list(b[1])] + ([b[2]] if len(b) > 2 else []) for b in wk.boxes] == rec["boxes"]
     g = _amr_gpu(wk, precision)
     us = [cuda(wk.level_u0(a)) for a in range(len(wk.boxes) + 1)]
     info = g.amr_solve(us, tol=tol, omega=wk.omega, smoother=wk.smoother, **opts)

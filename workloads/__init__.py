@@ -272,9 +272,11 @@ def topopt3d(nx: int = 257, ny: int = 129, nz: int = 129, psi_min: float = 1e-3,
 
 @dataclass
 class AmrWorkload:
-    """Base grid + nested refinement boxes (one per level).  psi is the same analytic
-    indicator evaluated at every level's cell centres; patch arrays cover the box
-    grown by one padding node per side (cells outside the domain get psi = 0)."""
+    """Base grid + nested refinement patches.  ``boxes[a-1]`` is patch a: ``(lo, hi)``
+    (one patch per level: parent a-1) or ``(lo, hi, parent)``, parents before their
+    children.  psi is the same analytic indicator evaluated at every patch's cell
+    centres; patch arrays cover the box grown by one padding node per side (cells
+    outside the domain get psi = 0)."""
     name: str
     dim: int
     n: tuple
@@ -296,17 +298,26 @@ class AmrWorkload:
             bits[comp] |= 1 << FACES[face]
         return tuple(bits)
 
+    def parent(self, a):
+        if a == 0:
+            return -1
+        b = self.boxes[a - 1]
+        return b[2] if len(b) > 2 else a - 1
+
+    def level(self, a):
+        return 0 if a == 0 else self.level(self.parent(a)) + 1
+
     def level_h(self, a):
-        return self.h / 2 ** a
+        return self.h / 2 ** self.level(a)
 
     def level_N(self, a):
-        return tuple((self.n[ax] - 1) * 2 ** a + 1 if ax < self.dim else 1 for ax in range(3))
+        return tuple((self.n[ax] - 1) * 2 ** self.level(a) + 1 if ax < self.dim else 1 for ax in range(3))
 
     def storage_shape(self, a):
-        """nodes per axis of level a's storage (full grid for a = 0)"""
+        """nodes per axis of patch a's storage (full grid for a = 0)"""
         if a == 0:
             return tuple(self.n)
-        lo, hi = self.boxes[a - 1]
+        lo, hi = self.boxes[a - 1][0], self.boxes[a - 1][1]
         return tuple(hi[ax] - lo[ax] + 3 if ax < self.dim else 1 for ax in range(3))
 
     def origin(self, a):
@@ -385,7 +396,115 @@ def tag_boxes(dim, n0, psi_fn, levels, threshold=0.1, grow=2):
     return boxes
 
 
-def voids_amr(dim=2, n0=129, levels=3, count=8, rmin=0.03, rmax=0.10, psi_min=1e-4, seed=2001):
+def _apart(b1, b2, dim, gap=4):
+    """Boxes (level node indices) at least ``gap`` nodes apart on some axis."""
+    return any(b1[0][ax] >= b2[1][ax] + gap or b2[0][ax] >= b1[1][ax] + gap for ax in range(dim))
+
+
+def _union(b1, b2, dim):
+    lo = tuple(min(b1[0][ax], b2[0][ax]) if ax < dim else 0 for ax in range(3))
+    hi = tuple(max(b1[1][ax], b2[1][ax]) if ax < dim else 0 for ax in range(3))
+    return (lo, hi)
+
+
+def _volume(b, dim):
+    return int(np.prod([b[1][ax] - b[0][ax] for ax in range(dim)]))
+
+
+def cluster_boxes(dim, n0, psi_fn, levels, threshold=0.1, grow=2, max_children=8):
+    """Several refinement boxes per level (tagging and clustering on the host):
+    inside each parent patch, the parent's cells where h |grad psi| (centred
+    differences of cell psi) exceeds ``threshold`` are dilated by ``grow`` cells and
+    split into connected components; each component's bounding box (even corners in
+    the child level, nested one parent cell inside the parent unless on the domain
+    boundary) is a child patch.  Boxes closer than two parent cells are merged into
+    their bounding box, and while a parent has more than ``max_children`` the pair
+    whose union adds the least volume is merged.  Returns [(lo, hi, parent)], parents
+    before children."""
+    from scipy import ndimage
+    h0 = 1.0 / (n0 - 1)
+    out = []                                      # (lo, hi, parent, level)
+    parents = [(None, None, -1, 0)]              # the base grid as patch 0
+    for L in range(1, levels + 1):
+        hp = h0 / 2 ** (L - 1)
+        Np = [(n0 - 1) * 2 ** (L - 1) + 1 if ax < dim else 1 for ax in range(3)]
+        nc = [Np[ax] - 1 if ax < dim else 1 for ax in range(3)]
+        axes = [(np.arange(nc[ax]) + 0.5) * hp if ax < dim else np.zeros(1) for ax in range(3)]
+        Z, Y, X = np.meshgrid(axes[2], axes[1], axes[0], indexing="ij")
+        psi = psi_fn(X, Y, Z)
+        grad = np.zeros(psi.shape)
+        for ax in range(dim):
+            axn = 2 - ax
+            d = (np.roll(psi, -1, axn) - np.roll(psi, 1, axn)) / 2.0
+            grad += d ** 2
+        tag = np.sqrt(grad) > threshold
+        conn = np.ones((3, 3, 3), bool)
+        if dim == 2:
+            conn[0] = conn[2] = False                 # the (z, y, x) arrays of a 2D grid have one z layer
+        if grow:
+            tag = ndimage.binary_dilation(tag, structure=conn, iterations=grow)
+        level_boxes = []
+        for pidx, (plo, phi, _, plev) in enumerate(parents):
+            if plev != L - 1:
+                continue
+            # child-level node range allowed inside this parent
+            amin, amax = [0, 0, 0], [0, 0, 0]
+            for ax in range(dim):
+                N = 2 * (Np[ax] - 1) + 1
+                if plo is None:
+                    amin[ax], amax[ax] = 0, N - 1
+                else:
+                    amin[ax] = 0 if plo[ax] == 0 else 2 * plo[ax] + 2
+                    amax[ax] = N - 1 if phi[ax] == Np[ax] - 1 else 2 * phi[ax] - 2
+            sl = tuple(slice(amin[ax] // 2, amax[ax] // 2) if ax < dim else slice(0, 1) for ax in (2, 1, 0))
+            sub = np.zeros(tag.shape, bool)
+            sub[sl] = tag[sl]
+            labels, _ = ndimage.label(sub, structure=conn)
+            boxes = []
+            for sls in ndimage.find_objects(labels):
+                if sls is None:
+                    continue
+                lo, hi = [0, 0, 0], [0, 0, 0]
+                for ax in range(dim):
+                    sa = sls[2 - ax]
+                    lo[ax] = max(2 * sa.start, amin[ax])
+                    hi[ax] = min(2 * sa.stop, amax[ax])
+                if all(hi[ax] - lo[ax] >= 2 for ax in range(dim)):
+                    boxes.append((tuple(lo), tuple(hi)))
+            changed = True
+            while changed:
+                changed = False
+                for i in range(len(boxes)):
+                    for j in range(i + 1, len(boxes)):
+                        if not _apart(boxes[i], boxes[j], dim):
+                            boxes[i] = _union(boxes[i], boxes[j], dim)
+                            del boxes[j]
+                            changed = True
+                            break
+                    if changed:
+                        break
+                if not changed and len(boxes) > max_children:
+                    best = None
+                    for i in range(len(boxes)):
+                        for j in range(i + 1, len(boxes)):
+                            u = _union(boxes[i], boxes[j], dim)
+                            cost = _volume(u, dim) - _volume(boxes[i], dim) - _volume(boxes[j], dim)
+                            if best is None or cost < best[0]:
+                                best = (cost, i, j, u)
+                    _, i, j, u = best
+                    boxes[i] = u
+                    del boxes[j]
+                    changed = True
+            for b in sorted(boxes):
+                level_boxes.append((b[0], b[1], pidx, L))
+        if not level_boxes:
+            break
+        parents = parents + level_boxes
+        out.extend(level_boxes)
+    return [(lo, hi, parent) for lo, hi, parent, _ in out]
+
+
+def voids_amr(dim=2, n0=129, levels=3, count=8, rmin=0.03, rmax=0.10, psi_min=1e-4, seed=2001, clustered=False):
     """Random non-overlapping voids (circles / spheres), tanh width 2 h_f with h_f the
     finest spacing, refined by tag_boxes."""
     st = _Stream(seed)
@@ -401,7 +520,7 @@ def voids_amr(dim=2, n0=129, levels=3, count=8, rmin=0.03, rmax=0.10, psi_min=1e
             v = v * _tanh_step(dist - r, 2.0 * hf)
         return v
 
-    boxes = tag_boxes(dim, n0, psi_fn, levels)
+    boxes = cluster_boxes(dim, n0, psi_fn, levels) if clustered else tag_boxes(dim, n0, psi_fn, levels)
     if dim == 2:
         bcs = [("-y", 0, 0.0), ("-y", 1, 0.0), ("+y", 0, 0.0), ("+y", 1, 0.01)]
         moduli = iso_cubic(1.0, 0.3)
@@ -411,7 +530,8 @@ def voids_amr(dim=2, n0=129, levels=3, count=8, rmin=0.03, rmax=0.10, psi_min=1e
         bcs = [(f, p, None) for f in ("-x", "+x", "-y", "+y", "-z", "+z") for p in range(3)]
         moduli = iso_cubic(1.0, 0.25)
     n = (n0, n0, n0 if dim == 3 else 1)
-    return AmrWorkload(f"voids_amr_{dim}d", dim, n, h0, moduli, bcs, psi_fn, psi_min, boxes,
+    return AmrWorkload(f"voids_amr_{dim}d" + ("_clustered" if clustered else ""), dim, n, h0, moduli, bcs, psi_fn,
+                       psi_min, boxes,
                        smoother="gs" if dim == 2 else "jacobi", omega=2.0 / 3.0 if dim == 2 else 0.5,
                        precision="fp64" if dim == 2 else "mixed", notes={"balls": balls},
                        affine=None if dim == 2 else 0.01)
