@@ -565,8 +565,8 @@ def run_amr(args, rank, world, local_rank):
             g.set_bc(face, comp, sbm.SBM_DIRICHLET_FROM_U)
         with torch.cuda.stream(stream):
             g.set_psi(psi_d[0], wk.psi_min)
-            for lo, hi in wk.boxes:
-                g.amr_add_level(lo, hi)
+            for a, b in enumerate(wk.boxes, start=1):
+                g.amr_add_box(wk.level(a), b[0], b[1])
             for a in range(1, nl):
                 g.amr_set_psi(a, psi_d[a], wk.psi_min)
         return g

@@ -128,6 +128,7 @@ struct sbm_grid_s {
     bool bottom_ready = false;
     unsigned version = 1;
     GraphSlot slots[2];
+    GraphSlot amr_slot;         // one outer iteration of the composite solve
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     std::string err;
     int npatch = 0;
@@ -1163,16 +1164,60 @@ sbm_status amr_run(sbm_grid G, const sbm_opts &o, sbm_info *info)
     }
     // SBM_MIXED: inner_cycles FP32 correction cycles per FP64 residual
     const int inner = std::is_same<T, float>::value ? o.inner_cycles : 1;
-    int ncycles = 0;
-    while (status == SBM_ERR_NOCONV && cyc < o.max_cycles) {
+    // one outer iteration: the correction cycles and the FP64 composite residual
+    // with its norm in scal[4]; captured once as a CUDA graph and replayed
+    auto body = [&]() -> cudaError_t {
         for (int it = 0; it < inner; ++it) {
             int cur[kMaxPatch + 1], cb = 0;
-            CK(amr_cycle<T>(G, o, nullptr, cur, &cb));
-            ++ncycles;
+            CKE(amr_cycle<T>(G, o, nullptr, cur, &cb));
             if constexpr (std::is_same<T, float>::value)
-                if (it + 1 < inner) CK(amr_inner_residual(G, cur, cb));
+                if (it + 1 < inner) CKE(amr_inner_residual(G, cur, cb));
         }
-        CK(amr_residual<T>(G, 2));
+        return amr_residual<T>(G, 2);
+    };
+    GraphSlot &gs = G->amr_slot;
+    const int mixed = std::is_same<T, float>::value ? 1 : 0;
+    if (o.use_graph) {
+        const bool match = gs.valid && gs.mixed == mixed && gs.smoother == o.smoother && gs.nu1 == o.nu1 &&
+                           gs.nu2 == o.nu2 && gs.inner == inner && gs.omega == o.omega && gs.version == G->version;
+        if (!match) {
+            if (gs.valid) cudaGraphExecDestroy(gs.exec);
+            gs.valid = false;
+            cudaGraph_t graph;
+            CK(cudaStreamBeginCapture(G->st, cudaStreamCaptureModeThreadLocal));
+            const long long c0 = g_launches;
+            cudaError_t e = body();
+            const long long nbody = g_launches - c0;
+            g_launches = c0;
+            cudaError_t e2 = cudaStreamEndCapture(G->st, &graph);
+            if (e != cudaSuccess || e2 != cudaSuccess) {
+                if (e2 == cudaSuccess) cudaGraphDestroy(graph);
+                return fail(G, SBM_ERR_CUDA, std::string("graph capture: ") +
+                                                 cudaGetErrorString(e != cudaSuccess ? e : e2));
+            }
+            e = cudaGraphInstantiate(&gs.exec, graph, 0ULL);
+            cudaGraphDestroy(graph);
+            if (e != cudaSuccess) return fail(G, SBM_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+            gs.valid = true;
+            gs.mixed = mixed;
+            gs.smoother = o.smoother;
+            gs.nu1 = o.nu1;
+            gs.nu2 = o.nu2;
+            gs.inner = inner;
+            gs.omega = o.omega;
+            gs.version = G->version;
+            gs.body_launches = nbody;
+        }
+    }
+    int ncycles = 0;
+    while (status == SBM_ERR_NOCONV && cyc < o.max_cycles) {
+        if (o.use_graph) {
+            CK(cudaGraphLaunch(gs.exec, G->st));
+            g_launches += gs.body_launches;
+        } else {
+            CK(body());
+        }
+        ncycles += inner;
         CK(cudaMemcpyAsync(G->hscal + 4, G->scal + 4, sizeof(double), cudaMemcpyDeviceToHost, G->st));
         CK(cudaStreamSynchronize(G->st));
         ++cyc;
@@ -1287,6 +1332,7 @@ sbm_status sbm_grid_destroy(sbm_grid G)
     if (G->st) cudaStreamSynchronize(G->st);
     for (auto &s : G->slots)
         if (s.valid) cudaGraphExecDestroy(s.exec);
+    if (G->amr_slot.valid) cudaGraphExecDestroy(G->amr_slot.exec);
     for (int l = 0; l < G->nl; ++l) {
         Level &L = G->L[l];
         void *ptrs[] = {L.psi64, L.psi32, L.du[0], L.du[1], L.df, L.dr, L.su[0], L.su[1], L.sf, L.sr, L.Ke64, L.Ke32};
@@ -2294,6 +2340,7 @@ sbm_status sbm_amr_add_box(sbm_grid G, int level, const sbm_box *box, int *index
     G->npatch = a;
     amr_refresh_infos(G);
     G->amr_psi_dirty = true;
+    ++G->version;               // captured cycles hold the old patch set
     if (index) *index = a;
     return SBM_OK;
 }
