@@ -185,3 +185,22 @@ def test_C5_voids_amr_3d_matches_oracle_record(built, base):
     wk = W.voids_amr(3, base, 2, count=16, rmin=0.04, rmax=0.12)
     err, sk, info = _amr_parity(rec, wk, "mixed", 1e-12, inner_cycles=6, max_cycles=500)
     assert err <= 1e-8 and sk <= 2e-8, (err, sk, info.cycles)
+
+
+@pytest.mark.parametrize("name,precision,opts", [
+    ("voids_amr_2d_clustered", "fp64", {}),
+    ("voids_amr_3d_clustered_65", "mixed", {"inner_cycles": 6}),
+    ("voids_amr_3d_clustered_129", "mixed", {"inner_cycles": 6}),
+])
+def test_clustered_hierarchies_match_oracle_records(built, name, precision, opts):
+    """Several patches per level (host tagging and clustering): the 2D voids at a
+    129^2 base + 3 levels (23 patches, FP64 colour Gauss-Seidel) and the 3D voids at
+    a 65^3 and a 129^3 base + 2 levels (mixed precision), against the oracle's
+    composite iteration at its FP64 floor; GPU at relres 1e-12 (D9)."""
+    rec = _record(name)
+    if name == "voids_amr_2d_clustered":
+        wk = W.voids_amr(2, 129, 3, clustered=True)
+    else:
+        wk = W.voids_amr(3, int(name.rsplit("_", 1)[1]), 2, count=8, rmin=0.04, rmax=0.08, clustered=True)
+    err, sk, info = _amr_parity(rec, wk, precision, 1e-12, max_cycles=500, **opts)
+    assert err <= 1e-8 and sk <= 2e-8, (err, sk, info.cycles)
