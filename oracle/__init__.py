@@ -514,3 +514,129 @@ def amr_solve(A: Amr, psis, fs, us, *, omega=0.5, omega_base=None, smoother_base
     st = _La().orc_amr_solve(C.byref(A.c()), _ptrs(psis), _ptrs(fs), _ptrs(us), C.cast(C.byref(o), C.c_void_p),
                              hist.ctypes.data_as(C.POINTER(C.c_double)), C.byref(cyc))
     return MGResult(us, st, cyc.value, hist[: cyc.value + 1])
+
+
+# ------------------------------------------------------------- regridding (Sec. 2.2)
+
+def _apart(b1, b2, dim, gap=4):
+    return any(b1[0][ax] >= b2[1][ax] + gap or b2[0][ax] >= b1[1][ax] + gap for ax in range(dim))
+
+
+def _union(b1, b2, dim):
+    return (tuple(min(b1[0][ax], b2[0][ax]) if ax < dim else 0 for ax in range(3)),
+            tuple(max(b1[1][ax], b2[1][ax]) if ax < dim else 0 for ax in range(3)))
+
+
+def _volume(b, dim):
+    return int(np.prod([b[1][ax] - b[0][ax] for ax in range(dim)]))
+
+
+def regrid_boxes(A: Amr, psis, level, threshold, grow, max_children=8):
+    """New refinement boxes of ``level`` from the patches of level-1 of the hierarchy
+    ``A`` (Sec. 2.2: refine where the indicator varies; the tagging criterion
+    h |grad psi| > threshold), psis[a] = patch a's cell psi (storage layout, padding
+    cells included).  Per parent patch, in patch order:
+      - cells of the parent's allowed region (child nodes [amin, amax]: the whole
+        level on the domain boundary, one parent cell inside the parent box
+        elsewhere) are tagged where h |grad psi| > threshold, grad psi by centred
+        differences of the cell values, a neighbour beyond the domain replaced by
+        the cell itself (no gradient across the domain boundary);
+      - the tags are dilated by ``grow`` cells (Chebyshev distance) and restricted
+        to the allowed region;
+      - connected components (cells sharing a face, edge or corner), in the order
+        of their first cell in x-fastest order, give boxes: child nodes
+        [2 c_min, 2 (c_max + 1)] clipped to [amin, amax], dropped if thinner than 2;
+      - while two boxes are closer than two parent cells (4 child nodes) on every
+        axis, the first such pair (i < j, in list order) becomes their union; while
+        more than ``max_children`` remain, the first pair whose union adds the
+        least volume is merged (and the closeness rule applied again);
+      - the boxes are sorted (lo, then hi, x first).
+    Returns [(lo, hi, parent)]."""
+    from scipy import ndimage
+    dim = A.base.dim
+    out = []
+    for pidx in range(A.nlev):
+        if A.level(pidx) != level - 1:
+            continue
+        P = A.level_problem(pidx)
+        o = A.origin(pidx)
+        Np = A.global_n(pidx)
+        ncs = [P.n[ax] - 1 if ax < dim else 1 for ax in range(3)]
+        psi = np.asarray(psis[pidx], dtype=np.float64).reshape(ncs[2], ncs[1], ncs[0])
+        amin, amax = [0, 0, 0], [0, 0, 0]
+        for ax in range(dim):
+            N = 2 * (Np[ax] - 1) + 1
+            if pidx == 0:
+                amin[ax], amax[ax] = 0, N - 1
+            else:
+                lo, hi = A.boxes[pidx - 1][0][ax], A.boxes[pidx - 1][1][ax]
+                amin[ax] = 0 if lo == 0 else 2 * lo + 2
+                amax[ax] = N - 1 if hi == Np[ax] - 1 else 2 * hi - 2
+        # global cell index of storage cell l on axis ax: l + o[ax]; allowed cells C:
+        # amin/2 <= C <= amax/2 - 1
+        allowed = np.ones(psi.shape, bool)
+        grids = np.meshgrid(*[np.arange(ncs[ax]) + o[ax] for ax in (2, 1, 0)], indexing="ij")
+        for ax in range(dim):
+            C = grids[2 - ax]
+            allowed &= (C >= amin[ax] // 2) & (C <= amax[ax] // 2 - 1)
+        tag = np.zeros(psi.shape, bool)
+        idx = np.argwhere(allowed)
+        for (k, j, i) in idx:
+            g2 = 0.0
+            for ax in range(dim):
+                l = [i, j, k]
+                up, dn = list(l), list(l)
+                up[ax] += 1
+                dn[ax] -= 1
+                Cu, Cd = up[ax] + o[ax], dn[ax] + o[ax]
+                if Cu > Np[ax] - 2:
+                    up = l
+                if Cd < 0:
+                    dn = l
+                d = (psi[up[2], up[1], up[0]] - psi[dn[2], dn[1], dn[0]]) / 2.0
+                g2 += d * d
+            tag[k, j, i] = np.sqrt(g2) > threshold
+        conn = np.ones((3, 3, 3), bool)
+        if dim == 2:
+            conn[0] = conn[2] = False
+        if grow:
+            tag = ndimage.binary_dilation(tag, structure=conn, iterations=grow)
+        tag &= allowed
+        labels, _ = ndimage.label(tag, structure=conn)
+        boxes = []
+        for sls in ndimage.find_objects(labels):
+            if sls is None:
+                continue
+            lo, hi = [0, 0, 0], [0, 0, 0]
+            for ax in range(dim):
+                sa = sls[2 - ax]
+                lo[ax] = max(2 * (sa.start + o[ax]), amin[ax])
+                hi[ax] = min(2 * (sa.stop + o[ax]), amax[ax])
+            if all(hi[ax] - lo[ax] >= 2 for ax in range(dim)):
+                boxes.append((tuple(lo), tuple(hi)))
+        changed = True
+        while changed:
+            changed = False
+            for i in range(len(boxes)):
+                for j in range(i + 1, len(boxes)):
+                    if not _apart(boxes[i], boxes[j], dim):
+                        boxes[i] = _union(boxes[i], boxes[j], dim)
+                        del boxes[j]
+                        changed = True
+                        break
+                if changed:
+                    break
+            if not changed and len(boxes) > max_children:
+                best = None
+                for i in range(len(boxes)):
+                    for j in range(i + 1, len(boxes)):
+                        u = _union(boxes[i], boxes[j], dim)
+                        cost = _volume(u, dim) - _volume(boxes[i], dim) - _volume(boxes[j], dim)
+                        if best is None or cost < best[0]:
+                            best = (cost, i, j, u)
+                _, i, j, u = best
+                boxes[i] = u
+                del boxes[j]
+                changed = True
+        out.extend((b[0], b[1], pidx) for b in sorted(boxes))
+    return out
