@@ -351,9 +351,31 @@ typedef struct {
  * a sibling, a ninth child, a 65th patch), SBM_ERR_OOM when the storage cannot
  * be allocated (nothing is kept). */
 sbm_status sbm_amr_add_box(sbm_grid grid, int level, const sbm_box *box, int *index);
+/* Box, refinement level and parent (0: the base grid) of patch a >= 1; any output
+ * pointer (host) may be NULL. */
+sbm_status sbm_amr_get_box(sbm_grid grid, int a, sbm_box *box, int *level, int *parent);
 /* sbm_amr_add_box at one level deeper than the deepest patch so far (level 1 on a
  * grid without patches): the one-patch-per-level hierarchy, patch a at level a. */
 sbm_status sbm_amr_add_level(sbm_grid grid, const sbm_box *box);
+/* Regridding (Sec. 2.2: refine where the indicator varies): build refinement level
+ * `level` (= deepest existing level + 1) from the psi the grid holds (the base grid's
+ * after sbm_set_psi, each patch's after sbm_amr_set_psi; floored at psi_min).  For each
+ * patch of level-1 (the base grid for level 1), in patch order:
+ *   - on the device, its cells in the allowed region (one parent cell inside its box,
+ *     the whole level on the domain boundary) are tagged where h |grad psi| >
+ *     threshold (centred differences of the cell values, no gradient across the
+ *     domain boundary);
+ *   - on the host: the tags are dilated by `grow` cells (Chebyshev distance) and
+ *     restricted to the allowed region; connected components (cells sharing a face,
+ *     edge or corner), in the order of their first cell, give boxes (child nodes
+ *     [2 c_min, 2 (c_max + 1)], clipped to the allowed region, dropped if thinner than
+ *     2); boxes closer than two parent cells are merged into their union and, while
+ *     more than 8 remain, the pair whose union adds the least volume; the boxes are
+ *     sorted by (lo, hi), x first.
+ * The boxes are added as patches (sbm_amr_add_box, parents in patch order); their psi
+ * is 0 until sbm_amr_set_psi.  *nadded (host, may be NULL) receives the number added.
+ * SBM_ERR_ARG for another level or bad parameters, SBM_ERR_STATE before sbm_set_psi. */
+sbm_status sbm_amr_regrid(sbm_grid grid, int level, double threshold, int grow, int *nadded);
 /* psi of patch a (device, FP64) on the cells of the padded box, floored at psi_min.
  * Covered parent cells are replaced by fine means at the next solve. */
 sbm_status sbm_amr_set_psi(sbm_grid grid, int a, const double *psi_cells, double psi_min);

@@ -192,6 +192,22 @@ class Grid:
         self.patches = getattr(self, "patches", []) + [(tuple(b.lo), tuple(b.hi), level, idx.value)]
         return idx.value
 
+    def amr_regrid(self, level, threshold=0.1, grow=2):
+        """Tag and cluster a new refinement level from the grid's psi (sbm_amr_regrid);
+        returns the (lo, hi, index) of the patches added."""
+        n = C.c_int(0)
+        first = len(getattr(self, "patches", [])) + 1
+        self._check(lib().sbm_amr_regrid(self._h, level, threshold, grow, C.byref(n)))
+        shape = _capi.sbm_box()
+        out = []
+        for a in range(first, first + n.value):
+            self._check(lib().sbm_amr_get_box(self._h, a, C.byref(shape), None, None))
+            lo, hi = tuple(shape.lo), tuple(shape.hi)
+            self.boxes = getattr(self, "boxes", []) + [(lo, hi)]
+            self.patches = getattr(self, "patches", []) + [(lo, hi, level, a)]
+            out.append((lo, hi, a))
+        return out
+
     def amr_set_psi(self, a: int, psi: torch.Tensor, psi_min: float):
         self._check(lib().sbm_amr_set_psi(self._h, a, _ptr(psi), psi_min))
         self.psi_version += 1

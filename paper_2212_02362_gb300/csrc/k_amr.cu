@@ -514,6 +514,41 @@ __global__ void k_amr_get_cells(const Geom s, const double *lev, const double *p
     packed[i + (long long)ncx * (j + (long long)ncy * k)] = psi[o] > psi_min ? lev[o] : 0.0;
 }
 
+// Regridding tags: storage cell (i,j,k) of a patch (or of the base level) gets 1
+// when its global cell index lies in [cmin, cmax] on every axis and h |grad psi|
+// > thr, grad psi by centred differences of the cell values, a neighbour beyond the
+// domain replaced by the cell itself.  Output packed over the storage cells
+// (x fastest).
+__global__ void k_amr_tag(const Geom s, const AmrInfo L, const double *psi, double thr, int3 cmin, int3 cmax,
+                          unsigned char *tags)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z * blockDim.z + threadIdx.z;
+    const bool d3 = L.dim == 3;
+    const int ncx = s.nx - 1, ncy = s.ny - 1, ncz = d3 ? s.nz - 1 : 1;
+    if (i >= ncx || j >= ncy || k >= ncz) return;
+    const int C[3] = {i + L.org[0], j + L.org[1], k + L.org[2]};
+    const int lo[3] = {cmin.x, cmin.y, cmin.z}, hi[3] = {cmax.x, cmax.y, cmax.z};
+    bool in = true;
+    for (int ax = 0; ax < L.dim; ++ax)
+        if (C[ax] < lo[ax] || C[ax] > hi[ax]) in = false;
+    unsigned char t = 0;
+    if (in) {
+        const int l[3] = {i, j, k};
+        double g2 = 0.0;
+        for (int ax = 0; ax < L.dim; ++ax) {
+            int up[3] = {l[0], l[1], l[2]}, dn[3] = {l[0], l[1], l[2]};
+            if (C[ax] + 1 <= L.N[ax] - 2) ++up[ax];
+            if (C[ax] - 1 >= 0) --dn[ax];
+            const double d = 0.5 * (psi[gidx(s, up[0], up[1], up[2])] - psi[gidx(s, dn[0], dn[1], dn[2])]);
+            g2 += d * d;
+        }
+        t = sqrt(g2) > thr ? 1 : 0;
+    }
+    tags[i + (long long)ncx * (j + (long long)ncy * k)] = t;
+}
+
 const dim3 kAmrBlock(32, 4, 2);
 inline dim3 amr_grid(const Geom &s) { return dim3((s.nx + 31) / 32, (s.ny + 3) / 4, (s.nz + 1) / 2); }
 
@@ -677,6 +712,15 @@ cudaError_t launch_amr_grad_chain(const Geom &sc, const AmrInfo &Lc, const Geom 
                                   double *gc, cudaStream_t st)
 {
     k_amr_grad_chain<<<amr_grid(sp), kAmrBlock, 0, st>>>(sc, Lc, sp, Lp, gp, gc);
+    ++g_launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_amr_tag(const Geom &s, const AmrInfo &L, const double *psi, double thr, const int cmin[3],
+                           const int cmax[3], unsigned char *tags, cudaStream_t st)
+{
+    k_amr_tag<<<amr_grid(s), kAmrBlock, 0, st>>>(s, L, psi, thr, make_int3(cmin[0], cmin[1], cmin[2]),
+                                                 make_int3(cmax[0], cmax[1], cmax[2]), tags);
     ++g_launches;
     return cudaGetLastError();
 }

@@ -2345,6 +2345,236 @@ sbm_status sbm_amr_add_box(sbm_grid G, int level, const sbm_box *box, int *index
     return SBM_OK;
 }
 
+// ------------------------------------------------------- regridding (host clustering)
+
+namespace {
+
+struct IBox {
+    int lo[3], hi[3];
+};
+
+bool boxes_apart(const IBox &a, const IBox &b, int d)
+{
+    for (int ax = 0; ax < d; ++ax)
+        if (a.lo[ax] >= b.hi[ax] + 4 || b.lo[ax] >= a.hi[ax] + 4) return true;
+    return false;
+}
+
+IBox box_union(const IBox &a, const IBox &b, int d)
+{
+    IBox u{};
+    for (int ax = 0; ax < d; ++ax) {
+        u.lo[ax] = std::min(a.lo[ax], b.lo[ax]);
+        u.hi[ax] = std::max(a.hi[ax], b.hi[ax]);
+    }
+    return u;
+}
+
+long long box_volume(const IBox &b, int d)
+{
+    long long v = 1;
+    for (int ax = 0; ax < d; ++ax) v *= b.hi[ax] - b.lo[ax];
+    return v;
+}
+
+// Boxes of one parent from its tags (storage cells n[0] x n[1] x n[2], x fastest,
+// global cell = storage cell + org): dilation by `grow` cells (Chebyshev distance,
+// separable), restriction to the allowed cells [cmin, cmax], connected components
+// (face, edge or corner neighbours) numbered in the order of their first cell,
+// bounding boxes in child nodes clipped to [amin, amax] (thinner than 2 dropped),
+// merging of boxes closer than two parent cells and, beyond max_children, of the
+// pair whose union adds the least volume; sorted by (lo, hi), x first.
+std::vector<IBox> cluster_tags(std::vector<unsigned char> &tag, const int n[3], int d, const int org[3], int grow,
+                               const int cmin[3], const int cmax[3], const int amin[3], const int amax[3],
+                               int max_children)
+{
+    auto at = [&](int i, int j, int k) -> long long { return i + (long long)n[0] * (j + (long long)n[1] * k); };
+    for (int ax = 0; ax < d && grow > 0; ++ax) {
+        std::vector<unsigned char> out(tag.size(), 0);
+        for (int k = 0; k < n[2]; ++k)
+            for (int j = 0; j < n[1]; ++j)
+                for (int i = 0; i < n[0]; ++i) {
+                    const int l[3] = {i, j, k};
+                    unsigned char v = 0;
+                    for (int off = -grow; off <= grow && !v; ++off) {
+                        int q[3] = {i, j, k};
+                        q[ax] = l[ax] + off;
+                        if (q[ax] < 0 || q[ax] >= n[ax]) continue;
+                        v = tag[at(q[0], q[1], q[2])];
+                    }
+                    out[at(i, j, k)] = v;
+                }
+        tag.swap(out);
+    }
+    for (int k = 0; k < n[2]; ++k)
+        for (int j = 0; j < n[1]; ++j)
+            for (int i = 0; i < n[0]; ++i) {
+                const int C[3] = {i + org[0], j + org[1], k + org[2]};
+                for (int ax = 0; ax < d; ++ax)
+                    if (C[ax] < cmin[ax] || C[ax] > cmax[ax]) tag[at(i, j, k)] = 0;
+            }
+    std::vector<IBox> boxes;
+    std::vector<int> seen(tag.size(), 0);
+    std::vector<long long> stack;
+    for (int k = 0; k < n[2]; ++k)
+        for (int j = 0; j < n[1]; ++j)
+            for (int i = 0; i < n[0]; ++i) {
+                if (!tag[at(i, j, k)] || seen[at(i, j, k)]) continue;
+                int lo[3] = {i, j, k}, hi[3] = {i, j, k};
+                stack.assign(1, at(i, j, k));
+                seen[at(i, j, k)] = 1;
+                while (!stack.empty()) {
+                    const long long c = stack.back();
+                    stack.pop_back();
+                    const int ci = (int)(c % n[0]), cj = (int)((c / n[0]) % n[1]), ck = (int)(c / ((long long)n[0] * n[1]));
+                    const int cc[3] = {ci, cj, ck};
+                    for (int ax = 0; ax < 3; ++ax) {
+                        lo[ax] = std::min(lo[ax], cc[ax]);
+                        hi[ax] = std::max(hi[ax], cc[ax]);
+                    }
+                    for (int dz = (d == 3 ? -1 : 0); dz <= (d == 3 ? 1 : 0); ++dz)
+                        for (int dy = -1; dy <= 1; ++dy)
+                            for (int dx = -1; dx <= 1; ++dx) {
+                                const int q[3] = {ci + dx, cj + dy, ck + dz};
+                                if (q[0] < 0 || q[1] < 0 || q[2] < 0 || q[0] >= n[0] || q[1] >= n[1] || q[2] >= n[2])
+                                    continue;
+                                const long long e = at(q[0], q[1], q[2]);
+                                if (tag[e] && !seen[e]) {
+                                    seen[e] = 1;
+                                    stack.push_back(e);
+                                }
+                            }
+                }
+                IBox b{};
+                bool thick = true;
+                for (int ax = 0; ax < d; ++ax) {
+                    b.lo[ax] = std::max(2 * (lo[ax] + org[ax]), amin[ax]);
+                    b.hi[ax] = std::min(2 * (hi[ax] + 1 + org[ax]), amax[ax]);
+                    thick = thick && b.hi[ax] - b.lo[ax] >= 2;
+                }
+                if (thick) boxes.push_back(b);
+            }
+    for (bool changed = true; changed;) {
+        changed = false;
+        for (size_t a = 0; a < boxes.size() && !changed; ++a)
+            for (size_t b = a + 1; b < boxes.size(); ++b)
+                if (!boxes_apart(boxes[a], boxes[b], d)) {
+                    boxes[a] = box_union(boxes[a], boxes[b], d);
+                    boxes.erase(boxes.begin() + b);
+                    changed = true;
+                    break;
+                }
+        if (!changed && (int)boxes.size() > max_children) {
+            long long best = 0;
+            size_t bi = 0, bj = 1;
+            bool have = false;
+            for (size_t a = 0; a < boxes.size(); ++a)
+                for (size_t b = a + 1; b < boxes.size(); ++b) {
+                    const long long cost = box_volume(box_union(boxes[a], boxes[b], d), d) - box_volume(boxes[a], d) -
+                                           box_volume(boxes[b], d);
+                    if (!have || cost < best) {
+                        best = cost;
+                        bi = a;
+                        bj = b;
+                        have = true;
+                    }
+                }
+            boxes[bi] = box_union(boxes[bi], boxes[bj], d);
+            boxes.erase(boxes.begin() + bj);
+            changed = true;
+        }
+    }
+    std::sort(boxes.begin(), boxes.end(), [](const IBox &x, const IBox &y) {
+        for (int ax = 0; ax < 3; ++ax)
+            if (x.lo[ax] != y.lo[ax]) return x.lo[ax] < y.lo[ax];
+        for (int ax = 0; ax < 3; ++ax)
+            if (x.hi[ax] != y.hi[ax]) return x.hi[ax] < y.hi[ax];
+        return false;
+    });
+    return boxes;
+}
+
+}  // namespace
+
+sbm_status sbm_amr_regrid(sbm_grid G, int level, double threshold, int grow, int *nadded)
+{
+    if (!G) return fail(nullptr, SBM_ERR_ARG, "null grid");
+    if (nadded) *nadded = 0;
+    if (!G->has_psi) return fail(G, SBM_ERR_STATE, "psi not set (sbm_set_psi)");
+    int deepest = 0;
+    for (int q = 1; q <= G->npatch; ++q) deepest = std::max(deepest, G->P[q - 1].level);
+    if (level != deepest + 1) return fail(G, SBM_ERR_ARG, "regridding builds the level below the deepest one");
+    if (!(threshold >= 0.0) || !std::isfinite(threshold) || grow < 0 || grow > 64)
+        return fail(G, SBM_ERR_ARG, "need threshold >= 0 and 0 <= grow <= 64");
+    CK(cudaSetDevice(G->dev));
+    amr_refresh_infos(G);
+    const int d = G->desc.dim;
+    std::vector<std::pair<int, IBox>> found;
+    for (int p = 0; p <= G->npatch; ++p) {
+        if ((p == 0 ? 0 : G->P[p - 1].level) != level - 1) continue;
+        const Geom &s = amr_geom(G, p);
+        const AmrInfo &L = amr_info(G, p);
+        const double *psi = p == 0 ? G->L[G->nl - 1].psi64 : G->P[p - 1].psi64;
+        int amin[3] = {0, 0, 0}, amax[3] = {0, 0, 0}, cmin[3] = {0, 0, 0}, cmax[3] = {0, 0, 0};
+        for (int ax = 0; ax < d; ++ax) {
+            const int Np = level_N(G, level - 1, ax), N = 2 * (Np - 1) + 1;
+            if (p == 0) {
+                amin[ax] = 0;
+                amax[ax] = N - 1;
+            } else {
+                const Patch &Pp = G->P[p - 1];
+                amin[ax] = Pp.lo[ax] == 0 ? 0 : 2 * Pp.lo[ax] + 2;
+                amax[ax] = Pp.hi[ax] == Np - 1 ? N - 1 : 2 * Pp.hi[ax] - 2;
+            }
+            cmin[ax] = amin[ax] / 2;
+            cmax[ax] = amax[ax] / 2 - 1;
+        }
+        const int n[3] = {s.nx - 1, s.ny - 1, d == 3 ? s.nz - 1 : 1};
+        const size_t nt = (size_t)n[0] * n[1] * n[2];
+        unsigned char *dtag = nullptr;
+        CK(cudaMalloc(&dtag, nt));
+        std::vector<unsigned char> tag(nt);
+        cudaError_t e = launch_amr_tag(s, L, psi, threshold, cmin, cmax, dtag, G->st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(tag.data(), dtag, nt, cudaMemcpyDeviceToHost, G->st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(G->st);
+        cudaFree(dtag);
+        if (e != cudaSuccess) return fail(G, SBM_ERR_CUDA, std::string("regrid tags: ") + cudaGetErrorString(e));
+        const int org[3] = {L.org[0], L.org[1], L.org[2]};
+        for (const IBox &b : cluster_tags(tag, n, d, org, grow, cmin, cmax, amin, amax, kMaxChild))
+            found.push_back({p, b});
+    }
+    int added = 0;
+    for (const auto &pb : found) {
+        sbm_box box{};
+        for (int ax = 0; ax < 3; ++ax) {
+            box.lo[ax] = pb.second.lo[ax];
+            box.hi[ax] = pb.second.hi[ax];
+        }
+        int idx = 0;
+        sbm_status st = sbm_amr_add_box(G, level, &box, &idx);
+        if (st != SBM_OK) return st;
+        if (G->P[idx - 1].parent != pb.first) return fail(G, SBM_ERR_STATE, "regridded box found another parent");
+        ++added;
+        if (nadded) *nadded = added;
+    }
+    return SBM_OK;
+}
+
+sbm_status sbm_amr_get_box(sbm_grid G, int a, sbm_box *box, int *level, int *parent)
+{
+    if (!G) return fail(nullptr, SBM_ERR_ARG, "null grid");
+    if (a < 1 || a > G->npatch) return fail(G, SBM_ERR_ARG, "patch index out of range");
+    const Patch &Pt = G->P[a - 1];
+    if (box)
+        for (int ax = 0; ax < 3; ++ax) {
+            box->lo[ax] = Pt.lo[ax];
+            box->hi[ax] = Pt.hi[ax];
+        }
+    if (level) *level = Pt.level;
+    if (parent) *parent = Pt.parent;
+    return SBM_OK;
+}
+
 sbm_status sbm_amr_add_level(sbm_grid G, const sbm_box *box)
 {
     if (!G) return fail(nullptr, SBM_ERR_ARG, "null grid");

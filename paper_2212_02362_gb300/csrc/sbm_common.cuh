@@ -315,6 +315,10 @@ cudaError_t launch_l2_read(const void *buf, size_t bytes, float *sink, cudaStrea
 cudaError_t launch_amr_ghostT(const Geom &sc, const AmrInfo &Lc, const Geom &sp, const AmrInfo &Lp, const double *wc,
                               double *wp, int with_solved, cudaStream_t st);
 cudaError_t launch_amr_mask_solved(const Geom &s, const AmrInfo &L, double *x, cudaStream_t st);
+// regridding: tags of h |grad psi| > thr on the storage cells whose global index is
+// in [cmin, cmax] (packed over the storage cells)
+cudaError_t launch_amr_tag(const Geom &s, const AmrInfo &L, const double *psi, double thr, const int cmin[3],
+                           const int cmax[3], unsigned char *tags, cudaStream_t st);
 cudaError_t launch_amr_scaleW(const Geom &s, const AmrInfo &L, const double *psi, double omega, const double kdiag[3],
                               const double *x, double *out, cudaStream_t st);
 cudaError_t launch_amr_restrictT(const Geom &sc, const AmrInfo &Lc, const Geom &sp, const AmrInfo &Lp,
