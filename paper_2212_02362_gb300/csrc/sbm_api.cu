@@ -79,6 +79,8 @@ struct Patch {
     float *Ke32 = nullptr;
 };
 
+constexpr int kBranches = 8;   // side streams for concurrent patches
+
 struct GraphSlot {
     bool valid = false;
     cudaGraphExec_t exec = nullptr;
@@ -129,6 +131,8 @@ struct sbm_grid_s {
     unsigned version = 1;
     GraphSlot slots[2];
     GraphSlot amr_slot;         // one outer iteration of the composite solve
+    cudaStream_t side[kBranches] = {};   // branches for the patches of one level
+    cudaEvent_t fork_ev = nullptr, join_ev[kBranches] = {};
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     std::string err;
     int npatch = 0;
@@ -738,6 +742,49 @@ const AmrInfo &amr_info(sbm_grid G, int a) { return a == 0 ? G->base_info : G->P
 int amr_parent(sbm_grid G, int a) { return G->P[a - 1].parent; }
 double *amr_u64(sbm_grid G, int a) { return a == 0 ? G->amr_u0 : G->P[a - 1].u64; }
 
+// The patches of each refinement level (index = level), in patch order.
+std::vector<std::vector<int>> amr_by_level(sbm_grid G)
+{
+    std::vector<std::vector<int>> out(1);
+    for (int a = 1; a <= G->npatch; ++a) {
+        const int L = G->P[a - 1].level;
+        if ((int)out.size() <= L) out.resize(L + 1);
+        out[L].push_back(a);
+    }
+    return out;
+}
+
+// work(a) for every patch a of `list`, the patches spread over the grid's side
+// streams (each branch ordered after everything enqueued on the grid stream so
+// far; the grid stream then waits for all branches).  Patches of one level touch
+// disjoint data (their own storage; a child's restriction writes only the parent
+// nodes it covers), so their kernels may run concurrently; under stream capture
+// the branches become parallel paths of the graph.
+template <typename F>
+cudaError_t amr_branches(sbm_grid G, const std::vector<int> &list, F &&work)
+{
+    if (list.size() <= 1 || !G->side[0]) {
+        for (int a : list) CKE(work(a));
+        return cudaSuccess;
+    }
+    cudaStream_t main = G->st;
+    const int nb = std::min((int)list.size(), kBranches);
+    CKE(cudaEventRecord(G->fork_ev, main));
+    for (int b = 0; b < nb; ++b) CKE(cudaStreamWaitEvent(G->side[b], G->fork_ev, 0));
+    cudaError_t err = cudaSuccess;
+    for (size_t i = 0; i < list.size() && err == cudaSuccess; ++i) {
+        G->st = G->side[i % nb];
+        err = work(list[i]);
+    }
+    G->st = main;
+    for (int b = 0; b < nb; ++b) {
+        cudaError_t e = cudaEventRecord(G->join_ev[b], G->side[b]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(main, G->join_ev[b], 0);
+        if (err == cudaSuccess) err = e;
+    }
+    return err;
+}
+
 template <typename T> struct PP;
 template <> struct PP<double> {
     static double *e(Patch &P, int i) { return P.de[i]; }
@@ -852,13 +899,19 @@ cudaError_t amr_residual(sbm_grid G, int which)
     long long off = 0;
     CKE(launch_amr_sumsq_round<T>(B.g, G->base_info, G->amr_r0, base_rhs, G->amr_part, G->st));
     off += amr_blocks(B.g);
+    std::vector<long long> offs(G->npatch + 1, 0);
+    std::vector<int> all;
     for (int a = 1; a <= G->npatch; ++a) {
+        offs[a] = off;
+        off += amr_blocks(G->P[a - 1].s);
+        all.push_back(a);
+    }
+    CKE(amr_branches(G, all, [&](int a) -> cudaError_t {
         Patch &Pt = G->P[a - 1];
         CKE(sweep_view<double>(G, Pt, kResidual, Pt.u64, Pt.f64, Pt.r64, 0.0));
         CKE(launch_amr_mask(Pt.s, Pt.info, Pt.r64, G->st));
-        CKE(launch_amr_sumsq_round<T>(Pt.s, Pt.info, Pt.r64, PP<T>::rhs(Pt), G->amr_part + off, G->st));
-        off += amr_blocks(Pt.s);
-    }
+        return launch_amr_sumsq_round<T>(Pt.s, Pt.info, Pt.r64, PP<T>::rhs(Pt), G->amr_part + offs[a], G->st);
+    }));
     return launch_norm_final(G->amr_part, (int)off, G->scal, which, G->st);
 }
 
@@ -874,36 +927,41 @@ cudaError_t amr_cycle(sbm_grid G, const sbm_opts &o, double *const *target = nul
     const int A = G->npatch;
     Level &B = G->L[G->nl - 1];
     int cur[kMaxPatch + 1] = {0};
-    // finest first (every child before its parent)
-    for (int a = A; a >= 1; --a) {
-        Patch &Pt = G->P[a - 1];
-        CKE(cudaMemsetAsync(PP<T>::e(Pt, 0), 0, patch_bytes(Pt, sizeof(T)), G->st));
-        CKE(cudaMemsetAsync(PP<T>::e(Pt, 1), 0, patch_bytes(Pt, sizeof(T)), G->st));
-        cur[a] = 0;
-        CKE(patch_smooth<T>(G, Pt, cur[a], o, o.nu1, false));
-        CKE(sweep_view<T>(G, Pt, kResidual, PP<T>::e(Pt, cur[a]), PP<T>::rhs(Pt), PP<T>::res(Pt), 0.0));
-        const int pa = Pt.parent;
-        CKE(launch_amr_restrict<T>(Pt.s, Pt.info, amr_geom(G, pa), amr_info(G, pa), PP<T>::res(Pt), amr_rhs<T>(G, pa),
-                                   G->st));
-    }
+    const std::vector<std::vector<int>> lev = amr_by_level(G);
+    // finest level first (every child before its parent); the patches of a level concurrently
+    for (int L = (int)lev.size() - 1; L >= 1; --L)
+        CKE(amr_branches(G, lev[L], [&](int a) -> cudaError_t {
+            Patch &Pt = G->P[a - 1];
+            CKE(cudaMemsetAsync(PP<T>::e(Pt, 0), 0, patch_bytes(Pt, sizeof(T)), G->st));
+            CKE(cudaMemsetAsync(PP<T>::e(Pt, 1), 0, patch_bytes(Pt, sizeof(T)), G->st));
+            cur[a] = 0;
+            CKE(patch_smooth<T>(G, Pt, cur[a], o, o.nu1, false));
+            CKE(sweep_view<T>(G, Pt, kResidual, PP<T>::e(Pt, cur[a]), PP<T>::rhs(Pt), PP<T>::res(Pt), 0.0));
+            const int pa = Pt.parent;
+            return launch_amr_restrict<T>(Pt.s, Pt.info, amr_geom(G, pa), amr_info(G, pa), PP<T>::res(Pt),
+                                          amr_rhs<T>(G, pa), G->st);
+        }));
     T *base_rhs = std::is_same<T, double>::value ? (T *)B.df : (T *)B.sf;
     CKE(cudaMemsetAsync(P<T>::u(B, 0), 0, level_bytes(B, sizeof(T)), G->st));
     int cb = 0;
     CKE(vcycle<T>(G, G->nl - 1, cb, o, base_rhs));
-    // coarsest first (every parent's final correction before its children)
-    for (int a = 1; a <= A; ++a) {
-        Patch &Pt = G->P[a - 1];
-        const int pa = Pt.parent;
-        CKE(launch_amr_ghost<T>(Pt.s, Pt.info, amr_geom(G, pa), amr_info(G, pa), PP<T>::e(Pt, cur[a]),
-                                amr_e<T>(G, pa, cur, cb), 1, G->st));
-        CKE(patch_smooth<T>(G, Pt, cur[a], o, o.nu2, true));
-    }
+    // coarsest level first (every parent's final correction before its children)
+    for (int L = 1; L < (int)lev.size(); ++L)
+        CKE(amr_branches(G, lev[L], [&](int a) -> cudaError_t {
+            Patch &Pt = G->P[a - 1];
+            const int pa = Pt.parent;
+            CKE(launch_amr_ghost<T>(Pt.s, Pt.info, amr_geom(G, pa), amr_info(G, pa), PP<T>::e(Pt, cur[a]),
+                                    amr_e<T>(G, pa, cur, cb), 1, G->st));
+            return patch_smooth<T>(G, Pt, cur[a], o, o.nu2, true);
+        }));
     // u += e on owned free dofs (target: the composite solution, or other level arrays)
     CKE(launch_amr_update<T>(B.g, G->base_info, P<T>::u(B, cb), target ? target[0] : G->amr_u0, G->st));
-    for (int a = 1; a <= A; ++a) {
+    std::vector<int> all;
+    for (int a = 1; a <= A; ++a) all.push_back(a);
+    CKE(amr_branches(G, all, [&](int a) -> cudaError_t {
         Patch &Pt = G->P[a - 1];
-        CKE(launch_amr_update<T>(Pt.s, Pt.info, PP<T>::e(Pt, cur[a]), target ? target[a] : Pt.u64, G->st));
-    }
+        return launch_amr_update<T>(Pt.s, Pt.info, PP<T>::e(Pt, cur[a]), target ? target[a] : Pt.u64, G->st);
+    }));
     if (cur_out)
         for (int a = 0; a <= A; ++a) cur_out[a] = cur[a];
     if (cb_out) *cb_out = cb;
@@ -1090,6 +1148,13 @@ sbm_status amr_alloc_adjoint(sbm_grid G)
 sbm_status amr_prepare(sbm_grid G)
 {
     amr_refresh_infos(G);
+    if (!G->side[0] && G->npatch > 1) {
+        for (int b = 0; b < kBranches; ++b) {
+            CK(cudaStreamCreateWithFlags(&G->side[b], cudaStreamNonBlocking));
+            CK(cudaEventCreateWithFlags(&G->join_ev[b], cudaEventDisableTiming));
+        }
+        CK(cudaEventCreateWithFlags(&G->fork_ev, cudaEventDisableTiming));
+    }
     for (int a = 1; a <= G->npatch; ++a) {
         Patch &Pt = G->P[a - 1];
         Pt.c64 = make_coef<double>(Pt.s.dim, Pt.h, G->mod[0], G->mod[1], G->mod[2]);
@@ -1333,6 +1398,11 @@ sbm_status sbm_grid_destroy(sbm_grid G)
     for (auto &s : G->slots)
         if (s.valid) cudaGraphExecDestroy(s.exec);
     if (G->amr_slot.valid) cudaGraphExecDestroy(G->amr_slot.exec);
+    for (int b = 0; b < kBranches; ++b) {
+        if (G->side[b]) cudaStreamDestroy(G->side[b]);
+        if (G->join_ev[b]) cudaEventDestroy(G->join_ev[b]);
+    }
+    if (G->fork_ev) cudaEventDestroy(G->fork_ev);
     for (int l = 0; l < G->nl; ++l) {
         Level &L = G->L[l];
         void *ptrs[] = {L.psi64, L.psi32, L.du[0], L.du[1], L.df, L.dr, L.su[0], L.su[1], L.sf, L.sr, L.Ke64, L.Ke32};
