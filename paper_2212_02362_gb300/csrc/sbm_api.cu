@@ -144,6 +144,8 @@ struct sbm_grid_s {
     double *amr_u0 = nullptr, *amr_r0 = nullptr;   // composite solution / residual on the base level
     double *adj[9][kMaxPatch + 1] = {};                // adjoint iteration vectors [vector][patch]
     double *top = nullptr;      // topology optimisation: psi, eta scratch, partial sums, scalars
+    double *src_sig = nullptr;  // source terms: cell stresses of the eigenstrain
+    size_t src_bytes = 0;
 };
 
 namespace {
@@ -1414,7 +1416,7 @@ sbm_status sbm_grid_destroy(sbm_grid G)
         for (double *q : vec)
             if (q) cudaFree(q);
     void *ptrs[] = {G->fsrc, G->fadj, G->psi_raw, G->rho, G->part, G->scal, G->dbad, G->A64, G->A32, G->gjtmp, G->gjbar, G->gather,
-                    G->derr, G->dgate, G->amr_part, G->amr_u0, G->amr_r0, G->dhist, G->top};
+                    G->derr, G->dgate, G->amr_part, G->amr_u0, G->amr_r0, G->dhist, G->top, G->src_sig};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (G->hscal) cudaFreeHost(G->hscal);
@@ -1977,7 +1979,19 @@ sbm_status sbm_source_terms(sbm_grid G, int level, const double *psi, const doub
     CK(cudaSetDevice(G->dev));
     const Level &L = G->L[level];
     const int n[3] = {L.g.nx, L.g.ny, L.g.nz};
-    CK(launch_source_terms(L.g.dim, n, L.h, G->mod, psi, eps0, b, t, f, G->st));
+    double *sig = nullptr;
+    if (eps0) {
+        const size_t bytes = sizeof(double) * (L.g.dim == 3 ? 6 : 3) * (size_t)ncells_h(L.g);
+        if (G->src_bytes < bytes) {
+            if (G->src_sig) cudaFree(G->src_sig);
+            G->src_sig = nullptr;
+            G->src_bytes = 0;
+            CK(gmalloc(G, (void **)&G->src_sig, bytes));
+            G->src_bytes = bytes;
+        }
+        sig = G->src_sig;
+    }
+    CK(launch_source_terms(L.g.dim, n, L.h, G->mod, psi, eps0, b, t, f, sig, G->st));
     CK(cudaStreamSynchronize(G->st));
     return SBM_OK;
 }
@@ -2171,19 +2185,20 @@ sbm_status sbm_time_kernel(sbm_grid G, int which, int reps, int flush_l2, double
     if (which == SBM_K_FMA64 || which == SBM_K_FMA32) {
         CK(cudaMalloc(&scr, 64));
     } else if (which >= SBM_K_SOURCE) {
-        const size_t n = (size_t)NC * (nv + 4) + (size_t)NN * d * 3 + 2 * TB + 8;
+        const size_t n = (size_t)NC * (2 * nv + 4) + (size_t)NN * d * 3 + 2 * TB + 8;
         CK(cudaMalloc(&scr, sizeof(double) * n));
         CK(cudaMemsetAsync(scr, 0, sizeof(double) * n, G->st));
     }
     double *s_eps = scr, *s_eta = scr + NC * nv, *s_eta2 = s_eta + NC, *s_psi = s_eta2 + NC, *s_psi2 = s_psi + NC,
            *s_b = s_psi2 + NC, *s_t = s_b + NN * d, *s_f = s_t + NN * d, *s_part = s_f + NN * d,
-           *s_scal = s_part + 2 * TB;
+           *s_scal = s_part + 2 * TB, *s_sig = s_scal + 8;
     sbm_topopt_params tp{200.0, 0.01, 0.01, 400.0, 0.0, 0.25, 1.0, 1e-4, 1e-6};
     const TopoptArgs TA = topopt_args(G, &tp, 0);
     const int nsz[3] = {L.g.nx, L.g.ny, L.g.nz};
     auto launch = [&]() -> cudaError_t {
         if (which == SBM_K_RESIDUAL64) return residual64(G, G->fsrc, mixed, 5);
-        if (which == SBM_K_SOURCE) return launch_source_terms(d, nsz, L.h, G->mod, G->psi_raw, s_eps, s_b, s_t, s_f, G->st);
+        if (which == SBM_K_SOURCE)
+            return launch_source_terms(d, nsz, L.h, G->mod, G->psi_raw, s_eps, s_b, s_t, s_f, s_sig, G->st);
         if (which == SBM_K_TOPOPT)
             return launch_topopt_step(d, TA, L.c64, s_eta, s_b, L.psi64, s_scal, s_eta2, s_psi2, s_part, G->st);
         if (which == SBM_K_FMA64 || which == SBM_K_FMA32)

@@ -283,9 +283,11 @@ cudaError_t launch_product(int mode, int dim, const int n[3], double h, const do
                            cudaStream_t s);
 // Source terms of eq. SBMLinearElasticity (k_source.cu), FP64 packed arrays: the
 // load f of K u = f from a per-cell eigenstrain (Voigt, may be null), a nodal body
-// force b and a nodal diffuse traction t (either may be null).
+// force b and a nodal diffuse traction t (either may be null).  sig: scratch for the
+// cell stresses (d(d+1)/2 doubles per cell), needed when eps0 is given.
 cudaError_t launch_source_terms(int dim, const int n[3], double h, const double mod[3], const double *psi,
-                                const double *eps0, const double *b, const double *t, double *f, cudaStream_t s);
+                                const double *eps0, const double *b, const double *t, double *f, double *sig,
+                                cudaStream_t s);
 // Phase-field topology optimisation step (k_topopt.cu): node counts, the
 // coefficients of eq. topop_evolution and the grid factors.
 struct TopoptArgs {
