@@ -401,11 +401,14 @@ sbm_status sbm_amr_solve(sbm_grid grid, double *const *u, const sbm_opts *opts, 
  * only its owned free dofs count.  Out: lambda[a] (packed like u[a]), the solution of
  * A^T lambda = dJ/du for the composite operator A (0 off the owned free dofs), by the
  * transposed correction iteration lambda += B^T (dJ/du - A^T lambda), B^T the
- * transpose of one correction cycle (damped Jacobi: opts->smoother must be
- * SBM_JACOBI; on SBM_MIXED grids its stencil products and base V-cycle run in FP32,
+ * transpose of one correction cycle with damped-Jacobi patch sweeps (weight
+ * opts->omega; on SBM_MIXED grids its stencil products and base V-cycle run in FP32,
  * A^T lambda and the vector updates in FP64), to relative residual opts->tol within
- * opts->max_cycles iterations
- * (the iteration converges at the rate of the forward one); dJdpsi[a] (the
+ * opts->max_cycles iterations (the iteration converges at the rate of the forward one).
+ * With opts->smoother = SBM_MCGS the patch sweeps of B^T stay damped Jacobi (the
+ * transpose of a colour sweep is not a colour sweep) and the base V-cycle uses the
+ * colour smoother; B^T only preconditions, the fixed point A^T lambda = dJ/du is the
+ * same; dJdpsi[a] (the
  * array or all of dJdpsi may be null): dJ/dpsi of level a's cells, packed like the
  * psi of sbm_set_psi (a = 0) / sbm_amr_set_psi (a >= 1): -lambda_c^T S_c u_c, where a
  * coarse cell under a patch passes its gradient to its 2^d fine cells and keeps

@@ -2739,7 +2739,6 @@ sbm_status sbm_amr_adjoint(sbm_grid G, double *const *u, double *const *dJdu, do
     if ((s = setup_bottom(G)) != SBM_OK) return s;
     if ((s = amr_alloc_adjoint(G)) != SBM_OK) return s;
     const int A = G->npatch;
-    if (o.smoother != SBM_JACOBI) return fail(G, SBM_ERR_ARG, "the composite adjoint needs the Jacobi smoother");
     double *const *X = G->adj[0], *const *Gv = G->adj[1], *const *R = G->adj[2], *const *Zv = G->adj[3];
     const long long launches0 = g_launches;
     CK(cudaEventRecord(G->ev0, G->st));
