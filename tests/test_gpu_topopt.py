@@ -95,30 +95,31 @@ def test_topopt_step_parity_257x129x129(built):
     assert np.isclose(vol, P.h ** 3 * ref.sum(), rtol=1e-12)
 
 
-def test_topopt_loop_matches_the_oracle_loop(built):
-    """Six steps of the staggered loop on a 49 x 25 cantilever, FP64 solves to 1e-11
-    (relative to each warm start's initial residual), against the same loop through
-    the oracle (multigrid solve to 1e-12, then the step)."""
-    P, g, f = _cantilever(2, (49, 25))
-    V0 = 0.4 * P.ncells * P.h ** 2
+@pytest.mark.parametrize("dim,n,steps,omega", [(2, (49, 25), 6, 2.0 / 3.0), (3, (25, 9, 9), 4, 0.5)])
+def test_topopt_loop_matches_the_oracle_loop(built, dim, n, steps, omega):
+    """Steps of the staggered loop on a 49 x 25 and a 25 x 9 x 9 cantilever, FP64
+    solves to 1e-11 (relative to each warm start's initial residual), against the
+    same loop through the oracle (multigrid solve to 1e-12, then the step)."""
+    P, g, f = _cantilever(dim, n)
+    V0 = 0.4 * P.ncells * P.h ** dim
     T = _otp(P, V0=V0)
     eta0 = np.clip(0.5 + 0.3 * np.sin(np.arange(P.ncells) * 0.37), 0, 1)
-    steps, psi_min = 6, 1e-6
+    psi_min = 1e-6
     eta = cuda(eta0)
     u = torch.zeros(P.ndofs, dtype=torch.float64, device="cuda")
-    res = g.topopt_run(eta, u, steps, V0=V0, psi_min=psi_min, tol=1e-11, max_cycles=300, **PRM)
+    res = g.topopt_run(eta, u, steps, V0=V0, psi_min=psi_min, tol=1e-11, max_cycles=300, omega=omega, **PRM)
     assert res["steps"] == steps
     e_ref, u_ref = eta0.copy(), np.zeros(P.ndofs)
     comps = []
     for s in range(steps):
         psi = np.maximum(oracle.psi_of_eta(T, e_ref), psi_min)
-        u_ref = oracle.mg_solve(P, psi, f, u_ref, omega=2.0 / 3.0, tol=1e-12, max_cycles=400).u
-        comps.append(P.h ** 2 * (psi * -oracle.dJdpsi(P, u_ref, u_ref)).sum())
+        u_ref = oracle.mg_solve(P, psi, f, u_ref, omega=omega, tol=1e-12, max_cycles=400).u
+        comps.append(P.h ** dim * (psi * -oracle.dJdpsi(P, u_ref, u_ref)).sum())
         e_ref = oracle.topopt_step(P, T, e_ref, u_ref, step=s)
     got = host(eta)
     assert np.abs(got - e_ref).max() <= 1e-9 * np.abs(e_ref - eta0).max()
     assert np.allclose(res["compliance"], comps, rtol=1e-9)
-    assert np.allclose(res["volume"][-1], P.h ** 2 * e_ref.sum(), rtol=1e-12)
+    assert np.allclose(res["volume"][-1], P.h ** dim * e_ref.sum(), rtol=1e-12)
     assert np.abs(host(u) - u_ref).max() <= 1e-9 * np.abs(u_ref).max()
 
 
