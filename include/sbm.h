@@ -351,6 +351,13 @@ typedef struct {
  * a sibling, a ninth child, a 65th patch), SBM_ERR_OOM when the storage cannot
  * be allocated (nothing is kept). */
 sbm_status sbm_amr_add_box(sbm_grid grid, int level, const sbm_box *box, int *index);
+/* Remove every patch of refinement level >= `level` (>= 1) and free its storage; the
+ * remaining patches are renumbered 1, 2, ... in their previous order.  The psi of the
+ * base grid and of the kept patches is restored to what was set (their cells under
+ * removed patches lose the fine means), so a later sbm_amr_regrid / sbm_amr_add_box
+ * starts from the psi of the callers.  level = 1 leaves the base grid alone.  Together
+ * with sbm_amr_regrid: regridding of an evolving psi. */
+sbm_status sbm_amr_remove_levels(sbm_grid grid, int level);
 /* Box, refinement level and parent (0: the base grid) of patch a >= 1; any output
  * pointer (host) may be NULL. */
 sbm_status sbm_amr_get_box(sbm_grid grid, int a, sbm_box *box, int *level, int *parent);

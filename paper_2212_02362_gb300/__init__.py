@@ -208,6 +208,14 @@ class Grid:
             out.append((lo, hi, a))
         return out
 
+    def amr_remove_levels(self, level: int):
+        """Drop the patches of refinement level >= level (sbm_amr_remove_levels)."""
+        self._check(lib().sbm_amr_remove_levels(self._h, level))
+        kept = [p for p in getattr(self, "patches", []) if p[2] < level]
+        self.patches = [(lo, hi, lv, i + 1) for i, (lo, hi, lv, _) in enumerate(kept)]
+        self.boxes = [(lo, hi) for lo, hi, _, _ in self.patches]
+        self.psi_version += 1
+
     def amr_set_psi(self, a: int, psi: torch.Tensor, psi_min: float):
         self._check(lib().sbm_amr_set_psi(self._h, a, _ptr(psi), psi_min))
         self.psi_version += 1

@@ -94,6 +94,7 @@ _SIGS = {
     "sbm_amr_add_box": (C.c_int, [_grid, C.c_int, C.POINTER(sbm_box), C.POINTER(C.c_int)]),
     "sbm_amr_regrid": (C.c_int, [_grid, C.c_int, C.c_double, C.c_int, C.POINTER(C.c_int)]),
     "sbm_amr_get_box": (C.c_int, [_grid, C.c_int, C.POINTER(sbm_box), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "sbm_amr_remove_levels": (C.c_int, [_grid, C.c_int]),
     "sbm_amr_set_psi": (C.c_int, [_grid, C.c_int, _dptr, C.c_double]),
     "sbm_amr_set_source": (C.c_int, [_grid, C.c_int, _dptr]),
     "sbm_amr_solve": (C.c_int, [_grid, C.POINTER(C.c_void_p), C.POINTER(sbm_opts), C.POINTER(sbm_info)]),

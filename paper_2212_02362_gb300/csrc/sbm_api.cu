@@ -71,6 +71,7 @@ struct Patch {
     double *de[2] = {nullptr, nullptr}, *drhs = nullptr, *dres = nullptr;
     float *se[2] = {nullptr, nullptr}, *srhs = nullptr, *sres = nullptr;
     float *psiv32 = nullptr;  // psi32 on the view's cells, 0 on the padding (TMA sweep input)
+    double *psi_set = nullptr;  // psi as set (floored), before coarse means of children replace cells
     CUtensorMap tm32[2][3];   // 3D: TMA maps of (se[i], srhs, psiv32) over the storage
     bool has_tm = false;
     Coef<double> c64{};
@@ -1349,7 +1350,7 @@ sbm_status amr_unpack(sbm_grid G, double *base, double *const *pat, bool residua
 void free_patch(Patch &Pt)
 {
     void *ptrs[] = {Pt.psi64, Pt.psi32, Pt.u64, Pt.f64, Pt.r64, Pt.de[0], Pt.de[1], Pt.drhs, Pt.dres,
-                    Pt.se[0], Pt.se[1], Pt.srhs, Pt.sres, Pt.psiv32, Pt.Ke64, Pt.Ke32};
+                    Pt.se[0], Pt.se[1], Pt.srhs, Pt.sres, Pt.psiv32, Pt.Ke64, Pt.Ke32, Pt.psi_set};
     for (void *p : ptrs)
         if (p) cudaFree(p);
 }
@@ -2302,6 +2303,8 @@ static sbm_status patch_alloc(sbm_grid G, int a, Patch &Pt)
     }
     CK(gmalloc(G, (void **)&Pt.psiv32, sizeof(float) * g.cs));
     CK(cudaMemset(Pt.psiv32, 0, sizeof(float) * g.cs));
+    CK(gmalloc(G, (void **)&Pt.psi_set, sizeof(double) * g.cs));
+    CK(cudaMemset(Pt.psi_set, 0, sizeof(double) * g.cs));
     if (d == 3) {
         Pt.has_tm = true;
         for (int i = 0; i < 2; ++i)
@@ -2645,6 +2648,58 @@ sbm_status sbm_amr_regrid(sbm_grid G, int level, double threshold, int grow, int
     return SBM_OK;
 }
 
+sbm_status sbm_amr_remove_levels(sbm_grid G, int level)
+{
+    if (!G) return fail(nullptr, SBM_ERR_ARG, "null grid");
+    if (level < 1) return fail(G, SBM_ERR_ARG, "level must be >= 1");
+    CK(cudaSetDevice(G->dev));
+    CK(cudaStreamSynchronize(G->st));
+    int remap[kMaxPatch + 1];
+    remap[0] = 0;
+    int w = 0;
+    for (int a = 1; a <= G->npatch; ++a) {
+        if (G->P[a - 1].level >= level) {
+            free_patch(G->P[a - 1]);
+            G->P[a - 1] = Patch();
+            remap[a] = -1;
+        } else {
+            remap[a] = ++w;
+            if (w != a) {
+                G->P[w - 1] = G->P[a - 1];
+                G->P[a - 1] = Patch();
+            }
+        }
+    }
+    for (int a = 1; a <= w; ++a) G->P[a - 1].parent = remap[G->P[a - 1].parent];   // parents are kept
+    G->npatch = w;
+    // the adjoint vectors of the patches are sized per patch: reallocated on demand
+    for (auto &vec : G->adj)
+        for (int a = 1; a <= kMaxPatch; ++a)
+            if (vec[a]) {
+                cudaFree(vec[a]);
+                vec[a] = nullptr;
+            }
+    // psi as set: the base level's from its raw input, each kept patch's from its copy
+    // (the cells a removed child had replaced by coarse means get their own values back)
+    if (G->has_psi) {
+        Level &F = G->L[G->nl - 1];
+        CK(cudaMemsetAsync(G->dbad, 0, sizeof(int), G->st));
+        if (G->density) CK(launch_set_density(F.g, G->rho, G->psi_min, G->q, F.psi64, G->dbad, G->st));
+        else CK(launch_set_psi(F.g, G->psi_raw, G->psi_min, F.psi64, G->dbad, G->st));
+        sbm_status st = finish_psi(G);
+        if (st != SBM_OK) return st;
+    }
+    for (int a = 1; a <= w; ++a) {
+        Patch &Pt = G->P[a - 1];
+        CK(cudaMemcpyAsync(Pt.psi64, Pt.psi_set, sizeof(double) * Pt.s.cs, cudaMemcpyDeviceToDevice, G->st));
+    }
+    CK(cudaStreamSynchronize(G->st));
+    G->amr_psi_dirty = true;
+    ++G->version;
+    amr_refresh_infos(G);
+    return SBM_OK;
+}
+
 sbm_status sbm_amr_get_box(sbm_grid G, int a, sbm_box *box, int *level, int *parent)
 {
     if (!G) return fail(nullptr, SBM_ERR_ARG, "null grid");
@@ -2678,6 +2733,7 @@ sbm_status sbm_amr_set_psi(sbm_grid G, int a, const double *psi, double psi_min)
     Patch &Pt = G->P[a - 1];
     CK(cudaMemsetAsync(G->dbad, 0, sizeof(int), G->st));
     CK(launch_amr_set_cells(Pt.s, psi, psi_min, Pt.psi64, G->dbad, G->st));
+    CK(cudaMemcpyAsync(Pt.psi_set, Pt.psi64, sizeof(double) * Pt.s.cs, cudaMemcpyDeviceToDevice, G->st));
     int bad = 0;
     CK(cudaMemcpyAsync(&bad, G->dbad, sizeof(int), cudaMemcpyDeviceToHost, G->st));
     CK(cudaStreamSynchronize(G->st));

@@ -134,3 +134,78 @@ def test_two_levels_3d_and_solve(built):
     r = oracle.amr_residual(Ao, ps, fs, [host(u).copy() for u in us])
     rel = np.sqrt(sum((x ** 2).sum() for x in r)) / np.sqrt(sum((x ** 2).sum() for x in r0))
     assert rel <= 2e-10, rel
+
+
+def _grid2d(n0, fn, boxes_psi=None, bcs=True):
+    n = (n0, n0, 1)
+    h0 = 1.0 / (n0 - 1)
+    g = sbm.Grid(2, n, h0)
+    g.set_moduli(sbm.SBM_CUBIC, (1.0, 0.6, 0.5))
+    if bcs:
+        g.set_bc("-y", 0, sbm.SBM_DIRICHLET, 0.0)
+        g.set_bc("-y", 1, sbm.SBM_DIRICHLET, 0.0)
+        g.set_bc("+y", 0, sbm.SBM_DIRICHLET, 0.0)
+        g.set_bc("+y", 1, sbm.SBM_DIRICHLET, 0.01)
+    g.set_psi(cuda(_cells(2, n, (0, 0, 0), h0, fn)), PSI_MIN)
+    return g
+
+
+def _patch_psi(g, a, fn):
+    lo, hi = g.patches[a - 1][0], g.patches[a - 1][1]
+    lvl = g.patches[a - 1][2]
+    h = g.h / 2 ** lvl
+    n = (hi[0] - lo[0] + 3, hi[1] - lo[1] + 3, 1)
+    return _cells(2, n, (lo[0] - 1, lo[1] - 1, 0), h, fn)
+
+
+def _solve_all(g):
+    us = [torch.zeros(2 * g.nnodes(), dtype=torch.float64, device="cuda")]
+    for lo, hi, lvl, a in g.patches:
+        us.append(torch.zeros(2 * (hi[0] - lo[0] + 3) * (hi[1] - lo[1] + 3), dtype=torch.float64, device="cuda"))
+    info = g.amr_solve(us, tol=1e-12, max_cycles=400)
+    assert info.converged
+    return [host(u) for u in us]
+
+
+def test_remove_levels_and_regrid(built):
+    """Regrid two levels and solve; remove level 2: the solution equals that of a
+    fresh grid holding the level-1 patches only; remove level 1 as well: it equals
+    the single-grid solve; regrid again after the discs moved: the oracle's boxes of
+    the new psi (the psi the removed patches had overwritten is restored)."""
+    h0 = 1.0 / 64
+    fs = [_disc(0.3, 0.3, 0.1, h0), _disc(0.7, 0.68, 0.12, h0)]
+    fn = lambda X, Y, Z: np.prod([f(X, Y, Z) for f in fs], axis=0)
+    g = _grid2d(65, fn)
+    for L in (1, 2):
+        for lo, hi, a in g.amr_regrid(L, 0.1, 2):
+            g.amr_set_psi(a, cuda(_patch_psi(g, a, fn)), PSI_MIN)
+    assert max(p[2] for p in g.patches) == 2
+    _solve_all(g)
+    g.amr_remove_levels(2)
+    assert all(p[2] == 1 for p in g.patches) and len(g.patches) >= 2
+    got = _solve_all(g)
+    fresh = _grid2d(65, fn)
+    for lo, hi, lvl, a in g.patches:
+        assert fresh.amr_add_box(1, lo, hi) == a
+        fresh.amr_set_psi(a, cuda(_patch_psi(fresh, a, fn)), PSI_MIN)
+    ref = _solve_all(fresh)
+    scale = max(np.abs(r).max() for r in ref)
+    for x, y in zip(got, ref):
+        assert np.abs(x - y).max() <= 1e-12 * scale
+    g.amr_remove_levels(1)
+    assert not g.patches
+    u = torch.zeros(2 * g.nnodes(), dtype=torch.float64, device="cuda")
+    g.solve(u, tol=1e-12, max_cycles=400)
+    single = _grid2d(65, fn)
+    u1 = torch.zeros_like(u)
+    single.solve(u1, tol=1e-12, max_cycles=400)
+    assert np.abs(host(u) - host(u1)).max() <= 1e-12 * np.abs(host(u1)).max()
+    # the discs move: new base psi, regrid against the oracle
+    ms = [_disc(0.45, 0.35, 0.1, h0), _disc(0.5, 0.75, 0.08, h0)]
+    fm = lambda X, Y, Z: np.prod([f(X, Y, Z) for f in ms], axis=0)
+    base = _cells(2, (65, 65, 1), (0, 0, 0), h0, fm)
+    g.set_psi(cuda(base), PSI_MIN)
+    got = g.amr_regrid(1, 0.1, 2)
+    P = oracle.Problem(2, (65, 65, 1), h0, 1.0, 0.6, 0.5)
+    ref = oracle.regrid_boxes(oracle.Amr(P, []), [np.maximum(base, PSI_MIN)], 1, 0.1, 2)
+    assert [(tuple(lo), tuple(hi)) for lo, hi, _ in got] == [(tuple(lo), tuple(hi)) for lo, hi, _ in ref]
