@@ -338,30 +338,24 @@ __global__ void k_bottom_assemble(const Geom g, const double *__restrict__ psi, 
     }
 }
 
-// Dirichlet dofs: identity rows and columns (their correction is zero).
+// Dirichlet dofs: identity rows and columns (their correction is zero).  One thread
+// per matrix entry (t, m): it clears entry (t, m) and (m, t) when dof t is Dirichlet.
 __global__ void k_bottom_dirichlet(const Geom g, double *A)
 {
     const long long N = (long long)g.nx * g.ny * g.nz, n = N * g.dim;
-    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (t >= n) return;
+    const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (e >= n * n) return;
+    const long long t = e / n, m = e % n;
     const int p = (int)(t / N);
     int i, j, k;
     node_of(g, t % N, i, j, k);
     if (!is_dir(g, p, i, j, k)) return;
-    for (long long m = 0; m < n; ++m) {
-        A[t * n + m] = (m == t) ? 1.0 : 0.0;
-        A[m * n + t] = (m == t) ? 1.0 : 0.0;
-    }
+    A[t * n + m] = (m == t) ? 1.0 : 0.0;
+    A[m * n + t] = (m == t) ? 1.0 : 0.0;
 }
 
-// Gauss-Jordan inversion without pivoting (SPD matrix; Dirichlet rows and
-// columns are identity and are skipped as pivots).  For pivot k with p = a_kk:
-//   a_kk <- 1/p,  a_kj <- a_kj/p,  a_ik <- -a_ik/p,  a_ij <- a_ij - a_ik a_kj/p.
-// One cooperative launch runs every pivot: the grid updates the matrix row by
-// row (block per row, threads over columns), and while doing so copies the next
-// pivot's row and column into the other half of a double buffer, so one grid
-// barrier per pivot suffices.  Every wait is bounded (on timeout bar[2] is set
-// and the kernel ends).
+// Grid barriers of the bottom-level inversion: every wait is bounded (on timeout
+// bar[2] is set and the kernel ends).
 constexpr long long kGridSpinLimit = 1LL << 22;
 
 // Grid barrier number `phase` (1, 2, ...): every block adds 1 to a counter that is
@@ -389,58 +383,119 @@ __device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned nblocks, un
     return __syncthreads_and(ok) != 0;
 }
 
-__device__ __forceinline__ int next_pivot(const Geom &g, long long N, int k, int n)
-{
-    for (; k < n; ++k) {
-        int i, j, kk;
-        node_of(g, k % N, i, j, kk);
-        if (!is_dir(g, (int)(k / N), i, j, kk)) return k;
-    }
-    return n;
-}
+// In-place inversion of the dense bottom matrix (SPD, Dirichlet rows and columns
+// replaced by the identity) by block Gauss-Jordan: pivot blocks P of kGJB consecutive
+// indices, each pass
+//     A_PP <- A_PP^-1,  A_PQ <- A_PP^-1 A_PQ,  A_QP <- -A_QP A_PP^-1,
+//     A_QQ <- A_QQ - A_QP A_PP^-1 A_PQ          (Q = the other indices),
+// after the last pass A holds the inverse.  The principal blocks of an SPD matrix are
+// SPD, so no pivoting is needed.  One cooperative launch; each block owns rows
+// i = blockIdx.x + m gridDim.x; the pivot rows and columns of the next pass are
+// written to a double-buffered exchange area during the current pass, so one grid
+// barrier per pass (ceil(n / kGJB) of them) orders the passes.
+constexpr int kGJB = 16;
 
 __global__ void k_gauss_jordan(const Geom g, int n, double *A, double *tmp, unsigned *bar, int in_smem,
                                long long limit)
 {
-    // in_smem: the block's rows (blockIdx.x + m gridDim.x) live in shared memory
-    extern __shared__ double srow[];
-    const long long N = (long long)g.nx * g.ny * g.nz;
+    (void)g;
+    // dynamic shared memory: the kGJB pivot rows of the current pass (rs; in_smem bit 1,
+    // else they are read from the exchange buffer in L2), then, when in_smem bit 0, the
+    // block's rows (blockIdx.x + m gridDim.x)
+    extern __shared__ double smem_gj[];
+    const bool piv_smem = (in_smem & 2) != 0;
+    in_smem &= 1;
+    double *srow = smem_gj + (piv_smem ? (long long)kGJB * n : 0);
+    __shared__ double Pinv[kGJB][kGJB + 1];
+    __shared__ double mrow[kGJB];
     const unsigned nb = gridDim.x;
+    const long long xb = 2LL * kGJB * n;          // one exchange buffer: kGJB rows + kGJB columns
     if (in_smem)
         for (int i = blockIdx.x, m = 0; i < n; i += gridDim.x, ++m)
             for (int j = threadIdx.x; j < n; j += blockDim.x) srow[(long long)m * n + j] = A[(long long)i * n + j];
-    // tmp[b * 2n + j]: row of the pivot; tmp[b * 2n + n + i]: its column (both unscaled)
-    int k = next_pivot(g, N, 0, n);
-    if (k >= n) return;
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
-        tmp[t] = A[(long long)k * n + t];
-        tmp[n + t] = A[(long long)t * n + k];
+    // buffer 0 <- pivot rows R[r][j] = A[r][j] and columns C[i][r] = A[i][r] of block 0
+    {
+        const int b0 = min(kGJB, n);
+        for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < (long long)b0 * n;
+             t += (long long)gridDim.x * blockDim.x) {
+            const int r = (int)(t / n), j = (int)(t % n);
+            tmp[(long long)r * n + j] = A[(long long)r * n + j];
+            tmp[(long long)kGJB * n + (long long)j * kGJB + r] = A[(long long)j * n + r];
+        }
     }
     unsigned phase = 1;
     if (!grid_barrier(bar, nb, phase++, limit)) return;
     int cur = 0;
-    while (k < n) {
-        const int kn = next_pivot(g, N, k + 1, n);
-        const double *R = tmp + (long long)cur * 2 * n, *Cc = R + n;
-        double *Rn = tmp + (long long)(1 - cur) * 2 * n, *Cn = Rn + n;
-        // the pivot row and column were written by other blocks: read them from L2
-        const double ip = 1.0 / __ldcg(R + k);
-        for (int i = blockIdx.x, r = 0; i < n; i += gridDim.x, ++r) {
-            double *row = in_smem ? srow + (long long)r * n : A + (long long)i * n;
-            const double m = __ldcg(Cc + i);
-            for (int j = threadIdx.x; j < n; j += blockDim.x) {
-                const double rkj = (j == k) ? ip : __ldcg(R + j) * ip;
-                double v;
-                if (i == k) v = rkj;
-                else v = ((j == k) ? 0.0 : row[j]) - m * rkj;
-                row[j] = v;
-                if (i == kn) Rn[j] = v;
-                if (j == kn) Cn[i] = v;
+    for (int k0 = 0; k0 < n; k0 += kGJB) {
+        const int b = min(kGJB, n - k0);
+        const int k1 = k0 + kGJB, bn = min(kGJB, n - k1);      // the next pivot block (bn <= 0: none)
+        const double *R = tmp + cur * xb, *Cc = R + (long long)kGJB * n;
+        double *Rn = tmp + (1 - cur) * xb, *Cn = Rn + (long long)kGJB * n;
+        // Pinv = inverse of the pivot block (Gauss-Jordan on kGJB x kGJB in shared memory,
+        // one element per thread); the pivot rows were written by other blocks: read them
+        // from L2 into shared memory once per pass
+        for (int t = threadIdx.x; t < kGJB * kGJB; t += blockDim.x) {
+            const int r = t / kGJB, c = t % kGJB;
+            Pinv[r][c] = (r < b && c < b) ? __ldcg(R + (long long)r * n + k0 + c) : (r == c ? 1.0 : 0.0);
+        }
+        if (piv_smem)
+            for (int t = threadIdx.x; t < b * n; t += blockDim.x) smem_gj[t] = __ldcg(R + t);
+        // the exchange buffers alternate between passes: reads of them bypass L1
+        auto rget = [&](long long idx) -> double { return piv_smem ? smem_gj[idx] : __ldcg(R + idx); };
+        __syncthreads();
+        for (int q = 0; q < kGJB; ++q) {
+            double v = 0.0;
+            const int t = threadIdx.x, r = t / kGJB, c = t % kGJB;
+            if (t < kGJB * kGJB) {
+                const double ip = 1.0 / Pinv[q][q];
+                const double pqc = (c == q) ? ip : Pinv[q][c] * ip;
+                v = (r == q) ? pqc : ((c == q) ? 0.0 : Pinv[r][c]) - Pinv[r][q] * pqc;
             }
+            __syncthreads();
+            if (t < kGJB * kGJB) Pinv[r][c] = v;
+            __syncthreads();
+        }
+        for (int i = blockIdx.x, ri = 0; i < n; i += gridDim.x, ++ri) {
+            double *row = in_smem ? srow + (long long)ri * n : A + (long long)i * n;
+            const bool inP = i >= k0 && i < k0 + b;
+            // m_i = A_iP Pinv (rows outside P), or the row of Pinv (rows inside P)
+            if (threadIdx.x < kGJB) {
+                const int c = threadIdx.x;
+                double acc = 0.0;
+                if (inP) {
+                    acc = Pinv[i - k0][c];
+                } else {
+                    for (int r = 0; r < b; ++r) acc += __ldcg(Cc + (long long)i * kGJB + r) * Pinv[r][c];
+                }
+                mrow[c] = (c < b) ? acc : 0.0;
+            }
+            __syncthreads();
+            for (int j = threadIdx.x; j < n; j += blockDim.x) {
+                const bool jP = j >= k0 && j < k0 + b;
+                double v;
+                if (inP) {
+                    if (jP) {
+                        v = Pinv[i - k0][j - k0];
+                    } else {
+                        v = 0.0;
+                        for (int c = 0; c < b; ++c) v += mrow[c] * rget((long long)c * n + j);
+                    }
+                } else {
+                    if (jP) {
+                        v = -mrow[j - k0];
+                    } else {
+                        v = row[j];
+                        for (int c = 0; c < b; ++c) v -= mrow[c] * rget((long long)c * n + j);
+                    }
+                }
+                row[j] = v;
+                if (bn > 0 && i >= k1 && i < k1 + bn) Rn[(long long)(i - k1) * n + j] = v;
+                if (bn > 0 && j >= k1 && j < k1 + bn) Cn[(long long)i * kGJB + (j - k1)] = v;
+            }
+            __syncthreads();
         }
         if (!grid_barrier(bar, nb, phase++, limit)) return;
         cur ^= 1;
-        k = kn;
     }
     if (in_smem)
         for (int i = blockIdx.x, m = 0; i < n; i += gridDim.x, ++m)
@@ -654,7 +709,7 @@ cudaError_t launch_inner_gate(const double *part, int nparts, const double *scal
 cudaError_t launch_bottom_assemble(const Geom &g, const double *psi, const Coef<double> &c, double *A, cudaStream_t s)
 {
     const long long n = (long long)g.nx * g.ny * g.nz * g.dim;
-    k_bottom_assemble<<<nblk(n, 128), 128, 0, s>>>(g, psi, c, A);
+    k_bottom_assemble<<<nblk(n, 32), 32, 0, s>>>(g, psi, c, A);      // a column per thread, spread over SMs
     ++g_launches;
     return cudaGetLastError();
 }
@@ -662,7 +717,7 @@ cudaError_t launch_bottom_assemble(const Geom &g, const double *psi, const Coef<
 cudaError_t launch_bottom_dirichlet(const Geom &g, double *A, cudaStream_t s)
 {
     const long long n = (long long)g.nx * g.ny * g.nz * g.dim;
-    k_bottom_dirichlet<<<nblk(n), kThreads, 0, s>>>(g, A);
+    k_bottom_dirichlet<<<nblk((long long)n * n), kThreads, 0, s>>>(g, A);
     ++g_launches;
     return cudaGetLastError();
 }
@@ -679,8 +734,11 @@ cudaError_t launch_gauss_jordan(const Geom &g, int n, double *A, double *tmp, un
     if (nblocks > n) nblocks = n;
     // the rows of each block in shared memory when they fit
     const size_t rows_bytes = (size_t)((n + nblocks - 1) / nblocks) * n * sizeof(double);
-    int in_smem = rows_bytes <= 160 * 1024 ? 1 : 0;
-    const size_t smem = in_smem ? rows_bytes : 0;
+    const size_t pivot_bytes = (size_t)kGJB * n * sizeof(double);
+    const bool piv = pivot_bytes <= 160 * 1024;                 // the pivot rows in shared memory
+    const bool rows = (piv ? pivot_bytes : 0) + rows_bytes <= 200 * 1024;
+    int in_smem = (rows ? 1 : 0) | (piv ? 2 : 0);
+    const size_t smem = (piv ? pivot_bytes : 0) + (rows ? rows_bytes : 0);
     if (smem > 48 * 1024) {
         e = cudaFuncSetAttribute(k_gauss_jordan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;

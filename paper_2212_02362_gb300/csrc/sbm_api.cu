@@ -1525,7 +1525,7 @@ static sbm_status grid_create_impl(const sbm_grid_desc *d, sbm_grid G)
     G->nb = (int)(nnodes(B.g) * B.g.dim);
     CK(gmalloc(G, (void **)&G->A64, sizeof(double) * G->nb * G->nb));
     CK(gmalloc(G, (void **)&G->A32, sizeof(float) * G->nb * G->nb));
-    CK(gmalloc(G, (void **)&G->gjtmp, sizeof(double) * 4 * G->nb));
+    CK(gmalloc(G, (void **)&G->gjtmp, sizeof(double) * 4 * 16 * G->nb));   // 2 buffers x (16 rows + 16 columns)
     CK(gmalloc(G, (void **)&G->gjbar, sizeof(unsigned) * 4));
     CK(gmalloc(G, (void **)&G->gather, sizeof(int) * G->nb));
     {
