@@ -531,6 +531,72 @@ def run_ours(args, rank, world, local_rank):
         dist.destroy_process_group()
 
 
+def patch_smoother_roofline(wk, psi_h, precision, dev, stream, local_rank):
+    """Roofline of a composite solve's dominant kernel: one smoother sweep (the fused
+    2D colour Gauss-Seidel sweep, or the 3D Jacobi sweep) on the largest patch of the
+    finest level, timed by sbm_time_kernel on a grid with that patch's storage extents,
+    psi and spacing, every face fixed as on an interior patch view (same kernel, same
+    tiles), each launch after an L2 flush."""
+    import torch
+    import ctypes as C
+    import paper_2212_02362_gb300 as sbm
+    from paper_2212_02362_gb300 import _capi
+    nl = len(wk.boxes) + 1
+    lmax = max(wk.level(a) for a in range(1, nl))
+    a = max((a for a in range(1, nl) if wk.level(a) == lmax), key=lambda a: psi_h[a].numel())
+
+    def mg_extent(m):
+        # smallest c 2^k + 1 >= m nodes with 4 <= c <= 8: coarsens to a small dense bottom level
+        k = 0
+        while -(-(m - 1) // (1 << k)) > 8:
+            k += 1
+        return max(4, -(-(m - 1) // (1 << k))) * (1 << k) + 1
+
+    ns = wk.storage_shape(a)
+    n = tuple(mg_extent(ns[ax]) if ax < wk.dim else 1 for ax in range(3))
+    h, o = wk.level_h(a), wk.origin(a)
+    ncz = n[2] - 1 if wk.dim == 3 else 1
+    k_, j_, i_ = np.meshgrid(np.arange(ncz), np.arange(n[1] - 1), np.arange(n[0] - 1), indexing="ij")
+    X, Y = (i_ + o[0] + 0.5) * h, (j_ + o[1] + 0.5) * h
+    Z = (k_ + o[2] + 0.5) * h if wk.dim == 3 else np.zeros(X.shape)
+    psi_t = torch.from_numpy(np.ascontiguousarray(wk.psi_fn(X, Y, Z).reshape(-1), dtype=np.float64))
+    g = sbm.Grid(wk.dim, n, h, precision=precision, device=local_rank, stream=stream.cuda_stream)
+    g.set_moduli(sbm.SBM_CUBIC, wk.moduli)
+    faces = ("-x", "+x", "-y", "+y") + (("-z", "+z") if wk.dim == 3 else ())
+    for face in faces:
+        for comp in range(wk.dim):
+            g.set_bc(face, comp, sbm.SBM_DIRICHLET, 0.0)
+    gs = wk.smoother == "gs"
+    kid = _capi.SBM_K_GS if gs else _capi.SBM_K_JACOBI
+    ms, by, fl = C.c_double(), C.c_double(), C.c_double()
+    m64, f64 = C.c_double(), C.c_double()
+    with torch.cuda.stream(stream):
+        g.set_psi(psi_t.to(dev), wk.psi_min)
+        _capi.check(sbm.lib().sbm_time_kernel(g._h, kid, 20, 1, C.byref(ms), C.byref(by), C.byref(fl)), g._h)
+        _capi.check(sbm.lib().sbm_time_kernel(g._h, _capi.SBM_K_FMA64, 5, 0, C.byref(m64), None, C.byref(f64)), g._h)
+    hbm_peak, peak_kind = peaks()
+    gbs = by.value / (ms.value * 1e-3) / 1e9
+    gf = fl.value / (ms.value * 1e-3) / 1e9
+    fp64_rate = f64.value / (m64.value * 1e-3) / 1e9
+    nodes = int(np.prod(n))
+    where = (f"patch {a} (level {lmax}, {'x'.join(str(v) for v in ns[:wk.dim])} storage nodes) as a "
+             f"{'x'.join(str(v) for v in n[:wk.dim])} grid at its spacing and origin")
+    if gs and precision == "fp64":
+        roof = {"bound": "alu", "kernel": f"k_gs2_tile<double> (2D colour Gauss-Seidel sweep, one launch), {where}",
+                "achieved": gf, "peak": fp64_rate, "unit": "GFLOP/s", "frac": gf / fp64_rate,
+                "peak_kind": "measured FP64 multiply-add rate (register-only probe)",
+                "achieved_gbs": gbs, "frac_hbm": gbs / hbm_peak}
+    else:
+        name = "k_gs2_tile" if gs else ("k_sweep3_f2<Jacobi>" if wk.dim == 3 and precision == "mixed" else "sweep")
+        roof = {"bound": "hbm", "kernel": f"{name} (smoother sweep), {where}", "achieved": gbs, "peak": hbm_peak,
+                "unit": "GB/s", "frac": gbs / hbm_peak, "peak_kind": f"{peak_kind} (copy bandwidth)",
+                "gflops": gf, "frac_fp64_measured": gf / fp64_rate}
+    roof.update({"algorithmic_bytes": by.value, "algorithmic_flops": fl.value, "ms_per_launch": ms.value,
+                 "nodes": nodes, "traffic": None})
+    del g
+    return roof
+
+
 def run_amr(args, rank, world, local_rank):
     """Composite (block-structured refinement) solves: one step = one solve of the
     composite problem from the initial guess to relres 1e-10."""
@@ -660,6 +726,7 @@ def run_amr(args, rank, world, local_rank):
     if sampler:
         sampler.stop()
         clocks = sampler.summary(t_wall0, t_wall1)
+    roof = patch_smoother_roofline(wk, psi_h, precision, dev, stream, local_rank) if rank == 0 else None
     if rank == 0:
         cyc = infos[-1].cycles
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -676,7 +743,7 @@ def run_amr(args, rank, world, local_rank):
                            "l2": "flushed between timed steps (256 MB write, then 256 MB read of a second buffer)"},
                 "cycles_to_tol": cyc, "correction_cycles_to_tol": infos[-1].vcycles,
                 "cycles_per_s": cyc / (ms_per_step / 1e3), "fp64_solve": fp64,
-                "roofline": None, "cpu_baseline": None, "adjoint": adjoint,
+                "roofline": roof, "cpu_baseline": None, "adjoint": adjoint,
                 "e2e": {"value": world * unknowns / (statistics.mean(e2e_ms) / 1e3) / 1e6, "unit": UNIT,
                         "h2d_bytes_per_step": sum(t.numel() * 8 for t in psi_h + u0_h),
                         "d2h_bytes_per_step": sum(t.numel() * 8 for t in out_h)},

@@ -294,7 +294,7 @@ sbm_status sbm_set_wait_limit(sbm_grid grid, long long spins);
 
 /* ---- measurement ---- */
 enum { SBM_K_RESIDUAL64 = 0, SBM_K_JACOBI = 1, SBM_K_RESIDUAL = 2, SBM_K_SOURCE = 3, SBM_K_TOPOPT = 4,
-       SBM_K_FMA64 = 5, SBM_K_FMA32 = 6 };
+       SBM_K_FMA64 = 5, SBM_K_FMA32 = 6, SBM_K_GS = 7 };
 /* Launch one hot-path kernel of the finest level `reps` times back to back on
  * the grid stream between two CUDA events (after one untimed launch) and report
  * the mean duration per launch (host, ms), together with the algorithmic DRAM
@@ -310,6 +310,9 @@ enum { SBM_K_RESIDUAL64 = 0, SBM_K_JACOBI = 1, SBM_K_RESIDUAL = 2, SBM_K_SOURCE 
  *   SBM_K_FMA64/32    a register-only multiply-add probe on every SM (8 independent
  *                     chains per thread, 8 blocks of 256 threads per SM): the measured
  *                     FP64 / FP32 rate that ALU-bound kernels are compared with (bytes 0)
+ *   SBM_K_GS          one 2^d-colour Gauss-Seidel sweep (all colours, one launch) in the
+ *                     V-cycle precision; 2D grids only (SBM_ERR_ARG otherwise); flops 190
+ *                     per node (the row of K formed from the unit-psi cell matrix)
  * Bytes count one read of u, f and psi and one write of the output per node;
  * flops count the sum-factorised cell arithmetic per cell plus the per-node
  * gather and update.  flush_l2 != 0: before every launch a 256 MB scratch buffer

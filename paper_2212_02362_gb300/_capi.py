@@ -16,7 +16,7 @@ SBM_FP64, SBM_MIXED = 0, 1
 SBM_JACOBI, SBM_MCGS = 0, 1
 SBM_CUBIC, SBM_ISO_LAME, SBM_ISO_ENU = 0, 1, 2
 SBM_FREE, SBM_DIRICHLET, SBM_DIRICHLET_FROM_U = 0, 1, 2
-SBM_K_RESIDUAL64, SBM_K_JACOBI, SBM_K_RESIDUAL, SBM_K_SOURCE, SBM_K_TOPOPT, SBM_K_FMA64, SBM_K_FMA32 = range(7)
+SBM_K_RESIDUAL64, SBM_K_JACOBI, SBM_K_RESIDUAL, SBM_K_SOURCE, SBM_K_TOPOPT, SBM_K_FMA64, SBM_K_FMA32, SBM_K_GS = range(8)
 SBM_NOALLOC_MAX_BLOCKS = 16384
 
 

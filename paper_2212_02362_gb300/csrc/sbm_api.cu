@@ -320,7 +320,11 @@ cudaError_t smooth(sbm_grid G, int l, int &cur, const sbm_opts &o, int nsweeps, 
     Level &L = G->L[l];
     const int ncol = 1 << L.g.dim;
     for (int s = 0; s < nsweeps; ++s) {
-        if (o.smoother == SBM_MCGS) {
+        if (o.smoother == SBM_MCGS && L.g.dim == 2) {
+            CKE(launch_gs2_sweep<T>(L.g, P<T>::psi(L), P<T>::Ke(L), f, P<T>::u(L, cur), P<T>::u(L, 1 - cur),
+                                    descending ? 1 : 0, G->st, G->cur_gate));
+            cur ^= 1;
+        } else if (o.smoother == SBM_MCGS) {
             for (int c = 0; c < ncol; ++c)
                 CKE(launch_gs<T>(L.g, P<T>::psi(L), P<T>::Ke(L), f, P<T>::u(L, cur), descending ? ncol - 1 - c : c, G->st,
                                  G->cur_gate));
@@ -858,7 +862,11 @@ cudaError_t patch_smooth(sbm_grid G, Patch &Pt, int &cur, const sbm_opts &o, int
 {
     const int ncol = 1 << Pt.v.dim;
     for (int s = 0; s < n; ++s) {
-        if (o.smoother == SBM_MCGS) {
+        if (o.smoother == SBM_MCGS && Pt.v.dim == 2) {
+            CKE(launch_gs2_sweep<T>(Pt.v, PP<T>::psi(Pt) + Pt.voff, PP<T>::Ke(Pt), PP<T>::rhs(Pt) + Pt.voff,
+                                    PP<T>::e(Pt, cur) + Pt.voff, PP<T>::e(Pt, 1 - cur) + Pt.voff, desc ? 1 : 0, G->st));
+            cur ^= 1;
+        } else if (o.smoother == SBM_MCGS) {
             for (int c = 0; c < ncol; ++c)
                 CKE(launch_gs<T>(Pt.v, PP<T>::psi(Pt) + Pt.voff, PP<T>::Ke(Pt), PP<T>::rhs(Pt) + Pt.voff,
                                  PP<T>::e(Pt, cur) + Pt.voff, desc ? ncol - 1 - c : c, G->st));
@@ -2160,7 +2168,8 @@ sbm_status sbm_time_kernel(sbm_grid G, int which, int reps, int flush_l2, double
 {
     sbm_status s = check_ready(G);
     if (s != SBM_OK) return s;
-    if (which < SBM_K_RESIDUAL64 || which > SBM_K_FMA32 || reps < 1) return fail(G, SBM_ERR_ARG, "bad kernel id or reps");
+    if (which < SBM_K_RESIDUAL64 || which > SBM_K_GS || reps < 1) return fail(G, SBM_ERR_ARG, "bad kernel id or reps");
+    if (which == SBM_K_GS && G->desc.dim != 2) return fail(G, SBM_ERR_ARG, "SBM_K_GS times the 2D colour sweep");
     CK(cudaSetDevice(G->dev));
     const int fine = G->nl - 1;
     Level &L = G->L[fine];
@@ -2208,7 +2217,8 @@ sbm_status sbm_time_kernel(sbm_grid G, int which, int reps, int flush_l2, double
         sbm_opts o;
         sbm_default_opts(&o);
         o.nu1 = 1;
-        if (which == SBM_K_JACOBI) {
+        if (which == SBM_K_GS) o.smoother = SBM_MCGS;
+        if (which == SBM_K_JACOBI || which == SBM_K_GS) {
             if (mixed) return smooth<float>(G, fine, cur, o, 1, false, L.sf);
             return smooth<double>(G, fine, cur, o, 1, false, L.df);
         }
@@ -2274,6 +2284,11 @@ sbm_status sbm_time_kernel(sbm_grid G, int which, int reps, int flush_l2, double
     if (which == SBM_K_RESIDUAL64) per_node = mixed ? (8.0 * d + 8.0 * d + 8.0 + 4.0 * d) : (8.0 * (3 * d + 1));
     else per_node = (mixed ? 4.0 : 8.0) * (3 * d + 1);
     if (bytes) *bytes = per_node * nn;
+    if (which == SBM_K_GS) {
+        // per relaxed node: 4 cells x (16 + 2 + 4) multiply-adds, then the 2-component update
+        if (flops) *flops = 190.0 * nn;
+        return SBM_OK;
+    }
     if (flops) *flops = cellf * nc + (which == SBM_K_JACOBI ? nodef : nodef - 11.0) * nn;
     return SBM_OK;
 }

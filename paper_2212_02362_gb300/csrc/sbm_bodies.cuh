@@ -34,6 +34,31 @@ __device__ __forceinline__ void finalize(const SweepArgs<T, TO> &a, int gx, int 
     }
 }
 
+// finalize with the node's right-hand side already loaded (fv[p] = f[p] at the node).
+template <typename T, typename TO, int MODE>
+__device__ __forceinline__ void finalize_f(const SweepArgs<T, TO> &a, int gx, int gy, int gz, const T *Ku,
+                                           T psisum, const T *uval, const T *fv, double &ssq)
+{
+    const Geom &g = a.g;
+    const long long o = gidx(g, gx, gy, gz);
+    if (MODE == kJacobi) {
+        const T ip = T(1) / psisum;
+        for (int p = 0; p < g.dim; ++p) {
+            T v = uval[p];
+            if (!is_dir(g, p, gx, gy, gz)) v += (fv[p] - Ku[p]) * ip * a.wk[p];
+            a.out[p * g.cs + o] = TO(v);
+        }
+    } else if (MODE == kResidual) {
+        for (int p = 0; p < g.dim; ++p) {
+            T r = is_dir(g, p, gx, gy, gz) ? T(0) : fv[p] - Ku[p];
+            a.out[p * g.cs + o] = TO(r);
+            ssq += double(r) * double(r);
+        }
+    } else {
+        for (int p = 0; p < g.dim; ++p) a.out[p * g.cs + o] = TO(Ku[p]);
+    }
+}
+
 // Small 3D levels (FP32), one cell of a node's eight: thread c of the node's group
 // of eight evaluates the cell of which node (i, j, k) is corner c (bit m = the
 // node's offset along axis m within the cell) and returns the force on that

@@ -190,6 +190,12 @@ template <typename T>
 cudaError_t launch_gs(const Geom &g, const T *psi, const T *Ke, const T *f, T *u, int colour,
                       cudaStream_t s, const int *gate = nullptr);
 
+// One 2D colour Gauss-Seidel sweep (all four colours, ascending or descending) in one
+// launch, reading uin and writing every node of the grid to uout (uout != uin).
+template <typename T>
+cudaError_t launch_gs2_sweep(const Geom &g, const T *psi, const T *Ke, const T *f, const T *uin, T *uout,
+                             int descending, cudaStream_t s, const int *gate = nullptr);
+
 template <typename T>
 cudaError_t launch_restrict(const Geom &gf, const Geom &gc, const T *rf, T *fc, cudaStream_t s,
                             const int *gate = nullptr, T *zero_uc = nullptr);

@@ -85,3 +85,19 @@ def test_noalloc_argument_checks_run_on_the_host(libpath):
     # beyond the fixed scratch: rejected before the device is touched
     assert call(2, (4097, 4097, 1), 1.0 / 4096, (1.0, 0.6, 0.5)) == _capi.SBM_ERR_ARG
     assert b"fixed scratch" in lib.sbm_last_error(None)
+
+
+def test_enum_constants_match_header():
+    """Every `NAME = value` of the header's enums has the same value in the binding."""
+    from paper_2212_02362_gb300 import _capi
+    consts = {}
+    for hdr in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = re.sub(r"/\*.*?\*/", "", open(hdr).read(), flags=re.S)
+        for body in re.findall(r"enum\s*\w*\s*\{(.*?)\}", text, flags=re.S):
+            for name, val in re.findall(r"\b(SBM_[A-Z0-9_]+)\s*=\s*(-?\d+)", body):
+                consts[name] = int(val)
+    assert "SBM_K_GS" in consts
+    for name, val in consts.items():
+        if hasattr(_capi, name):
+            assert getattr(_capi, name) == val, name
+    assert all(hasattr(_capi, n) for n in consts if n.startswith("SBM_K_")), consts

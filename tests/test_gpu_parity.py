@@ -27,6 +27,7 @@ import paper_2212_02362_gb300 as sbm  # noqa: E402
 CASES = {
     "plate65": lambda: W.plate_hole(65),
     "ragged2d": lambda: random_workload(2, (73, 45), 101),
+    "wide2d": lambda: random_workload(2, (161, 99), 103),
     "damage33": lambda: W.damage3d(33),
     "ragged3d": lambda: random_workload(3, (73, 45, 21), 202),
     # large enough for the warp-specialised FP32 kernel: ragged x tile (97 = 3 x 31 + 4),
@@ -118,6 +119,29 @@ def test_colour_gs_sweep_parity(built, case, descending):
     ref = oracle.gs_sweep(P, _floored(wk), wk.f, u, descending)
     got = host(g.smooth(g.finest, cuda(wk.f), cuda(u), "gs", descending=descending))
     assert _rel(got - u, ref - u) <= 1e-11
+
+
+@pytest.mark.parametrize("case", ["plate65", "ragged2d", "wide2d"])
+@pytest.mark.parametrize("descending", [False, True])
+@pytest.mark.parametrize("fp32", [False, True])
+def test_colour_gs_sweep_every_level(built, case, descending, fp32):
+    """The one-launch 2D colour sweep (32 x 32 tiles, four-node halo) on every level of
+    the hierarchy: levels of several tiles with ragged edges down to levels smaller
+    than one tile, against the oracle's sequential colour sweep."""
+    wk = CASES[case]()
+    g = gpu_grid(wk)
+    probs, psis = _level_problems(wk)
+    assert g.nlevels == len(probs)
+    for l in range(g.nlevels):
+        P = probs[l]
+        f = W.uniform(30 + l, P.ndofs, -1, 1) * ~oracle.dirichlet_mask(P)
+        u = W.uniform(50 + l, P.ndofs, -1e-1, 1e-1)
+        ref = oracle.gs_sweep(P, psis[l], f, u, descending)
+        got = host(g.smooth(l, cuda(f), cuda(u), "gs", descending=descending, fp32=fp32))
+        assert _rel(got - u, ref - u) <= (1e-4 if fp32 else 1e-11), l
+        # Dirichlet dofs keep their values exactly
+        mask = oracle.dirichlet_mask(P)
+        assert np.array_equal(got[mask], u[mask]) if not fp32 else np.allclose(got[mask], u[mask], rtol=1e-7)
 
 
 @pytest.mark.parametrize("case", ["plate65", "ragged2d", "damage33", "ragged3d"])
