@@ -100,29 +100,6 @@ __device__ __forceinline__ bool thread_node(const Geom &s, const AmrInfo &L, int
     return true;
 }
 
-// Value of a parent-level field at child global coordinates g (linear
-// interpolation; coincident nodes copy); 0 outside the parent's storage.
-template <typename T>
-__device__ __forceinline__ T parent_interp(const Geom &sp, const AmrInfo &Lp, const T *up, int p, const int g[3])
-{
-    T s = T(0);
-    int nodd = 0;
-    for (int ax = 0; ax < Lp.dim; ++ax) nodd += g[ax] & 1;
-    for (int c = 0; c < (1 << Lp.dim); ++c) {
-        int l[3] = {0, 0, 0};
-        bool skip = false;
-        for (int ax = 0; ax < Lp.dim; ++ax) {
-            const int bit = (c >> ax) & 1;
-            if (!(g[ax] & 1) && bit) skip = true;
-            l[ax] = (g[ax] >> 1) + ((g[ax] & 1) ? bit : 0) - Lp.org[ax];
-        }
-        if (skip) continue;
-        if (l[0] < 0 || l[1] < 0 || l[2] < 0 || l[0] >= sp.nx || l[1] >= sp.ny || l[2] >= sp.nz) continue;
-        s += up[p * sp.cs + gidx(sp, l[0], l[1], l[2])];
-    }
-    return s * (T(1) / T(1 << nodd));
-}
-
 __global__ void k_amr_mask(const Geom s, const AmrInfo L, double *r)
 {
     int i, j, k, g[3];
@@ -177,19 +154,84 @@ __global__ void k_amr_view_cells(const Geom s, const float *src, float *dst)
 // mode 0: ghosts <- interpolated parent values (owned/active nodes untouched).
 // mode 1: correction prolongation: nodes solved on this level (inside the box or
 //         on a domain face) += interpolated parent correction; ghosts <- it.
-template <typename T>
+// One thread per parent cell B (global parent coordinates): the 2^d corners B + c
+// are loaded once (0 outside the parent's storage) and the child nodes 2B + delta,
+// delta in {0,1}^d, of the child's storage are written; a child node's value is the
+// sum of its corners (corner 0 on even axes, both on odd ones, ascending order)
+// times 2^-(odd axes).  In mode 0 a block whose child nodes are all solved returns
+// before loading.
+template <typename T, int D>
 __global__ void k_amr_ghost(const Geom sc, const AmrInfo Lc, const Geom sp, const AmrInfo Lp, T *uc, const T *up,
-                            int mode)
+                            int mode, int3 b0, int3 nb)
 {
-    int i, j, k, g[3];
-    if (!thread_node(sc, Lc, i, j, k, g)) return;
-    const long long o = gidx(sc, i, j, k);
-    const bool solved = axes_owned(Lc, g);
-    const bool in = inside_domain(Lc, g);
-    for (int p = 0; p < Lc.dim; ++p) {
-        const T v = in ? parent_interp<T>(sp, Lp, up, p, g) : T(0);
-        if (!solved) uc[p * sc.cs + o] = v;
-        else if (mode == 1 && !domain_dirichlet(Lc, g, p)) uc[p * sc.cs + o] += v;
+    const int bx = blockIdx.x * blockDim.x + threadIdx.x, by = blockIdx.y * blockDim.y + threadIdx.y,
+              bz = blockIdx.z * blockDim.z + threadIdx.z;
+    if (bx >= nb.x || by >= nb.y || bz >= nb.z) return;
+    const int B[3] = {b0.x + bx, b0.y + by, b0.z + bz};
+    const int sn[3] = {sp.nx, sp.ny, sp.nz}, cn[3] = {sc.nx, sc.ny, sc.nz};
+    if (mode != 1) {
+        bool all_solved = true;
+#pragma unroll
+        for (int d = 0; d < (1 << D); ++d) {
+            const int g[3] = {2 * B[0] + (d & 1), 2 * B[1] + ((d >> 1) & 1), D == 3 ? 2 * B[2] + (d >> 2) : 0};
+            if (!axes_owned(Lc, g)) all_solved = false;
+        }
+        if (all_solved) return;
+    }
+    T v[1 << D][D];
+#pragma unroll
+    for (int c = 0; c < (1 << D); ++c) {
+        const int l[3] = {B[0] + (c & 1) - Lp.org[0], B[1] + ((c >> 1) & 1) - Lp.org[1],
+                          D == 3 ? B[2] + (c >> 2) - Lp.org[2] : 0};
+        bool in = true;
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax)
+            if (l[ax] < 0 || l[ax] >= sn[ax]) in = false;
+        const long long o = in ? gidx(sp, l[0], l[1], l[2]) : 0;
+#pragma unroll
+        for (int p = 0; p < D; ++p) v[c][p] = in ? up[p * sp.cs + o] : T(0);
+    }
+#pragma unroll
+    for (int d = 0; d < (1 << D); ++d) {
+        const int dl[3] = {d & 1, (d >> 1) & 1, D == 3 ? d >> 2 : 0};
+        const int g[3] = {2 * B[0] + dl[0], 2 * B[1] + dl[1], 2 * B[2] + dl[2]};
+        int l[3];
+        bool in = true;
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax) {
+            l[ax] = g[ax] - Lc.org[ax];
+            if (l[ax] < 0 || l[ax] >= cn[ax]) in = false;
+        }
+        if (!in) continue;
+        const bool solved = axes_owned(Lc, g);
+        if (solved && mode != 1) continue;
+        T val[D];
+#pragma unroll
+        for (int p = 0; p < D; ++p) val[p] = T(0);
+        if (inside_domain(Lc, g)) {
+            int nodd = 0;
+#pragma unroll
+            for (int c = 0; c < (1 << D); ++c) {
+                bool use = true;
+#pragma unroll
+                for (int ax = 0; ax < D; ++ax)
+                    if (!dl[ax] && ((c >> ax) & 1)) use = false;
+                if (!use) continue;
+#pragma unroll
+                for (int p = 0; p < D; ++p) val[p] += v[c][p];
+            }
+#pragma unroll
+            for (int ax = 0; ax < D; ++ax) nodd += dl[ax];
+            const T sc_ = T(1) / T(1 << nodd);
+#pragma unroll
+            for (int p = 0; p < D; ++p) val[p] *= sc_;
+        }
+        const long long o = gidx(sc, l[0], l[1], l[2]);
+#pragma unroll
+        for (int p = 0; p < D; ++p) {
+            if (!solved) uc[p * sc.cs + o] = val[p];
+            else if (!domain_dirichlet(Lc, g, p)) uc[p * sc.cs + o] += val[p];
+        }
     }
 }
 
@@ -205,21 +247,18 @@ __global__ void k_amr_restrict(const Geom sc, const AmrInfo Lc, const Geom sp, c
     const T w[3] = {T(0.5), T(1), T(0.5)};
     const T scale = d3 ? T(0.125) : T(0.25);
     const long long op = gidx(sp, i, j, k);
-    for (int p = 0; p < Lp.dim; ++p) {
-        T s = T(0);
-        if (!domain_dirichlet(Lp, g, p)) {
-            for (int dk = (d3 ? -1 : 0); dk <= (d3 ? 1 : 0); ++dk)
-                for (int dj = -1; dj <= 1; ++dj)
-                    for (int di = -1; di <= 1; ++di) {
-                        const int li = 2 * g[0] + di - Lc.org[0], lj = 2 * g[1] + dj - Lc.org[1];
-                        const int lk = d3 ? 2 * g[2] + dk - Lc.org[2] : 0;
-                        if (li < 0 || lj < 0 || lk < 0 || li >= sc.nx || lj >= sc.ny || lk >= sc.nz) continue;
-                        s += w[di + 1] * w[dj + 1] * (d3 ? w[dk + 1] : T(1)) * rc[p * sc.cs + gidx(sc, li, lj, lk)];
-                    }
-            s *= scale;
-        }
-        rhsp[p * sp.cs + op] = s;
-    }
+    T s[3] = {T(0), T(0), T(0)};
+    for (int dk = (d3 ? -1 : 0); dk <= (d3 ? 1 : 0); ++dk)
+        for (int dj = -1; dj <= 1; ++dj)
+            for (int di = -1; di <= 1; ++di) {
+                const int li = 2 * g[0] + di - Lc.org[0], lj = 2 * g[1] + dj - Lc.org[1];
+                const int lk = d3 ? 2 * g[2] + dk - Lc.org[2] : 0;
+                if (li < 0 || lj < 0 || lk < 0 || li >= sc.nx || lj >= sc.ny || lk >= sc.nz) continue;
+                const T wt = w[di + 1] * w[dj + 1] * (d3 ? w[dk + 1] : T(1));
+                const long long oc = gidx(sc, li, lj, lk);
+                for (int p = 0; p < Lp.dim; ++p) s[p] += wt * rc[p * sc.cs + oc];
+            }
+    for (int p = 0; p < Lp.dim; ++p) rhsp[p * sp.cs + op] = domain_dirichlet(Lp, g, p) ? T(0) : s[p] * scale;
 }
 
 // u += e on owned free dofs.
@@ -298,29 +337,44 @@ __global__ void k_amr_set_cells(const Geom s, const double *packed, double psi_m
 // box region, inside the domain), with the interpolation weights (1 on coincident
 // axes, 1/2 on odd ones), and adds the sum to wp.
 // with_solved != 0: also the child's solved free nodes (the correction
-// prolongation adds the interpolated parent value there).
+// prolongation adds the interpolated parent value there).  The child nodes around
+// parent node G are enumerated directly (clipped to the child's storage and the
+// domain); a parent whose whole neighbourhood lies strictly inside the child's box
+// has no ghost child and is skipped when only ghosts count.
 __global__ void k_amr_ghostT(const Geom sc, const AmrInfo Lc, const Geom sp, const AmrInfo Lp, const double *wc,
                              double *wp, int with_solved)
 {
     int i, j, k, G[3];
     if (!thread_node(sp, Lp, i, j, k, G)) return;
-    const bool d3 = Lp.dim == 3;
-    const long long op = gidx(sp, i, j, k);
-    for (int p = 0; p < Lp.dim; ++p) {
-        double s = 0.0;
-        for (int dk = (d3 ? -1 : 0); dk <= (d3 ? 1 : 0); ++dk)
-            for (int dj = -1; dj <= 1; ++dj)
-                for (int di = -1; di <= 1; ++di) {
-                    const int g[3] = {2 * G[0] + di, 2 * G[1] + dj, d3 ? 2 * G[2] + dk : 0};
-                    const int l[3] = {g[0] - Lc.org[0], g[1] - Lc.org[1], g[2] - Lc.org[2]};
-                    if (l[0] < 0 || l[1] < 0 || l[2] < 0 || l[0] >= sc.nx || l[1] >= sc.ny || l[2] >= sc.nz) continue;
-                    if (!inside_domain(Lc, g)) continue;
-                    if (axes_owned(Lc, g) && (!with_solved || domain_dirichlet(Lc, g, p))) continue;
-                    const double w = (di ? 0.5 : 1.0) * (dj ? 0.5 : 1.0) * (dk ? 0.5 : 1.0);
-                    s += w * wc[p * sc.cs + gidx(sc, l[0], l[1], l[2])];
-                }
-        wp[p * sp.cs + op] += s;
+    const int D = Lp.dim;
+    const int sn[3] = {sc.nx, sc.ny, sc.nz};
+    int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+    bool interior = true;
+    for (int ax = 0; ax < D; ++ax) {
+        const int c = 2 * G[ax];
+        lo[ax] = max(max(c - 1, Lc.org[ax]), 0);
+        hi[ax] = min(min(c + 1, Lc.org[ax] + sn[ax] - 1), Lc.N[ax] - 1);
+        if (lo[ax] > hi[ax]) return;
+        if (!(c - 1 > Lc.lo[ax] && c + 1 < Lc.hi[ax])) interior = false;
     }
+    if (interior && !with_solved) return;
+    double acc[3] = {0.0, 0.0, 0.0};
+    for (int gz = lo[2]; gz <= hi[2]; ++gz)
+        for (int gy = lo[1]; gy <= hi[1]; ++gy)
+            for (int gx = lo[0]; gx <= hi[0]; ++gx) {
+                const int g[3] = {gx, gy, gz};
+                const bool own = axes_owned(Lc, g);
+                if (own && !with_solved) continue;
+                const double w = (gx != 2 * G[0] ? 0.5 : 1.0) * (gy != 2 * G[1] ? 0.5 : 1.0) *
+                                 (D == 3 && gz != 2 * G[2] ? 0.5 : 1.0);
+                const long long o = gidx(sc, gx - Lc.org[0], gy - Lc.org[1], gz - Lc.org[2]);
+                for (int p = 0; p < D; ++p) {
+                    if (own && domain_dirichlet(Lc, g, p)) continue;
+                    acc[p] += w * wc[p * sc.cs + o];
+                }
+            }
+    const long long op = gidx(sp, i, j, k);
+    for (int p = 0; p < D; ++p) wp[p * sp.cs + op] += acc[p];
 }
 
 // Zero everything but the solved free dofs (box region, not on a Dirichlet face):
@@ -360,38 +414,101 @@ __global__ void k_amr_scaleW(const Geom s, const AmrInfo L, const double *psi, d
     const double kd[3] = {k0, k1, k2};
     for (int p = 0; p < L.dim; ++p) {
         const bool free = solved && !domain_dirichlet(L, g, p) && ps > 0.0 && kd[p] != 0.0;
-        out[p * s.cs + o] = free ? omega / (kd[p] * ps) * x[p * s.cs + o] : 0.0;
+        out[p * s.cs + o] = free ? omega / (kd[p] * ps) * (x ? x[p * s.cs + o] : 1.0) : 0.0;
     }
+}
+
+// One transposed damped-Jacobi sweep, first half: t = W eb (W from k_amr_scaleW with
+// x = null: 0 off the solved free dofs), rb += t, and t written in the precision of
+// the stencil product that follows (every storage node).
+template <typename TS>
+__global__ void k_amr_jacT_scale(long long n, const double *__restrict__ W, const double *__restrict__ eb,
+                                 double *__restrict__ rb, TS *__restrict__ t)
+{
+    const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const double v = W[q] * eb[q];
+    rb[q] += v;
+    t[q] = TS(v);
+}
+
+// eb -= y on the nodes of a patch view (extents of v, storage strides; both arrays
+// start at the storage origin, the view at element offset voff).
+template <typename TS>
+__global__ void k_sub_view(const Geom v, long long voff, const TS *__restrict__ y, double *__restrict__ eb)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z * blockDim.z + threadIdx.z;
+    if (i >= v.nx || j >= v.ny || k >= v.nz) return;
+    const long long o = voff + gidx(v, i, j, k);
+    for (int p = 0; p < v.dim; ++p) eb[p * v.cs + o] -= double(y[p * v.cs + o]);
 }
 
 // Transpose of the full-weighting restriction onto the covered parent nodes:
 // child node g collects scale * w(g - 2G) * rp(G) from the parents G covered by
-// this child with
-// |g - 2G| <= 1 (parents on a Dirichlet face of the component contribute 0).
+// this child with |g - 2G| <= 1 (parents on a Dirichlet face of the component
+// contribute 0).  One thread per parent cell B (global parent coordinates): it
+// loads the 2^d corners B + c once (0 where not covered, outside the parent's
+// storage or Dirichlet) and writes the child nodes 2B + delta, delta in {0,1}^d,
+// that lie in the child's storage: even axes take corner 0 with weight 1, odd axes
+// corners 0 and 1 with weight 1/2, summed in ascending parent order.
+template <int D>
 __global__ void k_amr_restrictT(const Geom sc, const AmrInfo Lc, const Geom sp, const AmrInfo Lp, const double *rp,
-                                double *rc)
+                                double *rc, int3 b0, int3 nb)
 {
-    int i, j, k, g[3];
-    if (!thread_node(sc, Lc, i, j, k, g)) return;
-    const bool d3 = Lc.dim == 3;
-    const double scale = d3 ? 0.125 : 0.25;
-    const long long oc = gidx(sc, i, j, k);
-    for (int p = 0; p < Lc.dim; ++p) {
-        double s = 0.0;
-        // parents G with 2G in {g-1, g, g+1} per axis
-        for (int dk = (d3 ? -1 : 0); dk <= (d3 ? 1 : 0); ++dk)
-            for (int dj = -1; dj <= 1; ++dj)
-                for (int di = -1; di <= 1; ++di) {
-                    const int t[3] = {g[0] + di, g[1] + dj, d3 ? g[2] + dk : 0};
-                    if ((t[0] & 1) || (t[1] & 1) || (t[2] & 1)) continue;
-                    const int G[3] = {t[0] / 2, t[1] / 2, t[2] / 2};
-                    if (!covered_by(Lc, G) || domain_dirichlet(Lp, G, p)) continue;
-                    const int l[3] = {G[0] - Lp.org[0], G[1] - Lp.org[1], G[2] - Lp.org[2]};
-                    if (l[0] < 0 || l[1] < 0 || l[2] < 0 || l[0] >= sp.nx || l[1] >= sp.ny || l[2] >= sp.nz) continue;
-                    const double w = (di ? 0.5 : 1.0) * (dj ? 0.5 : 1.0) * (dk ? 0.5 : 1.0);
-                    s += scale * w * rp[p * sp.cs + gidx(sp, l[0], l[1], l[2])];
-                }
-        rc[p * sc.cs + oc] = s;
+    const int bx = blockIdx.x * blockDim.x + threadIdx.x, by = blockIdx.y * blockDim.y + threadIdx.y,
+              bz = blockIdx.z * blockDim.z + threadIdx.z;
+    if (bx >= nb.x || by >= nb.y || bz >= nb.z) return;
+    const int B[3] = {b0.x + bx, b0.y + by, b0.z + bz};
+    const int sn[3] = {sp.nx, sp.ny, sp.nz}, cn[3] = {sc.nx, sc.ny, sc.nz};
+    const double scale = D == 3 ? 0.125 : 0.25;
+    double v[1 << D][D];
+#pragma unroll
+    for (int c = 0; c < (1 << D); ++c) {
+        const int G[3] = {B[0] + (c & 1), B[1] + ((c >> 1) & 1), D == 3 ? B[2] + (c >> 2) : 0};
+        bool in = covered_by(Lc, G);
+        int l[3];
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax) {
+            l[ax] = G[ax] - Lp.org[ax];
+            if (l[ax] < 0 || l[ax] >= sn[ax]) in = false;
+        }
+        const long long o = in ? gidx(sp, l[0], l[1], l[2]) : 0;
+#pragma unroll
+        for (int p = 0; p < D; ++p) v[c][p] = (in && !domain_dirichlet(Lp, G, p)) ? rp[p * sp.cs + o] : 0.0;
+    }
+#pragma unroll
+    for (int d = 0; d < (1 << D); ++d) {
+        const int dl[3] = {d & 1, (d >> 1) & 1, D == 3 ? d >> 2 : 0};
+        int l[3];
+        bool in = true;
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax) {
+            l[ax] = 2 * B[ax] + dl[ax] - Lc.org[ax];
+            if (l[ax] < 0 || l[ax] >= cn[ax]) in = false;
+        }
+        if (!in) continue;
+        double acc[D];
+#pragma unroll
+        for (int p = 0; p < D; ++p) acc[p] = 0.0;
+#pragma unroll
+        for (int c = 0; c < (1 << D); ++c) {
+            const int cb[3] = {c & 1, (c >> 1) & 1, c >> 2};
+            bool use = true;
+            double w = 1.0;
+#pragma unroll
+            for (int ax = 0; ax < D; ++ax) {
+                if (!dl[ax] && cb[ax]) use = false;
+                if (dl[ax]) w *= 0.5;
+            }
+            if (!use) continue;
+#pragma unroll
+            for (int p = 0; p < D; ++p) acc[p] += scale * w * v[c][p];
+        }
+        const long long oc = gidx(sc, l[0], l[1], l[2]);
+#pragma unroll
+        for (int p = 0; p < D; ++p) rc[p * sc.cs + oc] = acc[p];
     }
 }
 
@@ -552,6 +669,26 @@ __global__ void k_amr_tag(const Geom s, const AmrInfo L, const double *psi, doub
 const dim3 kAmrBlock(32, 4, 2);
 inline dim3 amr_grid(const Geom &s) { return dim3((s.nx + 31) / 32, (s.ny + 3) / 4, (s.nz + 1) / 2); }
 
+// Parent cells B (global parent coordinates, first b0, counts nb) whose child
+// blocks 2B + {0,1}^d cover the child's storage, and the launch grid over them.
+dim3 child_blocks(const Geom &sc, const AmrInfo &Lc, int3 &b0, int3 &nb)
+{
+    int lo[3] = {0, 0, 0}, n[3] = {1, 1, 1};
+    const int cn[3] = {sc.nx, sc.ny, sc.nz};
+    for (int ax = 0; ax < sc.dim; ++ax) {
+        const int g0 = Lc.org[ax], g1 = Lc.org[ax] + cn[ax] - 1;
+        lo[ax] = (g0 >= 0 ? g0 : g0 - 1) / 2;        // floor(g0 / 2)
+        n[ax] = (g1 >= 0 ? g1 : g1 - 1) / 2 - lo[ax] + 1;
+    }
+    b0 = make_int3(lo[0], lo[1], lo[2]);
+    nb = make_int3(n[0], n[1], n[2]);
+    Geom gb = sc;
+    gb.nx = n[0];
+    gb.ny = n[1];
+    gb.nz = n[2];
+    return amr_grid(gb);
+}
+
 }  // namespace
 
 long long amr_blocks(const Geom &s)
@@ -606,7 +743,10 @@ template <typename T>
 cudaError_t launch_amr_ghost(const Geom &sc, const AmrInfo &Lc, const Geom &sp, const AmrInfo &Lp, T *uc, const T *up,
                              int mode, cudaStream_t st)
 {
-    k_amr_ghost<T><<<amr_grid(sc), kAmrBlock, 0, st>>>(sc, Lc, sp, Lp, uc, up, mode);
+    int3 b0, nb;
+    const dim3 gr = child_blocks(sc, Lc, b0, nb);
+    if (sc.dim == 3) k_amr_ghost<T, 3><<<gr, kAmrBlock, 0, st>>>(sc, Lc, sp, Lp, uc, up, mode, b0, nb);
+    else k_amr_ghost<T, 2><<<gr, kAmrBlock, 0, st>>>(sc, Lc, sp, Lp, uc, up, mode, b0, nb);
     ++g_launches;
     return cudaGetLastError();
 }
@@ -676,10 +816,35 @@ cudaError_t launch_amr_scaleW(const Geom &s, const AmrInfo &L, const double *psi
     return cudaGetLastError();
 }
 
+template <typename TS>
+cudaError_t launch_amr_jacT_scale(long long n, const double *W, const double *eb, double *rb, TS *t, cudaStream_t st)
+{
+    k_amr_jacT_scale<TS><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, W, eb, rb, t);
+    ++g_launches;
+    return cudaGetLastError();
+}
+template cudaError_t launch_amr_jacT_scale<float>(long long, const double *, const double *, double *, float *,
+                                                  cudaStream_t);
+template cudaError_t launch_amr_jacT_scale<double>(long long, const double *, const double *, double *, double *,
+                                                   cudaStream_t);
+
+template <typename TS>
+cudaError_t launch_sub_view(const Geom &v, long long voff, const TS *y, double *eb, cudaStream_t st)
+{
+    k_sub_view<TS><<<amr_grid(v), kAmrBlock, 0, st>>>(v, voff, y, eb);
+    ++g_launches;
+    return cudaGetLastError();
+}
+template cudaError_t launch_sub_view<float>(const Geom &, long long, const float *, double *, cudaStream_t);
+template cudaError_t launch_sub_view<double>(const Geom &, long long, const double *, double *, cudaStream_t);
+
 cudaError_t launch_amr_restrictT(const Geom &sc, const AmrInfo &Lc, const Geom &sp, const AmrInfo &Lp,
                                  const double *rp, double *rc, cudaStream_t st)
 {
-    k_amr_restrictT<<<amr_grid(sc), kAmrBlock, 0, st>>>(sc, Lc, sp, Lp, rp, rc);
+    int3 b0, nb;
+    const dim3 gr = child_blocks(sc, Lc, b0, nb);
+    if (sc.dim == 3) k_amr_restrictT<3><<<gr, kAmrBlock, 0, st>>>(sc, Lc, sp, Lp, rp, rc, b0, nb);
+    else k_amr_restrictT<2><<<gr, kAmrBlock, 0, st>>>(sc, Lc, sp, Lp, rp, rc, b0, nb);
     ++g_launches;
     return cudaGetLastError();
 }

@@ -1062,53 +1062,71 @@ cudaError_t amr_apply_T(sbm_grid G, double *const *x, double *const *out)
     return cudaSuccess;
 }
 
-// y = K x on patch a's view, 0 elsewhere (FP64 vectors).  Inside the transposed
-// correction cycle of a mixed-precision grid the product is taken in FP32 (x
-// rounded into the patch's FP32 correction buffer, the FP32 sweep, the result
-// widened): the cycle only preconditions the adjoint iteration, whose fixed point
-// A^T lambda = g is set by the FP64 A^T alone.
-cudaError_t view_apply(sbm_grid G, Patch &Pt, const double *x, double *y, size_t n)
+// eb -= K_a x on patch a's view, the product taken in FP32 on mixed-precision grids:
+// x is rounded into the patch's FP32 correction buffer (or used as is on FP64
+// grids), the stencil writes every view node of the residual buffer, and those are
+// subtracted.  Inside the transposed correction cycle this is enough: the cycle only
+// preconditions the adjoint iteration, whose fixed point A^T lambda = g is set by
+// the FP64 A^T alone.
+cudaError_t view_apply_sub(sbm_grid G, Patch &Pt, const double *x, double *eb, size_t n)
 {
-    CKE(cudaMemsetAsync(y, 0, sizeof(double) * n, G->st));
-    if (G->desc.precision != SBM_MIXED) return sweep_view<double>(G, Pt, kApply, x, nullptr, y, 0.0);
+    if (G->desc.precision != SBM_MIXED) {
+        CKE(sweep_view<double>(G, Pt, kApply, x, nullptr, Pt.dres, 0.0));
+        return launch_sub_view<double>(Pt.v, Pt.voff, Pt.dres, eb, G->st);
+    }
     CKE(launch_round((long long)n, x, Pt.se[0], G->st));
-    CKE(cudaMemsetAsync(Pt.sres, 0, sizeof(float) * n, G->st));
     CKE(sweep_view<float>(G, Pt, kApply, Pt.se[0], nullptr, Pt.sres, 0.0));
-    return launch_add<float>((long long)n, Pt.sres, y, G->st);
+    return launch_sub_view<float>(Pt.v, Pt.voff, Pt.sres, eb, G->st);
 }
 
 // One transposed (damped-Jacobi) sweep on patch a's solved dofs: eb <- eb - K_a W eb
 // and rb += W eb, with W the Jacobi scaling (the transpose of e <- e + W (r - K e)).
-cudaError_t patch_jacobiT(sbm_grid G, int a, const sbm_opts &o, double *eb, double *rb, double *t1, double *t2)
+// W (vector 5 of adj, set by amr_adjoint_scaling) is 0 off the solved free dofs; the
+// scaled vector goes straight into the stencil's input buffer.
+cudaError_t patch_jacobiT(sbm_grid G, int a, double *eb, double *rb)
 {
     Patch &Pt = G->P[a - 1];
-    const size_t n = amr_vec_len(G, a);
-    CKE(launch_amr_scaleW(Pt.s, Pt.info, Pt.psi64, o.omega, Pt.c64.kdiag, eb, t1, G->st));
-    CKE(view_apply(G, Pt, t1, t2, n));
-    CKE(launch_lincomb((long long)n, 1.0, eb, -1.0, t2, 0.0, nullptr, eb, G->st));
-    return launch_lincomb((long long)n, 1.0, rb, 1.0, t1, 0.0, nullptr, rb, G->st);
+    const long long n = (long long)amr_vec_len(G, a);
+    const double *W = G->adj[5][a];
+    if (G->desc.precision != SBM_MIXED) {
+        CKE(launch_amr_jacT_scale<double>(n, W, eb, rb, Pt.de[0], G->st));
+        CKE(sweep_view<double>(G, Pt, kApply, Pt.de[0], nullptr, Pt.dres, 0.0));
+        return launch_sub_view<double>(Pt.v, Pt.voff, Pt.dres, eb, G->st);
+    }
+    CKE(launch_amr_jacT_scale<float>(n, W, eb, rb, Pt.se[0], G->st));
+    CKE(sweep_view<float>(G, Pt, kApply, Pt.se[0], nullptr, Pt.sres, 0.0));
+    return launch_sub_view<float>(Pt.v, Pt.voff, Pt.sres, eb, G->st);
+}
+
+// W of every patch for relaxation weight omega (vector 5 of adj).
+cudaError_t amr_adjoint_scaling(sbm_grid G, double omega)
+{
+    for (int a = 1; a <= G->npatch; ++a) {
+        Patch &Pt = G->P[a - 1];
+        CKE(launch_amr_scaleW(Pt.s, Pt.info, Pt.psi64, omega, Pt.c64.kdiag, nullptr, G->adj[5][a], G->st));
+    }
+    return cudaSuccess;
 }
 
 // z = B^T y: the transpose of one correction cycle (Jacobi smoother; its stencil
-// products and base V-cycle in FP32 on mixed-precision grids, see view_apply), taken
+// products and base V-cycle in FP32 on mixed-precision grids, see view_apply_sub), taken
 // step by step in reverse: the update's mask; per patch, finest first, the
 // post-smoothing sweeps transposed and the correction prolongation transposed
 // (into the parent's adjoint); the base V-cycle (symmetric); per patch, coarsest
 // first, the restriction onto covered parents transposed, the residual
 // transposed and the pre-smoothing sweeps transposed; z = the right-hand sides'
-// adjoints on the owned free dofs.  Scratch: vectors 6, 7, 8 of adj.
+// adjoints on the owned free dofs.  y is overwritten (it becomes the corrections'
+// adjoints).  Scratch: vector 7 of adj (5 holds W).
 cudaError_t amr_precondT(sbm_grid G, const sbm_opts &o, double *const *y, double *const *z)
 {
     const int A = G->npatch;
     Level &B = G->L[G->nl - 1];
-    double *const *EB = G->adj[6];     // adjoints of the corrections e_a
+    double *const *EB = y;             // adjoints of the corrections e_a (y is consumed)
     double *const *T1 = G->adj[7];
-    double *const *T2 = G->adj[8];
     // z holds the right-hand sides' adjoints while they accumulate
     CKE(cv_zero(G, z));
-    CKE(cv_lincomb(G, 1.0, y, 0.0, y, 0.0, nullptr, EB));
     for (int a = A; a >= 1; --a) {
-        for (int s_ = 0; s_ < o.nu2; ++s_) CKE(patch_jacobiT(G, a, o, EB[a], z[a], T1[a], T2[a]));
+        for (int s_ = 0; s_ < o.nu2; ++s_) CKE(patch_jacobiT(G, a, EB[a], z[a]));
         const int pa = amr_parent(G, a);
         CKE(launch_amr_ghostT(amr_geom(G, a), amr_info(G, a), amr_geom(G, pa), amr_info(G, pa), EB[a], EB[pa], 1,
                               G->st));
@@ -1137,9 +1155,8 @@ cudaError_t amr_precondT(sbm_grid G, const sbm_opts &o, double *const *y, double
         // residual r = rhs - K e (solved dofs): rhs_adj += res_adj, e_adj -= K res_adj
         const size_t n = amr_vec_len(G, a);
         CKE(launch_lincomb((long long)n, 1.0, z[a], 1.0, T1[a], 0.0, nullptr, z[a], G->st));
-        CKE(view_apply(G, G->P[a - 1], T1[a], T2[a], n));
-        CKE(launch_lincomb((long long)n, 1.0, EB[a], -1.0, T2[a], 0.0, nullptr, EB[a], G->st));
-        for (int s_ = 0; s_ < o.nu1; ++s_) CKE(patch_jacobiT(G, a, o, EB[a], z[a], T1[a], T2[a]));
+        CKE(view_apply_sub(G, G->P[a - 1], T1[a], EB[a], n));
+        for (int s_ = 0; s_ < o.nu1; ++s_) CKE(patch_jacobiT(G, a, EB[a], z[a]));
     }
     for (int a = 0; a <= A; ++a) CKE(launch_amr_mask(amr_geom(G, a), amr_info(G, a), z[a], G->st));
     return cudaSuccess;
@@ -2809,6 +2826,7 @@ sbm_status sbm_amr_adjoint(sbm_grid G, double *const *u, double *const *dJdu, do
     if ((s = amr_prepare(G)) != SBM_OK) return s;
     if ((s = setup_bottom(G)) != SBM_OK) return s;
     if ((s = amr_alloc_adjoint(G)) != SBM_OK) return s;
+    CK(amr_adjoint_scaling(G, o.omega));
     const int A = G->npatch;
     double *const *X = G->adj[0], *const *Gv = G->adj[1], *const *R = G->adj[2], *const *Zv = G->adj[3];
     const long long launches0 = g_launches;
