@@ -45,6 +45,8 @@ AMR_WORKLOADS = {
     "voids_amr_2d": lambda: W.voids_amr(2, 129, 3),
     # 3D refinement: 129^3 base + 2 levels around 16 spherical voids, triaxial loading
     "voids_amr_3d": lambda: W.voids_amr(3, 129, 2, count=16, rmin=0.04, rmax=0.12),
+    # the same recipe at base 65^3 (the base of its oracle record)
+    "voids_amr_3d_65": lambda: W.voids_amr(3, 65, 2, count=16, rmin=0.04, rmax=0.12),
     # several patches per level from tagging and clustering on the host
     "voids_amr_2d_clustered": lambda: W.voids_amr(2, 129, 3, clustered=True),
     "voids_amr_3d_clustered": lambda: W.voids_amr(3, 129, 2, count=8, rmin=0.04, rmax=0.08, clustered=True),
@@ -572,7 +574,9 @@ def patch_smoother_roofline(wk, psi_h, precision, dev, stream, local_rank):
     m64, f64 = C.c_double(), C.c_double()
     with torch.cuda.stream(stream):
         g.set_psi(psi_t.to(dev), wk.psi_min)
+        torch.cuda.nvtx.range_push("roofline")        # lets a profiler select exactly these launches
         _capi.check(sbm.lib().sbm_time_kernel(g._h, kid, 20, 1, C.byref(ms), C.byref(by), C.byref(fl)), g._h)
+        torch.cuda.nvtx.range_pop()
         _capi.check(sbm.lib().sbm_time_kernel(g._h, _capi.SBM_K_FMA64, 5, 0, C.byref(m64), None, C.byref(f64)), g._h)
     hbm_peak, peak_kind = peaks()
     gbs = by.value / (ms.value * 1e-3) / 1e9
@@ -647,7 +651,11 @@ def run_amr(args, rank, world, local_rank):
                     u.copy_(u0)
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
+                if i >= nwarm:
+                    torch.cuda.nvtx.range_push("solve")   # lets a profiler select the timed solves
                 info = g.amr_solve(us, **opts)
+                if i >= nwarm:
+                    torch.cuda.nvtx.range_pop()
                 e1.record(stream)
                 e1.synchronize()
                 if i >= nwarm:
@@ -690,7 +698,9 @@ def run_amr(args, rank, world, local_rank):
             dJ = [torch.ones_like(u) for u in us]
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
+            torch.cuda.nvtx.range_push("adjoint")
             _, grads, ai = g.amr_adjoint(us, dJ, omega=wk.omega, tol=1e-10, max_cycles=500)
+            torch.cuda.nvtx.range_pop()
             e1.record(stream)
             e1.synchronize()
         adjoint = {"ms": e0.elapsed_time(e1), "iterations": ai.cycles, "relres": ai.relres,
