@@ -699,14 +699,17 @@ def run_amr(args, rank, world, local_rank):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             torch.cuda.nvtx.range_push("adjoint")
-            _, grads, ai = g.amr_adjoint(us, dJ, omega=wk.omega, tol=1e-10, max_cycles=500)
+            _, grads, ai = g.amr_adjoint(us, dJ, omega=wk.omega, tol=1e-10, max_cycles=500,
+                                         inner_cycles=opts["inner_cycles"])
             torch.cuda.nvtx.range_pop()
             e1.record(stream)
             e1.synchronize()
-        adjoint = {"ms": e0.elapsed_time(e1), "iterations": ai.cycles, "relres": ai.relres,
+        adjoint = {"ms": e0.elapsed_time(e1), "iterations": ai.vcycles, "fp64_residuals": ai.cycles,
+                   "relres": ai.relres,
                    "objective": "J = sum of u over owned free dofs",
-                   "method": "transposed correction iteration (FP64 A^T and updates; the transposed cycle "
-                             "in FP32 on mixed grids) + dJ/dpsi of every level",
+                   "method": "transposed correction iteration (FP64 A^T lambda and updates; on mixed grids the "
+                             "transposed cycle's stencil products in FP32 and, with inner_cycles k, k transposed "
+                             "cycles per FP64 A^T lambda with FP32-product residual updates) + dJ/dpsi of every level",
                    "grad_norm": sum(float(t.norm()) ** 2 for t in grads) ** 0.5}
     # end to end: host psi and initial guess in, solution out
     out_h = [torch.empty_like(u).pin_memory() for u in u0_h]

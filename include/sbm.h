@@ -414,7 +414,11 @@ sbm_status sbm_amr_solve(sbm_grid grid, double *const *u, const sbm_opts *opts, 
  * transpose of one correction cycle with damped-Jacobi patch sweeps (weight
  * opts->omega; on SBM_MIXED grids its stencil products and base V-cycle run in FP32,
  * A^T lambda and the vector updates in FP64), to relative residual opts->tol within
- * opts->max_cycles iterations (the iteration converges at the rate of the forward one).
+ * opts->max_cycles transposed cycles (the iteration converges at the rate of the forward
+ * one).  On SBM_MIXED grids with opts->inner_cycles = k > 1, each FP64 residual is
+ * followed by k transposed cycles on the correction equation A^T d = r whose residual
+ * updates take FP32 stencil products, then lambda += d (as sbm_amr_solve runs k FP32
+ * cycles per FP64 residual); k = 1: one cycle per FP64 residual.
  * With opts->smoother = SBM_MCGS the patch sweeps of B^T stay damped Jacobi (the
  * transpose of a colour sweep is not a colour sweep) and the base V-cycle uses the
  * colour smoother; B^T only preconditions, the fixed point A^T lambda = dJ/du is the
@@ -423,7 +427,8 @@ sbm_status sbm_amr_solve(sbm_grid grid, double *const *u, const sbm_opts *opts, 
  * psi of sbm_set_psi (a = 0) / sbm_amr_set_psi (a >= 1): -lambda_c^T S_c u_c, where a
  * coarse cell under a patch passes its gradient to its 2^d fine cells and keeps
  * none (its psi is the fine mean), and 0 where psi sits at psi_min.  All pointers
- * are device pointers.  info: cycles = Krylov iterations, relres, history.
+ * are device pointers.  info: cycles = FP64 residuals (outer iterations), vcycles =
+ * transposed cycles, relres, history (one entry per FP64 residual).
  * SBM_ERR_STATE without patch levels (use sbm_adjoint); status otherwise as for
  * sbm_solve. */
 sbm_status sbm_amr_adjoint(sbm_grid grid, double *const *u, double *const *dJdu, double *const *lambda,

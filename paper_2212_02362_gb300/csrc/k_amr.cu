@@ -432,17 +432,18 @@ __global__ void k_amr_jacT_scale(long long n, const double *__restrict__ W, cons
     t[q] = TS(v);
 }
 
-// eb -= y on the nodes of a patch view (extents of v, storage strides; both arrays
-// start at the storage origin, the view at element offset voff).
+// eb += alpha y on the nodes of a patch view (extents of v, storage strides; both
+// arrays start at the storage origin, the view at element offset voff).
 template <typename TS>
-__global__ void k_sub_view(const Geom v, long long voff, const TS *__restrict__ y, double *__restrict__ eb)
+__global__ void k_axpy_view(const Geom v, long long voff, double alpha, const TS *__restrict__ y,
+                            double *__restrict__ eb)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const int k = blockIdx.z * blockDim.z + threadIdx.z;
     if (i >= v.nx || j >= v.ny || k >= v.nz) return;
     const long long o = voff + gidx(v, i, j, k);
-    for (int p = 0; p < v.dim; ++p) eb[p * v.cs + o] -= double(y[p * v.cs + o]);
+    for (int p = 0; p < v.dim; ++p) eb[p * v.cs + o] += alpha * double(y[p * v.cs + o]);
 }
 
 // Transpose of the full-weighting restriction onto the covered parent nodes:
@@ -829,14 +830,15 @@ template cudaError_t launch_amr_jacT_scale<double>(long long, const double *, co
                                                    cudaStream_t);
 
 template <typename TS>
-cudaError_t launch_sub_view(const Geom &v, long long voff, const TS *y, double *eb, cudaStream_t st)
+cudaError_t launch_axpy_view(const Geom &v, long long voff, double alpha, const TS *y, double *eb, cudaStream_t st)
 {
-    k_sub_view<TS><<<amr_grid(v), kAmrBlock, 0, st>>>(v, voff, y, eb);
+    k_axpy_view<TS><<<amr_grid(v), kAmrBlock, 0, st>>>(v, voff, alpha, y, eb);
     ++g_launches;
     return cudaGetLastError();
 }
-template cudaError_t launch_sub_view<float>(const Geom &, long long, const float *, double *, cudaStream_t);
-template cudaError_t launch_sub_view<double>(const Geom &, long long, const double *, double *, cudaStream_t);
+template cudaError_t launch_axpy_view<float>(const Geom &, long long, double, const float *, double *, cudaStream_t);
+template cudaError_t launch_axpy_view<double>(const Geom &, long long, double, const double *, double *,
+                                              cudaStream_t);
 
 cudaError_t launch_amr_restrictT(const Geom &sc, const AmrInfo &Lc, const Geom &sp, const AmrInfo &Lp,
                                  const double *rp, double *rc, cudaStream_t st)

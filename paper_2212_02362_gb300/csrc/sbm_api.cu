@@ -1062,6 +1062,39 @@ cudaError_t amr_apply_T(sbm_grid G, double *const *x, double *const *out)
     return cudaSuccess;
 }
 
+// out = A^T x with the stencil products in FP32 (x rounded into the FP32 buffers of
+// each level, the FP32 apply, the products widened into the FP64 vectors), the
+// ghost, injection and ownership transposes in FP64: the operator of the inner
+// transposed iterations on mixed-precision grids.
+cudaError_t amr_apply_T32(sbm_grid G, double *const *x, double *const *out)
+{
+    const int A = G->npatch;
+    Level &B = G->L[G->nl - 1];
+    CKE(cv_zero(G, out));
+    const long long n0 = (long long)amr_vec_len(G, 0);
+    CKE(launch_round(n0, x[0], B.su[0], G->st));
+    CKE(sweep<float>(G, G->nl - 1, kApply, B.su[0], nullptr, B.sr, nullptr, 0.0));
+    CKE(launch_add<float>(n0, B.sr, out[0], G->st));
+    for (int a = 1; a <= A; ++a) {
+        Patch &Pt = G->P[a - 1];
+        CKE(launch_round((long long)amr_vec_len(G, a), x[a], Pt.se[0], G->st));
+        CKE(sweep_view<float>(G, Pt, kApply, Pt.se[0], nullptr, Pt.sres, 0.0));
+        CKE(launch_axpy_view<float>(Pt.v, Pt.voff, 1.0, Pt.sres, out[a], G->st));
+    }
+    for (int a = A; a >= 1; --a) {
+        const int pa = amr_parent(G, a);
+        CKE(launch_amr_ghostT(amr_geom(G, a), amr_info(G, a), amr_geom(G, pa), amr_info(G, pa), out[a], out[pa], 0,
+                              G->st));
+    }
+    for (int c = 1; c <= A; ++c) {
+        const int pa = amr_parent(G, c);
+        CKE(launch_amr_injectT(amr_geom(G, c), amr_info(G, c), amr_geom(G, pa), amr_info(G, pa), out[pa], out[c],
+                               G->st));
+    }
+    for (int a = 0; a <= A; ++a) CKE(launch_amr_mask(amr_geom(G, a), amr_info(G, a), out[a], G->st));
+    return cudaSuccess;
+}
+
 // eb -= K_a x on patch a's view, the product taken in FP32 on mixed-precision grids:
 // x is rounded into the patch's FP32 correction buffer (or used as is on FP64
 // grids), the stencil writes every view node of the residual buffer, and those are
@@ -1072,11 +1105,11 @@ cudaError_t view_apply_sub(sbm_grid G, Patch &Pt, const double *x, double *eb, s
 {
     if (G->desc.precision != SBM_MIXED) {
         CKE(sweep_view<double>(G, Pt, kApply, x, nullptr, Pt.dres, 0.0));
-        return launch_sub_view<double>(Pt.v, Pt.voff, Pt.dres, eb, G->st);
+        return launch_axpy_view<double>(Pt.v, Pt.voff, -1.0, Pt.dres, eb, G->st);
     }
     CKE(launch_round((long long)n, x, Pt.se[0], G->st));
     CKE(sweep_view<float>(G, Pt, kApply, Pt.se[0], nullptr, Pt.sres, 0.0));
-    return launch_sub_view<float>(Pt.v, Pt.voff, Pt.sres, eb, G->st);
+    return launch_axpy_view<float>(Pt.v, Pt.voff, -1.0, Pt.sres, eb, G->st);
 }
 
 // One transposed (damped-Jacobi) sweep on patch a's solved dofs: eb <- eb - K_a W eb
@@ -1091,11 +1124,11 @@ cudaError_t patch_jacobiT(sbm_grid G, int a, double *eb, double *rb)
     if (G->desc.precision != SBM_MIXED) {
         CKE(launch_amr_jacT_scale<double>(n, W, eb, rb, Pt.de[0], G->st));
         CKE(sweep_view<double>(G, Pt, kApply, Pt.de[0], nullptr, Pt.dres, 0.0));
-        return launch_sub_view<double>(Pt.v, Pt.voff, Pt.dres, eb, G->st);
+        return launch_axpy_view<double>(Pt.v, Pt.voff, -1.0, Pt.dres, eb, G->st);
     }
     CKE(launch_amr_jacT_scale<float>(n, W, eb, rb, Pt.se[0], G->st));
     CKE(sweep_view<float>(G, Pt, kApply, Pt.se[0], nullptr, Pt.sres, 0.0));
-    return launch_sub_view<float>(Pt.v, Pt.voff, Pt.sres, eb, G->st);
+    return launch_axpy_view<float>(Pt.v, Pt.voff, -1.0, Pt.sres, eb, G->st);
 }
 
 // W of every patch for relaxation weight omega (vector 5 of adj).
@@ -2854,13 +2887,35 @@ sbm_status sbm_amr_adjoint(sbm_grid G, double *const *u, double *const *dJdu, do
     }
     // lambda <- lambda + B^T (g - A^T lambda): the transposed correction iteration,
     // which converges at the rate of the forward one
+    // On mixed-precision grids with inner_cycles k > 1, each outer iteration runs k
+    // transposed cycles on the correction equation A^T d = r, their residual updates
+    // with FP32 stencil products (amr_apply_T32), before lambda += d and the FP64
+    // residual, as the forward solve runs k FP32 cycles per FP64 residual.
     double rel = bnorm > 0.0 ? 1.0 : 0.0;
-    int it = 0;
+    int it = 0, inner = 0;
+    const int kin = (G->desc.precision == SBM_MIXED && o.inner_cycles > 1) ? o.inner_cycles : 1;
     sbm_status status = bnorm > 0.0 ? SBM_ERR_NOCONV : SBM_OK;
     CK(cv_lincomb(G, 1.0, Gv, 0.0, Gv, 0.0, nullptr, R));
-    while (status == SBM_ERR_NOCONV && it < o.max_cycles) {
-        CK(amr_precondT(G, o, R, Zv));
-        CK(cv_lincomb(G, 1.0, X, 1.0, Zv, 0.0, nullptr, X));
+    while (status == SBM_ERR_NOCONV && inner < o.max_cycles) {
+        if (kin == 1) {
+            CK(amr_precondT(G, o, R, Zv));
+            CK(cv_lincomb(G, 1.0, X, 1.0, Zv, 0.0, nullptr, X));
+            ++inner;
+        } else {
+            double *const *D = G->adj[4], *const *RI = G->adj[6], *const *Zi = G->adj[8];
+            CK(cv_zero(G, D));
+            CK(cv_lincomb(G, 1.0, R, 0.0, R, 0.0, nullptr, RI));
+            for (int m = 0; m < kin && inner < o.max_cycles; ++m) {
+                CK(amr_precondT(G, o, RI, Zi));
+                CK(cv_lincomb(G, 1.0, D, 1.0, Zi, 0.0, nullptr, D));
+                ++inner;
+                if (m + 1 < kin && inner < o.max_cycles) {
+                    CK(amr_apply_T32(G, D, Zv));
+                    CK(cv_lincomb(G, 1.0, R, -1.0, Zv, 0.0, nullptr, RI));
+                }
+            }
+            CK(cv_lincomb(G, 1.0, X, 1.0, D, 0.0, nullptr, X));
+        }
         CK(amr_apply_T(G, X, Zv));
         CK(cv_lincomb(G, 1.0, Gv, -1.0, Zv, 0.0, nullptr, R));
         double rn = 0.0;
@@ -2899,7 +2954,7 @@ sbm_status sbm_amr_adjoint(sbm_grid G, double *const *u, double *const *dJdu, do
     if (info) {
         info->status = status;
         info->cycles = it;
-        info->vcycles = it;
+        info->vcycles = inner;
         info->relres = rel;
         info->solve_ms = ms;
         info->launches = g_launches - launches0;

@@ -333,9 +333,9 @@ cudaError_t launch_amr_scaleW(const Geom &s, const AmrInfo &L, const double *psi
 // damped-Jacobi sweep, W from launch_amr_scaleW with x = null.
 template <typename TS>
 cudaError_t launch_amr_jacT_scale(long long n, const double *W, const double *eb, double *rb, TS *t, cudaStream_t st);
-// eb -= y on the nodes of view v (storage strides; the view at element offset voff).
+// eb += alpha y on the nodes of view v (storage strides; the view at element offset voff).
 template <typename TS>
-cudaError_t launch_sub_view(const Geom &v, long long voff, const TS *y, double *eb, cudaStream_t st);
+cudaError_t launch_axpy_view(const Geom &v, long long voff, double alpha, const TS *y, double *eb, cudaStream_t st);
 cudaError_t launch_amr_restrictT(const Geom &sc, const AmrInfo &Lc, const Geom &sp, const AmrInfo &Lp,
                                  const double *rp, double *rc, cudaStream_t st);
 cudaError_t launch_amr_injectT(const Geom &sc, const AmrInfo &Lc, const Geom &sp, const AmrInfo &Lp, const double *wp,

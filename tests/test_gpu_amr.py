@@ -259,14 +259,15 @@ def _filled_dense_solution(A, psis, fs, us0):
 
 
 @pytest.mark.parametrize("case", list(SMALL))
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("precision,inner", [("fp64", 1), ("mixed", 1), ("mixed", 6)])
 @pytest.mark.parametrize("smoother", ["jacobi", "gs"])
-def test_composite_adjoint_matches_dense_oracle(built, case, precision, smoother):
+def test_composite_adjoint_matches_dense_oracle(built, case, precision, inner, smoother):
     """lambda of A^T lambda = g and dJ/dpsi per level against the oracle's dense
     transpose solve and its composite gradient (floor cells masked); the
     transposed correction iteration converges like the forward one, also on grids
     whose smoother is colour Gauss-Seidel (Jacobi patch sweeps in B^T, the colour
-    smoother in the base V-cycle)."""
+    smoother in the base V-cycle), and with 6 inner transposed cycles per FP64
+    A^T lambda whose residual updates take FP32 stencil products."""
     wk = SMALL[case]()
     A, psis = _oracle(wk)
     fs = [W.uniform(800 + a, A.level_problem(a).ndofs, -1, 1) for a in range(A.nlev)]
@@ -281,9 +282,9 @@ def test_composite_adjoint_matches_dense_oracle(built, case, precision, smoother
     ref = oracle.amr_dJdpsi(A, us, lams)
     g = _gpu(wk, precision)
     lg, gg, info = g.amr_adjoint([cuda(u) for u in us], [cuda(x) for x in gs], tol=1e-12, max_cycles=300,
-                                 omega=wk.omega, smoother=smoother)
+                                 omega=wk.omega, smoother=smoother, inner_cycles=inner)
     assert info.converged, info
-    assert info.cycles <= 60, info.cycles
+    assert info.vcycles <= 80, info.vcycles
     num = np.sqrt(sum(((host(lg[a]) - lams[a]) ** 2).sum() for a in range(A.nlev)))
     assert num <= 1e-9 * np.linalg.norm(lam), num / np.linalg.norm(lam)
     scale = max(np.abs(r).max() for r in ref)
