@@ -83,7 +83,7 @@ typedef struct {
     int use_graph;         /* 1: replay the cycle as a CUDA graph; 0: launch eagerly */
     double inner_rtol;     /* SBM_MIXED, > 0: inner_cycles is a maximum; the FP32 V-cycles of an outer
                               iteration stop (on the device) once the FP32 residual after a V-cycle's
-                              pre-smoothing is <= max(inner_rtol * |r64|, tol/10 * |r0|); 0: fixed count */
+                              pre-smoothing is <= max(inner_rtol * |r64|, tol/2 * |r0|); 0: fixed count */
 } sbm_opts;
 
 typedef struct {
