@@ -17,7 +17,8 @@ bench.py reports the error of its timed solve against the damage_3d records.
     python tests/golden/make_golden.py damage_3d_129      # ~4 min of one CPU core
     python tests/golden/make_golden.py topopt_3d          # ~20 min
     python tests/golden/make_golden.py voids_amr_2d       # 129^2 base + 3 levels
-    python tests/golden/make_golden.py voids_amr_3d_65    # 65^3 base + 2 levels, ~1 h
+    python tests/golden/make_golden.py voids_amr_3d_65    # 65^3 base + 2 levels, ~6 h (400 cycles to its floor)
+    python tests/golden/make_golden.py voids_amr_3d_clustered_129    # ~3 h
 """
 import json
 import os
