@@ -533,6 +533,15 @@ def run_ours(args, rank, world, local_rank):
         dist.destroy_process_group()
 
 
+def mg_extent(m):
+    """Smallest c 2^k + 1 >= m nodes with 4 <= c <= 8: an axis that coarsens down to
+    4 .. 8 cells, so that a grid of such extents has a small dense bottom level."""
+    k = 0
+    while -(-(m - 1) // (1 << k)) > 8:
+        k += 1
+    return max(4, -(-(m - 1) // (1 << k))) * (1 << k) + 1
+
+
 def patch_smoother_roofline(wk, psi_h, precision, dev, stream, local_rank):
     """Roofline of a composite solve's dominant kernel: one smoother sweep (the fused
     2D colour Gauss-Seidel sweep, or the 3D Jacobi sweep) on the largest patch of the
@@ -546,13 +555,6 @@ def patch_smoother_roofline(wk, psi_h, precision, dev, stream, local_rank):
     nl = len(wk.boxes) + 1
     lmax = max(wk.level(a) for a in range(1, nl))
     a = max((a for a in range(1, nl) if wk.level(a) == lmax), key=lambda a: psi_h[a].numel())
-
-    def mg_extent(m):
-        # smallest c 2^k + 1 >= m nodes with 4 <= c <= 8: coarsens to a small dense bottom level
-        k = 0
-        while -(-(m - 1) // (1 << k)) > 8:
-            k += 1
-        return max(4, -(-(m - 1) // (1 << k))) * (1 << k) + 1
 
     ns = wk.storage_shape(a)
     n = tuple(mg_extent(ns[ax]) if ax < wk.dim else 1 for ax in range(3))
